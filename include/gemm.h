@@ -1,0 +1,172 @@
+/*
+ * gb300-sgemm: C ABI of a GB300 (sm_103a) library for generalized matrix
+ * multiplication in FP32 semantics,
+ *
+ *                 C = alpha * A * B + beta * C
+ *
+ * the computation the Tiramisu paper (arXiv 1804.10694) uses as its running
+ * example and benchmarks as sgemm (Section I; Section VI-A).  The tensor-core
+ * modes compute each product as three split-precision tensor-core products
+ * (bf16 or tf32 hi/lo parts, FP32 accumulation, per-block power-of-two
+ * scaling); the SIMT mode is a plain FP32 CUDA-core kernel.
+ *
+ * Conventions for every call below:
+ *   - Layout: row-major.  A is M x K with lda >= K, B is K x N with ldb >= N,
+ *     C is M x N with ldc >= N (leading dimensions in elements).  A and B must
+ *     not overlap C.
+ *   - Memory: matrix pointers are DEVICE pointers owned by the caller (except
+ *     gemm_f32_host); the library never frees them.  Plans own their
+ *     workspace (packed operand planes, block exponents, split-K partials,
+ *     descriptor tables, CUDA graphs) and release it in *_destroy.
+ *   - BLAS special cases: M == 0 or N == 0 is a no-op; K == 0 or alpha == 0
+ *     gives C = beta * C without reading A or B; beta == 0 makes C
+ *     write-only (NaN/Inf in the old C do not propagate).
+ *   - Streams: every compute call is asynchronous and ordered on the given
+ *     stream (0 = legacy default stream).  A device fault in a kernel shows up
+ *     as GEMM_ERR_CUDA on a later call; a kernel that gave up waiting on
+ *     its own pipeline raises the device error word read by
+ *     gemm_device_error().
+ *   - Errors: no exception crosses the ABI.  Invalid arguments are rejected
+ *     with GEMM_ERR_INVALID_ARG before anything is launched.  The text of the
+ *     last error of the calling thread is returned by gemm_last_error().
+ *   - Threads: calls are thread-safe; a plan must not be executed
+ *     concurrently on two streams (its workspace is shared).
+ */
+#ifndef GB300_SGEMM_GEMM_H
+#define GB300_SGEMM_GEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as CUDA's cudaStream_t (a CUstream handle); 0 = default stream. */
+typedef struct CUstream_st* gemm_stream_t;
+
+typedef enum {
+  GEMM_OK = 0,
+  GEMM_ERR_INVALID_ARG = 1,      /* bad size, leading dimension, pointer or handle */
+  GEMM_ERR_ALIGNMENT = 2,        /* pointer alignment the call requires is not met */
+  GEMM_ERR_ALLOC = 3,            /* device or host allocation failed */
+  GEMM_ERR_CUDA = 4,             /* a CUDA runtime/driver call failed */
+  GEMM_ERR_UNSUPPORTED_DEVICE = 5, /* tensor-core modes need compute capability 10.3 */
+  GEMM_ERR_TIMEOUT = 6,          /* a kernel gave up waiting on its own pipeline */
+  GEMM_ERR_IO = 7                /* file could not be read, written or parsed */
+} gemm_status;
+
+typedef enum {
+  GEMM_MODE_AUTO = 0,     /* BF16X3 on sm_103, else error */
+  GEMM_MODE_F32_SIMT = 1, /* plain FP32 CUDA-core kernel (reference form) */
+  GEMM_MODE_BF16X3 = 2,   /* split-precision bf16 x3 tensor-core kernel */
+  GEMM_MODE_TF32X3 = 3    /* split-precision tf32 x3 tensor-core kernel */
+} gemm_mode;
+
+typedef enum {
+  GEMM_SELECT_DEFAULT = 0,    /* built-in heuristic */
+  GEMM_SELECT_MODEL = 1,      /* argmin of the loaded MLP cost model (else heuristic) */
+  GEMM_SELECT_TABLE = 2,      /* loaded autotune table, exact shape match (else heuristic) */
+  GEMM_SELECT_EXHAUSTIVE = 3  /* time every candidate now, keep the fastest */
+} gemm_select;
+
+typedef struct gemm_plan_s* gemm_plan_t;
+typedef struct gemm_grouped_plan_s* gemm_grouped_plan_t;
+
+/* Tile configuration of the tensor-core kernels (one entry of the candidate
+ * table that the autotuner and the cost model choose from; the paper tunes
+ * tile size and unroll factor, Section VI-A). */
+typedef struct {
+  int block_n;     /* output tile width (tile height is 128) */
+  int stages;      /* depth of the shared-memory operand ring */
+  int split_k;     /* number of K partitions (partials reduced in fixed order) */
+  int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (0 = whole K) */
+  int group_m;     /* raster: output tiles walked in groups of this many along M */
+} gemm_config;
+
+/* ---------------------------------------------------------------- gemm -- */
+
+/* C = alpha*A*B + beta*C on the default stream, mode AUTO, default tiles.
+ * Definition: paper Section I.  Plans are created and cached internally per
+ * (shape, leading dimensions, mode, stream). */
+gemm_status gemm_f32(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
+
+/* As gemm_f32 with an explicit mode, tile-selection policy and stream. */
+gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                        int64_t ldc, gemm_mode mode, gemm_select sel, gemm_stream_t stream);
+
+/* As gemm_f32_ex, but A, B and C are HOST pointers (pageable or pinned): the
+ * call copies A, B (and C when beta != 0) to device buffers it keeps per
+ * thread, computes, copies C back and synchronizes the stream before
+ * returning. */
+gemm_status gemm_f32_host(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                          int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                          int64_t ldc, gemm_mode mode, gemm_stream_t stream);
+
+/* ---------------------------------------------------------------- plans -- */
+
+/* Create a plan for one shape: picks the tile configuration (policy `sel`),
+ * allocates the packed-operand workspace and encodes the TMA descriptors.
+ * Errors: INVALID_ARG (negative sizes, ld below row length), ALLOC, CUDA,
+ * UNSUPPORTED_DEVICE. */
+gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                             int64_t ldc, gemm_mode mode, gemm_select sel, gemm_plan_t* out);
+
+/* Create a plan with an explicit candidate configuration id (see
+ * gemm_config_count / gemm_config_get). */
+gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                                    int64_t ldc, gemm_mode mode, int config_id, gemm_plan_t* out);
+
+/* Run the plan: split/pack of A and B, the gemm kernel, and the split-K
+ * reduction when split_k > 1, all on `stream`.  No host synchronization, so
+ * the call may be captured into a CUDA graph. */
+gemm_status gemm_plan_execute(gemm_plan_t plan, float alpha, const float* A, const float* B,
+                              float beta, float* C, gemm_stream_t stream);
+
+/* Resolved mode, configuration id (-1 for SIMT) and workspace bytes. */
+gemm_status gemm_plan_info(gemm_plan_t plan, int* mode, int* config_id, size_t* workspace_bytes);
+
+gemm_status gemm_plan_destroy(gemm_plan_t plan);
+
+/* --------------------------------------------------- tile configurations -- */
+
+/* Number of candidate configurations for a tensor-core mode (0 for SIMT). */
+int gemm_config_count(gemm_mode mode);
+gemm_status gemm_config_get(gemm_mode mode, int config_id, gemm_config* out);
+/* Heuristic default configuration id for a shape. */
+int gemm_config_default(gemm_mode mode, int64_t M, int64_t N, int64_t K);
+
+/* ----------------------------------------------------------- diagnostics -- */
+
+/* Text of the calling thread's last error ("" if none).  Valid until the
+ * thread's next library call. */
+const char* gemm_last_error(void);
+
+/* Reads and clears the current device's kernel error word: GEMM_OK, or
+ * GEMM_ERR_TIMEOUT if a kernel abandoned a pipeline wait.  Synchronizes the
+ * device. */
+gemm_status gemm_device_error(void);
+
+/* Number of streaming multiprocessors of the current device. */
+int gemm_device_sm_count(void);
+
+/* The packing stage alone (the paper's "array packing", Section I), exposed
+ * so that it can be checked bit for bit: splits the FP32 matrix X (rows x cols,
+ * leading dimension ld, device memory) into hi/lo planes
+ * planes[2][rows][pitch] (bf16 for BF16X3, tf32 values in 32-bit containers
+ * for TF32X3; pitch = cols rounded up to 8 resp. 4) and writes the per-block
+ * max |x| bit patterns to amax[ceil(rows/128)].  `transpose` != 0 treats X as
+ * a K x N matrix B and writes planes[2][N][pitch] with
+ * amax[ceil(N/128)] (blocks of 128 columns).  All pointers are device
+ * pointers; amax must be zeroed by the caller. */
+gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t cols,
+                            const float* X, int64_t ld, void* planes, int64_t pitch,
+                            unsigned* amax, gemm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_SGEMM_GEMM_H */

@@ -1,0 +1,81 @@
+// Declarations shared by the library's translation units (not part of the
+// public C ABI, which is include/gemm.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace gb {
+
+// ---------------------------------------------------------------- precision
+enum class Prec : int { F32 = 0, BF16 = 1, TF32 = 2 };
+
+inline int prec_elem_bytes(Prec p) { return p == Prec::BF16 ? 2 : 4; }
+// Elements of one 128-byte k-chunk (one swizzle span) per precision.
+inline int prec_chunk_elems(Prec p) { return p == Prec::BF16 ? 64 : 32; }
+// Row pitch of the packed planes: K rounded up so that a row is 16-byte aligned.
+inline int64_t packed_k_pitch(Prec p, int64_t K) {
+  const int64_t q = p == Prec::BF16 ? 8 : 4;
+  return (K + q - 1) / q * q;
+}
+
+constexpr int kScaleBlock = 128;   // rows of A / columns of B sharing one exponent
+
+// --------------------------------------------------- tensor-core kernel args
+struct TcArgs {
+  int M, N, K;
+  int tiles_m, tiles_n, num_tiles, num_units;
+  int split_k, chunks_total, chunks_per_split;
+  int kb;        // k-chunks accumulated in TMEM before the epilogue folds them in
+  int group_m;   // raster: tiles grouped along M
+  float alpha, beta;
+  float* C;
+  int64_t ldc;
+  int c_vec4;    // C base 16-byte aligned and ldc % 4 == 0
+  const unsigned* amaxA;   // per 128-row block of A: bit pattern of max |a|
+  const unsigned* amaxB;   // per 128-column block of B
+  float* partial;          // split-K partial sums [split][M][N], null when split_k == 1
+  int* err;
+};
+
+struct TcLaunch {
+  int bn;          // tile N (64 or 128)
+  Prec prec;       // BF16 or TF32
+  int grid;
+};
+
+// Returns the dynamic shared memory a tensor-core kernel variant needs.
+int tc_smem_bytes(int bn, Prec prec);
+cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const TcArgs& a, cudaStream_t s);
+// C = alpha * sum_s partial[s] + beta * C over the split-K partial sums.
+cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float alpha,
+                                 float beta, float* C, int64_t ldc, cudaStream_t s);
+
+// ------------------------------------------------------------ SIMT kernel
+cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                             int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                             int64_t ldc, cudaStream_t s);
+// C = beta * C (K == 0 or alpha == 0), C write-only when beta == 0.
+cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t ldc, cudaStream_t s);
+
+// ------------------------------------------------------------ split / pack
+// Per-block max |x| as float bit patterns (atomicMax on unsigned).
+// blocks_along_rows: A (blocks of 128 rows); else B (blocks of 128 columns).
+cudaError_t absmax_launch(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                          bool blocks_along_rows, unsigned* amax, cudaStream_t s);
+// A (rows x cols, ld) -> planes [2][rows][pitch] of hi/lo (bf16 or tf32-in-fp32).
+cudaError_t split_rows_launch(Prec p, const float* X, int64_t rows, int64_t cols, int64_t ld,
+                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s);
+// B (K x N, ld) -> transposed planes [2][N][pitch] of hi/lo.
+cudaError_t split_cols_launch(Prec p, const float* X, int64_t K, int64_t N, int64_t ld,
+                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s);
+
+// ------------------------------------------------------------ grouped
+struct GroupedProblem;   // defined in grouped.cu / runtime
+
+// --------------------------------------------------------------- MLP
+// (declared in mlp.cu users through runtime.cpp)
+
+}  // namespace gb

@@ -1,0 +1,605 @@
+// Host runtime behind the C ABI (include/gemm.h): argument validation, BLAS
+// special cases, per-device state, the candidate tile-configuration table,
+// plans (workspace + TMA descriptors), the internal plan cache and the
+// host-buffer entry point.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/gemm.h"
+#include "internal.h"
+#include "runtime.h"
+
+namespace gb {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string t_last_error;
+
+gemm_status fail(gemm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return st;
+}
+
+gemm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(GEMM_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+void clear_error() { t_last_error.clear(); }
+
+// ------------------------------------------------------------ device state
+struct DeviceState {
+  bool init = false;
+  int sms = 0;
+  int cc_major = 0, cc_minor = 0;
+  int* err_word = nullptr;
+};
+
+static std::mutex g_dev_mutex;
+static DeviceState g_devices[64];
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn g_encode = nullptr;
+
+gemm_status device_state(DeviceState** out, int* dev_out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "device index %d", dev);
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  DeviceState& d = g_devices[dev];
+  if (!d.init) {
+    if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+    cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if ((e = cudaMalloc(&d.err_word, sizeof(int))) != cudaSuccess)
+      return fail(GEMM_ERR_ALLOC, "cudaMalloc(error word): %s", cudaGetErrorString(e));
+    if ((e = cudaMemset(d.err_word, 0, sizeof(int))) != cudaSuccess)
+      return cuda_fail(e, "cudaMemset(error word)");
+    d.init = true;
+  }
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled entry point not found");
+    g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  *out = &d;
+  if (dev_out) *dev_out = dev;
+  return GEMM_OK;
+}
+
+bool device_has_tcgen05(const DeviceState& d) { return d.cc_major == 10 && d.cc_minor == 3; }
+
+// ------------------------------------------------------ configuration table
+// Candidates of the tensor-core kernels.  The same table serves BF16X3 and
+// TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way).
+static const std::vector<gemm_config>& config_table() {
+  static const std::vector<gemm_config> table = [] {
+    std::vector<gemm_config> t;
+    const int bns[] = {128, 64};
+    const int splits[] = {1, 2, 3, 4, 6, 8};
+    const int kbs[] = {1, 2, 4, 0};
+    const int groups[] = {16, 1};
+    for (int bn : bns)
+      for (int sk : splits)
+        for (int kb : kbs)
+          for (int g : groups) {
+            gemm_config c;
+            c.block_n = bn;
+            c.stages = bn == 64 ? 4 : 3;
+            c.split_k = sk;
+            c.kb = kb;
+            c.group_m = g;
+            t.push_back(c);
+          }
+    return t;
+  }();
+  return table;
+}
+
+int config_count(gemm_mode mode) {
+  return (mode == GEMM_MODE_BF16X3 || mode == GEMM_MODE_TF32X3) ? (int)config_table().size() : 0;
+}
+
+bool config_get(int id, gemm_config* out) {
+  const auto& t = config_table();
+  if (id < 0 || id >= (int)t.size()) return false;
+  *out = t[id];
+  return true;
+}
+
+static int find_config(int bn, int sk, int kb, int g) {
+  const auto& t = config_table();
+  for (int i = 0; i < (int)t.size(); ++i)
+    if (t[i].block_n == bn && t[i].split_k == sk && t[i].kb == kb && t[i].group_m == g) return i;
+  return 0;
+}
+
+int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
+  if (config_count(mode) == 0) return -1;
+  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  const int bn = N <= 64 ? 64 : 128;
+  const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
+  const int64_t chunks = (K + prec_chunk_elems(p) - 1) / prec_chunk_elems(p);
+  int sk = 1;
+  const int cand[] = {1, 2, 3, 4, 6, 8};
+  for (int c : cand) {
+    if (c > chunks / 4) break;            // keep at least 4 k-chunks per split
+    sk = c;
+    if (tiles * c >= (int64_t)sms * 9 / 10) break;
+  }
+  if (tiles >= (int64_t)sms) sk = 1;
+  return find_config(bn, sk, 2, 16);
+}
+
+// -------------------------------------------------------------------- plans
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
+                                 int64_t pitch, int box_rows) {
+  const int es = prec_elem_bytes(p);
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 2};
+  cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(rows * pitch * es)};
+  cuuint32_t box[3] = {(cuuint32_t)prec_chunk_elems(p), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUtensorMapDataType dt =
+      p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = g_encode(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) rows=%lld K=%lld pitch=%lld",
+                (int)r, (long long)rows, (long long)K, (long long)pitch);
+  return GEMM_OK;
+}
+
+gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc) {
+  if (M < 0 || N < 0 || K < 0) return fail(GEMM_ERR_INVALID_ARG, "negative size M=%lld N=%lld K=%lld",
+                                           (long long)M, (long long)N, (long long)K);
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX)
+    return fail(GEMM_ERR_INVALID_ARG, "size above 2^31-1");
+  if (lda < std::max<int64_t>(K, 1)) return fail(GEMM_ERR_INVALID_ARG, "lda=%lld < max(K,1)", (long long)lda);
+  if (ldb < std::max<int64_t>(N, 1)) return fail(GEMM_ERR_INVALID_ARG, "ldb=%lld < max(N,1)", (long long)ldb);
+  if (ldc < std::max<int64_t>(N, 1)) return fail(GEMM_ERR_INVALID_ARG, "ldc=%lld < max(N,1)", (long long)ldc);
+  return GEMM_OK;
+}
+
+static gemm_status resolve_mode(gemm_mode mode, const DeviceState& d, gemm_mode* out) {
+  if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
+  if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
+    return fail(GEMM_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+  if (mode != GEMM_MODE_F32_SIMT && !device_has_tcgen05(d))
+    return fail(GEMM_ERR_UNSUPPORTED_DEVICE,
+                "tensor-core modes need compute capability 10.3 (device is %d.%d)", d.cc_major,
+                d.cc_minor);
+  *out = mode;
+  return GEMM_OK;
+}
+
+gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out) {
+  if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
+  *out = nullptr;
+  gemm_status st = validate_shape(M, N, K, lda, ldb, ldc);
+  if (st != GEMM_OK) return st;
+  DeviceState* dev;
+  int devidx;
+  if ((st = device_state(&dev, &devidx)) != GEMM_OK) return st;
+  gemm_mode m;
+  if ((st = resolve_mode(mode, *dev, &m)) != GEMM_OK) return st;
+
+  std::unique_ptr<gemm_plan_s> p(new gemm_plan_s());
+  p->M = M, p->N = N, p->K = K, p->lda = lda, p->ldb = ldb, p->ldc = ldc;
+  p->mode = m;
+  p->device = devidx;
+  p->sms = dev->sms;
+  p->err_word = dev->err_word;
+  if (m == GEMM_MODE_F32_SIMT || M == 0 || N == 0 || K == 0) {
+    p->config_id = -1;
+    *out = p.release();
+    return GEMM_OK;
+  }
+  p->prec = m == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  if (config_id < 0) {
+    config_id = select_config(m, M, N, K, lda, ldb, ldc, sel, dev->sms);
+    if (config_id < 0) return fail(GEMM_ERR_INVALID_ARG, "no configuration for mode");
+  }
+  if (!config_get(config_id, &p->cfg))
+    return fail(GEMM_ERR_INVALID_ARG, "configuration id %d out of range", config_id);
+  p->config_id = config_id;
+
+  const Prec pr = p->prec;
+  const int es = prec_elem_bytes(pr);
+  p->pitch = packed_k_pitch(pr, K);
+  const int64_t chunks = (K + prec_chunk_elems(pr) - 1) / prec_chunk_elems(pr);
+  int sk = std::max(1, std::min<int>(p->cfg.split_k, (int)chunks));
+  const int64_t per = (chunks + sk - 1) / sk;
+  sk = (int)((chunks + per - 1) / per);   // no empty split
+  const int bn = p->cfg.block_n;
+  const int64_t tiles_m = (M + 127) / 128, tiles_n = (N + bn - 1) / bn;
+
+  // workspace: A planes | B planes | amax A | amax B | split-K partials
+  const size_t bytesA = (size_t)2 * M * p->pitch * es;
+  const size_t bytesB = (size_t)2 * N * p->pitch * es;
+  const size_t nblkA = (size_t)(M + kScaleBlock - 1) / kScaleBlock;
+  const size_t nblkB = (size_t)(N + kScaleBlock - 1) / kScaleBlock;
+  size_t off = 0;
+  const size_t offA = off; off = align_up(off + bytesA, 256);
+  const size_t offB = off; off = align_up(off + bytesB, 256);
+  const size_t offAmax = off; off = align_up(off + (nblkA + nblkB) * sizeof(unsigned), 256);
+  const size_t offPart = off;
+  if (sk > 1) off = align_up(off + (size_t)sk * M * N * sizeof(float), 256);
+  p->ws_bytes = off;
+  cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GEMM_ERR_ALLOC, "cudaMalloc(%zu bytes) for the plan workspace: %s", p->ws_bytes,
+                cudaGetErrorString(e));
+  }
+  char* w = static_cast<char*>(p->ws);
+  p->planesA = w + offA;
+  p->planesB = w + offB;
+  p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
+  p->amaxB = p->amaxA + nblkA;
+  p->amax_bytes = (nblkA + nblkB) * sizeof(unsigned);
+  p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
+
+  if ((st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128)) != GEMM_OK) return st;
+  if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn)) != GEMM_OK) return st;
+
+  TcArgs& a = p->args;
+  a.M = (int)M, a.N = (int)N, a.K = (int)K;
+  a.tiles_m = (int)tiles_m, a.tiles_n = (int)tiles_n;
+  a.num_tiles = (int)(tiles_m * tiles_n);
+  a.split_k = sk;
+  a.num_units = a.num_tiles * sk;
+  a.chunks_total = (int)chunks;
+  a.chunks_per_split = (int)per;
+  a.kb = p->cfg.kb > 0 ? p->cfg.kb : (int)chunks;
+  a.group_m = std::max(1, std::min<int>(p->cfg.group_m, (int)tiles_m));
+  a.ldc = ldc;
+  a.amaxA = p->amaxA;
+  a.amaxB = p->amaxB;
+  a.partial = p->partial;
+  a.err = dev->err_word;
+  p->launch.bn = bn;
+  p->launch.prec = pr;
+  p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
+  *out = p.release();
+  return GEMM_OK;
+}
+
+gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const float* B, float beta,
+                              float* C, cudaStream_t s) {
+  if (!p) return fail(GEMM_ERR_INVALID_ARG, "null plan");
+  const int64_t M = p->M, N = p->N, K = p->K;
+  if (M == 0 || N == 0) return GEMM_OK;
+  if (!C) return fail(GEMM_ERR_INVALID_ARG, "null C");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != p->device)
+    return fail(GEMM_ERR_INVALID_ARG, "plan was created on device %d, current device is %d",
+                p->device, dev);
+  cudaError_t e;
+  if (K == 0 || alpha == 0.0f) {
+    if ((e = scale_c_launch(M, N, beta, C, p->ldc, s)) != cudaSuccess)
+      return cuda_fail(e, "scale_c launch");
+    return GEMM_OK;
+  }
+  if (!A || !B) return fail(GEMM_ERR_INVALID_ARG, "null A or B");
+  if (p->mode == GEMM_MODE_F32_SIMT) {
+    if ((e = simt_gemm_launch(M, N, K, alpha, A, p->lda, B, p->ldb, beta, C, p->ldc, s)) != cudaSuccess)
+      return cuda_fail(e, "simt gemm launch");
+    return GEMM_OK;
+  }
+  if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemsetAsync(amax)");
+  if ((e = absmax_launch(A, M, K, p->lda, true, p->amaxA, s)) != cudaSuccess)
+    return cuda_fail(e, "absmax(A) launch");
+  if ((e = absmax_launch(B, K, N, p->ldb, false, p->amaxB, s)) != cudaSuccess)
+    return cuda_fail(e, "absmax(B) launch");
+  if ((e = split_rows_launch(p->prec, A, M, K, p->lda, p->amaxA, p->planesA, p->pitch, s)) != cudaSuccess)
+    return cuda_fail(e, "split(A) launch");
+  if ((e = split_cols_launch(p->prec, B, K, N, p->ldb, p->amaxB, p->planesB, p->pitch, s)) != cudaSuccess)
+    return cuda_fail(e, "split(B) launch");
+  TcArgs a = p->args;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.c_vec4 = (p->ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+  if ((e = tc_gemm_launch(p->launch, p->tmA, p->tmB, a, s)) != cudaSuccess)
+    return cuda_fail(e, "tensor-core gemm launch");
+  if (a.split_k > 1) {
+    if ((e = splitk_reduce_launch(a.M, a.N, a.split_k, a.partial, alpha, beta, C, p->ldc, s)) != cudaSuccess)
+      return cuda_fail(e, "split-K reduce launch");
+  }
+  return GEMM_OK;
+}
+
+void plan_destroy_impl(gemm_plan_t p) {
+  if (!p) return;
+  if (p->ws) cudaFree(p->ws);
+  delete p;
+}
+
+// --------------------------------------------------------------- plan cache
+struct CacheKey {
+  int dev;
+  int64_t M, N, K, lda, ldb, ldc;
+  int mode, sel;
+  uintptr_t stream;
+  bool operator<(const CacheKey& o) const {
+    return std::tie(dev, M, N, K, lda, ldb, ldc, mode, sel, stream) <
+           std::tie(o.dev, o.M, o.N, o.K, o.lda, o.ldb, o.ldc, o.mode, o.sel, o.stream);
+  }
+  bool operator==(const CacheKey& o) const { return !(*this < o) && !(o < *this); }
+};
+
+static std::mutex g_cache_mutex;
+static std::map<CacheKey, gemm_plan_t> g_cache;
+static std::list<CacheKey> g_lru;
+constexpr size_t kCacheMax = 16;
+
+gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                        gemm_mode mode, gemm_select sel, cudaStream_t s, gemm_plan_t* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  CacheKey key{dev, M, N, K, lda, ldb, ldc, (int)mode, (int)sel, reinterpret_cast<uintptr_t>(s)};
+  std::lock_guard<std::mutex> lk(g_cache_mutex);
+  auto it = g_cache.find(key);
+  if (it != g_cache.end()) {
+    g_lru.remove(key);
+    g_lru.push_front(key);
+    *out = it->second;
+    return GEMM_OK;
+  }
+  gemm_plan_t p = nullptr;
+  gemm_status st = plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, &p);
+  if (st != GEMM_OK) return st;
+  if (g_cache.size() >= kCacheMax) {
+    const CacheKey victim = g_lru.back();
+    g_lru.pop_back();
+    // the victim may still be in use on its stream: wait for the device first
+    cudaDeviceSynchronize();
+    plan_destroy_impl(g_cache[victim]);
+    g_cache.erase(victim);
+  }
+  g_cache[key] = p;
+  g_lru.push_front(key);
+  *out = p;
+  return GEMM_OK;
+}
+
+// ----------------------------------------------------- host-buffer entry
+struct HostBuffers {
+  int dev = -1;
+  float *A = nullptr, *B = nullptr, *C = nullptr;
+  size_t nA = 0, nB = 0, nC = 0;
+  ~HostBuffers() {
+    if (A) cudaFree(A);
+    if (B) cudaFree(B);
+    if (C) cudaFree(C);
+  }
+};
+static thread_local HostBuffers t_host;
+
+static gemm_status grow(float** p, size_t* cap, size_t n) {
+  if (*cap >= n) return GEMM_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  cudaError_t e = cudaMalloc(p, n * sizeof(float));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GEMM_ERR_ALLOC, "cudaMalloc(%zu bytes) for host-call buffers", n * sizeof(float));
+  }
+  *cap = n;
+  return GEMM_OK;
+}
+
+gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                           const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                           gemm_mode mode, cudaStream_t s) {
+  gemm_status st = validate_shape(M, N, K, lda, ldb, ldc);
+  if (st != GEMM_OK) return st;
+  if (M == 0 || N == 0) return GEMM_OK;
+  if (!C || (K > 0 && alpha != 0.0f && (!A || !B))) return fail(GEMM_ERR_INVALID_ARG, "null host pointer");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (t_host.dev != dev) {
+    t_host.~HostBuffers();
+    new (&t_host) HostBuffers();
+    t_host.dev = dev;
+  }
+  const bool need_ab = K > 0 && alpha != 0.0f;
+  const size_t nA = need_ab ? (size_t)(M - 1) * lda + K : 0;
+  const size_t nB = need_ab ? (size_t)(K - 1) * ldb + N : 0;
+  const size_t nC = (size_t)(M - 1) * ldc + N;
+  if ((st = grow(&t_host.A, &t_host.nA, std::max<size_t>(nA, 1))) != GEMM_OK) return st;
+  if ((st = grow(&t_host.B, &t_host.nB, std::max<size_t>(nB, 1))) != GEMM_OK) return st;
+  if ((st = grow(&t_host.C, &t_host.nC, nC)) != GEMM_OK) return st;
+  cudaError_t e;
+  if (need_ab) {
+    if ((e = cudaMemcpyAsync(t_host.A, A, nA * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "copy A to device");
+    if ((e = cudaMemcpyAsync(t_host.B, B, nB * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "copy B to device");
+  }
+  if (beta != 0.0f) {
+    if ((e = cudaMemcpyAsync(t_host.C, C, nC * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "copy C to device");
+  }
+  gemm_plan_t p = nullptr;
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
+  if ((st = plan_execute_impl(p, alpha, t_host.A, t_host.B, beta, t_host.C, s)) != GEMM_OK) return st;
+  if ((e = cudaMemcpyAsync(C, t_host.C, nC * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "copy C to host");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return GEMM_OK;
+}
+
+}  // namespace gb
+
+// =================================================================== C ABI
+using namespace gb;
+
+extern "C" {
+
+gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                        gemm_mode mode, gemm_select sel, gemm_stream_t stream) {
+  clear_error();
+  gemm_status st = validate_shape(M, N, K, lda, ldb, ldc);
+  if (st != GEMM_OK) return st;
+  if (M == 0 || N == 0) return GEMM_OK;
+  if (!C || (K > 0 && alpha != 0.0f && (!A || !B))) return fail(GEMM_ERR_INVALID_ARG, "null pointer");
+  gemm_plan_t p = nullptr;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p)) != GEMM_OK) return st;
+  return plan_execute_impl(p, alpha, A, B, beta, C, s);
+}
+
+gemm_status gemm_f32(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, float beta, float* C, int64_t ldc) {
+  return gemm_f32_ex(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, GEMM_MODE_AUTO,
+                     GEMM_SELECT_DEFAULT, nullptr);
+}
+
+gemm_status gemm_f32_host(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                          const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                          gemm_mode mode, gemm_stream_t stream) {
+  clear_error();
+  return host_gemm_impl(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, mode,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                             gemm_mode mode, gemm_select sel, gemm_plan_t* out) {
+  clear_error();
+  return plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, out);
+}
+
+gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                                    int64_t ldc, gemm_mode mode, int config_id, gemm_plan_t* out) {
+  clear_error();
+  if (config_id < 0 && mode != GEMM_MODE_F32_SIMT)
+    return fail(GEMM_ERR_INVALID_ARG, "negative configuration id");
+  return plan_create_impl(M, N, K, lda, ldb, ldc, mode, config_id, GEMM_SELECT_DEFAULT, out);
+}
+
+gemm_status gemm_plan_execute(gemm_plan_t plan, float alpha, const float* A, const float* B,
+                              float beta, float* C, gemm_stream_t stream) {
+  clear_error();
+  return plan_execute_impl(plan, alpha, A, B, beta, C, reinterpret_cast<cudaStream_t>(stream));
+}
+
+gemm_status gemm_plan_info(gemm_plan_t plan, int* mode, int* config_id, size_t* workspace_bytes) {
+  clear_error();
+  if (!plan) return fail(GEMM_ERR_INVALID_ARG, "null plan");
+  if (mode) *mode = (int)plan->mode;
+  if (config_id) *config_id = plan->config_id;
+  if (workspace_bytes) *workspace_bytes = plan->ws_bytes;
+  return GEMM_OK;
+}
+
+gemm_status gemm_plan_destroy(gemm_plan_t plan) {
+  clear_error();
+  plan_destroy_impl(plan);
+  return GEMM_OK;
+}
+
+int gemm_config_count(gemm_mode mode) { return config_count(mode); }
+
+gemm_status gemm_config_get(gemm_mode mode, int config_id, gemm_config* out) {
+  clear_error();
+  if (!out) return fail(GEMM_ERR_INVALID_ARG, "null output");
+  if (config_count(mode) == 0) return fail(GEMM_ERR_INVALID_ARG, "mode has no configurations");
+  if (!config_get(config_id, out)) return fail(GEMM_ERR_INVALID_ARG, "configuration id out of range");
+  return GEMM_OK;
+}
+
+int gemm_config_default(gemm_mode mode, int64_t M, int64_t N, int64_t K) {
+  int sms = 152;
+  DeviceState* d;
+  if (device_state(&d, nullptr) == GEMM_OK) sms = d->sms;
+  return default_config(mode == GEMM_MODE_AUTO ? GEMM_MODE_BF16X3 : mode, M, N, K, sms);
+}
+
+const char* gemm_last_error(void) { return t_last_error.c_str(); }
+
+gemm_status gemm_device_error(void) {
+  clear_error();
+  DeviceState* d;
+  gemm_status st = device_state(&d, nullptr);
+  if (st != GEMM_OK) return st;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  int v = 0;
+  if ((e = cudaMemcpy(&v, d->err_word, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "read error word");
+  if (v != 0) {
+    cudaMemset(d->err_word, 0, sizeof(int));
+    return fail(GEMM_ERR_TIMEOUT, "a kernel abandoned a pipeline wait (error word %d)", v);
+  }
+  return GEMM_OK;
+}
+
+int gemm_device_sm_count(void) {
+  DeviceState* d;
+  if (device_state(&d, nullptr) != GEMM_OK) return -1;
+  return d->sms;
+}
+
+gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t cols, const float* X,
+                            int64_t ld, void* planes, int64_t pitch, unsigned* amax,
+                            gemm_stream_t stream) {
+  clear_error();
+  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
+    return fail(GEMM_ERR_INVALID_ARG, "split_pack needs BF16X3 or TF32X3");
+  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  if (rows < 0 || cols < 0 || ld < std::max<int64_t>(cols, 1))
+    return fail(GEMM_ERR_INVALID_ARG, "bad split_pack shape");
+  if (rows == 0 || cols == 0) return GEMM_OK;
+  if (!X || !planes || !amax) return fail(GEMM_ERR_INVALID_ARG, "null pointer");
+  // K is the row length of the planes: cols of A, rows of B
+  const int64_t K = transpose ? rows : cols;
+  if (pitch != packed_k_pitch(p, K))
+    return fail(GEMM_ERR_INVALID_ARG, "pitch must be %lld", (long long)packed_k_pitch(p, K));
+  if (reinterpret_cast<uintptr_t>(planes) % 16)
+    return fail(GEMM_ERR_ALIGNMENT, "planes must be 16-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (!transpose) {
+    if ((e = absmax_launch(X, rows, cols, ld, true, amax, s)) != cudaSuccess) return cuda_fail(e, "absmax");
+    if ((e = split_rows_launch(p, X, rows, cols, ld, amax, planes, pitch, s)) != cudaSuccess)
+      return cuda_fail(e, "split rows");
+  } else {
+    if ((e = absmax_launch(X, rows, cols, ld, false, amax, s)) != cudaSuccess) return cuda_fail(e, "absmax");
+    if ((e = split_cols_launch(p, X, rows, cols, ld, amax, planes, pitch, s)) != cudaSuccess)
+      return cuda_fail(e, "split cols");
+  }
+  return GEMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Host-side runtime structures shared by runtime.cpp and the tuning code.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/gemm.h"
+#include "internal.h"
+
+struct gemm_plan_s {
+  int64_t M = 0, N = 0, K = 0, lda = 0, ldb = 0, ldc = 0;
+  gemm_mode mode = GEMM_MODE_F32_SIMT;
+  int config_id = -1;
+  gemm_config cfg{};
+  int device = 0;
+  int sms = 0;
+  int* err_word = nullptr;
+  gb::Prec prec = gb::Prec::F32;
+  int64_t pitch = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* planesA = nullptr;
+  void* planesB = nullptr;
+  unsigned* amaxA = nullptr;
+  unsigned* amaxB = nullptr;
+  size_t amax_bytes = 0;
+  float* partial = nullptr;
+  CUtensorMap tmA{}, tmB{};
+  gb::TcArgs args{};
+  gb::TcLaunch launch{};
+};
+
+namespace gb {
+
+gemm_status fail(gemm_status st, const char* fmt, ...);
+gemm_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc);
+
+int config_count(gemm_mode mode);
+bool config_get(int id, gemm_config* out);
+int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms);
+// Configuration for a new plan under a selection policy (tuning code).
+int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                  int64_t ldc, gemm_select sel, int sms);
+
+gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out);
+gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const float* B, float beta,
+                              float* C, cudaStream_t s);
+void plan_destroy_impl(gemm_plan_t p);
+
+}  // namespace gb

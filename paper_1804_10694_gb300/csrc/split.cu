@@ -1,0 +1,276 @@
+// Operand packing for the split-precision gemm ("array packing" in the
+// paper's gemm recipe, Section I and Section VI-A).  Each FP32 operand is
+// rewritten once, before the main loop, as two planes of lower precision:
+//     x' = x * 2^-e            (e = block exponent, exponent-field arithmetic)
+//     hi = RN(x'),  lo = RN(x' - hi)
+// with RN round-to-nearest-even to bf16 (hardware conversion) or to tf32
+// (bit arithmetic below; the planes keep tf32 values in 32-bit containers).
+// A is kept row-major (K contiguous); B is transposed so that both operands
+// are K-major for the tensor-core kernel.  Rows of the planes are padded to
+// a 16-byte pitch with zeros.
+//
+// Blocks: A uses one exponent per 128 rows (all of K), B one per 128 columns
+// (all of K), from a first pass that takes max |x| per block.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "scale.cuh"
+
+namespace gb {
+
+namespace {
+
+// ------------------------------------------------------------------ max |x|
+// One CTA reduces a 32-row x 128-column tile (which lies inside one block of
+// either kind) and folds it into the block's slot with an unsigned atomicMax
+// on the bit pattern of |x| (non-negative floats order like their bits; NaN
+// patterns sort above Inf, so a NaN marks the block as non-finite).
+template <bool VEC>
+__global__ void absmax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
+                              int blocks_along_rows, unsigned* __restrict__ amax) {
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * 32;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 128;
+  const int t = threadIdx.x;
+  const int cq = (t & 31) * 4;
+  unsigned m = 0;
+  for (int rr = t >> 5; rr < 32; rr += 8) {
+    const int64_t r = r0 + rr;
+    if (r >= rows) break;
+    const float* p = X + r * ld + c0 + cq;
+    if (VEC && c0 + cq + 3 < cols) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      m = max(m, __float_as_uint(v.x) & 0x7FFFFFFFu);
+      m = max(m, __float_as_uint(v.y) & 0x7FFFFFFFu);
+      m = max(m, __float_as_uint(v.z) & 0x7FFFFFFFu);
+      m = max(m, __float_as_uint(v.w) & 0x7FFFFFFFu);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c0 + cq + i < cols) m = max(m, __float_as_uint(p[i]) & 0x7FFFFFFFu);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ unsigned wm[8];
+  if ((t & 31) == 0) wm[t >> 5] = m;
+  __syncthreads();
+  if (t == 0) {
+    unsigned b = wm[0];
+    for (int i = 1; i < 8; ++i) b = max(b, wm[i]);
+    const int64_t slot = blocks_along_rows ? r0 / kScaleBlock : c0 / kScaleBlock;
+    atomicMax(amax + slot, b);
+  }
+}
+
+// ---------------------------------------------------------------- rounding
+__device__ __forceinline__ float round_tf32_rne(float x) {
+  const unsigned u = __float_as_uint(x);
+  if ((u & 0x7F800000u) == 0x7F800000u) return x;   // Inf / NaN unchanged
+  const unsigned r = (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
+  return __uint_as_float(r);
+}
+
+struct HiLoBf16 {
+  __nv_bfloat16 hi, lo;
+};
+
+__device__ __forceinline__ HiLoBf16 split_bf16(float xs) {
+  HiLoBf16 o;
+  o.hi = __float2bfloat16_rn(xs);
+  if (isfinite(xs)) {
+    o.lo = __float2bfloat16_rn(xs - __bfloat162float(o.hi));
+  } else {
+    o.hi = __float2bfloat16_rn(xs);
+    o.lo = __float2bfloat16_rn(0.0f);
+  }
+  return o;
+}
+
+__device__ __forceinline__ void split_tf32(float xs, float& hi, float& lo) {
+  hi = round_tf32_rne(xs);
+  lo = isfinite(xs) ? round_tf32_rne(xs - hi) : 0.0f;
+}
+
+// --------------------------------------------------------- A: row-major split
+// Thread handles 4 consecutive k of one row; padding k in [K, pitch) gets 0.
+template <bool TF32, bool VEC>
+__global__ void split_rows_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                  int64_t ld, const unsigned* __restrict__ amax,
+                                  void* __restrict__ planes, int64_t pitch) {
+  const int64_t quads = pitch / 4;
+  const int64_t total = rows * quads;
+  const int64_t plane = rows * pitch;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = idx / quads;
+    const int64_t k = (idx % quads) * 4;
+    const float sc = pow2f(-block_exponent(amax[r / kScaleBlock]));
+    float v[4];
+    const float* p = X + r * ld + k;
+    if (VEC && k + 3 < cols) {
+      const float4 q = *reinterpret_cast<const float4*>(p);
+      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = (k + i < cols) ? p[i] : 0.0f;
+    }
+    const int64_t o = r * pitch + k;
+    if (TF32) {
+      float* P = static_cast<float*>(planes);
+      float4 h, l;
+      split_tf32(v[0] * sc, h.x, l.x);
+      split_tf32(v[1] * sc, h.y, l.y);
+      split_tf32(v[2] * sc, h.z, l.z);
+      split_tf32(v[3] * sc, h.w, l.w);
+      *reinterpret_cast<float4*>(P + o) = h;
+      *reinterpret_cast<float4*>(P + plane + o) = l;
+    } else {
+      __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+      __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const HiLoBf16 s = split_bf16(v[i] * sc);
+        h[i] = s.hi;
+        l[i] = s.lo;
+      }
+      *reinterpret_cast<uint2*>(P + o) = *reinterpret_cast<const uint2*>(h);
+      *reinterpret_cast<uint2*>(P + plane + o) = *reinterpret_cast<const uint2*>(l);
+    }
+  }
+}
+
+// ---------------------------------------------------- B: transposing split
+// CTA handles a 64 (k) x 64 (n) tile: coalesced loads along n into shared
+// memory, then each thread writes 16 consecutive k of one output row n.
+template <bool TF32, bool VEC>
+__global__ void split_cols_kernel(const float* __restrict__ X, int64_t K, int64_t N, int64_t ld,
+                                  const unsigned* __restrict__ amax, void* __restrict__ planes,
+                                  int64_t pitch) {
+  __shared__ float tile[64][65];
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * 64;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * 64;
+  const int t = threadIdx.x;
+  {
+    const int cn = (t & 15) * 4;
+    for (int kr = t >> 4; kr < 64; kr += 16) {
+      const int64_t k = k0 + kr;
+      float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (k < K) {
+        const float* p = X + k * ld + n0 + cn;
+        if (VEC && n0 + cn + 3 < N) {
+          const float4 q = *reinterpret_cast<const float4*>(p);
+          v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (n0 + cn + i < N) v[i] = p[i];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tile[kr][cn + i] = v[i];
+    }
+  }
+  __syncthreads();
+  const int nl = t >> 2;              // 0..63
+  const int kl = (t & 3) * 16;        // 0, 16, 32, 48
+  const int64_t n = n0 + nl;
+  if (n >= N) return;
+  const float sc = pow2f(-block_exponent(amax[n / kScaleBlock]));
+  const int64_t plane = N * pitch;
+  const int64_t obase = n * pitch + k0 + kl;
+  if (k0 + kl >= pitch) return;
+  const bool whole = k0 + kl + 16 <= pitch;
+  if (TF32) {
+    float* P = static_cast<float*>(planes);
+    float h[16], l[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) split_tf32(tile[kl + i][nl] * sc, h[i], l[i]);
+    if (whole) {
+#pragma unroll
+      for (int i = 0; i < 16; i += 4) {
+        *reinterpret_cast<float4*>(P + obase + i) = make_float4(h[i], h[i + 1], h[i + 2], h[i + 3]);
+        *reinterpret_cast<float4*>(P + plane + obase + i) =
+            make_float4(l[i], l[i + 1], l[i + 2], l[i + 3]);
+      }
+    } else {
+      for (int i = 0; i < 16 && k0 + kl + i < pitch; ++i) {
+        P[obase + i] = h[i];
+        P[plane + obase + i] = l[i];
+      }
+    }
+  } else {
+    __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+    __align__(16) __nv_bfloat16 h[16], l[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const HiLoBf16 s = split_bf16(tile[kl + i][nl] * sc);
+      h[i] = s.hi;
+      l[i] = s.lo;
+    }
+    if (whole) {
+      *reinterpret_cast<uint4*>(P + obase) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(P + obase + 8) = *reinterpret_cast<const uint4*>(h + 8);
+      *reinterpret_cast<uint4*>(P + plane + obase) = *reinterpret_cast<const uint4*>(l);
+      *reinterpret_cast<uint4*>(P + plane + obase + 8) = *reinterpret_cast<const uint4*>(l + 8);
+    } else {
+      // pitch is a multiple of 8 elements: write whole 8-element groups
+      for (int i = 0; i < 16 && k0 + kl + i < pitch; i += 8) {
+        *reinterpret_cast<uint4*>(P + obase + i) = *reinterpret_cast<const uint4*>(h + i);
+        *reinterpret_cast<uint4*>(P + plane + obase + i) = *reinterpret_cast<const uint4*>(l + i);
+      }
+    }
+  }
+}
+
+int grid_for(int64_t work, int threads) {
+  int64_t b = (work + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  if (b < 1) b = 1;
+  return static_cast<int>(b);
+}
+
+}  // namespace
+
+cudaError_t absmax_launch(const float* X, int64_t rows, int64_t cols, int64_t ld,
+                          bool blocks_along_rows, unsigned* amax, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>((cols + 127) / 128), static_cast<unsigned>((rows + 31) / 32));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  const bool vec = ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+  if (vec)
+    absmax_kernel<true><<<grid, 256, 0, s>>>(X, rows, cols, ld, blocks_along_rows ? 1 : 0, amax);
+  else
+    absmax_kernel<false><<<grid, 256, 0, s>>>(X, rows, cols, ld, blocks_along_rows ? 1 : 0, amax);
+  return cudaGetLastError();
+}
+
+cudaError_t split_rows_launch(Prec p, const float* X, int64_t rows, int64_t cols, int64_t ld,
+                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s) {
+  const bool vec = ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+  const int grid = grid_for(rows * (pitch / 4), 256);
+  if (p == Prec::TF32) {
+    if (vec) split_rows_kernel<true, true><<<grid, 256, 0, s>>>(X, rows, cols, ld, amax, planes, pitch);
+    else split_rows_kernel<true, false><<<grid, 256, 0, s>>>(X, rows, cols, ld, amax, planes, pitch);
+  } else {
+    if (vec) split_rows_kernel<false, true><<<grid, 256, 0, s>>>(X, rows, cols, ld, amax, planes, pitch);
+    else split_rows_kernel<false, false><<<grid, 256, 0, s>>>(X, rows, cols, ld, amax, planes, pitch);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t split_cols_launch(Prec p, const float* X, int64_t K, int64_t N, int64_t ld,
+                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>((N + 63) / 64), static_cast<unsigned>((pitch + 63) / 64));
+  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+  const bool vec = ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+  if (p == Prec::TF32) {
+    if (vec) split_cols_kernel<true, true><<<grid, 256, 0, s>>>(X, K, N, ld, amax, planes, pitch);
+    else split_cols_kernel<true, false><<<grid, 256, 0, s>>>(X, K, N, ld, amax, planes, pitch);
+  } else {
+    if (vec) split_cols_kernel<false, true><<<grid, 256, 0, s>>>(X, K, N, ld, amax, planes, pitch);
+    else split_cols_kernel<false, false><<<grid, 256, 0, s>>>(X, K, N, ld, amax, planes, pitch);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace gb

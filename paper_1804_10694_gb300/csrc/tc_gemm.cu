@@ -1,0 +1,397 @@
+// Split-precision tensor-core gemm for sm_103a: C = alpha * A * B + beta * C
+// with FP32 semantics, computed as three bf16 (or tf32) tensor-core products
+// per k-step, hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory.
+//
+// The paper's gemm recipe (Section I; Section VI-A) is two-level tiling,
+// array packing, register blocking and prefetching, with full tiles kept
+// apart from partial ones, and on GPUs coalesced accesses plus explicit
+// staging global -> shared -> registers with synchronization.  On sm_103a that
+// becomes:
+//   * packing: a separate pass writes each operand as hi/lo planes, K-major,
+//     with per-block power-of-two scaling (split.cu);
+//   * tiling: persistent CTAs walk 128 x BN output tiles (optionally split
+//     along K); each tile's k-loop streams 128-byte k-chunks of the four
+//     planes through a STAGES-deep shared-memory ring filled by TMA;
+//   * register blocking -> tensor memory: one elected thread issues
+//     tcgen05.mma into a TMEM accumulator (two buffers, so the epilogue of one
+//     accumulation block overlaps the MMAs of the next);
+//   * full vs partial tiles: TMA zero-fills the out-of-range part of edge
+//     tiles on load, so the main loop never branches; only the epilogue
+//     masks rows/columns, and full tiles take a vectorised store path;
+//   * accumulation blocks: every kb k-chunks the epilogue warps fold the TMEM
+//     partial sum into FP32 registers with round-to-nearest adds, which bounds
+//     how many products the tensor core's own accumulation chains together.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2..5 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+#include "scale.cuh"
+
+namespace gb {
+
+template <int BN, bool TF32>
+struct TcCfg {
+  static constexpr int BM = 128;
+  static constexpr int ROW_BYTES = 128;                // one k-chunk of one row
+  static constexpr int A_PLANE = BM * ROW_BYTES;       // 16 KB
+  static constexpr int B_PLANE = BN * ROW_BYTES;
+  static constexpr int STAGE = 2 * A_PLANE + 2 * B_PLANE;
+  static constexpr int STAGES = BN == 64 ? 4 : 3;
+  static constexpr int BK = TF32 ? 32 : 64;            // elements per k-chunk
+  static constexpr int TMEM_COLS = 2 * BN;             // two accumulator buffers
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+  static constexpr int THREADS = 192;
+  static_assert(STAGES * STAGE + BAR_BYTES + 1024 <= 232448, "shared memory budget");
+};
+
+struct TileCoord {
+  int tm, tn, ks;
+};
+
+__device__ __forceinline__ TileCoord decode_unit(const TcArgs& a, int u) {
+  TileCoord c;
+  const int t = u % a.num_tiles;
+  c.ks = u / a.num_tiles;
+  const int group_tiles = a.group_m * a.tiles_n;
+  const int g = t / group_tiles;
+  const int first_m = g * a.group_m;
+  const int rows_in_group = min(a.tiles_m - first_m, a.group_m);
+  const int r = t % group_tiles;
+  c.tm = first_m + r % rows_in_group;
+  c.tn = r / rows_in_group;
+  return c;
+}
+
+template <int BN, bool TF32>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs a) {
+  using Cfg = TcCfg<BN, TF32>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t sbase = (raw + 1023u) & ~1023u;
+  uint8_t* smem = smem_raw + (sbase - raw);
+
+  // barrier block after the stage ring
+  uint8_t* bar_area = smem + STAGES * Cfg::STAGE;
+  const uint32_t bar0 = sbase + STAGES * Cfg::STAGE;
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * (2 * STAGES + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf_bar(b), 1);
+      mbar_init(acce_bar(b), 128);
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t stage = 0, phase = 0;
+      uint32_t last_phase[STAGES];
+      bool issued[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued[s] = false, last_phase[s] = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
+        const TileCoord tc = decode_unit(a, u);
+        const int c0 = tc.ks * a.chunks_per_split;
+        const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
+        for (int c = c0; c < c1; ++c) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full_bar(stage);
+          mbar_arrive_expect_tx(fb, Cfg::STAGE);
+          const uint32_t sA = sbase + stage * Cfg::STAGE;
+          const int kx = c * Cfg::BK;
+          tma_load_3d(sA, &tmA, fb, kx, tc.tm * Cfg::BM, 0);
+          tma_load_3d(sA + Cfg::A_PLANE, &tmA, fb, kx, tc.tm * Cfg::BM, 1);
+          tma_load_3d(sA + 2 * Cfg::A_PLANE, &tmB, fb, kx, tc.tn * BN, 0);
+          tma_load_3d(sA + 2 * Cfg::A_PLANE + Cfg::B_PLANE, &tmB, fb, kx, tc.tn * BN, 1);
+          issued[stage] = true;
+          last_phase[stage] = phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // abort: let every copy this thread started land before shared memory is released
+        for (int s = 0; s < STAGES; ++s)
+          if (issued[s]) mbar_wait_drain(full_bar(s), last_phase[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f32acc(TF32, 128, BN);
+      uint32_t stage = 0, phase = 0, ab = 0, aphase = 0;
+      bool ok = true;
+      bool any = false;
+      for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
+        const TileCoord tc = decode_unit(a, u);
+        const int c0 = tc.ks * a.chunks_per_split;
+        const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
+        for (int cb = c0; ok && cb < c1; cb += a.kb) {
+          const int ce = min(cb + a.kb, c1);
+          if (!mbar_wait(acce_bar(ab), aphase ^ 1u, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = tmem_base + ab * BN;
+          for (int c = cb; c < ce; ++c) {
+            if (!mbar_wait(full_bar(stage), phase, abort_flag, a.err)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sAhi = sbase + stage * Cfg::STAGE;
+            const uint32_t sAlo = sAhi + Cfg::A_PLANE;
+            const uint32_t sBhi = sAhi + 2 * Cfg::A_PLANE;
+            const uint32_t sBlo = sBhi + Cfg::B_PLANE;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t off = kk * 32;   // 32 bytes = one MMA's K slice
+              const uint64_t dAhi = sdesc_k_sw128(sAhi + off);
+              const uint64_t dAlo = sdesc_k_sw128(sAlo + off);
+              const uint64_t dBhi = sdesc_k_sw128(sBhi + off);
+              const uint64_t dBlo = sdesc_k_sw128(sBlo + off);
+              const uint32_t acc = (c > cb || kk > 0) ? 1u : 0u;
+              if (TF32) {
+                umma_tf32(d, dAlo, dBhi, idesc, acc);
+                umma_tf32(d, dAhi, dBlo, idesc, 1u);
+                umma_tf32(d, dAhi, dBhi, idesc, 1u);
+              } else {
+                umma_bf16(d, dAlo, dBhi, idesc, acc);
+                umma_bf16(d, dAhi, dBlo, idesc, 1u);
+                umma_bf16(d, dAhi, dBhi, idesc, 1u);
+              }
+            }
+            any = true;
+            umma_commit(empty_bar(stage));
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+          if (!ok) break;
+          umma_commit(accf_bar(ab));
+          ab ^= 1u;
+          if (ab == 0) aphase ^= 1u;
+        }
+      }
+      if (any) {
+        // every MMA this thread issued has finished before TMEM is released
+        umma_commit(drain_bar);
+        mbar_wait_drain(drain_bar, 0);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int row_in_tile = q * 32 + lane;
+    uint32_t ab = 0, aphase = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
+      const TileCoord tc = decode_unit(a, u);
+      const int c0 = tc.ks * a.chunks_per_split;
+      const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
+      float S[BN];
+      int blk = 0;
+      for (int cb = c0; cb < c1; cb += a.kb, ++blk) {
+        // the whole warp must agree before the warp-collective TMEM loads
+        const bool waited = mbar_wait(accf_bar(ab), aphase, abort_flag, a.err);
+        if (!__all_sync(0xffffffffu, waited)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * BN;
+#pragma unroll
+        for (int j = 0; j < BN / 32; ++j) {
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(taddr + j * 32, r);
+          tmem_wait_ld();
+          if (blk == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[j * 32 + i] = __uint_as_float(r[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[j * 32 + i] += __uint_as_float(r[i]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(acce_bar(ab));
+        ab ^= 1u;
+        if (ab == 0) aphase ^= 1u;
+      }
+      if (!ok) break;
+
+      // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
+      // applied before the power of two, so that a result in range is not
+      // lost to an overflow of the unscaled sum (the power of two is exact).
+      const int row = tc.tm * 128 + row_in_tile;
+      const int col0 = tc.tn * BN;
+      const int e = block_exponent(a.amaxA[tc.tm]) + block_exponent(a.amaxB[col0 / kScaleBlock]);
+      float alpha = a.alpha;
+      const float beta = a.beta;
+      if (a.split_k > 1) {
+        // partial sums keep alpha out (the reduction applies it)
+        if (e != 0) {
+#pragma unroll
+          for (int i = 0; i < BN; ++i) S[i] = scale_pow2(S[i], e);
+        }
+      } else if (e != 0) {
+#pragma unroll
+        for (int i = 0; i < BN; ++i) S[i] = scale_pow2(alpha * S[i], e);
+        alpha = 1.0f;
+      }
+      if (row >= a.M) continue;
+      if (a.split_k > 1) {
+        float* prow = a.partial + (static_cast<int64_t>(tc.ks) * a.M + row) * a.N;
+#pragma unroll
+        for (int i = 0; i < BN; ++i)
+          if (col0 + i < a.N) prow[col0 + i] = S[i];
+        continue;
+      }
+      float* crow = a.C + static_cast<int64_t>(row) * a.ldc;
+      if (a.c_vec4 && col0 + BN <= a.N) {
+        float4* c4 = reinterpret_cast<float4*>(crow + col0);
+#pragma unroll
+        for (int i = 0; i < BN / 4; ++i) {
+          float4 o;
+          if (beta != 0.0f) {
+            const float4 old = c4[i];
+            o.x = fmaf(alpha, S[4 * i + 0], beta * old.x);
+            o.y = fmaf(alpha, S[4 * i + 1], beta * old.y);
+            o.z = fmaf(alpha, S[4 * i + 2], beta * old.z);
+            o.w = fmaf(alpha, S[4 * i + 3], beta * old.w);
+          } else {
+            o.x = alpha * S[4 * i + 0];
+            o.y = alpha * S[4 * i + 1];
+            o.z = alpha * S[4 * i + 2];
+            o.w = alpha * S[4 * i + 3];
+          }
+          c4[i] = o;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < BN; ++i) {
+          const int col = col0 + i;
+          if (col < a.N) {
+            const float v = beta != 0.0f ? fmaf(alpha, S[i], beta * crow[col]) : alpha * S[i];
+            crow[col] = v;
+          }
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+  }
+}
+
+// Split-K fix-up: C = alpha * sum_s partial[s] + beta * C, partials summed in
+// increasing s (a fixed order, so results do not depend on timing).
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
+                                     float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+  const int64_t total = static_cast<int64_t>(M) * N;
+  const int64_t plane = total;
+  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float s = partial[idx];
+    for (int k = 1; k < splits; ++k) s += partial[k * plane + idx];
+    const int64_t r = idx / N, c = idx % N;
+    float* cp = C + r * ldc + c;
+    *cp = beta != 0.0f ? fmaf(alpha, s, beta * *cp) : alpha * s;
+  }
+}
+
+int tc_smem_bytes(int bn, Prec prec) {
+  if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true>::SMEM : TcCfg<128, true>::SMEM;
+  return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
+}
+
+template <int BN, bool TF32>
+static cudaError_t launch_variant(int grid, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                  const TcArgs& a, cudaStream_t s) {
+  using Cfg = TcCfg<BN, TF32>;
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured_device != dev) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  tc_gemm_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const TcArgs& a, cudaStream_t s) {
+  if (l.prec == Prec::TF32) {
+    if (l.bn == 64) return launch_variant<64, true>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, true>(l.grid, tmA, tmB, a, s);
+  } else {
+    if (l.bn == 64) return launch_variant<64, false>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, false>(l.grid, tmA, tmB, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float alpha,
+                                 float beta, float* C, int64_t ldc, cudaStream_t s) {
+  const int64_t total = static_cast<int64_t>(M) * N;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  splitk_reduce_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(M, N, splits, partial, alpha, beta,
+                                                               C, ldc);
+  return cudaGetLastError();
+}
+
+}  // namespace gb

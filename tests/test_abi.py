@@ -1,0 +1,83 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every
+function include/*.h declares, the ctypes table mirrors the header, and
+argument validation rejects bad calls before touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import paper_1804_10694_gb300 as pkg
+from paper_1804_10694_gb300 import _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(gemm_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = pkg.load()
+    declared = _declared_functions()
+    assert len(declared) >= 10
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_ctypes_table_mirrors_header():
+    assert _declared_functions() == set(_native.SIGNATURES)
+
+
+def test_config_table():
+    n = pkg.config_count("bf16x3")
+    assert n == pkg.config_count("tf32x3") > 0
+    assert pkg.config_count("simt") == 0
+    seen = set()
+    for i in range(n):
+        c = pkg.config_get("bf16x3", i)
+        assert c["block_n"] in (64, 128)
+        assert c["split_k"] >= 1 and c["kb"] >= 0 and c["group_m"] >= 1
+        key = tuple(sorted(c.items()))
+        assert key not in seen
+        seen.add(key)
+    with pytest.raises(pkg.GemmError):
+        pkg.config_get("bf16x3", n)
+
+
+def test_invalid_arguments_rejected_before_launch():
+    lib = pkg.load()
+    # negative size, ld below row length, null pointers: no device needed
+    assert lib.gemm_f32(-1, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == 1
+    assert lib.gemm_f32(4, 4, 8, 1.0, None, 7, None, 4, 0.0, None, 4) == 1
+    assert b"lda" in lib.gemm_last_error()
+    assert lib.gemm_f32(4, 4, 4, 1.0, None, 4, None, 3, 0.0, None, 4) == 1
+    assert lib.gemm_f32(4, 5, 4, 1.0, None, 4, None, 5, 0.0, None, 4) == 1
+    assert lib.gemm_f32(4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == 1   # null C
+    h = ctypes.c_void_p()
+    assert lib.gemm_plan_create(-3, 4, 4, 4, 4, 4, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create(4, 4, 4, 4, 4, 4, 2, 0, None) == 1
+    assert lib.gemm_plan_execute(None, 1.0, None, None, 0.0, None, None) == 1
+    assert lib.gemm_plan_create_config(4, 4, 4, 4, 4, 4, 2, -1, ctypes.byref(h)) == 1
+    # empty problems are no-ops even without a device
+    assert lib.gemm_f32(0, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4) == 0
+    assert lib.gemm_f32(4, 0, 4, 1.0, None, 4, None, 1, 0.0, None, 1) == 0
+
+
+def test_split_pack_argument_checks():
+    lib = pkg.load()
+    assert lib.gemm_split_pack(1, 0, 4, 4, None, 4, None, 8, None, None) == 1   # SIMT mode
+    assert lib.gemm_split_pack(2, 0, 4, 4, None, 3, None, 8, None, None) == 1   # ld < cols
+    assert lib.gemm_split_pack(2, 0, 0, 4, None, 4, None, 8, None, None) == 0   # empty
+
+
+def test_build_flags_target_sm103a():
+    from paper_1804_10694_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH

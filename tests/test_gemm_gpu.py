@@ -1,0 +1,263 @@
+"""GPU parity of every gemm mode against the FP64 CPU oracle, through the C ABI.
+
+Bar: relative Frobenius error <= 1e-5 on every result; bit-exact results on
+integer-valued inputs (products and sums exact in FP32); identical results
+across tile configurations on integer inputs (a schedule must not change the
+answer, Tiramisu Section III); full and partial tiles alike (Section V-B)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1804_10694_gb300 as pkg
+import workloads as W
+from gpu_helpers import (MODES, TOL, check_padding_untouched, dev, rel_err_rows, run_gemm,
+                         sample_rows, square_inputs)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    pkg.load()
+    yield
+    pkg.device_error()
+
+
+# ------------------------------------------------------------ small parity
+@pytest.mark.parametrize("mode", MODES)
+def test_config0_512_cubed(mode):
+    sa, sb, sc = W.seeds(W.CONFIG_SMALL)
+    n = 512
+    A, B, C0 = W.uniform(n, n, sa), W.uniform(n, n, sb), W.uniform(n, n, sc)
+    ref = oracle.gemm_f64(n, n, n, 1.5, A, B, 0.5, C0)
+    got = run_gemm(mode, n, n, n, 1.5, A, B, 0.5, C0)
+    assert oracle.rel_frob(got, ref) <= TOL
+
+
+RAGGED = [(300, 260, 333, 0), (129, 257, 1060, 1), (1060, 1060, 1060, 0), (1, 1, 1, 0),
+          (5, 3, 7, 3), (128, 128, 64, 0), (17, 300, 5, 1), (260, 65, 97, 3), (2, 500, 1, 0),
+          (777, 64, 129, 0), (64, 777, 4099, 1)]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("M,N,K,pad", RAGGED)
+@pytest.mark.parametrize("alpha,beta", W.ALPHA_BETA)
+def test_ragged_shapes(mode, M, N, K, pad, alpha, beta):
+    A = W.uniform(M, K, 11, ld=K + pad)
+    B = W.uniform(K, N, 12, ld=N + pad)
+    C0 = W.uniform(M, N, 13, ld=N + pad)
+    ref = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
+    got = run_gemm(mode, M, N, K, alpha, A, B, beta, C0)
+    assert oracle.rel_frob(got, ref) <= TOL, (M, N, K)
+    check_padding_untouched(C0, got, N)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("alpha,beta", W.ALPHA_BETA)
+def test_integer_inputs_bit_exact(mode, alpha, beta):
+    M, N, K = 700, 650, 1100
+    A, B, C0 = W.integers(M, K, 1), W.integers(K, N, 2), W.integers(M, N, 3)
+    ref = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
+    got = run_gemm(mode, M, N, K, alpha, A, B, beta, C0)
+    assert np.array_equal(got, ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_brute_force_tiny_shapes(mode):
+    shapes = [(m, n, k) for m in range(1, 10) for n in range(1, 10) for k in range(1, 10)][::11]
+    shapes += [(13, 17, 31), (33, 13, 17), (127, 129, 31), (129, 127, 33), (31, 255, 257)]
+    for i, (M, N, K) in enumerate(shapes):
+        pad = (0, 1, 3)[i % 3]
+        A = W.uniform(M, K, 500 + i, ld=K + pad)
+        B = W.uniform(K, N, 600 + i, ld=N + pad)
+        C0 = W.uniform(M, N, 700 + i, ld=N + pad)
+        ref = oracle.gemm_f64(M, N, K, 1.5, A, B, -0.75, C0)
+        got = run_gemm(mode, M, N, K, 1.5, A, B, -0.75, C0)
+        assert oracle.rel_frob(got, ref) <= TOL, (M, N, K)
+        check_padding_untouched(C0, got, N)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_blas_special_cases(mode):
+    M, N, K = 70, 50, 40
+    A, B, C0 = W.uniform(M, K, 1), W.uniform(K, N, 2), W.uniform(M, N, 3)
+    # K == 0 -> C = beta*C
+    got = run_gemm(mode, M, N, 0, 1.0, A, B, 0.5, C0)
+    assert np.array_equal(got, (C0 * np.float32(0.5)))
+    # alpha == 0: A and B are not read (NaN there must not propagate)
+    Anan = np.full_like(A, np.nan)
+    got = run_gemm(mode, M, N, K, 0.0, Anan, B, 2.0, C0)
+    assert np.array_equal(got, C0 * np.float32(2.0))
+    # beta == 0: old C is not read
+    Cnan = np.full_like(C0, np.nan)
+    got = run_gemm(mode, M, N, K, 1.0, A, B, 0.0, Cnan)
+    ref = oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)
+    assert np.isfinite(got).all() and oracle.rel_frob(got, ref) <= TOL
+    # NaN in A propagates to its row only
+    Ap = A.copy()
+    Ap[3, 7] = np.nan
+    got = run_gemm(mode, M, N, K, 1.0, Ap, B, 0.0, C0)
+    assert np.isnan(got[3]).all()
+    assert np.isfinite(np.delete(got, 3, axis=0)).all()
+
+
+# ------------------------------------------------------------- split/pack
+@pytest.mark.parametrize("mode,prec", [("bf16x3", "bf16"), ("tf32x3", "tf32")])
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("gen", ["uniform", "wide", "tiny"])
+def test_split_pack_bit_exact(mode, prec, transpose, gen):
+    from oracle import split
+    rows, cols = (300, 77) if not transpose else (77, 300)
+    if gen == "uniform":
+        X = W.uniform(rows, cols, 5, ld=cols + 3)
+    elif gen == "wide":
+        X = W.wide_range(rows, cols, 6, ld=cols + 3, lo=-40, hi=40)
+    else:
+        X = W.scaled(W.uniform(rows, cols, 7), -120)
+        X = W._with_ld(X, cols + 3, np.nan)
+    planes, amax = pkg.split_pack(dev(X)[:, :cols], mode=mode, transpose=transpose)
+    torch.cuda.synchronize()
+    P = planes.float().cpu().numpy()
+    logical = X[:, :cols]
+    src = logical.T.copy() if transpose else logical
+    prow, K = src.shape
+    hi, lo, exps = split.split_rows(src, prow, K, prec)
+    got_exps = [split.block_exponent(np.array([v], np.int32).view(np.float32)[0])
+                for v in amax.cpu().numpy()]
+    assert list(exps) == got_exps
+    assert np.array_equal(P[0, :, :K].view(np.uint32), hi.view(np.uint32))
+    assert np.array_equal(P[1, :, :K].view(np.uint32), lo.view(np.uint32))
+    assert not P[:, :, K:].any()          # pitch padding is zero
+
+
+# --------------------------------------------------- schedule invariance
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_every_configuration(mode):
+    M, N, K = 520, 390, 700
+    A, B, C0 = W.uniform(M, K, 31), W.uniform(K, N, 32), W.uniform(M, N, 33)
+    Ai, Bi, Ci = W.integers(M, K, 34), W.integers(K, N, 35), W.integers(M, N, 36)
+    ref = oracle.gemm_f64(M, N, K, 1.5, A, B, 0.5, C0)
+    refi = oracle.gemm_f64(M, N, K, 1.5, Ai, Bi, 0.5, Ci).astype(np.float32)
+    for cid in range(pkg.config_count(mode)):
+        got = run_gemm(mode, M, N, K, 1.5, A, B, 0.5, C0, config_id=cid)
+        assert oracle.rel_frob(got, ref) <= TOL, pkg.config_get(mode, cid)
+        goti = run_gemm(mode, M, N, K, 1.5, Ai, Bi, 0.5, Ci, config_id=cid)
+        assert np.array_equal(goti, refi), pkg.config_get(mode, cid)
+
+
+# ------------------------------------------------------ full-size configs
+@pytest.mark.parametrize("n", W.SQUARE_SWEEP)
+@pytest.mark.parametrize("alpha,beta", W.ALPHA_BETA)
+def test_square_sweep(n, alpha, beta):
+    """Square sweep at full size: every mode against oracle rows (full oracle
+    up to 2048, sampled rows above)."""
+    A, B, C0 = square_inputs(n, W.CONFIG_SWEEP)
+    rows = list(range(n)) if n <= 2048 else sample_rows(n, 40)
+    ref = oracle.gemm_f64_rows(rows, n, n, alpha, A, B, beta, C0)
+    for mode in MODES:
+        got = run_gemm(mode, n, n, n, alpha, A, B, beta, C0)
+        err = rel_err_rows(got, rows, ref, n)
+        assert err <= TOL, (mode, n, err)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_wide_range_8192(mode):
+    n = 8192
+    A, B, C0 = square_inputs(n, W.CONFIG_WIDE, "wide")
+    rows = sample_rows(n, 32, seed=2)
+    ref = oracle.gemm_f64_rows(rows, n, n, 1.0, A, B, 0.0, C0)
+    got = run_gemm(mode, n, n, n, 1.0, A, B, 0.0, C0)
+    assert rel_err_rows(got, rows, ref, n) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "simt"])
+def test_integer_8192_bit_exact(mode):
+    n = 8192
+    A, B, C0 = square_inputs(n, W.CONFIG_WIDE, "int")
+    rows = sample_rows(n, 32, seed=3)
+    ref = oracle.gemm_f64_rows(rows, n, n, 1.5, A, B, 0.5, C0)
+    got = run_gemm(mode, n, n, n, 1.5, A, B, 0.5, C0)
+    assert np.array_equal(got[rows], ref.astype(np.float32))
+
+
+@pytest.mark.parametrize("M,N,K", W.CONV_SHAPES)
+def test_conv_shapes(M, N, K):
+    sa, sb, _ = W.seeds(W.CONFIG_CONV)
+    A, B = W.uniform(M, K, sa), W.uniform(K, N, sb)
+    C0 = np.zeros((M, N), np.float32)
+    rows = sample_rows(M, 64, seed=4)
+    ref = oracle.gemm_f64_rows(rows, N, K, 1.0, A, B, 0.0, None)
+    for mode in MODES:
+        got = run_gemm(mode, M, N, K, 1.0, A, B, 0.0, C0)
+        assert rel_err_rows(got, rows, ref, N) <= TOL, mode
+
+
+# ------------------------------------------------------ block scaling
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_scaling_keeps_tiny_and_huge_operands(mode):
+    M, N, K = 300, 200, 500
+    base_a, base_b = W.uniform(M, K, 41), W.uniform(K, N, 42)
+    # tiny: products near 2^-120 (low parts far below the normal range unscaled)
+    A, B = W.scaled(base_a, -100), W.scaled(base_b, -20)
+    ref = oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)
+    got = run_gemm(mode, M, N, K, 1.0, A, B, 0.0, np.zeros((M, N), np.float32))
+    assert oracle.rel_frob(got, ref) <= TOL
+    # huge: A*B overflows FP32 but alpha*A*B does not
+    A, B = W.scaled(base_a, 64), W.scaled(base_b, 64)
+    alpha = math.ldexp(1.0, -20)
+    ref = oracle.gemm_f64(M, N, K, alpha, A, B, 0.0, None)
+    got = run_gemm(mode, M, N, K, alpha, A, B, 0.0, np.zeros((M, N), np.float32))
+    assert np.isfinite(got).all()
+    assert oracle.rel_frob(got, ref) <= TOL
+
+
+# ------------------------------------------------------- API surfaces
+def test_host_buffer_entry_point():
+    M, N, K = 333, 222, 444
+    A, B, C0 = W.uniform(M, K, 51), W.uniform(K, N, 52), W.uniform(M, N, 53)
+    ref = oracle.gemm_f64(M, N, K, 1.5, A, B, 0.5, C0)
+    for mode in MODES:
+        C = C0.copy()
+        pkg.gemm_host(A, B, C, 1.5, 0.5, mode=mode)
+        assert oracle.rel_frob(C, ref) <= TOL, mode
+
+
+def test_plan_replays_in_cuda_graph():
+    M, N, K = 640, 384, 1024
+    A, B, C0 = W.uniform(M, K, 61), W.uniform(K, N, 62), W.uniform(M, N, 63)
+    dA, dB = dev(A), dev(B)
+    dC_eager, dC_graph = dev(C0), dev(C0)
+    plan = pkg.Plan(M, N, K, mode="bf16x3")
+    plan.execute(dA, dB, dC_eager, 1.5, 0.5)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        plan.execute(dA, dB, dC_graph, 1.0, 0.0, stream=s)     # warm-up outside capture
+        torch.cuda.synchronize()
+        dC_graph.copy_(dev(C0))
+        with torch.cuda.graph(g, stream=s):
+            plan.execute(dA, dB, dC_graph, 1.5, 0.5, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(dC_graph, dC_eager)
+    plan.destroy()
+
+
+def test_torch_tensor_api_and_views():
+    M, N, K = 200, 150, 300
+    A = torch.from_numpy(W.uniform(M, K + 5, 71)).cuda()[:, :K]   # ld = K + 5
+    B = torch.from_numpy(W.uniform(K, N, 72)).cuda()
+    C = torch.zeros(M, N, device="cuda")
+    pkg.gemm(A, B, C, mode="bf16x3")
+    ref = oracle.gemm_f64(M, N, K, 1.0, A.cpu().numpy(), B.cpu().numpy(), 0.0, None)
+    assert oracle.rel_frob(C.cpu().numpy(), ref) <= TOL
+    with pytest.raises(ValueError):
+        pkg.gemm(A.t(), B, C)
+
+
+def test_device_error_word_clear():
+    pkg.device_error()
