@@ -1,0 +1,411 @@
+#!/usr/bin/env python
+"""Benchmark of the split-precision sgemm: C = alpha*A*B + beta*C in FP32
+semantics (the Tiramisu paper's sgemm, Section VI-A), prints ONE JSON line.
+
+Step = one full pass of the hot path on the top size of the square sweep,
+M = N = K = 8192, alpha = 1.5, beta = 0.5, uniform[-1, 1] inputs: the split /
+pack of A and B, the tcgen05 BF16x3 gemm kernel with its fused alpha/beta
+epilogue.  Inputs (768 MiB) exceed L2 (~126 MB), so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched by torchrun: every rank runs its own independent problem
+(weak scaling, no collective on the data path); timing is the max over ranks.
+--impl reference times the FP64 CPU oracle on bounded row samples of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SIZE = 8192
+ALPHA, BETA = 1.5, 0.5
+METRIC = "sgemm TFLOP/s at <=1e-5 rel err vs FP64 (split-BF16 TC vs plain FP32), % of peak"
+WORKLOAD = ("sgemm M=N=K=8192 row-major, alpha=1.5 beta=0.5, A,B,C iid uniform[-1,1] "
+            "(top size of the square sweep), split-precision BF16x3 tcgen05 path")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tc_gemm_bf16x3_8192_traffic.json")
+TC_SOURCE = os.path.join(ROOT, "paper_1804_10694_gb300", "csrc", "tc_gemm.cu")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--mode", default="bf16x3", choices=("bf16x3", "tf32x3", "simt"))
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--size", type=int, default=SIZE,
+                   help="M = N = K (profiling cases only; the reported workload is 8192)")
+    p.add_argument("--kernel-only", action="store_true",
+                   help="only warm-up and timed plan executions (for ncu captures)")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------- helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def inputs(n: int = SIZE):
+    import workloads as W
+    sa, sb, sc = W.seeds(W.CONFIG_SWEEP)
+    return W.uniform(n, n, sa + n), W.uniform(n, n, sb + n), W.uniform(n, n, sc + n)
+
+
+def run_kernel_only(args, local):
+    """Warm-up and timed executions of one plan, nothing else: the command
+    the ncu captures profile."""
+    import torch
+    import paper_1804_10694_gb300 as pkg
+    torch.cuda.set_device(local)
+    n = args.size
+    A, B, C0 = inputs(n)
+    dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C0))
+    plan = pkg.Plan(n, n, n, mode=args.mode)
+    for _ in range(args.warmup + args.steps):
+        plan.execute(dA, dB, dC, ALPHA, BETA)
+    torch.cuda.synchronize()
+    pkg.device_error()
+    plan.destroy()
+    print(json.dumps({"kernel_only": True, "size": n, "mode": args.mode,
+                      "executions": args.warmup + args.steps}))
+
+
+def source_digest(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_per_launch():
+    """DRAM bytes per launch of the gemm kernel from the committed ncu summary,
+    or None if missing or taken on a different kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f)
+    if d.get("source_sha256_16") != source_digest(TC_SOURCE):
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+def cpu_baseline(A, B, C0, target_s: float = 12.0, max_rows: int = 4096):
+    """The FP64 oracle as it stands on the host cores: sampled rows of the
+    same product, grown until about target_s seconds of CPU work."""
+    import numpy as np
+    import oracle
+    n = SIZE
+    rng = np.random.default_rng(12345)
+    order = rng.permutation(n)
+    done, t_total, rows_done, results = 0, 0.0, [], []
+    batch = 16
+    while t_total < target_s and done < max_rows:
+        rows = sorted(order[done:done + batch].tolist())
+        t0 = time.perf_counter()
+        out = oracle.gemm_f64_rows(rows, n, n, ALPHA, A, B, BETA, C0)
+        t_total += time.perf_counter() - t0
+        rows_done += rows
+        results.append(out)
+        done += batch
+        batch = min(batch * 2, 512)
+    ref = np.concatenate(results, axis=0)
+    flops = 2.0 * len(rows_done) * n * n
+    return {"value": flops / t_total / 1e12, "unit": "TFLOP/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(rows_done)} random rows of the 8192^3 product (alpha=1.5, beta=0.5), "
+                      f"FP64 i-k-j loop, {t_total:.1f} s"}, rows_done, ref
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_1804_10694_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    A, B, C0 = inputs()
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC0 = torch.from_numpy(C0).cuda()
+    dC = dC0.clone()
+    n = SIZE
+    flops = 2.0 * n ** 3
+    stream = torch.cuda.current_stream()
+    plan = pkg.Plan(n, n, n, mode=args.mode)
+    info = plan.info()
+
+    # correctness sample (checked below against the CPU-baseline rows)
+    plan.execute(dA, dB, dC, ALPHA, BETA)
+    torch.cuda.synchronize()
+    first_result = dC.cpu().numpy()
+
+    for _ in range(args.warmup):
+        plan.execute(dA, dB, dC, ALPHA, BETA)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    if args.mode != "simt":
+        plan.profile(args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)   # let the sampler take its first reading
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.execute(dA, dB, dC, ALPHA, BETA)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * flops / (ms * 1e-3) / 1e12
+    prof = plan.profile_read() if args.mode != "simt" else None
+    plan.profile(0)
+
+    pk, pk_kind = peaks()
+    roofline = None
+    launches_per_step = 1
+    if prof and prof["records"] > 0:
+        main_ms = prof["main_ms"] / prof["records"]
+        pack_ms = prof["pack_ms"] / prof["records"]
+        tensor_flops = 3.0 * flops                          # hi*hi + hi*lo + lo*hi
+        achieved = tensor_flops / (main_ms * 1e-3) / 1e12
+        peak = pk["bf16_tflops"]
+        traffic = traffic_per_launch()
+        roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "kernel": "tc_gemm_kernel<128,bf16>" if args.mode == "bf16x3" else "tc_gemm_kernel<128,tf32>",
+                    "peak_kind": f"{pk_kind} bf16 dense burst" + (
+                        " (tf32 runs at half the bf16 rate)" if args.mode == "tf32x3" else ""),
+                    "algorithmic_flops_per_launch": tensor_flops,
+                    "kernel_ms": round(main_ms, 4), "pack_ms": round(pack_ms, 4),
+                    "fp32_equiv_tflops_kernel": round(flops / (main_ms * 1e-3) / 1e12, 1),
+                    "fp32_equiv_peak": round(peak / 3.0, 1)}
+        launches_per_step = 5 + (1 if prof["reduce_ms"] > 0.001 else 0)
+
+    # plain FP32 CUDA-core kernel on the same workload (reference form)
+    simt = None
+    if args.mode != "simt":
+        dCs = dC0.clone()
+        for _ in range(2):
+            pkg.gemm(dA, dB, dCs, ALPHA, BETA, mode="simt")
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 5))
+        s0.record(stream)
+        for _ in range(reps):
+            pkg.gemm(dA, dB, dCs, ALPHA, BETA, mode="simt")
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1) / reps
+        simt = flops / (sms * 1e-3) / 1e12
+
+    # end to end through the host-buffer entry point (copies inside the call)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.from_numpy(C0.copy()).pin_memory()
+    pkg.gemm_host(hA, hB, hC, ALPHA, BETA, mode=args.mode)      # warm (device buffers, plan)
+    e2e_reps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        pkg.gemm_host(hA, hB, hC, ALPHA, BETA, mode=args.mode)
+    e2e_s = (time.perf_counter() - t0) / e2e_reps
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": round(world * flops / e2e_s / 1e12, 2), "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+           "ms_per_step": round(e2e_s * 1e3, 3),
+           "api": "gemm_f32_host (pinned host A, B, C; H2D + gemm + D2H + stream sync per call)"}
+
+    base = None
+    rel = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        base, rows, ref = cpu_baseline(A, B, C0)
+        rel = oracle.rel_frob(np.ascontiguousarray(first_result[rows]), ref)
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16x3": "bf16x3 (bf16 products, f32 accumulate)",
+                  "tf32x3": "tf32x3 (tf32 products, f32 accumulate)", "simt": "f32"}[args.mode],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.mode == "bf16x3" else WORKLOAD.replace("BF16x3", args.mode),
+                   "M": n, "N": n, "K": n, "alpha": ALPHA, "beta": BETA, "mode": args.mode,
+                   "config_id": info["config_id"],
+                   "l2": "inputs (768 MiB) larger than L2, no flush",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "roofline": roofline,
+        "cpu_baseline": base,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "simt_tflops": round(simt, 2) if simt else None,
+        "speedup_vs_simt": round(value / world / simt, 2) if simt else None,
+        "rel_frob_sampled": rel,
+    }
+    print(json.dumps(out), flush=True)
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    A, B, C0 = inputs()
+    n = SIZE
+    # bounded sample per step: enough rows for about 4 s of CPU work
+    probe_rows = [0, 1, 2, 3]
+    t0 = time.perf_counter()
+    oracle.gemm_f64_rows(probe_rows, n, n, ALPHA, A, B, BETA, C0)
+    per_row = max((time.perf_counter() - t0) / len(probe_rows), 1e-4)
+    rows_per_step = int(max(8, min(1024, 4.0 / per_row)))
+    rows = list(range(rows_per_step))
+    for _ in range(args.warmup):
+        oracle.gemm_f64_rows(rows[:8], n, n, ALPHA, A, B, BETA, C0)
+    times = []
+    for s in range(args.steps):
+        r = [(x + s * rows_per_step) % n for x in rows]
+        t0 = time.perf_counter()
+        oracle.gemm_f64_rows(r, n, n, ALPHA, A, B, BETA, C0)
+        times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = 2.0 * rows_per_step * n * n / step_s / 1e12
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD.replace("split-precision BF16x3 tcgen05 path",
+                                                 "FP64 CPU oracle"),
+                   "M": n, "N": n, "K": n, "alpha": ALPHA, "beta": BETA,
+                   "sample_rows_per_step": rows_per_step},
+        "cpu_baseline": {"value": round(value, 5), "unit": "TFLOP/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{rows_per_step} rows of the 8192^3 product per step, FP64"},
+        "e2e": {"value": round(value, 5), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    elif args.kernel_only:
+        run_kernel_only(args, local)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -80,7 +80,7 @@ typedef struct {
   int block_n;     /* output tile width (tile height is 128) */
   int stages;      /* depth of the shared-memory operand ring */
   int split_k;     /* number of K partitions (partials reduced in fixed order) */
-  int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (0 = whole K) */
+  int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (1..8) */
   int group_m;     /* raster: output tiles walked in groups of this many along M */
 } gemm_config;
 
@@ -129,6 +129,18 @@ gemm_status gemm_plan_execute(gemm_plan_t plan, float alpha, const float* A, con
 gemm_status gemm_plan_info(gemm_plan_t plan, int* mode, int* config_id, size_t* workspace_bytes);
 
 gemm_status gemm_plan_destroy(gemm_plan_t plan);
+
+/* Stage timing with CUDA events recorded on the execution stream: for the
+ * next `max_records` executions of a tensor-core plan, events are recorded at
+ * the start of packing, around the main gemm kernel and at the end (split-K
+ * reduction).  0 turns timing off and frees the events.  Not for use while a
+ * stream is being captured into a graph. */
+gemm_status gemm_plan_profile(gemm_plan_t plan, int max_records);
+
+/* Waits for the recorded executions and returns their count and the summed
+ * milliseconds of packing, main kernel and reduction. */
+gemm_status gemm_plan_profile_read(gemm_plan_t plan, int* records, float* pack_ms, float* main_ms,
+                                   float* reduce_ms);
 
 /* --------------------------------------------------- tile configurations -- */
 

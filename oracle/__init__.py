@@ -14,4 +14,4 @@ Modules:
   mlp    -- the cost model's MLP: forward, MSE loss, analytic backward, Adam.
 """
 from .gemm import (build, gemm_f64, gemm_f64_rows, rel_frob, gemm_exact,  # noqa: F401
-                   library_path)
+                   library_path, num_threads)

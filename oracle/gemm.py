@@ -55,6 +55,8 @@ def _load():
             lib.oracle_gemm_f64_rows.restype = None
             lib.oracle_rel_frob.argtypes = [i64, i64, vp, i64, vp, i64]
             lib.oracle_rel_frob.restype = ctypes.c_double
+            lib.oracle_num_threads.argtypes = []
+            lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -112,6 +114,11 @@ def gemm_f64_rows(rows, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndarr
                              B.shape[1], ctypes.c_float(beta), _ptr(C0), ldc,
                              _ptr(rows), len(rows), _ptr(out))
     return out
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return int(_load().oracle_num_threads())
 
 
 def rel_frob(got: np.ndarray, ref: np.ndarray) -> float:

@@ -85,3 +85,14 @@ double oracle_rel_frob(int64_t M, int64_t N, const float* got, int64_t ldg,
     if (den == 0.0) return __builtin_sqrt(num);
     return __builtin_sqrt(num / den);
 }
+
+/* Threads the OpenMP loops above use (for reporting the CPU baseline). */
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

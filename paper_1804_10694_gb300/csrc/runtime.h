@@ -3,6 +3,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/gemm.h"
 #include "internal.h"
 
@@ -27,6 +29,10 @@ struct gemm_plan_s {
   CUtensorMap tmA{}, tmB{};
   gb::TcArgs args{};
   gb::TcLaunch launch{};
+  // stage timing (gemm_plan_profile): four events per recorded execution,
+  // at the start of packing, before and after the main kernel, at the end
+  int prof_max = 0, prof_n = 0;
+  std::vector<cudaEvent_t> prof_events;
 };
 
 namespace gb {

@@ -274,11 +274,9 @@ __global__ void __launch_bounds__(192, 1)
       float alpha = a.alpha;
       const float beta = a.beta;
       if (a.split_k > 1) {
-        // partial sums keep alpha out (the reduction applies it)
-        if (e != 0) {
+        // split-K partials carry alpha already (the reduction adds beta*C)
 #pragma unroll
-          for (int i = 0; i < BN; ++i) S[i] = scale_pow2(S[i], e);
-        }
+        for (int i = 0; i < BN; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
       } else if (e != 0) {
 #pragma unroll
         for (int i = 0; i < BN; ++i) S[i] = scale_pow2(alpha * S[i], e);
@@ -333,10 +331,11 @@ __global__ void __launch_bounds__(192, 1)
   }
 }
 
-// Split-K fix-up: C = alpha * sum_s partial[s] + beta * C, partials summed in
-// increasing s (a fixed order, so results do not depend on timing).
+// Split-K fix-up: C = sum_s partial[s] + beta * C, where each partial already
+// holds alpha * (its share of A*B); partials are summed in increasing s (a
+// fixed order, so results do not depend on timing).
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
-                                     float alpha, float beta, float* __restrict__ C, int64_t ldc) {
+                                     float beta, float* __restrict__ C, int64_t ldc) {
   const int64_t total = static_cast<int64_t>(M) * N;
   const int64_t plane = total;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -345,7 +344,7 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
     for (int k = 1; k < splits; ++k) s += partial[k * plane + idx];
     const int64_t r = idx / N, c = idx % N;
     float* cp = C + r * ldc + c;
-    *cp = beta != 0.0f ? fmaf(alpha, s, beta * *cp) : alpha * s;
+    *cp = beta != 0.0f ? s + beta * *cp : s;
   }
 }
 
@@ -383,14 +382,14 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   return cudaErrorInvalidValue;
 }
 
-cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float alpha,
-                                 float beta, float* C, int64_t ldc, cudaStream_t s) {
+cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float beta,
+                                 float* C, int64_t ldc, cudaStream_t s) {
   const int64_t total = static_cast<int64_t>(M) * N;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  splitk_reduce_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(M, N, splits, partial, alpha, beta,
-                                                               C, ldc);
+  splitk_reduce_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(M, N, splits, partial, beta, C,
+                                                               ldc);
   return cudaGetLastError();
 }
 
