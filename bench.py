@@ -43,8 +43,8 @@ TC_SOURCE = os.path.join(ROOT, "paper_1804_10694_gb300", "csrc", "tc_gemm.cu")
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--mode", default="bf16x3", choices=("bf16x3", "tf32x3", "simt"))
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -240,6 +240,10 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     first_result = dC.cpu().numpy()
 
+    # clocks are sampled from just before the warm-up to the end of the timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)   # let the sampler take its first reading
     for _ in range(args.warmup):
         plan.execute(dA, dB, dC, ALPHA, BETA)
     torch.cuda.synchronize()
@@ -247,9 +251,6 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     if args.mode != "simt":
         plan.profile(args.steps)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)   # let the sampler take its first reading
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
