@@ -177,6 +177,31 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
                             const float* X, int64_t ld, void* planes, int64_t pitch,
                             unsigned* amax, gemm_stream_t stream);
 
+/* ------------------------------------------------- allocation-free path -- */
+
+/* C = alpha*A*B + beta*C with the BF16x3 tensor-core kernel, for callers that
+ * cannot allocate device memory: for example a thread capturing a stream in a
+ * mode where allocation is illegal, a framework whose caching allocator holds
+ * (nearly) all of device memory, or a latency-critical path that cannot
+ * afford the device synchronisation cudaMalloc/cudaFree may imply.  The paper
+ * has no counterpart: it is an interface convenience of this library.
+ *
+ * The call allocates nothing.  Its scratch (packed hi/lo operand planes and
+ * block maxima) is a fixed 64 MiB static device array that every GPU which
+ * loads this code holds until the process exits; a problem needing more,
+ * 4 * (M + N) * roundup(K, 8) bytes plus 4 * (ceil(M/128) + ceil(N/128)) for
+ * the maxima (each part rounded up to 256 bytes), is rejected with
+ * GEMM_ERR_INVALID_ARG (for square problems the limit is about
+ * M = N = K = 2896).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and each call
+ * overwrites it, so calls that overlap on the GPU (other streams, other host
+ * threads) race.  Pointers, layout, special cases and errors are as for
+ * gemm_f32_ex; no split-K is used and the call never synchronises. */
+gemm_status gemm_f32_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                                    int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                                    int64_t ldc, gemm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
