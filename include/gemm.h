@@ -142,6 +142,111 @@ gemm_status gemm_plan_profile(gemm_plan_t plan, int max_records);
 gemm_status gemm_plan_profile_read(gemm_plan_t plan, int* records, float* pack_ms, float* main_ms,
                                    float* reduce_ms);
 
+/* --------------------------------------------------------- grouped gemm -- */
+
+/* Plan for G independent problems C_g = alpha_g*A_g*B_g + beta_g*C_g with
+ * their own shapes and leading dimensions (arrays of G entries, caller's
+ * order).  The tensor-core modes run every problem in ONE persistent kernel
+ * launch (after one launch that takes all block maxima and one that writes all
+ * hi/lo planes); tiles are walked problem by problem, longest K first.  The
+ * tile width and TMEM fold length are chosen by `sel`: DEFAULT uses a
+ * heuristic (tile width with less padding waste), EXHAUSTIVE times the
+ * candidates on synthetic data now (the project's autotuner).  SIMT mode runs
+ * one plain FP32 launch per problem.  The plan owns its packed planes,
+ * problem tables and CUDA graph. */
+gemm_status gemm_grouped_plan_create(int G, const int64_t* M, const int64_t* N, const int64_t* K,
+                                     const int64_t* lda, const int64_t* ldb, const int64_t* ldc,
+                                     gemm_mode mode, gemm_select sel, gemm_grouped_plan_t* out);
+
+/* As gemm_grouped_plan_create with an explicit tile width (64 or 128) and TMEM
+ * fold length kb (1..8). */
+gemm_status gemm_grouped_plan_create_config(int G, const int64_t* M, const int64_t* N,
+                                            const int64_t* K, const int64_t* lda,
+                                            const int64_t* ldb, const int64_t* ldc, gemm_mode mode,
+                                            int block_n, int kb, gemm_grouped_plan_t* out);
+
+/* Execute: alpha/beta are HOST arrays of G scalars, A/B/C HOST arrays of G
+ * DEVICE pointers (caller's order).  The first call captures the launches
+ * into a CUDA graph, later calls replay it; the per-problem pointers and
+ * scalars are uploaded (stream-ordered, before the replay) only when they
+ * change.  No host synchronisation. */
+gemm_status gemm_grouped_execute(gemm_grouped_plan_t plan, const float* alpha, const float* const* A,
+                                 const float* const* B, const float* beta, float* const* C,
+                                 gemm_stream_t stream);
+
+/* Same computation without the graph: launches directly on `stream`. */
+gemm_status gemm_grouped_execute_eager(gemm_grouped_plan_t plan, const float* alpha,
+                                       const float* const* A, const float* const* B,
+                                       const float* beta, float* const* C, gemm_stream_t stream);
+
+/* Tile width, TMEM fold length, total output tiles, workspace bytes. */
+gemm_status gemm_grouped_plan_info(gemm_grouped_plan_t plan, int* block_n, int* kb, int* tiles,
+                                   size_t* workspace_bytes);
+
+gemm_status gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
+
+/* ------------------------------------------------------------ autotuning -- */
+
+/* Autotune (paper Section VI-A: tile sizes chosen by search): for each of the
+ * G shapes (M, N, K triples, tight leading dimensions) time every distinct
+ * candidate configuration of `mode` on synthetic uniform data, `reps` CUDA-
+ * event-timed executions after two warm-ups, median.  Appends one CSV row per
+ * (shape, configuration) to out_path ("M,N,K,mode,config_id,median_ms,
+ * block_n,split_k,kb,group_m"; header written to a new file; NULL = no file)
+ * and records the fastest configuration per shape in the process-wide table
+ * used by GEMM_SELECT_TABLE.  Synchronises the device. */
+gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps, const char* out_path);
+
+/* Load timing rows (the CSV above) into the tuned table. */
+gemm_status gemm_autotune_load(const char* path);
+
+/* Fastest configuration and its median time for a shape in the tuned table
+ * (GEMM_ERR_INVALID_ARG if the shape was never tuned). */
+gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, gemm_mode mode, int* config_id,
+                               float* ms);
+
+/* ------------------------------------------------------------ cost model -- */
+
+/* Number of input features of the cost model (14). */
+int gemm_costmodel_feature_count(void);
+
+/* Features of one (shape, configuration) pair for an `sms`-SM device, written
+ * to out[gemm_costmodel_feature_count()]: log2 M, N, K; tile width / 128;
+ * log2 split-K; fold length / 8; log2 raster group; log2 tiles; log2(1 +
+ * waves); fill of the last wave; padded-work fraction; log2 arithmetic
+ * intensity; log2 k-chunks per split; 1 for TF32X3. */
+gemm_status gemm_costmodel_features(int64_t M, int64_t N, int64_t K, gemm_mode mode, int config_id,
+                                    int sms, float* out);
+
+/* Train the MLP cost model (features -> 64 -> ReLU -> 64 -> ReLU -> 1,
+ * predicting normalised log time) on the GPU from autotuner timing rows:
+ * `epochs` full-batch Adam steps, weights initialised from `seed`.  The model
+ * becomes the process-wide model used by GEMM_SELECT_MODEL and is written to
+ * out_model (text; NULL = not saved).  final_loss (optional) receives the
+ * training MSE in normalised units. */
+gemm_status gemm_costmodel_train(const char* timings_path, int epochs, uint64_t seed,
+                                 const char* out_model, float* final_loss);
+
+/* Load a saved cost model (GEMM_ERR_IO if the file is missing or malformed). */
+gemm_status gemm_costmodel_load(const char* path);
+
+/* Configuration with the smallest predicted time for a shape (one batched
+ * forward pass over the distinct candidates on the GPU) and that time. */
+gemm_status gemm_costmodel_predict(int64_t M, int64_t N, int64_t K, gemm_mode mode, int* config_id,
+                                   float* pred_ms);
+
+/* The training kernels alone, for checking them: loss and gradient of the MSE
+ * at parameters theta (flat layout W1[64][F], b1[64], W2[64][64], b2[64],
+ * w3[64], b3; F = gemm_costmodel_feature_count()) over n samples X[n][F] with
+ * targets t[n]; HOST pointers, computed on the GPU. */
+gemm_status gemm_mlp_loss_grad(int n, const float* theta, const float* X, const float* t, float* loss,
+                               float* grad);
+
+/* One Adam update on the GPU of P parameters (HOST arrays updated in place;
+ * step counts from 1). */
+gemm_status gemm_mlp_adam_step(int P, float* theta, const float* grad, float* m, float* v, int step,
+                               float lr, float beta1, float beta2, float eps);
+
 /* --------------------------------------------------- tile configurations -- */
 
 /* Number of candidate configurations for a tensor-core mode (0 for SIMT). */

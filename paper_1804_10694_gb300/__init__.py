@@ -214,3 +214,142 @@ def split_pack(X, mode="bf16x3", transpose: bool = False, stream=None):
     check(load().gemm_split_pack(m, 1 if transpose else 0, rows, cols, px, ld, planes.data_ptr(),
                                  pitch, amax.data_ptr(), _stream_handle(stream)))
     return planes, amax
+
+
+# ------------------------------------------------------------------ grouped
+def _i64_array(vals):
+    arr = (ctypes.c_int64 * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+class GroupedPlan:
+    """Plan for G independent gemms run in one persistent launch (see
+    gemm_grouped_plan_create).  shapes: list of (M, N, K); leading dimensions
+    default to the row lengths."""
+
+    def __init__(self, shapes, lds=None, mode="bf16x3", select="default", block_n=None, kb=None):
+        lib = load()
+        self._lib = lib
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        G = len(self.shapes)
+        if lds is None:
+            lds = [(max(k, 1), max(n, 1), max(n, 1)) for (m, n, k) in self.shapes]
+        self.lds = [tuple(int(x) for x in l) for l in lds]
+        arrs = [_i64_array([s[i] for s in self.shapes]) for i in range(3)]
+        larrs = [_i64_array([l[i] for l in self.lds]) for i in range(3)]
+        h = ctypes.c_void_p()
+        if block_n is None:
+            check(lib.gemm_grouped_plan_create(G, *arrs, *larrs, _mode(mode), _select(select),
+                                               ctypes.byref(h)))
+        else:
+            check(lib.gemm_grouped_plan_create_config(G, *arrs, *larrs, _mode(mode), int(block_n),
+                                                      int(kb if kb else 4), ctypes.byref(h)))
+        self._h = h
+        self.G = G
+
+    def execute(self, As, Bs, Cs, alphas, betas, stream=None, graph: bool = True):
+        """As, Bs, Cs: sequences of CUDA tensors (or integer device pointers)."""
+        G = self.G
+
+        def ptr(x):
+            return x if isinstance(x, int) else x.data_ptr()
+        pa = (ctypes.c_void_p * G)(*[ptr(x) for x in As])
+        pb = (ctypes.c_void_p * G)(*[ptr(x) for x in Bs])
+        pc = (ctypes.c_void_p * G)(*[ptr(x) for x in Cs])
+        al = (ctypes.c_float * G)(*[float(a) for a in alphas])
+        be = (ctypes.c_float * G)(*[float(b) for b in betas])
+        fn = self._lib.gemm_grouped_execute if graph else self._lib.gemm_grouped_execute_eager
+        check(fn(self._h, al, pa, pb, be, pc, _stream_handle(stream)))
+
+    def info(self) -> dict:
+        bn, kb, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        w = ctypes.c_size_t()
+        check(self._lib.gemm_grouped_plan_info(self._h, ctypes.byref(bn), ctypes.byref(kb),
+                                               ctypes.byref(t), ctypes.byref(w)))
+        return {"block_n": bn.value, "kb": kb.value, "tiles": t.value, "workspace_bytes": w.value}
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            check(self._lib.gemm_grouped_plan_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------- tuning and model
+def autotune(shapes, mode="bf16x3", reps: int = 5, out_path: str | None = None):
+    """Time every distinct configuration of each (M, N, K) shape; rows are
+    appended to out_path (CSV) and the best per shape enters the tuned table."""
+    flat = [int(x) for s in shapes for x in s]
+    arr = _i64_array(flat) if flat else None
+    check(load().gemm_autotune(arr, len(shapes), _mode(mode), int(reps),
+                               out_path.encode() if out_path else None))
+
+
+def autotune_load(path: str):
+    check(load().gemm_autotune_load(path.encode()))
+
+
+def autotune_best(M, N, K, mode="bf16x3"):
+    cid, ms = ctypes.c_int(), ctypes.c_float()
+    check(load().gemm_autotune_best(M, N, K, _mode(mode), ctypes.byref(cid), ctypes.byref(ms)))
+    return cid.value, ms.value
+
+
+def costmodel_feature_count() -> int:
+    return load().gemm_costmodel_feature_count()
+
+
+def costmodel_features(M, N, K, mode, config_id, sms=None):
+    import numpy as np
+    out = np.zeros(costmodel_feature_count(), dtype=np.float32)
+    check(load().gemm_costmodel_features(M, N, K, _mode(mode), int(config_id),
+                                         int(sms if sms else 152), out.ctypes.data))
+    return out
+
+
+def costmodel_train(timings_path: str, epochs: int = 2000, seed: int = 0,
+                    out_model: str | None = None) -> float:
+    loss = ctypes.c_float()
+    check(load().gemm_costmodel_train(timings_path.encode(), int(epochs), int(seed),
+                                      out_model.encode() if out_model else None,
+                                      ctypes.byref(loss)))
+    return loss.value
+
+
+def costmodel_load(path: str):
+    check(load().gemm_costmodel_load(path.encode()))
+
+
+def costmodel_predict(M, N, K, mode="bf16x3"):
+    cid, ms = ctypes.c_int(), ctypes.c_float()
+    check(load().gemm_costmodel_predict(M, N, K, _mode(mode), ctypes.byref(cid), ctypes.byref(ms)))
+    return cid.value, ms.value
+
+
+def mlp_loss_grad(theta, X, t):
+    """GPU loss and gradient of the cost model's MLP (float32 numpy in/out)."""
+    import numpy as np
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    grad = np.zeros_like(theta)
+    loss = ctypes.c_float()
+    check(load().gemm_mlp_loss_grad(X.shape[0], theta.ctypes.data, X.ctypes.data, t.ctypes.data,
+                                    ctypes.byref(loss), grad.ctypes.data))
+    return loss.value, grad
+
+
+def mlp_adam_step(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    import numpy as np
+    theta = np.array(theta, dtype=np.float32)
+    m = np.array(m, dtype=np.float32)
+    v = np.array(v, dtype=np.float32)
+    grad = np.ascontiguousarray(grad, dtype=np.float32)
+    check(load().gemm_mlp_adam_step(theta.size, theta.ctypes.data, grad.ctypes.data, m.ctypes.data,
+                                    v.ctypes.data, int(step), lr, beta1, beta2, eps))
+    return theta, m, v

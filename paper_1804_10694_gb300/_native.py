@@ -49,6 +49,24 @@ SIGNATURES = {
     "gemm_device_sm_count": (i32, []),
     "gemm_split_pack": (i32, [i32, i32, i64, i64, vp, i64, vp, i64, vp, vp]),
     "gemm_f32_bf16x3_noalloc": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
+    "gemm_grouped_plan_create": (i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(vp)]),
+    "gemm_grouped_plan_create_config": (i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, i32,
+                                              ctypes.POINTER(vp)]),
+    "gemm_grouped_execute": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "gemm_grouped_execute_eager": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+    "gemm_grouped_plan_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]),
+    "gemm_grouped_plan_destroy": (i32, [vp]),
+    "gemm_autotune": (i32, [vp, i32, i32, i32, cp]),
+    "gemm_autotune_load": (i32, [cp]),
+    "gemm_autotune_best": (i32, [i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(f32)]),
+    "gemm_costmodel_feature_count": (i32, []),
+    "gemm_costmodel_features": (i32, [i64, i64, i64, i32, i32, i32, vp]),
+    "gemm_costmodel_train": (i32, [cp, i32, u64, cp, ctypes.POINTER(f32)]),
+    "gemm_costmodel_load": (i32, [cp]),
+    "gemm_costmodel_predict": (i32, [i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(f32)]),
+    "gemm_mlp_loss_grad": (i32, [i32, vp, vp, vp, ctypes.POINTER(f32), vp]),
+    "gemm_mlp_adam_step": (i32, [i32, vp, vp, vp, vp, i32, f32, f32, f32, f32]),
 }
 
 

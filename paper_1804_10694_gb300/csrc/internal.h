@@ -49,6 +49,9 @@ struct TcLaunch {
 
 // Returns the dynamic shared memory a tensor-core kernel variant needs.
 int tc_smem_bytes(int bn, Prec prec);
+// Raise the shared-memory limit of a tile-width/precision variant on the
+// current device (call outside stream capture; idempotent).
+cudaError_t tc_prepare(int bn, Prec prec);
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s);
 // C = sum_s partial[s] + beta * C over the split-K partial sums (alpha is
@@ -76,9 +79,45 @@ cudaError_t split_cols_launch(Prec p, const float* X, int64_t K, int64_t N, int6
                               const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s);
 
 // ------------------------------------------------------------ grouped
-struct GroupedProblem;   // defined in grouped.cu / runtime
+// Static description of one problem of a grouped gemm, device resident
+// (written once when the plan is created).  The tensor maps come first: a
+// tensor map in global memory must be 64-byte aligned.
+struct alignas(128) GroupedProblem {
+  CUtensorMap tmA;          // hi/lo planes of A
+  CUtensorMap tmB;          // hi/lo planes of B (transposed)
+  void* planesA;
+  void* planesB;
+  unsigned* amaxA;
+  unsigned* amaxB;
+  int64_t pitch, lda, ldb, ldc;
+  int M, N, K, chunks, tiles_m, tiles_n;
+};
 
-// --------------------------------------------------------------- MLP
-// (declared in mlp.cu users through runtime.cpp)
+// Per-execution values of one problem (rewritten when they change).
+struct GroupedPtrs {
+  const float* A;
+  const float* B;
+  float* C;
+  float alpha, beta;
+  int c_vec4;
+  int pad;
+};
+
+struct GroupedArgs {
+  const GroupedProblem* probs;
+  const GroupedPtrs* ptrs;
+  const int* tile_prefix;   // G + 1 entries: first output tile of each problem
+  int G, num_units, kb, group_m;
+  int* err;
+};
+
+cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s);
+int grouped_absmax_items(int64_t M, int64_t N, int64_t K);
+int grouped_split_items(int64_t M, int64_t N, int64_t pitch);
+// Block maxima and hi/lo planes of every problem (two launches); the block
+// maxima must have been zeroed.
+cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const GroupedPtrs* ptrs,
+                                const int* absmax_prefix, int absmax_total, const int* split_prefix,
+                                int split_total, int G, int sms, cudaStream_t s);
 
 }  // namespace gb

@@ -162,6 +162,26 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
 
 // -------------------------------------------------------------------- plans
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
+                                 int64_t pitch, int box_rows);
+
+gemm_status device_err_word(int** out) {
+  DeviceState* d;
+  gemm_status st = device_state(&d, nullptr);
+  if (st != GEMM_OK) return st;
+  *out = d->err_word;
+  return GEMM_OK;
+}
+
+gemm_status encode_planes_map(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
+                              int64_t pitch, int box_rows) {
+  if (!g_encode) {
+    DeviceState* d;
+    gemm_status st = device_state(&d, nullptr);
+    if (st != GEMM_OK) return st;
+  }
+  return encode_planes(map, p, base, rows, K, pitch, box_rows);
+}
 
 static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
                                  int64_t pitch, int box_rows) {
@@ -216,7 +236,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   gemm_mode m;
   if ((st = resolve_mode(mode, *dev, &m)) != GEMM_OK) return st;
 
-  std::unique_ptr<gemm_plan_s> p(new gemm_plan_s());
+  std::unique_ptr<gemm_plan_s, void (*)(gemm_plan_t)> p(new gemm_plan_s(), plan_destroy_impl);
   p->M = M, p->N = N, p->K = K, p->lda = lda, p->ldb = ldb, p->ldc = ldc;
   p->mode = m;
   p->device = devidx;
@@ -293,6 +313,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->launch.bn = bn;
   p->launch.prec = pr;
   p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
+  if ((e = tc_prepare(bn, pr)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
   *out = p.release();
   return GEMM_OK;
 }

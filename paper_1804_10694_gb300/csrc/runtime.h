@@ -55,4 +55,26 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
                               float* C, cudaStream_t s);
 void plan_destroy_impl(gemm_plan_t p);
 
+// The current device's kernel error word (allocated on first use).
+gemm_status device_err_word(int** out);
+// 3-D tensor map over hi/lo planes [2][rows][pitch] with box {chunk, box_rows, 1}.
+gemm_status encode_planes_map(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
+                              int64_t pitch, int box_rows);
+
+// Grouped plans (grouped.cpp) and their tuning (autotune.cpp).
+gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const int64_t* K,
+                                const int64_t* lda, const int64_t* ldb, const int64_t* ldc,
+                                gemm_mode mode, int bn_override, int kb_override,
+                                gemm_grouped_plan_t* out);
+gemm_status grouped_execute_impl(gemm_grouped_plan_t p, const float* alpha, const float* const* A,
+                                 const float* const* B, const float* beta, float* const* C,
+                                 cudaStream_t s, bool use_graph);
+void grouped_destroy_impl(gemm_grouped_plan_t p);
+gemm_status grouped_tune_and_create(int G, const int64_t* M, const int64_t* N, const int64_t* K,
+                                    const int64_t* lda, const int64_t* ldb, const int64_t* ldc,
+                                    gemm_mode mode, gemm_grouped_plan_t* out);
+
+// Uniform[-1, 1) fill from a counter-based hash (timing inputs of the tuner).
+cudaError_t fill_uniform_launch(float* x, size_t n, uint64_t seed, cudaStream_t s);
+
 }  // namespace gb

@@ -49,34 +49,111 @@ struct TcCfg {
   static_assert(STAGES * STAGE + BAR_BYTES + 1024 <= 232448, "shared memory budget");
 };
 
-struct TileCoord {
-  int tm, tn, ks;
+// One unit of work of a CTA: an output tile (tm, tn) of problem `prob` and
+// the range [c0, c1) of 128-byte k-chunks it covers (all of K unless split).
+struct Work {
+  int prob, tm, tn, ks, c0, c1;
 };
 
-__device__ __forceinline__ TileCoord decode_unit(const TcArgs& a, int u) {
-  TileCoord c;
-  const int t = u % a.num_tiles;
-  c.ks = u / a.num_tiles;
-  const int group_tiles = a.group_m * a.tiles_n;
+// Per-problem values the epilogue needs.
+struct EpiView {
+  int M, N;
+  float* C;
+  int64_t ldc;
+  float alpha, beta;
+  const unsigned* amaxA;
+  const unsigned* amaxB;
+  float* partial;
+  int split_k;
+  int c_vec4;
+};
+
+__device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
+  const int group_tiles = group_m * tiles_n;
   const int g = t / group_tiles;
-  const int first_m = g * a.group_m;
-  const int rows_in_group = min(a.tiles_m - first_m, a.group_m);
+  const int first_m = g * group_m;
+  const int rows_in_group = min(tiles_m - first_m, group_m);
   const int r = t % group_tiles;
-  c.tm = first_m + r % rows_in_group;
-  c.tn = r / rows_in_group;
-  return c;
+  tm = first_m + r % rows_in_group;
+  tn = r / rows_in_group;
 }
 
-template <int BN, bool TF32>
-__global__ void __launch_bounds__(192, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const TcArgs a) {
+// Scheduling policy of one gemm: units are (split, tile) pairs.
+struct SingleSched {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  const TcArgs* a;
+  __device__ int units() const { return a->num_units; }
+  __device__ int kb() const { return a->kb; }
+  __device__ int* err() const { return a->err; }
+  __device__ Work work(int u) const {
+    Work w;
+    const int t = u % a->num_tiles;
+    w.prob = 0;
+    w.ks = u / a->num_tiles;
+    raster(t, a->tiles_m, a->tiles_n, a->group_m, w.tm, w.tn);
+    w.c0 = w.ks * a->chunks_per_split;
+    w.c1 = min(w.c0 + a->chunks_per_split, a->chunks_total);
+    return w;
+  }
+  __device__ const CUtensorMap* mapA(int) const { return tmA; }
+  __device__ const CUtensorMap* mapB(int) const { return tmB; }
+  __device__ EpiView epi(int) const {
+    EpiView v;
+    v.M = a->M, v.N = a->N, v.C = a->C, v.ldc = a->ldc, v.alpha = a->alpha, v.beta = a->beta;
+    v.amaxA = a->amaxA, v.amaxB = a->amaxB, v.partial = a->partial, v.split_k = a->split_k;
+    v.c_vec4 = a->c_vec4;
+    return v;
+  }
+};
+
+// Scheduling policy of a grouped launch: units are the tiles of all problems,
+// numbered problem after problem (problems ordered longest-K first on the
+// host); a unit finds its problem by binary search in the tile prefix sums.
+struct GroupedSched {
+  const GroupedArgs* a;
+  __device__ int units() const { return a->num_units; }
+  __device__ int kb() const { return a->kb; }
+  __device__ int* err() const { return a->err; }
+  __device__ Work work(int u) const {
+    int lo = 0, hi = a->G - 1;
+    while (lo < hi) {   // last g with tile_prefix[g] <= u
+      const int mid = (lo + hi + 1) >> 1;
+      if (a->tile_prefix[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    const GroupedProblem& p = a->probs[lo];
+    Work w;
+    w.prob = lo;
+    w.ks = 0;
+    raster(u - a->tile_prefix[lo], p.tiles_m, p.tiles_n, min(a->group_m, p.tiles_m), w.tm, w.tn);
+    w.c0 = 0;
+    w.c1 = p.chunks;
+    return w;
+  }
+  __device__ const CUtensorMap* mapA(int g) const { return &a->probs[g].tmA; }
+  __device__ const CUtensorMap* mapB(int g) const { return &a->probs[g].tmB; }
+  __device__ EpiView epi(int g) const {
+    const GroupedProblem& p = a->probs[g];
+    const GroupedPtrs& q = a->ptrs[g];
+    EpiView v;
+    v.M = p.M, v.N = p.N, v.C = q.C, v.ldc = p.ldc, v.alpha = q.alpha, v.beta = q.beta;
+    v.amaxA = p.amaxA, v.amaxB = p.amaxB, v.partial = nullptr, v.split_k = 1;
+    v.c_vec4 = q.c_vec4;
+    return v;
+  }
+};
+
+template <int BN, bool TF32, class Sched>
+__device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   using Cfg = TcCfg<BN, TF32>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
   uint8_t* smem = smem_raw + (sbase - raw);
+  int* const err = sc.err();
+  const int nunits = sc.units();
+  const int kb = sc.kb();
 
   // barrier block after the stage ring
   uint8_t* bar_area = smem + STAGES * Cfg::STAGE;
@@ -105,10 +182,6 @@ __global__ void __launch_bounds__(192, 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
-    tma_prefetch_desc(&tmA);
-    tma_prefetch_desc(&tmB);
-  }
   if (warp == 1) {
     tmem_alloc(smem_u32(tmem_slot), Cfg::TMEM_COLS);
     tmem_relinquish();
@@ -126,12 +199,18 @@ __global__ void __launch_bounds__(192, 1)
       bool issued[STAGES];
       for (int s = 0; s < STAGES; ++s) issued[s] = false, last_phase[s] = 0;
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
-        const TileCoord tc = decode_unit(a, u);
-        const int c0 = tc.ks * a.chunks_per_split;
-        const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
-        for (int c = c0; c < c1; ++c) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.err)) {
+      int last_prob = -1;
+      for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        const Work w = sc.work(u);
+        const CUtensorMap* mA = sc.mapA(w.prob);
+        const CUtensorMap* mB = sc.mapB(w.prob);
+        if (w.prob != last_prob) {
+          tma_prefetch_desc(mA);
+          tma_prefetch_desc(mB);
+          last_prob = w.prob;
+        }
+        for (int c = w.c0; c < w.c1; ++c) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, err)) {
             ok = false;
             break;
           }
@@ -139,10 +218,10 @@ __global__ void __launch_bounds__(192, 1)
           mbar_arrive_expect_tx(fb, Cfg::STAGE);
           const uint32_t sA = sbase + stage * Cfg::STAGE;
           const int kx = c * Cfg::BK;
-          tma_load_3d(sA, &tmA, fb, kx, tc.tm * Cfg::BM, 0);
-          tma_load_3d(sA + Cfg::A_PLANE, &tmA, fb, kx, tc.tm * Cfg::BM, 1);
-          tma_load_3d(sA + 2 * Cfg::A_PLANE, &tmB, fb, kx, tc.tn * BN, 0);
-          tma_load_3d(sA + 2 * Cfg::A_PLANE + Cfg::B_PLANE, &tmB, fb, kx, tc.tn * BN, 1);
+          tma_load_3d(sA, mA, fb, kx, w.tm * Cfg::BM, 0);
+          tma_load_3d(sA + Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, 1);
+          tma_load_3d(sA + 2 * Cfg::A_PLANE, mB, fb, kx, w.tn * BN, 0);
+          tma_load_3d(sA + 2 * Cfg::A_PLANE + Cfg::B_PLANE, mB, fb, kx, w.tn * BN, 1);
           issued[stage] = true;
           last_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -164,20 +243,18 @@ __global__ void __launch_bounds__(192, 1)
       uint32_t stage = 0, phase = 0, ab = 0, aphase = 0;
       bool ok = true;
       bool any = false;
-      for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
-        const TileCoord tc = decode_unit(a, u);
-        const int c0 = tc.ks * a.chunks_per_split;
-        const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
-        for (int cb = c0; ok && cb < c1; cb += a.kb) {
-          const int ce = min(cb + a.kb, c1);
-          if (!mbar_wait(acce_bar(ab), aphase ^ 1u, abort_flag, a.err)) {
+      for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+        const Work w = sc.work(u);
+        for (int cb = w.c0; ok && cb < w.c1; cb += kb) {
+          const int ce = min(cb + kb, w.c1);
+          if (!mbar_wait(acce_bar(ab), aphase ^ 1u, abort_flag, err)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t d = tmem_base + ab * BN;
           for (int c = cb; c < ce; ++c) {
-            if (!mbar_wait(full_bar(stage), phase, abort_flag, a.err)) {
+            if (!mbar_wait(full_bar(stage), phase, abort_flag, err)) {
               ok = false;
               break;
             }
@@ -230,15 +307,13 @@ __global__ void __launch_bounds__(192, 1)
     const int row_in_tile = q * 32 + lane;
     uint32_t ab = 0, aphase = 0;
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < a.num_units; u += gridDim.x) {
-      const TileCoord tc = decode_unit(a, u);
-      const int c0 = tc.ks * a.chunks_per_split;
-      const int c1 = min(c0 + a.chunks_per_split, a.chunks_total);
+    for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+      const Work w = sc.work(u);
       float S[BN];
       int blk = 0;
-      for (int cb = c0; cb < c1; cb += a.kb, ++blk) {
+      for (int cb = w.c0; cb < w.c1; cb += kb, ++blk) {
         // the whole warp must agree before the warp-collective TMEM loads
-        const bool waited = mbar_wait(accf_bar(ab), aphase, abort_flag, a.err);
+        const bool waited = mbar_wait(accf_bar(ab), aphase, abort_flag, err);
         if (!__all_sync(0xffffffffu, waited)) {
           ok = false;
           break;
@@ -264,16 +339,23 @@ __global__ void __launch_bounds__(192, 1)
         if (ab == 0) aphase ^= 1u;
       }
       if (!ok) break;
+      const EpiView v = sc.epi(w.prob);
+      if (blk == 0 || v.alpha == 0.0f) {
+        // K == 0 or alpha == 0 (grouped problems only): C = beta * C; the
+        // planes of such a problem are not packed, so their TMEM sum is unused
+#pragma unroll
+        for (int i = 0; i < BN; ++i) S[i] = 0.0f;
+      }
 
       // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
       // applied before the power of two, so that a result in range is not
       // lost to an overflow of the unscaled sum (the power of two is exact).
-      const int row = tc.tm * 128 + row_in_tile;
-      const int col0 = tc.tn * BN;
-      const int e = block_exponent(a.amaxA[tc.tm]) + block_exponent(a.amaxB[col0 / kScaleBlock]);
-      float alpha = a.alpha;
-      const float beta = a.beta;
-      if (a.split_k > 1) {
+      const int row = w.tm * 128 + row_in_tile;
+      const int col0 = w.tn * BN;
+      const int e = block_exponent(v.amaxA[w.tm]) + block_exponent(v.amaxB[col0 / kScaleBlock]);
+      float alpha = v.alpha;
+      const float beta = v.beta;
+      if (v.split_k > 1) {
         // split-K partials carry alpha already (the reduction adds beta*C)
 #pragma unroll
         for (int i = 0; i < BN; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
@@ -282,16 +364,16 @@ __global__ void __launch_bounds__(192, 1)
         for (int i = 0; i < BN; ++i) S[i] = scale_pow2(alpha * S[i], e);
         alpha = 1.0f;
       }
-      if (row >= a.M) continue;
-      if (a.split_k > 1) {
-        float* prow = a.partial + (static_cast<int64_t>(tc.ks) * a.M + row) * a.N;
+      if (row >= v.M) continue;
+      if (v.split_k > 1) {
+        float* prow = v.partial + (static_cast<int64_t>(w.ks) * v.M + row) * v.N;
 #pragma unroll
         for (int i = 0; i < BN; ++i)
-          if (col0 + i < a.N) prow[col0 + i] = S[i];
+          if (col0 + i < v.N) prow[col0 + i] = S[i];
         continue;
       }
-      float* crow = a.C + static_cast<int64_t>(row) * a.ldc;
-      if (a.c_vec4 && col0 + BN <= a.N) {
+      float* crow = v.C + static_cast<int64_t>(row) * v.ldc;
+      if (v.c_vec4 && col0 + BN <= v.N) {
         float4* c4 = reinterpret_cast<float4*>(crow + col0);
 #pragma unroll
         for (int i = 0; i < BN / 4; ++i) {
@@ -314,9 +396,9 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int i = 0; i < BN; ++i) {
           const int col = col0 + i;
-          if (col < a.N) {
-            const float v = beta != 0.0f ? fmaf(alpha, S[i], beta * crow[col]) : alpha * S[i];
-            crow[col] = v;
+          if (col < v.N) {
+            const float val = beta != 0.0f ? fmaf(alpha, S[i], beta * crow[col]) : alpha * S[i];
+            crow[col] = val;
           }
         }
       }
@@ -329,6 +411,20 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
   }
+}
+
+template <int BN, bool TF32>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs a) {
+  SingleSched sc{&tmA, &tmB, &a};
+  tc_gemm_body<BN, TF32>(sc);
+}
+
+template <int BN, bool TF32>
+__global__ void __launch_bounds__(192, 1) tc_grouped_kernel(const GroupedArgs a) {
+  GroupedSched sc{&a};
+  tc_gemm_body<BN, TF32>(sc);
 }
 
 // Split-K fix-up: C = sum_s partial[s] + beta * C, where each partial already
@@ -353,19 +449,45 @@ int tc_smem_bytes(int bn, Prec prec) {
   return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
 }
 
+// The dynamic shared memory limit of every kernel variant is raised once per
+// device and thread, outside any stream capture: plans call tc_prepare when
+// they are created, launches call it again (a no-op after the first time).
+template <int BN, bool TF32>
+static cudaError_t prepare_variant() {
+  using Cfg = TcCfg<BN, TF32>;
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured_device != dev) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg::SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    configured_device = dev;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_prepare(int bn, Prec prec) {
+  if (prec == Prec::TF32) {
+    if (bn == 64) return prepare_variant<64, true>();
+    if (bn == 128) return prepare_variant<128, true>();
+  } else {
+    if (bn == 64) return prepare_variant<64, false>();
+    if (bn == 128) return prepare_variant<128, false>();
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <int BN, bool TF32>
 static cudaError_t launch_variant(int grid, const CUtensorMap& tmA, const CUtensorMap& tmB,
                                   const TcArgs& a, cudaStream_t s) {
   using Cfg = TcCfg<BN, TF32>;
-  static thread_local int configured_device = -1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured_device != dev) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    if (e != cudaSuccess) return e;
-    configured_device = dev;
-  }
+  cudaError_t e = prepare_variant<BN, TF32>();
+  if (e != cudaSuccess) return e;
   tc_gemm_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
   return cudaGetLastError();
 }
@@ -378,6 +500,26 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   } else {
     if (l.bn == 64) return launch_variant<64, false>(l.grid, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, false>(l.grid, tmA, tmB, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int BN, bool TF32>
+static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaStream_t s) {
+  using Cfg = TcCfg<BN, TF32>;
+  cudaError_t e = prepare_variant<BN, TF32>();
+  if (e != cudaSuccess) return e;
+  tc_grouped_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s) {
+  if (prec == Prec::TF32) {
+    if (bn == 64) return launch_grouped_variant<64, true>(grid, a, s);
+    if (bn == 128) return launch_grouped_variant<128, true>(grid, a, s);
+  } else {
+    if (bn == 64) return launch_grouped_variant<64, false>(grid, a, s);
+    if (bn == 128) return launch_grouped_variant<128, false>(grid, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,31 @@
+// Shared declarations of the autotuner and the cost model.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/gemm.h"
+#include "internal.h"
+
+namespace gb {
+
+// A candidate configuration as it behaves on one shape.
+struct EffConfig {
+  int bn, split_k, chunks_per_split, kb, group_m;
+  int64_t tiles;
+};
+
+EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, int64_t K);
+// Candidate ids with pairwise different effective configurations on the shape.
+std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t K);
+bool table_lookup(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);
+// Cost-model argmin over the distinct configurations (GEMM_ERR_INVALID_ARG
+// when no model is loaded).
+gemm_status costmodel_pick(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);
+
+constexpr int kFeatures = 14;
+constexpr int kHidden = 64;
+// Input features of the cost model for a (shape, configuration) pair.
+void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const gemm_config& c,
+                        int sms, float* out);
+
+}  // namespace gb

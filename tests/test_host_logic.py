@@ -1,0 +1,112 @@
+"""CPU checks of host-side logic: cost-model features against the oracle's
+restatement, model/table file parsing and error handling, grouped-plan
+argument validation (no device is touched)."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import paper_1804_10694_gb300 as pkg
+from oracle import features as ofeat
+import workloads as W
+
+
+SHAPES = [(8192, 8192, 8192), (1060, 1060, 1060), (50176, 64, 576), (12544, 128, 1152),
+          (3136, 256, 2304), (33, 17, 5), (1, 1, 1), (129, 4099, 63), (300, 70, 20000)]
+
+
+@pytest.mark.parametrize("mode,tf32", [("bf16x3", False), ("tf32x3", True)])
+def test_features_match_oracle_restatement(mode, tf32):
+    n = pkg.config_count(mode)
+    assert pkg.costmodel_feature_count() == 14
+    for (M, N, K) in SHAPES:
+        for cid in range(0, n, 5):
+            cfg = pkg.config_get(mode, cid)
+            for sms in (152, 148):
+                got = pkg.costmodel_features(M, N, K, mode, cid, sms)
+                ref = np.array(ofeat.features(M, N, K, cfg, tf32, sms))
+                assert np.allclose(got, ref, rtol=1e-5, atol=1e-5), (M, N, K, cfg, got, ref)
+
+
+def test_features_reject_bad_arguments():
+    lib = pkg.load()
+    out = np.zeros(14, np.float32)
+    assert lib.gemm_costmodel_features(0, 4, 4, 2, 0, 152, out.ctypes.data) == 1
+    assert lib.gemm_costmodel_features(4, 4, 4, 1, 0, 152, out.ctypes.data) == 1   # SIMT
+    assert lib.gemm_costmodel_features(4, 4, 4, 2, 10 ** 6, 152, out.ctypes.data) == 1
+
+
+def test_costmodel_load_rejects_missing_and_corrupt_files(tmp_path):
+    lib = pkg.load()
+    assert lib.gemm_costmodel_load(str(tmp_path / "missing.txt").encode()) == 7
+    bad = tmp_path / "bad.txt"
+    bad.write_text("gb300-gemm-costmodel 1\nfeatures 14 hidden 64 params 5\n")
+    assert lib.gemm_costmodel_load(str(bad).encode()) == 7
+    assert b"malformed" in lib.gemm_last_error()
+    bad.write_text("not a model\n")
+    assert lib.gemm_costmodel_load(str(bad).encode()) == 7
+    # truncated theta
+    P = 64 * 14 + 64 + 64 * 64 + 64 + 64 + 1
+    txt = ("gb300-gemm-costmodel 1\nfeatures 14 hidden 64 params %d\nmean %s\nstd %s\n"
+           "target 0 1\ntheta %s\n" % (P, " ".join(["0"] * 14), " ".join(["1"] * 14),
+                                       " ".join(["0.5"] * (P - 3))))
+    bad.write_text(txt)
+    assert lib.gemm_costmodel_load(str(bad).encode()) == 7
+
+
+def test_costmodel_load_accepts_well_formed_file(tmp_path):
+    P = 64 * 14 + 64 + 64 * 64 + 64 + 64 + 1
+    good = tmp_path / "good.txt"
+    good.write_text("gb300-gemm-costmodel 1\nfeatures 14 hidden 64 params %d\nmean %s\nstd %s\n"
+                    "target -1.5 2\ntheta %s\n" % (P, " ".join(["0"] * 14), " ".join(["1"] * 14),
+                                                   " ".join(["0.01"] * P)))
+    assert pkg.load().gemm_costmodel_load(str(good).encode()) == 0
+
+
+def test_autotune_table_file_parsing(tmp_path):
+    lib = pkg.load()
+    assert lib.gemm_autotune_load(str(tmp_path / "none.csv").encode()) == 7
+    f = tmp_path / "t.csv"
+    f.write_text("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m\n"
+                 "777,555,333,2,3,0.5,128,1,2,1\n777,555,333,2,7,0.25,128,2,2,1\n"
+                 "777,555,333,2,99999,0.01,0,0,0,0\ngarbage line\n")
+    assert lib.gemm_autotune_load(str(f).encode()) == 0
+    assert pkg.autotune_best(777, 555, 333, "bf16x3") == (7, 0.25)
+    with pytest.raises(pkg.GemmError):
+        pkg.autotune_best(777, 555, 334, "bf16x3")
+
+
+def test_grouped_plan_argument_validation():
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    a = (ctypes.c_int64 * 2)(4, 4)
+    neg = (ctypes.c_int64 * 2)(4, -1)
+    small_ld = (ctypes.c_int64 * 2)(4, 3)
+    assert lib.gemm_grouped_plan_create(2, neg, a, a, a, a, a, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_grouped_plan_create(2, a, a, a, small_ld, a, a, 2, 0, ctypes.byref(h)) == 1
+    assert b"problem 1" in lib.gemm_last_error()
+    assert lib.gemm_grouped_plan_create(-1, a, a, a, a, a, a, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_grouped_plan_create(2, None, a, a, a, a, a, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_grouped_plan_create_config(2, a, a, a, a, a, a, 2, 96, 4, ctypes.byref(h)) == 1
+    assert lib.gemm_grouped_plan_create_config(2, a, a, a, a, a, a, 2, 128, 9, ctypes.byref(h)) == 1
+    assert lib.gemm_grouped_execute(None, None, None, None, None, None, None) == 1
+
+
+def test_grouped_workload_shapes():
+    shapes = W.grouped_shapes()
+    assert len(shapes) == 512
+    arr = np.array(shapes)
+    assert arr.min() >= 32 and arr.max() <= 1024
+    # log-uniform: the median of each dimension is near sqrt(32 * 1024) = 181
+    assert 120 < np.median(arr[:, 0]) < 260
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    assert 5e9 < flops < 6e10
+
+
+def test_training_shapes_bounded():
+    shapes = W.training_shapes(200, seed=7)
+    assert len(shapes) == 200
+    for m, n, k in shapes:
+        assert m * n * k <= 2 ** 37
+        assert min(m, n, k) >= 1

@@ -112,17 +112,20 @@ def grouped_shapes(count: int = 512, seed: int = 4000, lo: int = 32,
 
 
 def training_shapes(count: int, seed: int, lo: int = 32, hi: int = 65536,
-                    max_mnk_log2: float = 37.0) -> list[tuple[int, int, int]]:
+                    max_mnk_log2: float = 37.0,
+                    max_elems: int = 2 ** 27) -> list[tuple[int, int, int]]:
     """Shapes for autotuner timing runs: log-uniform M, N, K in [lo, hi] with
-    M*N*K <= 2**max_mnk_log2 (rejection sampled), plus conv-like skinny shapes
-    (large M, N in {32..512}, K = 9 * channels)."""
+    M*N*K <= 2**max_mnk_log2 and every operand at most max_elems elements
+    (rejection sampled), plus conv-like skinny shapes (large M, N in
+    {16..512}, K = 9 * channels)."""
     g = _rng(seed)
     out: list[tuple[int, int, int]] = []
     n_skinny = count // 5
     while len(out) < count - n_skinny:
-        m, n, k = np.rint(np.exp(g.uniform(math.log(lo), math.log(hi), size=3))).astype(np.int64)
-        if math.log2(float(m) * float(n) * float(k)) <= max_mnk_log2:
-            out.append((int(m), int(n), int(k)))
+        m, n, k = (int(x) for x in np.rint(np.exp(g.uniform(math.log(lo), math.log(hi), size=3))))
+        if (math.log2(float(m) * float(n) * float(k)) <= max_mnk_log2
+                and max(m * k, k * n, m * n) <= max_elems):
+            out.append((m, n, k))
     chans = (16, 32, 64, 128, 256, 512)
     while len(out) < count:
         cin = int(g.choice(chans))
@@ -130,6 +133,6 @@ def training_shapes(count: int, seed: int, lo: int = 32, hi: int = 65536,
         side = int(g.choice((7, 14, 28, 56, 112, 224)))
         m = side * side * int(g.choice((1, 2, 4)))
         k = 9 * cin
-        if math.log2(float(m) * cout * k) <= max_mnk_log2:
+        if math.log2(float(m) * cout * k) <= max_mnk_log2 and m * k <= max_elems:
             out.append((m, cout, k))
     return out
