@@ -52,6 +52,10 @@ def parse_args():
                    help="M = N = K (profiling cases only; the reported workload is 8192)")
     p.add_argument("--kernel-only", action="store_true",
                    help="only warm-up and timed plan executions (for ncu captures)")
+    p.add_argument("--no-other-workloads", action="store_true",
+                   help="skip the secondary measurements of the other workloads")
+    p.add_argument("--costmodel", default=os.path.join(ROOT, "paper_1804_10694_gb300", "data",
+                                                       "costmodel_gb300.txt"))
     return p.parse_args()
 
 
@@ -191,6 +195,106 @@ def traffic_per_launch():
     return d.get("dram_bytes_per_launch_full_size")
 
 
+def _median_ms(fn, reps, stream):
+    import torch
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def other_workloads(model_path: str | None):
+    """Secondary measurements on the other workloads (outside the timed
+    region; device-filled uniform[-1, 1] data, median of CUDA-event timings):
+    the square sweep in all three modes, the conv-as-gemm shapes with the
+    heuristic, the cost model's pick and the exhaustive best, and the
+    512-problem grouped gemm replayed from its CUDA graph."""
+    import torch
+    import paper_1804_10694_gb300 as pkg
+    import workloads as W
+    stream = torch.cuda.current_stream()
+    out = {"sweep": {}, "conv": {}, "grouped": None}
+    for n in W.SQUARE_SWEEP:
+        A = torch.empty(n, n, device="cuda").uniform_(-1, 1)
+        B = torch.empty(n, n, device="cuda").uniform_(-1, 1)
+        C = torch.empty(n, n, device="cuda").uniform_(-1, 1)
+        row = {}
+        for mode in ("bf16x3", "tf32x3", "simt"):
+            plan = pkg.Plan(n, n, n, mode=mode)
+            for _ in range(2):
+                plan.execute(A, B, C, 1.5, 0.5)
+            ms = _median_ms(lambda: plan.execute(A, B, C, 1.5, 0.5), 5 if n >= 4096 else 20, stream)
+            row[mode] = round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 2)
+            plan.destroy()
+        out["sweep"][str(n)] = row
+        del A, B, C
+    if model_path and os.path.exists(model_path):
+        pkg.costmodel_load(model_path)
+    for (M, N, K) in W.CONV_SHAPES:
+        A = torch.empty(M, K, device="cuda").uniform_(-1, 1)
+        B = torch.empty(K, N, device="cuda").uniform_(-1, 1)
+        C = torch.empty(M, N, device="cuda")
+        flops = 2.0 * M * N * K
+        res = {}
+        picks = {"heuristic": pkg.config_default("bf16x3", M, N, K)}
+        try:
+            picks["model"] = pkg.costmodel_predict(M, N, K, "bf16x3")[0]
+        except pkg.GemmError:
+            pass
+        pkg.autotune([(M, N, K)], mode="bf16x3", reps=5)
+        picks["exhaustive"] = pkg.autotune_best(M, N, K, "bf16x3")[0]
+        for name, cid in picks.items():
+            plan = pkg.Plan(M, N, K, mode="bf16x3", config_id=cid)
+            for _ in range(2):
+                plan.execute(A, B, C, 1.0, 0.0)
+            ms = _median_ms(lambda: plan.execute(A, B, C, 1.0, 0.0), 20, stream)
+            res[name] = {"tflops": round(flops / (ms * 1e-3) / 1e12, 2), "ms": round(ms, 4),
+                         "config": pkg.config_get("bf16x3", cid),
+                         "hbm_gbs": round(4.0 * (M * K + K * N + M * N) / (ms * 1e-3) / 1e9, 1)}
+            plan.destroy()
+        simt = pkg.Plan(M, N, K, mode="simt")
+        ms = _median_ms(lambda: simt.execute(A, B, C, 1.0, 0.0), 10, stream)
+        res["simt"] = {"tflops": round(flops / (ms * 1e-3) / 1e12, 2), "ms": round(ms, 4)}
+        simt.destroy()
+        out["conv"][f"{M}x{N}x{K}"] = res
+        del A, B, C
+    shapes = W.grouped_shapes()
+    As = [torch.empty(m, k, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
+    Bs = [torch.empty(k, n, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
+    Cs = [torch.empty(m, n, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
+    ones = [1.0] * len(shapes)
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    nbytes = sum(4.0 * (m * k + k * n + 2 * m * n) for m, n, k in shapes)
+    grouped = {}
+    for sel in ("default", "exhaustive"):
+        gp = pkg.GroupedPlan(shapes, mode="bf16x3", select=sel)
+        for _ in range(3):
+            gp.execute(As, Bs, Cs, ones, ones)          # first call captures the graph
+        ms = _median_ms(lambda: gp.execute(As, Bs, Cs, ones, ones), 20, stream)
+        grouped[sel] = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+                        "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), **gp.info()}
+        gp.destroy()
+    loop = {}
+    plans = [pkg.Plan(m, n, k, mode="bf16x3") for m, n, k in shapes]
+
+    def per_problem():
+        for p_, a_, b_, c_ in zip(plans, As, Bs, Cs):
+            p_.execute(a_, b_, c_, 1.0, 1.0)
+    per_problem()
+    ms = _median_ms(per_problem, 5, stream)
+    loop = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2)}
+    for p_ in plans:
+        p_.destroy()
+    out["grouped"] = {"problems": len(shapes), "gflop": round(flops / 1e9, 2),
+                      "graph_replay": grouped, "one_plan_per_problem_loop": loop}
+    return out
+
+
 def cpu_baseline(A, B, C0, target_s: float = 12.0, max_rows: int = 4096):
     """The FP64 oracle as it stands on the host cores: sampled rows of the
     same product, grown until about target_s seconds of CPU work."""
@@ -319,6 +423,10 @@ def run_ours(args, world, rank, local):
            "ms_per_step": round(e2e_s * 1e3, 3),
            "api": "gemm_f32_host (pinned host A, B, C; H2D + gemm + D2H + stream sync per call)"}
 
+    others = None
+    if rank == 0 and not args.no_other_workloads and args.mode == "bf16x3":
+        others = other_workloads(args.costmodel)
+
     base = None
     rel = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -348,6 +456,7 @@ def run_ours(args, world, rank, local):
         "simt_tflops": round(simt, 2) if simt else None,
         "speedup_vs_simt": round(value / world / simt, 2) if simt else None,
         "rel_frob_sampled": rel,
+        "other_workloads": others,
     }
     print(json.dumps(out), flush=True)
 

@@ -266,6 +266,13 @@ const char* gemm_last_error(void);
  * device. */
 gemm_status gemm_device_error(void);
 
+/* Self-test of failure detection: launches one kernel whose pipeline wait can
+ * never complete (an mbarrier nothing arrives on) and checks that the bounded
+ * wait gives up after its limit (about 2 s), that the kernel returns, and that
+ * the error is reported.  Returns GEMM_ERR_TIMEOUT (the expected outcome) and
+ * leaves the device error word cleared; anything else is a failure. */
+gemm_status gemm_selftest_wait_timeout(void);
+
 /* Number of streaming multiprocessors of the current device. */
 int gemm_device_sm_count(void);
 

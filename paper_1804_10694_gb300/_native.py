@@ -47,6 +47,7 @@ SIGNATURES = {
     "gemm_last_error": (cp, []),
     "gemm_device_error": (i32, []),
     "gemm_device_sm_count": (i32, []),
+    "gemm_selftest_wait_timeout": (i32, []),
     "gemm_split_pack": (i32, [i32, i32, i64, i64, vp, i64, vp, i64, vp, vp]),
     "gemm_f32_bf16x3_noalloc": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, vp]),
     "gemm_grouped_plan_create": (i32, [i32, vp, vp, vp, vp, vp, vp, i32, i32, ctypes.POINTER(vp)]),

@@ -269,9 +269,11 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     g.amaxA = p->d_amax + amax_off[slot];
     g.amaxB = g.amaxA + (p->M[i] + kScaleBlock - 1) / kScaleBlock + 1;
     const int64_t Ki = std::max<int64_t>(p->K[i], 1);
-    if ((st = encode_planes_map(&g.tmA, pr, g.planesA, std::max<int64_t>(p->M[i], 1), Ki, g.pitch, 128)) != GEMM_OK)
+    if ((st = encode_planes_map(&g.tmA, pr, g.planesA, std::max<int64_t>(p->M[i], 1), Ki, g.pitch, 128,
+                                128)) != GEMM_OK)
       return st;
-    if ((st = encode_planes_map(&g.tmB, pr, g.planesB, std::max<int64_t>(p->N[i], 1), Ki, g.pitch, p->bn)) != GEMM_OK)
+    if ((st = encode_planes_map(&g.tmB, pr, g.planesB, std::max<int64_t>(p->N[i], 1), Ki, g.pitch,
+                                p->bn, 128)) != GEMM_OK)
       return st;
   }
   if ((e = tc_prepare(p->bn, pr)) != cudaSuccess) return cuda_fail(e, "kernel attribute");

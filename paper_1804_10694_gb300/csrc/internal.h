@@ -42,13 +42,16 @@ struct TcArgs {
 };
 
 struct TcLaunch {
-  int bn;          // tile N (64 or 128)
+  int bn;          // tile N (64, 128 or 256)
   Prec prec;       // BF16 or TF32
   int grid;
 };
 
 // Returns the dynamic shared memory a tensor-core kernel variant needs.
 int tc_smem_bytes(int bn, Prec prec);
+// Bytes of one row per k-chunk of the kernel variant with tile width bn (the
+// swizzle width of its operand tiles: 128, or 64 for bn = 256).
+int tc_chunk_bytes(int bn);
 // Raise the shared-memory limit of a tile-width/precision variant on the
 // current device (call outside stream capture; idempotent).
 cudaError_t tc_prepare(int bn, Prec prec);

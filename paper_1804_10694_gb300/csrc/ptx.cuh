@@ -180,6 +180,24 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for the 64-byte swizzle: rows of 64 bytes, 8-row atoms of 512
+// bytes (stride-dimension offset 512), swizzle mode 4.
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(512 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(4) << 61;
+  return d;
+}
+
+template <int SW>
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
+  static_assert(SW == 128 || SW == 64, "swizzle width");
+  return SW == 128 ? sdesc_k_sw128(saddr) : sdesc_k_sw64(saddr);
+}
+
 // Instruction descriptor for kind::f16 (bf16 operands) / kind::tf32 with FP32
 // accumulation, dense, both operands K-major.
 //   bits 4-5 D format (1 = F32); bits 7-9 / 10-12 A / B format (1 = BF16, 2 = TF32)

@@ -104,17 +104,17 @@ constexpr int kMaxFoldChunks = 8;
 static const std::vector<gemm_config>& config_table() {
   static const std::vector<gemm_config> table = [] {
     std::vector<gemm_config> t;
-    const int bns[] = {128, 64};
     const int splits[] = {1, 2, 3, 4, 6, 8};
     const int kbs[] = {4, 2, 8};
     const int groups[] = {16, 1};
-    for (int bn : bns)
+    // tile widths in the order they were added (ids of earlier entries stay fixed)
+    for (int bn : {128, 64, 256})
       for (int sk : splits)
         for (int kb : kbs)
           for (int g : groups) {
             gemm_config c;
             c.block_n = bn;
-            c.stages = bn == 64 ? 4 : 3;
+            c.stages = bn == 128 ? 3 : 4;
             c.split_k = sk;
             c.kb = kb;
             c.group_m = g;
@@ -163,7 +163,7 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
 // -------------------------------------------------------------------- plans
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
-                                 int64_t pitch, int box_rows);
+                                 int64_t pitch, int box_rows, int sw);
 
 gemm_status device_err_word(int** out) {
   DeviceState* d;
@@ -174,27 +174,28 @@ gemm_status device_err_word(int** out) {
 }
 
 gemm_status encode_planes_map(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
-                              int64_t pitch, int box_rows) {
+                              int64_t pitch, int box_rows, int sw) {
   if (!g_encode) {
     DeviceState* d;
     gemm_status st = device_state(&d, nullptr);
     if (st != GEMM_OK) return st;
   }
-  return encode_planes(map, p, base, rows, K, pitch, box_rows);
+  return encode_planes(map, p, base, rows, K, pitch, box_rows, sw);
 }
 
 static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
-                                 int64_t pitch, int box_rows) {
+                                 int64_t pitch, int box_rows, int sw) {
   const int es = prec_elem_bytes(p);
+  // the box is one k-chunk wide: sw bytes, the swizzle span of the kernel variant
   cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 2};
   cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(rows * pitch * es)};
-  cuuint32_t box[3] = {(cuuint32_t)prec_chunk_elems(p), (cuuint32_t)box_rows, 1};
+  cuuint32_t box[3] = {(cuuint32_t)(sw / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dt =
       p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = g_encode(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) rows=%lld K=%lld pitch=%lld",
                 (int)r, (long long)rows, (long long)K, (long long)pitch);
@@ -259,11 +260,17 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   const Prec pr = p->prec;
   const int es = prec_elem_bytes(pr);
   p->pitch = packed_k_pitch(pr, K);
+  // split-K and the fold length are defined in 128-byte k-chunks; the kernel
+  // variant may step in narrower chunks (sw bytes), ratio kc of them per 128
   const int64_t chunks = (K + prec_chunk_elems(pr) - 1) / prec_chunk_elems(pr);
   int sk = std::max(1, std::min<int>(p->cfg.split_k, (int)chunks));
   const int64_t per = (chunks + sk - 1) / sk;
   sk = (int)((chunks + per - 1) / per);   // no empty split
   const int bn = p->cfg.block_n;
+  const int sw = tc_chunk_bytes(bn);
+  const int kc = 128 / sw;
+  const int64_t kchunk = sw / es;                       // elements per kernel chunk
+  const int64_t chunks_kernel = (K + kchunk - 1) / kchunk;
   const int64_t tiles_m = (M + 127) / 128, tiles_n = (N + bn - 1) / bn;
 
   // workspace: A planes | B planes | amax A | amax B | split-K partials
@@ -292,8 +299,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->amax_bytes = (nblkA + nblkB) * sizeof(unsigned);
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
-  if ((st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128)) != GEMM_OK) return st;
-  if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn)) != GEMM_OK) return st;
+  if ((st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK) return st;
+  if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn, sw)) != GEMM_OK) return st;
 
   TcArgs& a = p->args;
   a.M = (int)M, a.N = (int)N, a.K = (int)K;
@@ -301,9 +308,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.num_tiles = (int)(tiles_m * tiles_n);
   a.split_k = sk;
   a.num_units = a.num_tiles * sk;
-  a.chunks_total = (int)chunks;
-  a.chunks_per_split = (int)per;
-  a.kb = std::max(1, std::min(p->cfg.kb, kMaxFoldChunks));
+  a.chunks_total = (int)chunks_kernel;
+  a.chunks_per_split = (int)(per * kc);
+  a.kb = std::max(1, std::min(p->cfg.kb, kMaxFoldChunks)) * kc;
   a.group_m = std::max(1, std::min<int>(p->cfg.group_m, (int)tiles_m));
   a.ldc = ldc;
   a.amaxA = p->amaxA;

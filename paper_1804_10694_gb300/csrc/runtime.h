@@ -57,9 +57,10 @@ void plan_destroy_impl(gemm_plan_t p);
 
 // The current device's kernel error word (allocated on first use).
 gemm_status device_err_word(int** out);
-// 3-D tensor map over hi/lo planes [2][rows][pitch] with box {chunk, box_rows, 1}.
+// 3-D tensor map over hi/lo planes [2][rows][pitch] with box {sw bytes of K,
+// box_rows, 1} and the sw-byte swizzle (128 or 64).
 gemm_status encode_planes_map(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,
-                              int64_t pitch, int box_rows);
+                              int64_t pitch, int box_rows, int sw);
 
 // Grouped plans (grouped.cpp) and their tuning (autotune.cpp).
 gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const int64_t* K,

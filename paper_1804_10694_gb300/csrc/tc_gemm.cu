@@ -33,20 +33,29 @@
 
 namespace gb {
 
+// Tile and pipeline geometry of one kernel variant.  A k-chunk is one
+// swizzle span of every row: 128 bytes (BN 64 / 128) or 64 bytes (BN 256,
+// so that four stages of the wider B tile still fit in shared memory).
+// Tile width 256 uses two epilogue warpgroups, each folding and storing 128
+// of the columns, so that a thread's FP32 row fragment stays at 128 values.
 template <int BN, bool TF32>
 struct TcCfg {
   static constexpr int BM = 128;
-  static constexpr int ROW_BYTES = 128;                // one k-chunk of one row
-  static constexpr int A_PLANE = BM * ROW_BYTES;       // 16 KB
-  static constexpr int B_PLANE = BN * ROW_BYTES;
+  static constexpr int SW = BN == 256 ? 64 : 128;      // bytes of one row per k-chunk
+  static constexpr int A_PLANE = BM * SW;
+  static constexpr int B_PLANE = BN * SW;
   static constexpr int STAGE = 2 * A_PLANE + 2 * B_PLANE;
-  static constexpr int STAGES = BN == 64 ? 4 : 3;
-  static constexpr int BK = TF32 ? 32 : 64;            // elements per k-chunk
+  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
+  static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
+  static constexpr int EPI_WG = BN == 256 ? 2 : 1;     // epilogue warpgroups
+  static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int TMEM_COLS = 2 * BN;             // two accumulator buffers
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
-  static constexpr int THREADS = 192;
+  static constexpr int THREADS = 64 + 128 * EPI_WG;
   static_assert(STAGES * STAGE + BAR_BYTES + 1024 <= 232448, "shared memory budget");
+  static_assert(TMEM_COLS <= 512, "tensor memory budget");
 };
 
 // One unit of work of a CTA: an output tile (tm, tn) of problem `prob` and
@@ -176,7 +185,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf_bar(b), 1);
-      mbar_init(acce_bar(b), 128);
+      mbar_init(acce_bar(b), 128 * Cfg::EPI_WG);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
@@ -264,12 +273,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             const uint32_t sBhi = sAhi + 2 * Cfg::A_PLANE;
             const uint32_t sBlo = sBhi + Cfg::B_PLANE;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
+            for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
               const uint32_t off = kk * 32;   // 32 bytes = one MMA's K slice
-              const uint64_t dAhi = sdesc_k_sw128(sAhi + off);
-              const uint64_t dAlo = sdesc_k_sw128(sAlo + off);
-              const uint64_t dBhi = sdesc_k_sw128(sBhi + off);
-              const uint64_t dBlo = sdesc_k_sw128(sBlo + off);
+              const uint64_t dAhi = sdesc_k<Cfg::SW>(sAhi + off);
+              const uint64_t dAlo = sdesc_k<Cfg::SW>(sAlo + off);
+              const uint64_t dBhi = sdesc_k<Cfg::SW>(sBhi + off);
+              const uint64_t dBlo = sdesc_k<Cfg::SW>(sBlo + off);
               const uint32_t acc = (c > cb || kk > 0) ? 1u : 0u;
               if (TF32) {
                 umma_tf32(d, dAlo, dBhi, idesc, acc);
@@ -303,13 +312,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
+    constexpr int EC = Cfg::EPI_COLS;
     const int q = warp & 3;                 // TMEM lane quadrant of this warp
+    const int half = (warp - 2) >> 2;       // column group of this warpgroup
     const int row_in_tile = q * 32 + lane;
     uint32_t ab = 0, aphase = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       const Work w = sc.work(u);
-      float S[BN];
+      float S[EC];
       int blk = 0;
       for (int cb = w.c0; cb < w.c1; cb += kb, ++blk) {
         // the whole warp must agree before the warp-collective TMEM loads
@@ -319,9 +330,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * BN;
+        const uint32_t taddr =
+            tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * BN + half * EC;
 #pragma unroll
-        for (int j = 0; j < BN / 32; ++j) {
+        for (int j = 0; j < EC / 32; ++j) {
           uint32_t r[32];
           tmem_ld_32x32b_x32(taddr + j * 32, r);
           tmem_wait_ld();
@@ -344,39 +356,39 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         // K == 0 or alpha == 0 (grouped problems only): C = beta * C; the
         // planes of such a problem are not packed, so their TMEM sum is unused
 #pragma unroll
-        for (int i = 0; i < BN; ++i) S[i] = 0.0f;
+        for (int i = 0; i < EC; ++i) S[i] = 0.0f;
       }
 
       // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
       // applied before the power of two, so that a result in range is not
       // lost to an overflow of the unscaled sum (the power of two is exact).
       const int row = w.tm * 128 + row_in_tile;
-      const int col0 = w.tn * BN;
+      const int col0 = w.tn * BN + half * EC;
       const int e = block_exponent(v.amaxA[w.tm]) + block_exponent(v.amaxB[col0 / kScaleBlock]);
       float alpha = v.alpha;
       const float beta = v.beta;
       if (v.split_k > 1) {
         // split-K partials carry alpha already (the reduction adds beta*C)
 #pragma unroll
-        for (int i = 0; i < BN; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
+        for (int i = 0; i < EC; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
       } else if (e != 0) {
 #pragma unroll
-        for (int i = 0; i < BN; ++i) S[i] = scale_pow2(alpha * S[i], e);
+        for (int i = 0; i < EC; ++i) S[i] = scale_pow2(alpha * S[i], e);
         alpha = 1.0f;
       }
       if (row >= v.M) continue;
       if (v.split_k > 1) {
         float* prow = v.partial + (static_cast<int64_t>(w.ks) * v.M + row) * v.N;
 #pragma unroll
-        for (int i = 0; i < BN; ++i)
+        for (int i = 0; i < EC; ++i)
           if (col0 + i < v.N) prow[col0 + i] = S[i];
         continue;
       }
       float* crow = v.C + static_cast<int64_t>(row) * v.ldc;
-      if (v.c_vec4 && col0 + BN <= v.N) {
+      if (v.c_vec4 && col0 + EC <= v.N) {
         float4* c4 = reinterpret_cast<float4*>(crow + col0);
 #pragma unroll
-        for (int i = 0; i < BN / 4; ++i) {
+        for (int i = 0; i < EC / 4; ++i) {
           float4 o;
           if (beta != 0.0f) {
             const float4 old = c4[i];
@@ -394,7 +406,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         }
       } else {
 #pragma unroll
-        for (int i = 0; i < BN; ++i) {
+        for (int i = 0; i < EC; ++i) {
           const int col = col0 + i;
           if (col < v.N) {
             const float val = beta != 0.0f ? fmaf(alpha, S[i], beta * crow[col]) : alpha * S[i];
@@ -414,7 +426,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
 }
 
 template <int BN, bool TF32>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TcCfg<BN, TF32>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs a) {
   SingleSched sc{&tmA, &tmB, &a};
@@ -422,7 +434,7 @@ __global__ void __launch_bounds__(192, 1)
 }
 
 template <int BN, bool TF32>
-__global__ void __launch_bounds__(192, 1) tc_grouped_kernel(const GroupedArgs a) {
+__global__ void __launch_bounds__(TcCfg<BN, TF32>::THREADS, 1) tc_grouped_kernel(const GroupedArgs a) {
   GroupedSched sc{&a};
   tc_gemm_body<BN, TF32>(sc);
 }
@@ -445,9 +457,12 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
 }
 
 int tc_smem_bytes(int bn, Prec prec) {
-  if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true>::SMEM : TcCfg<128, true>::SMEM;
-  return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
+  if (prec == Prec::TF32)
+    return bn == 64 ? TcCfg<64, true>::SMEM : bn == 128 ? TcCfg<128, true>::SMEM : TcCfg<256, true>::SMEM;
+  return bn == 64 ? TcCfg<64, false>::SMEM : bn == 128 ? TcCfg<128, false>::SMEM : TcCfg<256, false>::SMEM;
 }
+
+int tc_chunk_bytes(int bn) { return bn == 256 ? 64 : 128; }
 
 // The dynamic shared memory limit of every kernel variant is raised once per
 // device and thread, outside any stream capture: plans call tc_prepare when
@@ -475,9 +490,11 @@ cudaError_t tc_prepare(int bn, Prec prec) {
   if (prec == Prec::TF32) {
     if (bn == 64) return prepare_variant<64, true>();
     if (bn == 128) return prepare_variant<128, true>();
+    if (bn == 256) return prepare_variant<256, true>();
   } else {
     if (bn == 64) return prepare_variant<64, false>();
     if (bn == 128) return prepare_variant<128, false>();
+    if (bn == 256) return prepare_variant<256, false>();
   }
   return cudaErrorInvalidValue;
 }
@@ -497,9 +514,11 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   if (l.prec == Prec::TF32) {
     if (l.bn == 64) return launch_variant<64, true>(l.grid, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, true>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 256) return launch_variant<256, true>(l.grid, tmA, tmB, a, s);
   } else {
     if (l.bn == 64) return launch_variant<64, false>(l.grid, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, false>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 256) return launch_variant<256, false>(l.grid, tmA, tmB, a, s);
   }
   return cudaErrorInvalidValue;
 }

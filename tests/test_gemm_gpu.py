@@ -261,3 +261,16 @@ def test_torch_tensor_api_and_views():
 
 def test_device_error_word_clear():
     pkg.device_error()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Failure detection without a fault: a wait on a barrier nothing arrives
+    on must give up after its limit and report GEMM_ERR_TIMEOUT; the device
+    then still runs gemms."""
+    lib = pkg.load()
+    assert lib.gemm_selftest_wait_timeout() == 6
+    pkg.device_error()            # cleared
+    M = N = K = 256
+    A, B = W.uniform(M, K, 1), W.uniform(K, N, 2)
+    got = run_gemm("bf16x3", M, N, K, 1.0, A, B, 0.0, np.zeros((M, N), np.float32))
+    assert oracle.rel_frob(got, oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)) <= TOL
