@@ -50,8 +50,12 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--size", type=int, default=SIZE,
                    help="M = N = K (profiling cases only; the reported workload is 8192)")
+    p.add_argument("--config-id", type=int, default=None,
+                   help="explicit tile configuration for --kernel-only (default: heuristic)")
     p.add_argument("--kernel-only", action="store_true",
                    help="only warm-up and timed plan executions (for ncu captures)")
+    p.add_argument("--case", default="square", choices=("square", "grouped"),
+                   help="workload of --kernel-only (square M=N=K=size, or the 512 grouped problems)")
     p.add_argument("--no-other-workloads", action="store_true",
                    help="skip the secondary measurements of the other workloads")
     p.add_argument("--costmodel", default=os.path.join(ROOT, "paper_1804_10694_gb300", "data",
@@ -165,10 +169,25 @@ def run_kernel_only(args, local):
     import torch
     import paper_1804_10694_gb300 as pkg
     torch.cuda.set_device(local)
+    if args.case == "grouped":
+        import workloads as W
+        shapes = W.grouped_shapes()
+        As = [torch.empty(m, k, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
+        Bs = [torch.empty(k, n_, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
+        Cs = [torch.empty(m, n_, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
+        gp = pkg.GroupedPlan(shapes, mode=args.mode)
+        ones = [1.0] * len(shapes)
+        for _ in range(args.warmup + args.steps):
+            gp.execute(As, Bs, Cs, ones, ones)
+        torch.cuda.synchronize()
+        pkg.device_error()
+        gp.destroy()
+        print(json.dumps({"kernel_only": True, "case": "grouped", "executions": args.warmup + args.steps}))
+        return
     n = args.size
     A, B, C0 = inputs(n)
     dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C0))
-    plan = pkg.Plan(n, n, n, mode=args.mode)
+    plan = pkg.Plan(n, n, n, mode=args.mode, config_id=args.config_id)
     for _ in range(args.warmup + args.steps):
         plan.execute(dA, dB, dC, ALPHA, BETA)
     torch.cuda.synchronize()

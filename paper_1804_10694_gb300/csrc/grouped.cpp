@@ -36,7 +36,7 @@ struct gemm_grouped_plan_s {
   size_t ws_bytes = 0;
   gb::GroupedProblem* d_probs = nullptr;
   gb::GroupedPtrs* d_ptrs = nullptr;
-  int* d_tile_prefix = nullptr;
+  gb::GroupedUnit* d_units = nullptr;
   int* d_absmax_prefix = nullptr;
   int* d_split_prefix = nullptr;
   unsigned* d_amax = nullptr;
@@ -83,7 +83,7 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   GroupedArgs a{};
   a.probs = p->d_probs;
   a.ptrs = p->d_ptrs;
-  a.tile_prefix = p->d_tile_prefix;
+  a.units = p->d_units;
   a.G = p->G;
   a.num_units = p->num_units;
   a.kb = p->kb;
@@ -247,8 +247,10 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   off = round256(off + (size_t)G * sizeof(GroupedProblem));
   const size_t off_ptrs = off;
   off = round256(off + (size_t)G * sizeof(GroupedPtrs));
+  const size_t off_units = off;
+  off = round256(off + (size_t)std::max(tile_prefix[G], 1) * sizeof(GroupedUnit));
   const size_t off_pref = off;
-  off = round256(off + (size_t)3 * (G + 1) * sizeof(int));
+  off = round256(off + (size_t)2 * (G + 1) * sizeof(int));
   p->ws_bytes = off;
   if ((e = cudaMalloc(&p->ws, p->ws_bytes)) != cudaSuccess) {
     cudaGetLastError();
@@ -258,8 +260,8 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   p->d_amax = reinterpret_cast<unsigned*>(w + off_amax);
   p->d_probs = reinterpret_cast<GroupedProblem*>(w + off_probs);
   p->d_ptrs = reinterpret_cast<GroupedPtrs*>(w + off_ptrs);
-  p->d_tile_prefix = reinterpret_cast<int*>(w + off_pref);
-  p->d_absmax_prefix = p->d_tile_prefix + (G + 1);
+  p->d_units = reinterpret_cast<GroupedUnit*>(w + off_units);
+  p->d_absmax_prefix = reinterpret_cast<int*>(w + off_pref);
   p->d_split_prefix = p->d_absmax_prefix + (G + 1);
   for (int slot = 0; slot < G; ++slot) {
     const int i = p->order[slot];
@@ -282,11 +284,28 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   p->split_total = spl_prefix[G];
   if ((e = cudaMemcpy(p->d_probs, hp.data(), (size_t)G * sizeof(GroupedProblem), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload of the problem table");
+  // unit table: each problem's tiles in grouped raster order (groups of
+  // group_m row tiles, columns inside a group, rows fastest)
+  std::vector<GroupedUnit> units;
+  units.reserve(p->num_units);
+  for (int slot = 0; slot < G; ++slot) {
+    const GroupedProblem& g = hp[slot];
+    const int gm = std::max(1, std::min(p->group_m, g.tiles_m));
+    for (int t = 0; t < g.tiles_m * g.tiles_n; ++t) {
+      const int group_tiles = gm * g.tiles_n;
+      const int first_m = (t / group_tiles) * gm;
+      const int rows = std::min(g.tiles_m - first_m, gm);
+      const int r = t % group_tiles;
+      units.push_back(GroupedUnit{slot, first_m + r % rows, r / rows, g.chunks});
+    }
+  }
   std::vector<int> pref;
-  pref.insert(pref.end(), tile_prefix.begin(), tile_prefix.end());
   pref.insert(pref.end(), abs_prefix.begin(), abs_prefix.end());
   pref.insert(pref.end(), spl_prefix.begin(), spl_prefix.end());
-  if ((e = cudaMemcpy(p->d_tile_prefix, pref.data(), pref.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+  if (!units.empty() &&
+      (e = cudaMemcpy(p->d_units, units.data(), units.size() * sizeof(GroupedUnit), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "upload of the unit table");
+  if ((e = cudaMemcpy(p->d_absmax_prefix, pref.data(), pref.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload of the prefix tables");
   *out = p.release();
   return GEMM_OK;

@@ -106,10 +106,16 @@ struct GroupedPtrs {
   int pad;
 };
 
+// One output tile of a grouped launch, precomputed on the host so that a CTA
+// finds its next tile with a single 16-byte load.
+struct GroupedUnit {
+  int prob, tm, tn, chunks;
+};
+
 struct GroupedArgs {
   const GroupedProblem* probs;
   const GroupedPtrs* ptrs;
-  const int* tile_prefix;   // G + 1 entries: first output tile of each problem
+  const GroupedUnit* units;   // num_units entries, problems longest-K first
   int G, num_units, kb, group_m;
   int* err;
 };

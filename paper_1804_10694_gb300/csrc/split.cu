@@ -267,9 +267,22 @@ __device__ __forceinline__ bool aligned16(const void* p, int64_t ld) {
   return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % 4 == 0);
 }
 
+// The problem prefix sums are staged in shared memory when they fit (the
+// launch passes their size as dynamic shared memory, 0 otherwise).
+__device__ __forceinline__ const int* stage_prefix(const int* __restrict__ prefix, int G) {
+  extern __shared__ int s_prefix[];
+  unsigned dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  if (dyn < (G + 1) * sizeof(int)) return prefix;
+  for (int i = threadIdx.x; i <= G; i += blockDim.x) s_prefix[i] = prefix[i];
+  __syncthreads();
+  return s_prefix;
+}
+
 __global__ void grouped_absmax_kernel(const GroupedProblem* __restrict__ probs,
                                       const GroupedPtrs* __restrict__ ptrs,
-                                      const int* __restrict__ prefix, int G) {
+                                      const int* __restrict__ prefix_g, int G) {
+  const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int g = find_problem(prefix, G, i);
@@ -294,7 +307,8 @@ __global__ void grouped_absmax_kernel(const GroupedProblem* __restrict__ probs,
 template <bool TF32>
 __global__ void grouped_split_kernel(const GroupedProblem* __restrict__ probs,
                                      const GroupedPtrs* __restrict__ ptrs,
-                                     const int* __restrict__ prefix, int G) {
+                                     const int* __restrict__ prefix_g, int G) {
+  const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int g = find_problem(prefix, G, i);
@@ -370,14 +384,15 @@ cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const Group
                                 int split_total, int G, int sms, cudaStream_t s) {
   const int ga = absmax_total < sms * 8 ? absmax_total : sms * 8;
   const int gs = split_total < sms * 8 ? split_total : sms * 8;
-  if (ga > 0) grouped_absmax_kernel<<<ga, 256, 0, s>>>(probs, ptrs, absmax_prefix, G);
+  const size_t dyn = (G + 1) <= 4096 ? (size_t)(G + 1) * sizeof(int) : 0;
+  if (ga > 0) grouped_absmax_kernel<<<ga, 256, dyn, s>>>(probs, ptrs, absmax_prefix, G);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (gs > 0) {
     if (p == Prec::TF32)
-      grouped_split_kernel<true><<<gs, 256, 0, s>>>(probs, ptrs, split_prefix, G);
+      grouped_split_kernel<true><<<gs, 256, dyn, s>>>(probs, ptrs, split_prefix, G);
     else
-      grouped_split_kernel<false><<<gs, 256, 0, s>>>(probs, ptrs, split_prefix, G);
+      grouped_split_kernel<false><<<gs, 256, dyn, s>>>(probs, ptrs, split_prefix, G);
   }
   return cudaGetLastError();
 }

@@ -117,26 +117,23 @@ struct SingleSched {
 };
 
 // Scheduling policy of a grouped launch: units are the tiles of all problems,
-// numbered problem after problem (problems ordered longest-K first on the
-// host); a unit finds its problem by binary search in the tile prefix sums.
+// listed problem after problem (problems ordered longest-K first on the host,
+// each problem's tiles in grouped raster order); the table gives a unit's
+// problem, tile coordinates and k-chunk count in one 16-byte load.
 struct GroupedSched {
   const GroupedArgs* a;
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
   __device__ Work work(int u) const {
-    int lo = 0, hi = a->G - 1;
-    while (lo < hi) {   // last g with tile_prefix[g] <= u
-      const int mid = (lo + hi + 1) >> 1;
-      if (a->tile_prefix[mid] <= u) lo = mid; else hi = mid - 1;
-    }
-    const GroupedProblem& p = a->probs[lo];
+    const int4 e = __ldg(reinterpret_cast<const int4*>(a->units) + u);
     Work w;
-    w.prob = lo;
+    w.prob = e.x;
+    w.tm = e.y;
+    w.tn = e.z;
     w.ks = 0;
-    raster(u - a->tile_prefix[lo], p.tiles_m, p.tiles_n, min(a->group_m, p.tiles_m), w.tm, w.tn);
     w.c0 = 0;
-    w.c1 = p.chunks;
+    w.c1 = e.w;
     return w;
   }
   __device__ const CUtensorMap* mapA(int g) const { return &a->probs[g].tmA; }
@@ -209,8 +206,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       for (int s = 0; s < STAGES; ++s) issued[s] = false, last_phase[s] = 0;
       bool ok = true;
       int last_prob = -1;
+      Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
       for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Work w = sc.work(u);
+        const Work w = wn;                         // next unit's entry loads early
+        if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         const CUtensorMap* mA = sc.mapA(w.prob);
         const CUtensorMap* mB = sc.mapB(w.prob);
         if (w.prob != last_prob) {
@@ -252,8 +251,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       uint32_t stage = 0, phase = 0, ab = 0, aphase = 0;
       bool ok = true;
       bool any = false;
+      Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
       for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Work w = sc.work(u);
+        const Work w = wn;
+        if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         for (int cb = w.c0; ok && cb < w.c1; cb += kb) {
           const int ce = min(cb + kb, w.c1);
           if (!mbar_wait(acce_bar(ab), aphase ^ 1u, abort_flag, err)) {
@@ -318,8 +319,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     const int row_in_tile = q * 32 + lane;
     uint32_t ab = 0, aphase = 0;
     bool ok = true;
+    Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
     for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-      const Work w = sc.work(u);
+      const Work w = wn;
+      if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
       float S[EC];
       int blk = 0;
       for (int cb = w.c0; cb < w.c1; cb += kb, ++blk) {
