@@ -10,8 +10,12 @@ where the paper is silent (it does not describe this method at all):
 
 * Block scaling: A is scaled per block of 128 rows (all of K), B per block of
   128 columns (all of K).  The block exponent is e = floor(log2(max |x|)),
-  clamped to [-126, 126]; e = 0 when the block is all zero or holds a
-  non-finite value.  The scaled value is x * 2**-e, one FP32 multiply.
+  clamped to [-126, 126], for blocks whose max lies outside [2**-48, 2**48);
+  e = 0 for blocks inside that range (there no product, no sum of up to
+  2**31 products and no low part of a significant element leaves the normal
+  range, so scaling brings nothing), for all-zero blocks and for blocks
+  holding a non-finite value.  The scaled value is x * 2**-e, one FP32
+  multiply.
 * hi = RN(x'), lo = RN(x' - hi) with RN round-to-nearest-even to bf16 (8-bit
   significand) or tf32 (11-bit significand); x' - hi is an FP32 subtraction.
   A non-finite x' gives hi = x', lo = 0.
@@ -54,15 +58,19 @@ def round_tf32(x: np.ndarray) -> np.ndarray:
     return out
 
 
+SAFE_EXP = 48  # blocks with max |x| in [2**-48, 2**48) are not scaled
+
+
 def block_exponent(absmax: float) -> int:
-    """floor(log2(absmax)) clamped to [-126, 126]; 0 for 0 or non-finite."""
+    """0 for 0, non-finite or max in [2**-48, 2**48); else floor(log2(absmax))
+    clamped to [-126, 126]."""
     a = float(absmax)
     if a == 0.0 or not np.isfinite(a):
         return 0
     bits = int(np.array([a], dtype=np.float32).view(np.uint32)[0])
-    e = ((bits >> 23) & 0xFF) - 127
-    if e < -126:          # subnormal maximum
-        e = -126
+    e = ((bits >> 23) & 0xFF) - 127          # -127 for a subnormal maximum
+    if -SAFE_EXP <= e < SAFE_EXP:
+        return 0
     return max(-126, min(126, e))
 
 

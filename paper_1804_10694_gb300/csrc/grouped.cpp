@@ -37,7 +37,7 @@ struct gemm_grouped_plan_s {
   gb::GroupedProblem* d_probs = nullptr;
   gb::GroupedPtrs* d_ptrs = nullptr;
   gb::GroupedUnit* d_units = nullptr;
-  int* d_absmax_prefix = nullptr;
+  int* d_absmax_prefix = nullptr;   // rescale-pass items
   int* d_split_prefix = nullptr;
   unsigned* d_amax = nullptr;
   size_t amax_bytes = 0;
@@ -77,8 +77,8 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   if (p->num_units == 0) return GEMM_OK;
   if ((e = cudaMemsetAsync(p->d_amax, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "clear block maxima");
-  if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_absmax_prefix, p->absmax_total,
-                               p->d_split_prefix, p->split_total, p->G, p->sms, s)) != cudaSuccess)
+  if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_split_prefix, p->split_total,
+                               p->d_absmax_prefix, p->absmax_total, p->G, p->sms, s)) != cudaSuccess)
     return cuda_fail(e, "grouped pack launch");
   GroupedArgs a{};
   a.probs = p->d_probs;
@@ -237,8 +237,8 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     amax_count += (size_t)(p->M[i] + kScaleBlock - 1) / kScaleBlock + (p->N[i] + kScaleBlock - 1) / kScaleBlock + 2;
     tile_prefix[slot + 1] = tile_prefix[slot] + g.tiles_m * g.tiles_n;
     const bool pack = !empty && p->K[i] > 0;
-    abs_prefix[slot + 1] = abs_prefix[slot] + (pack ? grouped_absmax_items(p->M[i], p->N[i], p->K[i]) : 0);
-    spl_prefix[slot + 1] = spl_prefix[slot] + (pack ? grouped_split_items(p->M[i], p->N[i], pitch) : 0);
+    spl_prefix[slot + 1] = spl_prefix[slot] + (pack ? pack_first_items(p->M[i], p->N[i], pitch) : 0);
+    abs_prefix[slot + 1] = abs_prefix[slot] + (pack ? pack_rescale_items(p->M[i], p->N[i], pitch) : 0);
   }
   const size_t off_amax = off;
   p->amax_bytes = amax_count * sizeof(unsigned);

@@ -70,16 +70,18 @@ cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const
 cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t ldc, cudaStream_t s);
 
 // ------------------------------------------------------------ split / pack
-// Per-block max |x| as float bit patterns (atomicMax on unsigned).
-// blocks_along_rows: A (blocks of 128 rows); else B (blocks of 128 columns).
-cudaError_t absmax_launch(const float* X, int64_t rows, int64_t cols, int64_t ld,
-                          bool blocks_along_rows, unsigned* amax, cudaStream_t s);
-// A (rows x cols, ld) -> planes [2][rows][pitch] of hi/lo (bf16 or tf32-in-fp32).
-cudaError_t split_rows_launch(Prec p, const float* X, int64_t rows, int64_t cols, int64_t ld,
-                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s);
-// B (K x N, ld) -> transposed planes [2][N][pitch] of hi/lo.
-cudaError_t split_cols_launch(Prec p, const float* X, int64_t K, int64_t N, int64_t ld,
-                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s);
+// Both operands in two launches: a first pass writing the unscaled hi/lo
+// planes and the per-block max |x| bit patterns (A: blocks of 128 rows, into
+// amaxA; B, transposed: blocks of 128 columns, into amaxB), then a pass that
+// re-splits the blocks needing a power-of-two scale.  The block maxima must
+// be zero on entry.  A (or B) may be null to pack only the other operand.
+// A: M x K (lda) -> planesA [2][M][pitch];  B: K x N (ldb) -> planesB [2][N][pitch].
+cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, void* planesA,
+                        void* planesB, int64_t pitch, int sms, cudaStream_t s);
+// Work items of the two passes for one problem (grouped prefix sums).
+int pack_first_items(int64_t M, int64_t N, int64_t pitch);
+int pack_rescale_items(int64_t M, int64_t N, int64_t pitch);
 
 // ------------------------------------------------------------ grouped
 // Static description of one problem of a grouped gemm, device resident
@@ -121,12 +123,11 @@ struct GroupedArgs {
 };
 
 cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s);
-int grouped_absmax_items(int64_t M, int64_t N, int64_t K);
-int grouped_split_items(int64_t M, int64_t N, int64_t pitch);
-// Block maxima and hi/lo planes of every problem (two launches); the block
-// maxima must have been zeroed.
+// Both pack passes for every problem (two launches, items found through the
+// prefix sums of pack_first_items / pack_rescale_items); the block maxima
+// must have been zeroed.
 cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const GroupedPtrs* ptrs,
-                                const int* absmax_prefix, int absmax_total, const int* split_prefix,
-                                int split_total, int G, int sms, cudaStream_t s);
+                                const int* first_prefix, int first_total, const int* rescale_prefix,
+                                int rescale_total, int G, int sms, cudaStream_t s);
 
 }  // namespace gb

@@ -157,12 +157,9 @@ extern "C" gemm_status gemm_f32_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, 
   unsigned* amaxB = amaxA + nblkA;
 
   if ((e = cudaMemsetAsync(amaxA, 0, bytesAmax, s)) != cudaSuccess) return cuda_fail(e, "clear block maxima");
-  if ((e = absmax_launch(A, M, K, lda, true, amaxA, s)) != cudaSuccess) return cuda_fail(e, "absmax(A)");
-  if ((e = absmax_launch(B, K, N, ldb, false, amaxB, s)) != cudaSuccess) return cuda_fail(e, "absmax(B)");
-  if ((e = split_rows_launch(Prec::BF16, A, M, K, lda, amaxA, planesA, pitch, s)) != cudaSuccess)
-    return cuda_fail(e, "split(A)");
-  if ((e = split_cols_launch(Prec::BF16, B, K, N, ldb, amaxB, planesB, pitch, s)) != cudaSuccess)
-    return cuda_fail(e, "split(B)");
+  if ((e = pack_launch(Prec::BF16, A, M, K, lda, B, N, ldb, amaxA, amaxB, planesA, planesB, pitch,
+                       d->sms, s)) != cudaSuccess)
+    return cuda_fail(e, "pack");
 
   const int bn = N <= 64 ? 64 : 128;
   CUtensorMap tmA, tmB;

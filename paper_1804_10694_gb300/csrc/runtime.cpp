@@ -114,7 +114,7 @@ static const std::vector<gemm_config>& config_table() {
           for (int g : groups) {
             gemm_config c;
             c.block_n = bn;
-            c.stages = bn == 128 ? 3 : 4;
+            c.stages = bn == 64 ? 4 : bn == 128 ? 3 : 2;
             c.split_k = sk;
             c.kb = kb;
             c.group_m = g;
@@ -353,14 +353,9 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   if (prof) cudaEventRecord(ev[0], s);
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
-  if ((e = absmax_launch(A, M, K, p->lda, true, p->amaxA, s)) != cudaSuccess)
-    return cuda_fail(e, "absmax(A) launch");
-  if ((e = absmax_launch(B, K, N, p->ldb, false, p->amaxB, s)) != cudaSuccess)
-    return cuda_fail(e, "absmax(B) launch");
-  if ((e = split_rows_launch(p->prec, A, M, K, p->lda, p->amaxA, p->planesA, p->pitch, s)) != cudaSuccess)
-    return cuda_fail(e, "split(A) launch");
-  if ((e = split_cols_launch(p->prec, B, K, N, p->ldb, p->amaxB, p->planesB, p->pitch, s)) != cudaSuccess)
-    return cuda_fail(e, "split(B) launch");
+  if ((e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->planesA,
+                       p->planesB, p->pitch, p->sms, s)) != cudaSuccess)
+    return cuda_fail(e, "pack launch");
   TcArgs a = p->args;
   a.alpha = alpha;
   a.beta = beta;
@@ -681,16 +676,14 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
   if (reinterpret_cast<uintptr_t>(planes) % 16)
     return fail(GEMM_ERR_ALIGNMENT, "planes must be 16-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int sms = gemm_device_sm_count();
+  if (sms <= 0) return fail(GEMM_ERR_CUDA, "no device");
   cudaError_t e;
-  if (!transpose) {
-    if ((e = absmax_launch(X, rows, cols, ld, true, amax, s)) != cudaSuccess) return cuda_fail(e, "absmax");
-    if ((e = split_rows_launch(p, X, rows, cols, ld, amax, planes, pitch, s)) != cudaSuccess)
-      return cuda_fail(e, "split rows");
-  } else {
-    if ((e = absmax_launch(X, rows, cols, ld, false, amax, s)) != cudaSuccess) return cuda_fail(e, "absmax");
-    if ((e = split_cols_launch(p, X, rows, cols, ld, amax, planes, pitch, s)) != cudaSuccess)
-      return cuda_fail(e, "split cols");
-  }
+  if (!transpose)
+    e = pack_launch(p, X, rows, cols, ld, nullptr, 0, 1, amax, nullptr, planes, nullptr, pitch, sms, s);
+  else
+    e = pack_launch(p, nullptr, 0, rows, 1, X, cols, ld, nullptr, amax, nullptr, planes, pitch, sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   return GEMM_OK;
 }
 

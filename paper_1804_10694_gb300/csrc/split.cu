@@ -10,12 +10,16 @@
 // a 16-byte pitch with zeros.
 //
 // Blocks: A uses one exponent per 128 rows (all of K), B one per 128 columns
-// (all of K), from a first pass that takes max |x| per block.
+// (all of K).  Most blocks need no scaling (e = 0, see scale.cuh), so packing
+// takes ONE pass over the operands: it writes the unscaled split and folds
+// max |x| of each block into the block's slot.  A second, cheap pass then
+// re-splits, with their exponent, only the blocks whose max lies outside the
+// safe range; every other CTA of that pass returns after one load.
 //
-// Every kernel is a thin wrapper around a per-tile device function; the
-// single-problem kernels map blockIdx to a tile, the grouped kernels map a
-// flattened item index to (problem, tile) through prefix sums, so one launch
-// packs every problem of a grouped gemm.
+// Every kernel is a thin wrapper around per-tile device functions; the
+// single-problem kernels walk the tiles of A and then of B in one launch, the
+// grouped kernels map a flattened item index to (problem, tile) through
+// prefix sums, so one launch packs every problem of a grouped gemm.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -26,47 +30,7 @@ namespace gb {
 
 namespace {
 
-// ------------------------------------------------------------------ max |x|
-// One CTA (256 threads) reduces a 32-row x 128-column tile, which lies inside
-// one block of either kind, and folds it into the block's slot with an
-// unsigned atomicMax on the bit pattern of |x| (non-negative floats order like
-// their bits; NaN patterns sort above Inf, so a NaN marks the block as
-// non-finite).
-__device__ __forceinline__ void absmax_tile(const float* __restrict__ X, int64_t rows, int64_t cols,
-                                            int64_t ld, int64_t r0, int64_t c0, bool vec,
-                                            bool blocks_along_rows, unsigned* __restrict__ amax) {
-  __shared__ unsigned wm[8];
-  const int t = threadIdx.x;
-  const int cq = (t & 31) * 4;
-  unsigned m = 0;
-  for (int rr = t >> 5; rr < 32; rr += 8) {
-    const int64_t r = r0 + rr;
-    if (r >= rows) break;
-    const float* p = X + r * ld + c0 + cq;
-    if (vec && c0 + cq + 3 < cols) {
-      const float4 v = *reinterpret_cast<const float4*>(p);
-      m = max(m, __float_as_uint(v.x) & 0x7FFFFFFFu);
-      m = max(m, __float_as_uint(v.y) & 0x7FFFFFFFu);
-      m = max(m, __float_as_uint(v.z) & 0x7FFFFFFFu);
-      m = max(m, __float_as_uint(v.w) & 0x7FFFFFFFu);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (c0 + cq + i < cols) m = max(m, __float_as_uint(p[i]) & 0x7FFFFFFFu);
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((t & 31) == 0) wm[t >> 5] = m;
-  __syncthreads();
-  if (t == 0) {
-    unsigned b = wm[0];
-    for (int i = 1; i < 8; ++i) b = max(b, wm[i]);
-    const int64_t slot = blocks_along_rows ? r0 / kScaleBlock : c0 / kScaleBlock;
-    atomicMax(amax + slot, b);
-  }
-  __syncthreads();   // wm is reused by the next tile of a grouped launch
-}
+enum Pass { kFirst = 0, kRescale = 1 };
 
 // ---------------------------------------------------------------- rounding
 __device__ __forceinline__ float round_tf32_rne(float x) {
@@ -92,24 +56,44 @@ __device__ __forceinline__ void split_tf32(float xs, float& hi, float& lo) {
   lo = isfinite(xs) ? round_tf32_rne(xs - hi) : 0.0f;
 }
 
+// |x| as an orderable bit pattern (non-negative floats order like their bits;
+// NaN patterns sort above Inf, so a NaN marks the block as non-finite).
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+
+// CTA-wide max of m folded into *slot (every thread of the CTA calls this).
+__device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
+  __shared__ unsigned wm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned b = wm[0];
+    for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) b = max(b, wm[i]);
+    if (b) atomicMax(slot, b);
+  }
+  __syncthreads();   // wm is reused by the next tile of a looping launch
+}
+
 // --------------------------------------------------------- A: row-major split
-// One CTA writes a 32-row x 128-column tile of the planes (columns of the
-// padded pitch); each thread handles 4 quads of 4 consecutive k.  Padding
-// k in [K, pitch) gets 0.
-template <bool TF32>
+// One CTA (256 threads) writes a 32-row x 128-column tile of the planes
+// (columns of the padded pitch, k in [K, pitch) gets 0); each thread handles
+// 4 quads of 4 consecutive k.  The 32 rows lie in one 128-row block.
+template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
-                                                const unsigned* __restrict__ amax,
+                                                unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t pitch,
                                                 int64_t r0, int64_t k0) {
   const int64_t plane = rows * pitch;
   const int t = threadIdx.x;
   const int kq = (t & 31) * 4;
+  const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[r0 / kScaleBlock]));
+  unsigned m = 0;
   for (int rr = t >> 5; rr < 32; rr += 8) {
     const int64_t r = r0 + rr;
     const int64_t k = k0 + kq;
     if (r >= rows || k >= pitch) continue;
-    const float sc = pow2f(-block_exponent(amax[r / kScaleBlock]));
     float v[4];
     const float* p = X + r * ld + k;
     if (vec && k + 3 < cols) {
@@ -118,6 +102,10 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = (k + i < cols) ? p[i] : 0.0f;
+    }
+    if (PASS == kFirst) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) m = max(m, abs_bits(v[i]));
     }
     const int64_t o = r * pitch + k;
     if (TF32) {
@@ -142,19 +130,21 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
       *reinterpret_cast<uint2*>(P + plane + o) = *reinterpret_cast<const uint2*>(l);
     }
   }
+  if (PASS == kFirst) fold_block_max(m, amax + r0 / kScaleBlock);
 }
 
 // ---------------------------------------------------- B: transposing split
 // One CTA handles a 64 (k) x 64 (n) tile: coalesced loads along n into shared
-// memory, then each thread writes 16 consecutive k of one output row n.
-template <bool TF32>
+// memory, then each thread writes 16 consecutive k of one output row n.  The
+// 64 columns lie in one 128-column block.
+template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
-                                                int64_t ld, bool vec,
-                                                const unsigned* __restrict__ amax,
+                                                int64_t ld, bool vec, unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t pitch,
                                                 int64_t n0, int64_t k0) {
   __shared__ float tile[64][65];
   const int t = threadIdx.x;
+  unsigned m = 0;
   {
     const int cn = (t & 15) * 4;
     for (int kr = t >> 4; kr < 64; kr += 16) {
@@ -172,7 +162,10 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
         }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) tile[kr][cn + i] = v[i];
+      for (int i = 0; i < 4; ++i) {
+        tile[kr][cn + i] = v[i];
+        if (PASS == kFirst) m = max(m, abs_bits(v[i]));
+      }
     }
   }
   __syncthreads();
@@ -180,7 +173,7 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
   const int kl = (t & 3) * 16;        // 0, 16, 32, 48
   const int64_t n = n0 + nl;
   if (n < N && k0 + kl < pitch) {
-    const float sc = pow2f(-block_exponent(amax[n / kScaleBlock]));
+    const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[n / kScaleBlock]));
     const int64_t plane = N * pitch;
     const int64_t obase = n * pitch + k0 + kl;
     const bool whole = k0 + kl + 16 <= pitch;
@@ -225,35 +218,83 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
       }
     }
   }
-  __syncthreads();   // the tile is reused by the next item of a grouped launch
+  if (PASS == kFirst)
+    fold_block_max(m, amax + n0 / kScaleBlock);   // its barriers also guard `tile`
+  else
+    __syncthreads();   // the tile is reused by the next item of a looping launch
+}
+
+// --------------------------------------------------- tile decomposition
+// First pass: A in 32-row x 128-column tiles, B in 64 x 64 tiles.
+// Rescale pass: A in 128-row x 128-column blocks (4 tiles), B in
+// 128-column x 64-k blocks (2 tiles); blocks that need no scaling return.
+struct PackShape {
+  const float* A;
+  const float* B;
+  int64_t M, N, K, lda, ldb, pitch;
+  bool vecA, vecB;
+  unsigned* amaxA;
+  unsigned* amaxB;
+  void* planesA;
+  void* planesB;
+
+  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * ((pitch + 127) / 128)); }
+  __device__ int first_items_b() const { return (int)(((N + 63) / 64) * ((pitch + 63) / 64)); }
+  __device__ int rescale_items_a() const { return (int)(((M + 127) / 128) * ((pitch + 127) / 128)); }
+  __device__ int rescale_items_b() const { return (int)(((N + 127) / 128) * ((pitch + 63) / 64)); }
+};
+
+template <bool TF32>
+__device__ __forceinline__ void first_item(const PackShape& p, int i) {
+  const int na = p.first_items_a();
+  if (i < na) {
+    const int cols = (int)((p.pitch + 127) / 128);
+    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
+                                  (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 128);
+  } else {
+    const int l = i - na;
+    const int ncols = (int)((p.N + 63) / 64);
+    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+                                  (int64_t)(l % ncols) * 64, (int64_t)(l / ncols) * 64);
+  }
+}
+
+template <bool TF32>
+__device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
+  const int na = p.rescale_items_a();
+  if (i < na) {
+    const int cols = (int)((p.pitch + 127) / 128);
+    const int64_t r0 = (int64_t)(i / cols) * 128, k0 = (int64_t)(i % cols) * 128;
+    if (block_exponent(p.amaxA[r0 / kScaleBlock]) == 0) return;   // uniform per CTA
+    for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
+      split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
+                                      r0 + 32 * q, k0);
+  } else {
+    const int l = i - na;
+    const int nblk = (int)((p.N + 127) / 128);
+    const int64_t n0 = (int64_t)(l % nblk) * 128, k0 = (int64_t)(l / nblk) * 64;
+    if (block_exponent(p.amaxB[n0 / kScaleBlock]) == 0) return;
+    for (int q = 0; q < 2 && n0 + 64 * q < p.N; ++q)
+      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+                                      n0 + 64 * q, k0);
+  }
 }
 
 // ------------------------------------------------ single-problem kernels
-__global__ void absmax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ld,
-                              bool vec, bool blocks_along_rows, unsigned* __restrict__ amax) {
-  absmax_tile(X, rows, cols, ld, static_cast<int64_t>(blockIdx.y) * 32,
-              static_cast<int64_t>(blockIdx.x) * 128, vec, blocks_along_rows, amax);
+template <bool TF32>
+__global__ void pack_first_kernel(const PackShape p) {
+  const int total = p.first_items_a() + p.first_items_b();
+  for (int i = blockIdx.x; i < total; i += gridDim.x) first_item<TF32>(p, i);
 }
 
 template <bool TF32>
-__global__ void split_rows_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
-                                  int64_t ld, bool vec, const unsigned* __restrict__ amax,
-                                  void* __restrict__ planes, int64_t pitch) {
-  split_rows_tile<TF32>(X, rows, cols, ld, vec, amax, planes, pitch,
-                        static_cast<int64_t>(blockIdx.y) * 32, static_cast<int64_t>(blockIdx.x) * 128);
-}
-
-template <bool TF32>
-__global__ void split_cols_kernel(const float* __restrict__ X, int64_t K, int64_t N, int64_t ld,
-                                  bool vec, const unsigned* __restrict__ amax,
-                                  void* __restrict__ planes, int64_t pitch) {
-  split_cols_tile<TF32>(X, K, N, ld, vec, amax, planes, pitch, static_cast<int64_t>(blockIdx.x) * 64,
-                        static_cast<int64_t>(blockIdx.y) * 64);
+__global__ void pack_rescale_kernel(const PackShape p) {
+  const int total = p.rescale_items_a() + p.rescale_items_b();
+  for (int i = blockIdx.x; i < total; i += gridDim.x) rescale_item<TF32>(p, i);
 }
 
 // ------------------------------------------------------ grouped kernels
-// Item i of a grouped pack launch: problem g with prefix[g] <= i < prefix[g+1];
-// the problem's first items belong to A, the rest to B.
+// Item i of a grouped pack launch: problem g with prefix[g] <= i < prefix[g+1].
 __device__ __forceinline__ int find_problem(const int* __restrict__ prefix, int G, int i) {
   int lo = 0, hi = G - 1;
   while (lo < hi) {
@@ -261,10 +302,6 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ prefix, int 
     if (prefix[mid] <= i) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-__device__ __forceinline__ bool aligned16(const void* p, int64_t ld) {
-  return (reinterpret_cast<uintptr_t>(p) % 16 == 0) && (ld % 4 == 0);
 }
 
 // The problem prefix sums are staged in shared memory when they fit (the
@@ -279,120 +316,84 @@ __device__ __forceinline__ const int* stage_prefix(const int* __restrict__ prefi
   return s_prefix;
 }
 
-__global__ void grouped_absmax_kernel(const GroupedProblem* __restrict__ probs,
-                                      const GroupedPtrs* __restrict__ ptrs,
-                                      const int* __restrict__ prefix_g, int G) {
+__device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, const GroupedPtrs& q) {
+  PackShape p;
+  p.A = q.A, p.B = q.B;
+  p.M = g.M, p.N = g.N, p.K = g.K, p.lda = g.lda, p.ldb = g.ldb, p.pitch = g.pitch;
+  p.vecA = (reinterpret_cast<uintptr_t>(q.A) % 16 == 0) && (g.lda % 4 == 0);
+  p.vecB = (reinterpret_cast<uintptr_t>(q.B) % 16 == 0) && (g.ldb % 4 == 0);
+  p.amaxA = g.amaxA, p.amaxB = g.amaxB;
+  p.planesA = g.planesA, p.planesB = g.planesB;
+  return p;
+}
+
+template <bool TF32, Pass PASS>
+__global__ void grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
+                                    const GroupedPtrs* __restrict__ ptrs,
+                                    const int* __restrict__ prefix_g, int G) {
   const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int g = find_problem(prefix, G, i);
-    const GroupedProblem& p = probs[g];
     const GroupedPtrs& q = ptrs[g];
     if (q.alpha == 0.0f) continue;   // A and B are not read when alpha == 0
-    const int local = i - prefix[g];
-    const int a_cols = (p.K + 127) / 128;
-    const int a_items = ((p.M + 31) / 32) * a_cols;
-    if (local < a_items) {
-      absmax_tile(q.A, p.M, p.K, p.lda, static_cast<int64_t>(local / a_cols) * 32,
-                  static_cast<int64_t>(local % a_cols) * 128, aligned16(q.A, p.lda), true, p.amaxA);
-    } else {
-      const int l = local - a_items;
-      const int b_cols = (p.N + 127) / 128;
-      absmax_tile(q.B, p.K, p.N, p.ldb, static_cast<int64_t>(l / b_cols) * 32,
-                  static_cast<int64_t>(l % b_cols) * 128, aligned16(q.B, p.ldb), false, p.amaxB);
-    }
+    const PackShape p = problem_shape(probs[g], q);
+    if (PASS == kFirst)
+      first_item<TF32>(p, i - prefix[g]);
+    else
+      rescale_item<TF32>(p, i - prefix[g]);
   }
 }
 
-template <bool TF32>
-__global__ void grouped_split_kernel(const GroupedProblem* __restrict__ probs,
-                                     const GroupedPtrs* __restrict__ ptrs,
-                                     const int* __restrict__ prefix_g, int G) {
-  const int* prefix = stage_prefix(prefix_g, G);
-  const int total = prefix[G];
-  for (int i = blockIdx.x; i < total; i += gridDim.x) {
-    const int g = find_problem(prefix, G, i);
-    const GroupedProblem& p = probs[g];
-    const GroupedPtrs& q = ptrs[g];
-    if (q.alpha == 0.0f) continue;   // A and B are not read when alpha == 0
-    const int local = i - prefix[g];
-    const int a_cols = static_cast<int>((p.pitch + 127) / 128);
-    const int a_items = ((p.M + 31) / 32) * a_cols;
-    if (local < a_items) {
-      split_rows_tile<TF32>(q.A, p.M, p.K, p.lda, aligned16(q.A, p.lda), p.amaxA, p.planesA, p.pitch,
-                            static_cast<int64_t>(local / a_cols) * 32,
-                            static_cast<int64_t>(local % a_cols) * 128);
-    } else {
-      const int l = local - a_items;
-      const int b_ncols = (p.N + 63) / 64;
-      split_cols_tile<TF32>(q.B, p.K, p.N, p.ldb, aligned16(q.B, p.ldb), p.amaxB, p.planesB, p.pitch,
-                            static_cast<int64_t>(l % b_ncols) * 64,
-                            static_cast<int64_t>(l / b_ncols) * 64);
-    }
-  }
-}
-
-bool vec_ok(const float* X, int64_t ld) {
-  return ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+int grid_for(int64_t items, int sms) {
+  const int64_t cap = static_cast<int64_t>(sms) * 8;
+  return static_cast<int>(items < cap ? (items > 0 ? items : 1) : cap);
 }
 
 }  // namespace
 
-// Items per problem of the grouped pack launches (host side, same tiling as
-// the kernels above).
-int grouped_absmax_items(int64_t M, int64_t N, int64_t K) {
-  return static_cast<int>(((M + 31) / 32) * ((K + 127) / 128) + ((K + 31) / 32) * ((N + 127) / 128));
-}
-int grouped_split_items(int64_t M, int64_t N, int64_t pitch) {
+// Items per problem of the two pack passes (host side, same tiling as above).
+int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
   return static_cast<int>(((M + 31) / 32) * ((pitch + 127) / 128) + ((N + 63) / 64) * ((pitch + 63) / 64));
 }
+int pack_rescale_items(int64_t M, int64_t N, int64_t pitch) {
+  return static_cast<int>(((M + 127) / 128) * ((pitch + 127) / 128) + ((N + 127) / 128) * ((pitch + 63) / 64));
+}
 
-cudaError_t absmax_launch(const float* X, int64_t rows, int64_t cols, int64_t ld,
-                          bool blocks_along_rows, unsigned* amax, cudaStream_t s) {
-  const dim3 grid(static_cast<unsigned>((cols + 127) / 128), static_cast<unsigned>((rows + 31) / 32));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  absmax_kernel<<<grid, 256, 0, s>>>(X, rows, cols, ld, vec_ok(X, ld), blocks_along_rows, amax);
+cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, void* planesA,
+                        void* planesB, int64_t pitch, int sms, cudaStream_t s) {
+  PackShape p;
+  p.A = A, p.B = B, p.M = A ? M : 0, p.N = B ? N : 0, p.K = K, p.lda = lda, p.ldb = ldb;
+  p.pitch = pitch;
+  p.vecA = A && lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+  p.vecB = B && ldb % 4 == 0 && reinterpret_cast<uintptr_t>(B) % 16 == 0;
+  p.amaxA = amaxA, p.amaxB = amaxB, p.planesA = planesA, p.planesB = planesB;
+  const int64_t first = pack_first_items(p.M, p.N, pitch);
+  const int64_t rescale = pack_rescale_items(p.M, p.N, pitch);
+  if (first == 0) return cudaSuccess;
+  if (prec == Prec::TF32) {
+    pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_rescale_kernel<true><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+  } else {
+    pack_first_kernel<false><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_rescale_kernel<false><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t split_rows_launch(Prec p, const float* X, int64_t rows, int64_t cols, int64_t ld,
-                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s) {
-  const dim3 grid(static_cast<unsigned>((pitch + 127) / 128), static_cast<unsigned>((rows + 31) / 32));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  const bool vec = vec_ok(X, ld);
-  if (p == Prec::TF32)
-    split_rows_kernel<true><<<grid, 256, 0, s>>>(X, rows, cols, ld, vec, amax, planes, pitch);
-  else
-    split_rows_kernel<false><<<grid, 256, 0, s>>>(X, rows, cols, ld, vec, amax, planes, pitch);
-  return cudaGetLastError();
-}
-
-cudaError_t split_cols_launch(Prec p, const float* X, int64_t K, int64_t N, int64_t ld,
-                              const unsigned* amax, void* planes, int64_t pitch, cudaStream_t s) {
-  const dim3 grid(static_cast<unsigned>((N + 63) / 64), static_cast<unsigned>((pitch + 63) / 64));
-  if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-  const bool vec = vec_ok(X, ld);
-  if (p == Prec::TF32)
-    split_cols_kernel<true><<<grid, 256, 0, s>>>(X, K, N, ld, vec, amax, planes, pitch);
-  else
-    split_cols_kernel<false><<<grid, 256, 0, s>>>(X, K, N, ld, vec, amax, planes, pitch);
-  return cudaGetLastError();
-}
-
-cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const GroupedPtrs* ptrs,
-                                const int* absmax_prefix, int absmax_total, const int* split_prefix,
-                                int split_total, int G, int sms, cudaStream_t s) {
-  const int ga = absmax_total < sms * 8 ? absmax_total : sms * 8;
-  const int gs = split_total < sms * 8 ? split_total : sms * 8;
-  const size_t dyn = (G + 1) <= 4096 ? (size_t)(G + 1) * sizeof(int) : 0;
-  if (ga > 0) grouped_absmax_kernel<<<ga, 256, dyn, s>>>(probs, ptrs, absmax_prefix, G);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (gs > 0) {
-    if (p == Prec::TF32)
-      grouped_split_kernel<true><<<gs, 256, dyn, s>>>(probs, ptrs, split_prefix, G);
-    else
-      grouped_split_kernel<false><<<gs, 256, dyn, s>>>(probs, ptrs, split_prefix, G);
+cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const GroupedPtrs* ptrs,
+                                const int* first_prefix, int first_total, const int* rescale_prefix,
+                                int rescale_total, int G, int sms, cudaStream_t s) {
+  const size_t dyn = (G + 1) <= 4096 ? static_cast<size_t>(G + 1) * sizeof(int) : 0;
+  if (first_total == 0) return cudaSuccess;
+  const int gf = grid_for(first_total, sms), gr = grid_for(rescale_total, sms);
+  if (prec == Prec::TF32) {
+    grouped_pack_kernel<true, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    grouped_pack_kernel<true, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G);
+  } else {
+    grouped_pack_kernel<false, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    grouped_pack_kernel<false, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G);
   }
   return cudaGetLastError();
 }

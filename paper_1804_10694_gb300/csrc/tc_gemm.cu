@@ -34,18 +34,19 @@
 namespace gb {
 
 // Tile and pipeline geometry of one kernel variant.  A k-chunk is one
-// swizzle span of every row: 128 bytes (BN 64 / 128) or 64 bytes (BN 256,
-// so that four stages of the wider B tile still fit in shared memory).
-// Tile width 256 uses two epilogue warpgroups, each folding and storing 128
-// of the columns, so that a thread's FP32 row fragment stays at 128 values.
+// swizzle span of every row, 128 bytes (the 64-byte swizzle also works,
+// sdesc_k<64>, but measured 25 % slower for BN 256 on GB300: 1.2 vs 1.6
+// PFLOP/s).  Tile width 256 uses two epilogue warpgroups, each folding and
+// storing 128 of the columns, so that a thread's FP32 row fragment stays at
+// 128 values; its 96 KB stages leave room for a 2-deep ring.
 template <int BN, bool TF32>
 struct TcCfg {
   static constexpr int BM = 128;
-  static constexpr int SW = BN == 256 ? 64 : 128;      // bytes of one row per k-chunk
+  static constexpr int SW = 128;                       // bytes of one row per k-chunk
   static constexpr int A_PLANE = BM * SW;
   static constexpr int B_PLANE = BN * SW;
   static constexpr int STAGE = 2 * A_PLANE + 2 * B_PLANE;
-  static constexpr int STAGES = BN == 128 ? 3 : 4;
+  static constexpr int STAGES = BN == 64 ? 4 : BN == 128 ? 3 : 2;
   static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
   static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
   static constexpr int EPI_WG = BN == 256 ? 2 : 1;     // epilogue warpgroups
@@ -465,7 +466,10 @@ int tc_smem_bytes(int bn, Prec prec) {
   return bn == 64 ? TcCfg<64, false>::SMEM : bn == 128 ? TcCfg<128, false>::SMEM : TcCfg<256, false>::SMEM;
 }
 
-int tc_chunk_bytes(int bn) { return bn == 256 ? 64 : 128; }
+int tc_chunk_bytes(int bn) {
+  (void)bn;   // every variant steps in 128-byte chunks (see TcCfg)
+  return 128;
+}
 
 // The dynamic shared memory limit of every kernel variant is raised once per
 // device and thread, outside any stream capture: plans call tc_prepare when

@@ -56,10 +56,14 @@ def test_round_tf32_matches_textbook_rounding_on_normals():
 
 
 def test_block_exponent_closed_forms():
-    assert split.block_exponent(1.0) == 0
-    assert split.block_exponent(0.75) == -1
-    assert split.block_exponent(8.0) == 3
-    assert split.block_exponent(15.99) == 3
+    # inside the safe range [2^-48, 2^48): no scaling
+    for v in (1.0, 0.75, 8.0, 15.99, 2.0 ** -48, 2.0 ** 48 * 0.99):
+        assert split.block_exponent(v) == 0
+    # outside: floor(log2 max), clamped to [-126, 126]
+    assert split.block_exponent(2.0 ** 48) == 48
+    assert split.block_exponent(2.0 ** -49) == -49
+    assert split.block_exponent(3.0 * 2.0 ** 60) == 61
+    assert split.block_exponent(0.7 * 2.0 ** -100) == -101
     assert split.block_exponent(2.0 ** -130) == -126
     assert split.block_exponent(2.0 ** -126) == -126
     assert split.block_exponent(3.0e38) == 126
@@ -73,7 +77,7 @@ def test_split_reconstructs_within_bound(prec, bits):
     X = W.uniform(300, 77, 9)
     hi, lo, exps = split.split_rows(X, 300, 77, prec)
     assert exps.shape == (3,)
-    assert (exps == -1).all() or (exps == 0).all() or set(exps) <= {-1, 0}
+    assert (exps == 0).all()
     x = X.astype(np.float64)
     s = np.repeat(np.ldexp(1.0, -exps.astype(np.int64)), 128)[:300, None]
     xs = x * s
@@ -94,8 +98,19 @@ def test_split_of_integers_has_zero_low_part():
     for prec in ("bf16", "tf32"):
         hi, lo, exps = split.split_rows(X, 256, 40, prec)
         assert (lo == 0).all()
-        assert np.array_equal(hi * np.float32(8.0), X)      # max |x| = 8 -> e = 3
-        assert (exps == 3).all()
+        assert np.array_equal(hi, X)          # max |x| = 8 is in the safe range: e = 0
+        assert (exps == 0).all()
+
+
+def test_split_scaling_changes_nothing_in_the_safe_range():
+    # a block near 2^60 (outside the safe range) is scaled by its exponent
+    # 2^-59 and splits into exactly the planes of the unscaled block times 2
+    X = W.uniform(128, 64, 10)
+    hi0, lo0, e0 = split.split_rows(X, 128, 64, "bf16")
+    big = W.scaled(X, 60)
+    hi1, lo1, e1 = split.split_rows(big, 128, 64, "bf16")
+    assert e0[0] == 0 and e1[0] == 59
+    assert np.array_equal(hi1, hi0 * np.float32(2.0)) and np.array_equal(lo1, lo0 * np.float32(2.0))
 
 
 def test_split_scaling_prevents_underflow_of_low_part():
