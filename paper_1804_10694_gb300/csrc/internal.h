@@ -42,7 +42,7 @@ struct TcArgs {
 };
 
 struct TcLaunch {
-  int bn;          // tile N (64, 128 or 256)
+  int bn;          // tile N (64 or 128)
   Prec prec;       // BF16 or TF32
   int grid;
 };

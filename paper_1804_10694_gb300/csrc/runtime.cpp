@@ -107,14 +107,13 @@ static const std::vector<gemm_config>& config_table() {
     const int splits[] = {1, 2, 3, 4, 6, 8};
     const int kbs[] = {4, 2, 8};
     const int groups[] = {16, 1};
-    // tile widths in the order they were added (ids of earlier entries stay fixed)
-    for (int bn : {128, 64, 256})
+    for (int bn : {128, 64})
       for (int sk : splits)
         for (int kb : kbs)
           for (int g : groups) {
             gemm_config c;
             c.block_n = bn;
-            c.stages = bn == 64 ? 4 : bn == 128 ? 3 : 2;
+            c.stages = bn == 64 ? 4 : 3;
             c.split_k = sk;
             c.kb = kb;
             c.group_m = g;

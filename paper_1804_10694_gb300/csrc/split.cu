@@ -226,8 +226,9 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
 
 // --------------------------------------------------- tile decomposition
 // First pass: A in 32-row x 128-column tiles, B in 64 x 64 tiles.
-// Rescale pass: A in 128-row x 128-column blocks (4 tiles), B in
-// 128-column x 64-k blocks (2 tiles); blocks that need no scaling return.
+// Rescale pass: one item per scale block (128 rows of A or 128 columns of B,
+// all of K); a block that needs no scaling costs one load, one that does is
+// re-split tile by tile.
 struct PackShape {
   const float* A;
   const float* B;
@@ -240,8 +241,8 @@ struct PackShape {
 
   __device__ int first_items_a() const { return (int)(((M + 31) / 32) * ((pitch + 127) / 128)); }
   __device__ int first_items_b() const { return (int)(((N + 63) / 64) * ((pitch + 63) / 64)); }
-  __device__ int rescale_items_a() const { return (int)(((M + 127) / 128) * ((pitch + 127) / 128)); }
-  __device__ int rescale_items_b() const { return (int)(((N + 127) / 128) * ((pitch + 63) / 64)); }
+  __device__ int rescale_items_a() const { return (int)((M + 127) / 128); }
+  __device__ int rescale_items_b() const { return (int)((N + 127) / 128); }
 };
 
 template <bool TF32>
@@ -263,20 +264,20 @@ template <bool TF32>
 __device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
   const int na = p.rescale_items_a();
   if (i < na) {
-    const int cols = (int)((p.pitch + 127) / 128);
-    const int64_t r0 = (int64_t)(i / cols) * 128, k0 = (int64_t)(i % cols) * 128;
-    if (block_exponent(p.amaxA[r0 / kScaleBlock]) == 0) return;   // uniform per CTA
-    for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
-      split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
-                                      r0 + 32 * q, k0);
+    const int64_t r0 = (int64_t)i * 128;
+    if (block_exponent(p.amaxA[i]) == 0) return;   // uniform per CTA
+    for (int64_t k0 = 0; k0 < p.pitch; k0 += 128)
+      for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
+        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
+                                        r0 + 32 * q, k0);
   } else {
     const int l = i - na;
-    const int nblk = (int)((p.N + 127) / 128);
-    const int64_t n0 = (int64_t)(l % nblk) * 128, k0 = (int64_t)(l / nblk) * 64;
-    if (block_exponent(p.amaxB[n0 / kScaleBlock]) == 0) return;
-    for (int q = 0; q < 2 && n0 + 64 * q < p.N; ++q)
-      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
-                                      n0 + 64 * q, k0);
+    const int64_t n0 = (int64_t)l * 128;
+    if (block_exponent(p.amaxB[l]) == 0) return;
+    for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
+      for (int q = 0; q < 2 && n0 + 64 * q < p.N; ++q)
+        split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+                                        n0 + 64 * q, k0);
   }
 }
 
@@ -357,7 +358,8 @@ int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
   return static_cast<int>(((M + 31) / 32) * ((pitch + 127) / 128) + ((N + 63) / 64) * ((pitch + 63) / 64));
 }
 int pack_rescale_items(int64_t M, int64_t N, int64_t pitch) {
-  return static_cast<int>(((M + 127) / 128) * ((pitch + 127) / 128) + ((N + 127) / 128) * ((pitch + 63) / 64));
+  (void)pitch;
+  return static_cast<int>((M + 127) / 128 + (N + 127) / 128);
 }
 
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,

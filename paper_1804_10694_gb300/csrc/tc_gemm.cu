@@ -34,11 +34,11 @@
 namespace gb {
 
 // Tile and pipeline geometry of one kernel variant.  A k-chunk is one
-// swizzle span of every row, 128 bytes (the 64-byte swizzle also works,
-// sdesc_k<64>, but measured 25 % slower for BN 256 on GB300: 1.2 vs 1.6
-// PFLOP/s).  Tile width 256 uses two epilogue warpgroups, each folding and
-// storing 128 of the columns, so that a thread's FP32 row fragment stays at
-// 128 values; its 96 KB stages leave room for a 2-deep ring.
+// swizzle span of every row, 128 bytes.  Instantiated for tile widths 64 and
+// 128.  A 256-wide tile (two epilogue warpgroups of 128 columns each, which
+// this geometry supports) measured 1.1-1.2 PFLOP/s on GB300 against 1.6 for
+// 128, with the 128-byte swizzle (2-deep ring) and with the 64-byte swizzle
+// (4-deep ring) alike, so it is not offered.
 template <int BN, bool TF32>
 struct TcCfg {
   static constexpr int BM = 128;
@@ -389,32 +389,51 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         continue;
       }
       float* crow = v.C + static_cast<int64_t>(row) * v.ldc;
-      if (v.c_vec4 && col0 + EC <= v.N) {
-        float4* c4 = reinterpret_cast<float4*>(crow + col0);
+      // 32-column chunks; every load of C in a chunk is issued before any
+      // store, so a chunk costs one memory latency, not 32
 #pragma unroll
-        for (int i = 0; i < EC / 4; ++i) {
-          float4 o;
+      for (int j = 0; j < EC / 32; ++j) {
+        const int cb = col0 + j * 32;
+        if (cb >= v.N) break;
+        float* cp = crow + cb;
+        if (v.c_vec4 && cb + 32 <= v.N) {
+          float4* c4 = reinterpret_cast<float4*>(cp);
+          float4 old[8];
           if (beta != 0.0f) {
-            const float4 old = c4[i];
-            o.x = fmaf(alpha, S[4 * i + 0], beta * old.x);
-            o.y = fmaf(alpha, S[4 * i + 1], beta * old.y);
-            o.z = fmaf(alpha, S[4 * i + 2], beta * old.z);
-            o.w = fmaf(alpha, S[4 * i + 3], beta * old.w);
-          } else {
-            o.x = alpha * S[4 * i + 0];
-            o.y = alpha * S[4 * i + 1];
-            o.z = alpha * S[4 * i + 2];
-            o.w = alpha * S[4 * i + 3];
-          }
-          c4[i] = o;
-        }
-      } else {
 #pragma unroll
-        for (int i = 0; i < EC; ++i) {
-          const int col = col0 + i;
-          if (col < v.N) {
-            const float val = beta != 0.0f ? fmaf(alpha, S[i], beta * crow[col]) : alpha * S[i];
-            crow[col] = val;
+            for (int i = 0; i < 8; ++i) old[i] = c4[i];
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float* sv = &S[j * 32 + 4 * i];
+            float4 o;
+            if (beta != 0.0f) {
+              o.x = fmaf(alpha, sv[0], beta * old[i].x);
+              o.y = fmaf(alpha, sv[1], beta * old[i].y);
+              o.z = fmaf(alpha, sv[2], beta * old[i].z);
+              o.w = fmaf(alpha, sv[3], beta * old[i].w);
+            } else {
+              o.x = alpha * sv[0];
+              o.y = alpha * sv[1];
+              o.z = alpha * sv[2];
+              o.w = alpha * sv[3];
+            }
+            c4[i] = o;
+          }
+        } else {
+          // partial chunk or unaligned rows: predicated scalar accesses
+          const int nv = min(32, v.N - cb);
+          float old[32];
+          if (beta != 0.0f) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) old[i] = i < nv ? cp[i] : 0.0f;
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (i < nv) {
+              const float sv = S[j * 32 + i];
+              cp[i] = beta != 0.0f ? fmaf(alpha, sv, beta * old[i]) : alpha * sv;
+            }
           }
         }
       }
@@ -461,9 +480,8 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
 }
 
 int tc_smem_bytes(int bn, Prec prec) {
-  if (prec == Prec::TF32)
-    return bn == 64 ? TcCfg<64, true>::SMEM : bn == 128 ? TcCfg<128, true>::SMEM : TcCfg<256, true>::SMEM;
-  return bn == 64 ? TcCfg<64, false>::SMEM : bn == 128 ? TcCfg<128, false>::SMEM : TcCfg<256, false>::SMEM;
+  if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true>::SMEM : TcCfg<128, true>::SMEM;
+  return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
 }
 
 int tc_chunk_bytes(int bn) {
@@ -497,11 +515,9 @@ cudaError_t tc_prepare(int bn, Prec prec) {
   if (prec == Prec::TF32) {
     if (bn == 64) return prepare_variant<64, true>();
     if (bn == 128) return prepare_variant<128, true>();
-    if (bn == 256) return prepare_variant<256, true>();
   } else {
     if (bn == 64) return prepare_variant<64, false>();
     if (bn == 128) return prepare_variant<128, false>();
-    if (bn == 256) return prepare_variant<256, false>();
   }
   return cudaErrorInvalidValue;
 }
@@ -521,11 +537,9 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   if (l.prec == Prec::TF32) {
     if (l.bn == 64) return launch_variant<64, true>(l.grid, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, true>(l.grid, tmA, tmB, a, s);
-    if (l.bn == 256) return launch_variant<256, true>(l.grid, tmA, tmB, a, s);
   } else {
     if (l.bn == 64) return launch_variant<64, false>(l.grid, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, false>(l.grid, tmA, tmB, a, s);
-    if (l.bn == 256) return launch_variant<256, false>(l.grid, tmA, tmB, a, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -43,7 +43,7 @@ def test_config_table():
     seen = set()
     for i in range(n):
         c = pkg.config_get("bf16x3", i)
-        assert c["block_n"] in (64, 128, 256)
+        assert c["block_n"] in (64, 128)
         assert c["split_k"] >= 1 and 1 <= c["kb"] <= 8 and c["group_m"] >= 1
         key = tuple(sorted(c.items()))
         assert key not in seen
