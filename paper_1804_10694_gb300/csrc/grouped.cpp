@@ -106,8 +106,6 @@ gemm_status upload_ptrs(gemm_grouped_plan_t p, const float* alpha, const float* 
     q.C = C[i];
     q.alpha = alpha[i];
     q.beta = beta[i];
-    q.c_vec4 = (p->ldc[i] % 4 == 0) && (reinterpret_cast<uintptr_t>(C[i]) % 16 == 0);
-    q.pad = 0;
     if (p->M[i] > 0 && p->N[i] > 0) {
       if (!C[i]) return fail(GEMM_ERR_INVALID_ARG, "null C for problem %d", i);
       if (p->K[i] > 0 && alpha[i] != 0.0f && (!A[i] || !B[i]))

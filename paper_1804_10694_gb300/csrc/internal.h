@@ -34,7 +34,6 @@ struct TcArgs {
   float alpha, beta;
   float* C;
   int64_t ldc;
-  int c_vec4;    // C base 16-byte aligned and ldc % 4 == 0
   const unsigned* amaxA;   // per 128-row block of A: bit pattern of max |a|
   const unsigned* amaxB;   // per 128-column block of B
   float* partial;          // split-K partial sums [split][M][N], null when split_k == 1
@@ -104,8 +103,6 @@ struct GroupedPtrs {
   const float* B;
   float* C;
   float alpha, beta;
-  int c_vec4;
-  int pad;
 };
 
 // One output tile of a grouped launch, precomputed on the host so that a CTA

@@ -181,7 +181,6 @@ extern "C" gemm_status gemm_f32_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, 
   a.beta = beta;
   a.C = C;
   a.ldc = ldc;
-  a.c_vec4 = (ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
   a.amaxA = amaxA;
   a.amaxB = amaxB;
   a.partial = nullptr;

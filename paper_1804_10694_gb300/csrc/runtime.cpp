@@ -359,7 +359,6 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.alpha = alpha;
   a.beta = beta;
   a.C = C;
-  a.c_vec4 = (p->ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
   if (prof) cudaEventRecord(ev[1], s);
   if ((e = tc_gemm_launch(p->launch, p->tmA, p->tmB, a, s)) != cudaSuccess)
     return cuda_fail(e, "tensor-core gemm launch");

@@ -76,9 +76,12 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
 }
 
 // --------------------------------------------------------- A: row-major split
-// One CTA (256 threads) writes a 32-row x 128-column tile of the planes
-// (columns of the padded pitch, k in [K, pitch) gets 0); each thread handles
-// 4 quads of 4 consecutive k.  The 32 rows lie in one 128-row block.
+// One CTA (256 threads, 8 warps) writes a 32-row x 256-column tile of the
+// planes (columns of the padded pitch; k in [K, pitch) gets 0).  Thread
+// (warp w, lane l) covers rows w, w+8, w+16, w+24 and the quads at columns
+// 4l and 4l + 128: its eight loads are issued before any use, so that enough
+// bytes are in flight to cover memory latency.  The 32 rows lie in one
+// 128-row block.
 template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
@@ -86,135 +89,151 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
                                                 void* __restrict__ planes, int64_t pitch,
                                                 int64_t r0, int64_t k0) {
   const int64_t plane = rows * pitch;
-  const int t = threadIdx.x;
-  const int kq = (t & 31) * 4;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[r0 / kScaleBlock]));
-  unsigned m = 0;
-  for (int rr = t >> 5; rr < 32; rr += 8) {
-    const int64_t r = r0 + rr;
-    const int64_t k = k0 + kq;
-    if (r >= rows || k >= pitch) continue;
-    float v[4];
-    const float* p = X + r * ld + k;
-    if (vec && k + 3 < cols) {
-      const float4 q = *reinterpret_cast<const float4*>(p);
-      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-    } else {
+  float v[4][2][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = (k + i < cols) ? p[i] : 0.0f;
-    }
-    if (PASS == kFirst) {
+  for (int i = 0; i < 4; ++i) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) m = max(m, abs_bits(v[i]));
-    }
-    const int64_t o = r * pitch + k;
-    if (TF32) {
-      float* P = static_cast<float*>(planes);
-      float4 h, l;
-      split_tf32(v[0] * sc, h.x, l.x);
-      split_tf32(v[1] * sc, h.y, l.y);
-      split_tf32(v[2] * sc, h.z, l.z);
-      split_tf32(v[3] * sc, h.w, l.w);
-      *reinterpret_cast<float4*>(P + o) = h;
-      *reinterpret_cast<float4*>(P + plane + o) = l;
-    } else {
-      __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-      __align__(8) __nv_bfloat16 h[4], l[4];
+    for (int c = 0; c < 2; ++c) {
+      const int64_t r = r0 + w + 8 * i;
+      const int64_t k = k0 + 128 * c + 4 * lane;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const HiLoBf16 s = split_bf16(v[i] * sc);
-        h[i] = s.hi;
-        l[i] = s.lo;
+      for (int j = 0; j < 4; ++j) v[i][c][j] = 0.0f;
+      if (r >= rows || k >= cols) continue;
+      const float* p = X + r * ld + k;
+      if (vec && k + 3 < cols) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[i][c][0] = q.x, v[i][c][1] = q.y, v[i][c][2] = q.z, v[i][c][3] = q.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (k + j < cols) v[i][c][j] = p[j];
       }
-      *reinterpret_cast<uint2*>(P + o) = *reinterpret_cast<const uint2*>(h);
-      *reinterpret_cast<uint2*>(P + plane + o) = *reinterpret_cast<const uint2*>(l);
+    }
+  }
+  unsigned m = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int64_t r = r0 + w + 8 * i;
+      const int64_t k = k0 + 128 * c + 4 * lane;
+      if (r >= rows || k >= pitch) continue;
+      const float* x = v[i][c];
+      if (PASS == kFirst) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m = max(m, abs_bits(x[j]));
+      }
+      const int64_t o = r * pitch + k;
+      if (TF32) {
+        float* P = static_cast<float*>(planes);
+        float4 h, l;
+        split_tf32(x[0] * sc, h.x, l.x);
+        split_tf32(x[1] * sc, h.y, l.y);
+        split_tf32(x[2] * sc, h.z, l.z);
+        split_tf32(x[3] * sc, h.w, l.w);
+        *reinterpret_cast<float4*>(P + o) = h;
+        *reinterpret_cast<float4*>(P + plane + o) = l;
+      } else {
+        __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+        __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const HiLoBf16 s = split_bf16(x[j] * sc);
+          h[j] = s.hi;
+          l[j] = s.lo;
+        }
+        *reinterpret_cast<uint2*>(P + o) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(P + plane + o) = *reinterpret_cast<const uint2*>(l);
+      }
     }
   }
   if (PASS == kFirst) fold_block_max(m, amax + r0 / kScaleBlock);
 }
 
 // ---------------------------------------------------- B: transposing split
-// One CTA handles a 64 (k) x 64 (n) tile: coalesced loads along n into shared
-// memory, then each thread writes 16 consecutive k of one output row n.  The
-// 64 columns lie in one 128-column block.
+// One CTA handles a 64 (k) x 128 (n) tile.  Load phase: warp w reads k-rows
+// w + 8i (i < 8), each lane a float4 of n (512 contiguous bytes per warp and
+// row); all eight loads are issued first, then stored to a shared tile whose
+// 132-float pitch keeps both phases free of bank conflicts.  Write phase:
+// thread t writes 32 consecutive k of output row n = t % 128 (k half t / 128).
+// The 128 columns are one 128-column block.
+constexpr int kColTilePitch = 132;
+
 template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
                                                 int64_t ld, bool vec, unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t pitch,
                                                 int64_t n0, int64_t k0) {
-  __shared__ float tile[64][65];
-  const int t = threadIdx.x;
+  __shared__ __align__(16) float tile[64 * kColTilePitch];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned m = 0;
   {
-    const int cn = (t & 15) * 4;
-    for (int kr = t >> 4; kr < 64; kr += 16) {
-      const int64_t k = k0 + kr;
-      float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (k < K) {
-        const float* p = X + k * ld + n0 + cn;
-        if (vec && n0 + cn + 3 < N) {
-          const float4 q = *reinterpret_cast<const float4*>(p);
-          v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-        } else {
+    const int64_t n = n0 + 4 * lane;
+    float4 v[8];
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (n0 + cn + i < N) v[i] = p[i];
-        }
+    for (int i = 0; i < 8; ++i) {
+      const int64_t k = k0 + w + 8 * i;
+      v[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (k >= K || n >= N) continue;
+      const float* p = X + k * ld + n;
+      if (vec && n + 3 < N) {
+        v[i] = *reinterpret_cast<const float4*>(p);
+      } else {
+        v[i].x = p[0];
+        if (n + 1 < N) v[i].y = p[1];
+        if (n + 2 < N) v[i].z = p[2];
+        if (n + 3 < N) v[i].w = p[3];
       }
+    }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        tile[kr][cn + i] = v[i];
-        if (PASS == kFirst) m = max(m, abs_bits(v[i]));
+    for (int i = 0; i < 8; ++i) {
+      *reinterpret_cast<float4*>(&tile[(w + 8 * i) * kColTilePitch + 4 * lane]) = v[i];
+      if (PASS == kFirst) {
+        m = max(m, abs_bits(v[i].x));
+        m = max(m, abs_bits(v[i].y));
+        m = max(m, abs_bits(v[i].z));
+        m = max(m, abs_bits(v[i].w));
       }
     }
   }
   __syncthreads();
-  const int nl = t >> 2;              // 0..63
-  const int kl = (t & 3) * 16;        // 0, 16, 32, 48
+  const int nl = threadIdx.x & 127;
+  const int kl = (threadIdx.x >> 7) * 32;
   const int64_t n = n0 + nl;
   if (n < N && k0 + kl < pitch) {
     const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[n / kScaleBlock]));
     const int64_t plane = N * pitch;
     const int64_t obase = n * pitch + k0 + kl;
-    const bool whole = k0 + kl + 16 <= pitch;
+    const int64_t avail = pitch - (k0 + kl);   // multiple of 8 (bf16) or 4 (tf32)
     if (TF32) {
       float* P = static_cast<float*>(planes);
-      float h[16], l[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) split_tf32(tile[kl + i][nl] * sc, h[i], l[i]);
-      if (whole) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-          *reinterpret_cast<float4*>(P + obase + i) = make_float4(h[i], h[i + 1], h[i + 2], h[i + 3]);
-          *reinterpret_cast<float4*>(P + plane + obase + i) =
-              make_float4(l[i], l[i + 1], l[i + 2], l[i + 3]);
-        }
-      } else {
-        for (int i = 0; i < 16 && k0 + kl + i < pitch; ++i) {
-          P[obase + i] = h[i];
-          P[plane + obase + i] = l[i];
-        }
+      for (int g = 0; g < 8; ++g) {
+        if (4 * g >= avail) break;
+        float4 h, l;
+        split_tf32(tile[(kl + 4 * g + 0) * kColTilePitch + nl] * sc, h.x, l.x);
+        split_tf32(tile[(kl + 4 * g + 1) * kColTilePitch + nl] * sc, h.y, l.y);
+        split_tf32(tile[(kl + 4 * g + 2) * kColTilePitch + nl] * sc, h.z, l.z);
+        split_tf32(tile[(kl + 4 * g + 3) * kColTilePitch + nl] * sc, h.w, l.w);
+        *reinterpret_cast<float4*>(P + obase + 4 * g) = h;
+        *reinterpret_cast<float4*>(P + plane + obase + 4 * g) = l;
       }
     } else {
       __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-      __align__(16) __nv_bfloat16 h[16], l[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const HiLoBf16 s = split_bf16(tile[kl + i][nl] * sc);
-        h[i] = s.hi;
-        l[i] = s.lo;
-      }
-      if (whole) {
-        *reinterpret_cast<uint4*>(P + obase) = *reinterpret_cast<const uint4*>(h);
-        *reinterpret_cast<uint4*>(P + obase + 8) = *reinterpret_cast<const uint4*>(h + 8);
-        *reinterpret_cast<uint4*>(P + plane + obase) = *reinterpret_cast<const uint4*>(l);
-        *reinterpret_cast<uint4*>(P + plane + obase + 8) = *reinterpret_cast<const uint4*>(l + 8);
-      } else {
-        // pitch is a multiple of 8 elements: write whole 8-element groups
-        for (int i = 0; i < 16 && k0 + kl + i < pitch; i += 8) {
-          *reinterpret_cast<uint4*>(P + obase + i) = *reinterpret_cast<const uint4*>(h + i);
-          *reinterpret_cast<uint4*>(P + plane + obase + i) = *reinterpret_cast<const uint4*>(l + i);
+      for (int g = 0; g < 4; ++g) {
+        if (8 * g >= avail) break;
+        __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const HiLoBf16 s = split_bf16(tile[(kl + 8 * g + i) * kColTilePitch + nl] * sc);
+          h[i] = s.hi;
+          l[i] = s.lo;
         }
+        *reinterpret_cast<uint4*>(P + obase + 8 * g) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(P + plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(l);
       }
     }
   }
@@ -225,7 +244,7 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
 }
 
 // --------------------------------------------------- tile decomposition
-// First pass: A in 32-row x 128-column tiles, B in 64 x 64 tiles.
+// First pass: A in 32-row x 256-column tiles, B in 64-k x 128-column tiles.
 // Rescale pass: one item per scale block (128 rows of A or 128 columns of B,
 // all of K); a block that needs no scaling costs one load, one that does is
 // re-split tile by tile.
@@ -239,8 +258,8 @@ struct PackShape {
   void* planesA;
   void* planesB;
 
-  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * ((pitch + 127) / 128)); }
-  __device__ int first_items_b() const { return (int)(((N + 63) / 64) * ((pitch + 63) / 64)); }
+  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * ((pitch + 255) / 256)); }
+  __device__ int first_items_b() const { return (int)(((N + 127) / 128) * ((pitch + 63) / 64)); }
   __device__ int rescale_items_a() const { return (int)((M + 127) / 128); }
   __device__ int rescale_items_b() const { return (int)((N + 127) / 128); }
 };
@@ -249,14 +268,14 @@ template <bool TF32>
 __device__ __forceinline__ void first_item(const PackShape& p, int i) {
   const int na = p.first_items_a();
   if (i < na) {
-    const int cols = (int)((p.pitch + 127) / 128);
+    const int cols = (int)((p.pitch + 255) / 256);
     split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
-                                  (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 128);
+                                  (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
   } else {
     const int l = i - na;
-    const int ncols = (int)((p.N + 63) / 64);
+    const int ncols = (int)((p.N + 127) / 128);
     split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
-                                  (int64_t)(l % ncols) * 64, (int64_t)(l / ncols) * 64);
+                                  (int64_t)(l % ncols) * 128, (int64_t)(l / ncols) * 64);
   }
 }
 
@@ -266,7 +285,7 @@ __device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
   if (i < na) {
     const int64_t r0 = (int64_t)i * 128;
     if (block_exponent(p.amaxA[i]) == 0) return;   // uniform per CTA
-    for (int64_t k0 = 0; k0 < p.pitch; k0 += 128)
+    for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
       for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
         split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
                                         r0 + 32 * q, k0);
@@ -275,9 +294,8 @@ __device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
     const int64_t n0 = (int64_t)l * 128;
     if (block_exponent(p.amaxB[l]) == 0) return;
     for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-      for (int q = 0; q < 2 && n0 + 64 * q < p.N; ++q)
-        split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
-                                        n0 + 64 * q, k0);
+      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+                                      n0, k0);
   }
 }
 
@@ -355,7 +373,7 @@ int grid_for(int64_t items, int sms) {
 
 // Items per problem of the two pack passes (host side, same tiling as above).
 int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
-  return static_cast<int>(((M + 31) / 32) * ((pitch + 127) / 128) + ((N + 63) / 64) * ((pitch + 63) / 64));
+  return static_cast<int>(((M + 31) / 32) * ((pitch + 255) / 256) + ((N + 127) / 128) * ((pitch + 63) / 64));
 }
 int pack_rescale_items(int64_t M, int64_t N, int64_t pitch) {
   (void)pitch;

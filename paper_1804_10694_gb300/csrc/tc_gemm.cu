@@ -52,10 +52,12 @@ struct TcCfg {
   static constexpr int EPI_WG = BN == 256 ? 2 : 1;     // epilogue warpgroups
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int TMEM_COLS = 2 * BN;             // two accumulator buffers
+  static constexpr int EPI_PITCH = 33;                 // floats per staged row (bank-conflict free)
+  static constexpr int EPI_BYTES = 4 * EPI_WG * 32 * EPI_PITCH * 4;   // one 32x32 buffer per epilogue warp
   static constexpr int BAR_BYTES = 256;
-  static constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+  static constexpr int SMEM = STAGES * STAGE + EPI_BYTES + BAR_BYTES + 1024;
   static constexpr int THREADS = 64 + 128 * EPI_WG;
-  static_assert(STAGES * STAGE + BAR_BYTES + 1024 <= 232448, "shared memory budget");
+  static_assert(SMEM <= 232448, "shared memory budget");
   static_assert(TMEM_COLS <= 512, "tensor memory budget");
 };
 
@@ -75,7 +77,6 @@ struct EpiView {
   const unsigned* amaxB;
   float* partial;
   int split_k;
-  int c_vec4;
 };
 
 __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
@@ -112,7 +113,6 @@ struct SingleSched {
     EpiView v;
     v.M = a->M, v.N = a->N, v.C = a->C, v.ldc = a->ldc, v.alpha = a->alpha, v.beta = a->beta;
     v.amaxA = a->amaxA, v.amaxB = a->amaxB, v.partial = a->partial, v.split_k = a->split_k;
-    v.c_vec4 = a->c_vec4;
     return v;
   }
 };
@@ -145,7 +145,6 @@ struct GroupedSched {
     EpiView v;
     v.M = p.M, v.N = p.N, v.C = q.C, v.ldc = p.ldc, v.alpha = q.alpha, v.beta = q.beta;
     v.amaxA = p.amaxA, v.amaxB = p.amaxB, v.partial = nullptr, v.split_k = 1;
-    v.c_vec4 = q.c_vec4;
     return v;
   }
 };
@@ -163,8 +162,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   const int kb = sc.kb();
 
   // barrier block after the stage ring
-  uint8_t* bar_area = smem + STAGES * Cfg::STAGE;
-  const uint32_t bar0 = sbase + STAGES * Cfg::STAGE;
+  float* epi_buf = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE);
+  uint8_t* bar_area = smem + STAGES * Cfg::STAGE + Cfg::EPI_BYTES;
+  const uint32_t bar0 = sbase + STAGES * Cfg::STAGE + Cfg::EPI_BYTES;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
@@ -317,7 +317,6 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     constexpr int EC = Cfg::EPI_COLS;
     const int q = warp & 3;                 // TMEM lane quadrant of this warp
     const int half = (warp - 2) >> 2;       // column group of this warpgroup
-    const int row_in_tile = q * 32 + lane;
     uint32_t ab = 0, aphase = 0;
     bool ok = true;
     Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
@@ -366,76 +365,58 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
       // applied before the power of two, so that a result in range is not
       // lost to an overflow of the unscaled sum (the power of two is exact).
-      const int row = w.tm * 128 + row_in_tile;
       const int col0 = w.tn * BN + half * EC;
       const int e = block_exponent(v.amaxA[w.tm]) + block_exponent(v.amaxB[col0 / kScaleBlock]);
       float alpha = v.alpha;
-      const float beta = v.beta;
-      if (v.split_k > 1) {
-        // split-K partials carry alpha already (the reduction adds beta*C)
+      float beta = v.beta;
+      if (v.split_k > 1 || e != 0) {
 #pragma unroll
         for (int i = 0; i < EC; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
-      } else if (e != 0) {
-#pragma unroll
-        for (int i = 0; i < EC; ++i) S[i] = scale_pow2(alpha * S[i], e);
         alpha = 1.0f;
       }
-      if (row >= v.M) continue;
+      // destination: C, or this split's partial-sum plane (the reduction
+      // kernel adds beta * C)
+      float* dst = v.C;
+      int64_t ldd = v.ldc;
       if (v.split_k > 1) {
-        float* prow = v.partial + (static_cast<int64_t>(w.ks) * v.M + row) * v.N;
-#pragma unroll
-        for (int i = 0; i < EC; ++i)
-          if (col0 + i < v.N) prow[col0 + i] = S[i];
-        continue;
+        dst = v.partial + static_cast<int64_t>(w.ks) * v.M * v.N;
+        ldd = v.N;
+        beta = 0.0f;
       }
-      float* crow = v.C + static_cast<int64_t>(row) * v.ldc;
-      // 32-column chunks; every load of C in a chunk is issued before any
-      // store, so a chunk costs one memory latency, not 32
+      // Store through shared memory: the warp stages each 32x32 chunk of its
+      // rows (lane = row) in a padded buffer, then walks the chunk one row at
+      // a time (lane = column), so every global load and store of the warp
+      // covers 128 contiguous bytes of one row whatever ldc or alignment.
+      float* buf = epi_buf + (warp - 2) * 32 * Cfg::EPI_PITCH;
+      const int row0 = w.tm * 128 + q * 32;
+      const int nrows = min(32, v.M - row0);
 #pragma unroll
       for (int j = 0; j < EC / 32; ++j) {
         const int cb = col0 + j * 32;
-        if (cb >= v.N) break;
-        float* cp = crow + cb;
-        if (v.c_vec4 && cb + 32 <= v.N) {
-          float4* c4 = reinterpret_cast<float4*>(cp);
-          float4 old[8];
-          if (beta != 0.0f) {
+        if (nrows <= 0 || cb >= v.N) break;   // uniform across the warp
 #pragma unroll
-            for (int i = 0; i < 8; ++i) old[i] = c4[i];
+        for (int i = 0; i < 32; ++i) buf[lane * Cfg::EPI_PITCH + i] = S[j * 32 + i];
+        __syncwarp();
+        const bool col_ok = cb + lane < v.N;
+        float* base = dst + static_cast<int64_t>(row0) * ldd + cb + lane;
+#pragma unroll
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+          float old[8];
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr) {
+            const int r = r0 + rr;
+            old[rr] = (beta != 0.0f && col_ok && r < nrows) ? base[r * ldd] : 0.0f;
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float* sv = &S[j * 32 + 4 * i];
-            float4 o;
-            if (beta != 0.0f) {
-              o.x = fmaf(alpha, sv[0], beta * old[i].x);
-              o.y = fmaf(alpha, sv[1], beta * old[i].y);
-              o.z = fmaf(alpha, sv[2], beta * old[i].z);
-              o.w = fmaf(alpha, sv[3], beta * old[i].w);
-            } else {
-              o.x = alpha * sv[0];
-              o.y = alpha * sv[1];
-              o.z = alpha * sv[2];
-              o.w = alpha * sv[3];
-            }
-            c4[i] = o;
-          }
-        } else {
-          // partial chunk or unaligned rows: predicated scalar accesses
-          const int nv = min(32, v.N - cb);
-          float old[32];
-          if (beta != 0.0f) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) old[i] = i < nv ? cp[i] : 0.0f;
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (i < nv) {
-              const float sv = S[j * 32 + i];
-              cp[i] = beta != 0.0f ? fmaf(alpha, sv, beta * old[i]) : alpha * sv;
+          for (int rr = 0; rr < 8; ++rr) {
+            const int r = r0 + rr;
+            if (col_ok && r < nrows) {
+              const float sv = buf[r * Cfg::EPI_PITCH + lane];
+              base[r * ldd] = beta != 0.0f ? fmaf(alpha, sv, beta * old[rr]) : alpha * sv;
             }
           }
         }
+        __syncwarp();
       }
     }
   }
