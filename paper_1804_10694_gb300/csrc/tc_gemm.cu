@@ -383,17 +383,47 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         ldd = v.N;
         beta = 0.0f;
       }
-      // Store through shared memory: the warp stages each 32x32 chunk of its
-      // rows (lane = row) in a padded buffer, then walks the chunk one row at
-      // a time (lane = column), so every global load and store of the warp
-      // covers 128 contiguous bytes of one row whatever ldc or alignment.
+      // Two store paths, chosen per 32-column chunk and uniform per warp.
+      // Aligned rows and a full chunk: each thread stores its own row with
+      // float4 accesses (C loads of the chunk issued first).  Otherwise
+      // (unaligned ldc, partial chunk or rows): the warp stages the 32x32
+      // chunk of its rows (lane = row) in a padded shared buffer, then walks
+      // it one row at a time (lane = column), so that every global access of
+      // the warp covers 128 contiguous bytes of one row whatever the alignment.
       float* buf = epi_buf + (warp - 2) * 32 * Cfg::EPI_PITCH;
       const int row0 = w.tm * 128 + q * 32;
       const int nrows = min(32, v.M - row0);
+      const bool rows_vec = nrows == 32 && (ldd & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
 #pragma unroll
       for (int j = 0; j < EC / 32; ++j) {
         const int cb = col0 + j * 32;
         if (nrows <= 0 || cb >= v.N) break;   // uniform across the warp
+        if (rows_vec && cb + 32 <= v.N) {
+          float4* c4 = reinterpret_cast<float4*>(dst + static_cast<int64_t>(row0 + lane) * ldd + cb);
+          float4 old[8];
+          if (beta != 0.0f) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) old[i] = c4[i];
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float* sv = &S[j * 32 + 4 * i];
+            float4 o;
+            if (beta != 0.0f) {
+              o.x = fmaf(alpha, sv[0], beta * old[i].x);
+              o.y = fmaf(alpha, sv[1], beta * old[i].y);
+              o.z = fmaf(alpha, sv[2], beta * old[i].z);
+              o.w = fmaf(alpha, sv[3], beta * old[i].w);
+            } else {
+              o.x = alpha * sv[0];
+              o.y = alpha * sv[1];
+              o.z = alpha * sv[2];
+              o.w = alpha * sv[3];
+            }
+            c4[i] = o;
+          }
+          continue;
+        }
 #pragma unroll
         for (int i = 0; i < 32; ++i) buf[lane * Cfg::EPI_PITCH + i] = S[j * 32 + i];
         __syncwarp();
