@@ -25,6 +25,7 @@ constexpr int kScaleBlock = 128;   // rows of A / columns of B sharing one expon
 // --------------------------------------------------- tensor-core kernel args
 struct TcArgs {
   int M, N, K;
+  int tm0;       // first row tile of this launch (a row panel); 0 for the whole matrix
   int tiles_m, tiles_n, num_tiles, num_units;
   int split_k, chunks_total, chunks_per_split;
   int kb;        // k-chunks accumulated in TMEM before the epilogue folds them in
@@ -78,6 +79,13 @@ cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t l
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
                         int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, void* planesA,
                         void* planesB, int64_t pitch, int sms, cudaStream_t s);
+// A row panel alone: rows [0, rows) of the panel starting at A, written to
+// the planes of the whole matrix at planesA (already offset to the panel's
+// first row) with hi-to-lo plane distance plane_stride elements; amaxA points
+// at the panel's first block (the panel starts on a 128-row boundary).
+cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
+                                   unsigned* amaxA, void* planesA, int64_t plane_stride,
+                                   int64_t pitch, int sms, cudaStream_t s);
 // Work items of the two passes for one problem (grouped prefix sums).
 int pack_first_items(int64_t M, int64_t N, int64_t pitch);
 int pack_rescale_items(int64_t M, int64_t N, int64_t pitch);

@@ -436,15 +436,30 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
 }
 
 // ----------------------------------------------------- host-buffer entry
+// gemm_f32_host keeps per-thread device copies of A, B, C and two copy
+// streams.  Large tensor-core problems are pipelined over row panels of A
+// and C: B is copied and packed first, then panel i's copy in (A rows and,
+// when beta != 0, C rows) overlaps panel i-1's pack + gemm, which overlaps
+// panel i-2's copy of C back to the host.
 struct HostBuffers {
   int dev = -1;
   float *A = nullptr, *B = nullptr, *C = nullptr;
   size_t nA = 0, nB = 0, nC = 0;
-  ~HostBuffers() {
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  std::vector<cudaEvent_t> ev;
+  void release() {
     if (A) cudaFree(A);
     if (B) cudaFree(B);
     if (C) cudaFree(C);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (h2d) cudaStreamDestroy(h2d);
+    if (d2h) cudaStreamDestroy(d2h);
+    A = B = C = nullptr;
+    nA = nB = nC = 0;
+    ev.clear();
+    h2d = d2h = nullptr;
   }
+  ~HostBuffers() { release(); }
 };
 static thread_local HostBuffers t_host;
 
@@ -462,6 +477,89 @@ static gemm_status grow(float** p, size_t* cap, size_t n) {
   return GEMM_OK;
 }
 
+static gemm_status host_streams(int nevents) {
+  cudaError_t e;
+  if (!t_host.h2d && (e = cudaStreamCreateWithFlags(&t_host.h2d, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  if (!t_host.d2h && (e = cudaStreamCreateWithFlags(&t_host.d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  while ((int)t_host.ev.size() < nevents) {
+    cudaEvent_t x;
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    t_host.ev.push_back(x);
+  }
+  return GEMM_OK;
+}
+
+// Pipelined path: tensor-core plan without split-K, M spanning >= 2 panels.
+static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, const float* B,
+                                    float beta, float* C, cudaStream_t s) {
+  const int64_t M = p->M, N = p->N, K = p->K, lda = p->lda, ldb = p->ldb, ldc = p->ldc;
+  const int64_t tiles_m = (M + 127) / 128;
+  const int npan = (int)std::min<int64_t>(4, tiles_m);
+  const int64_t tiles_per = (tiles_m + npan - 1) / npan;
+  gemm_status st = host_streams(2 + 2 * npan);
+  if (st != GEMM_OK) return st;
+  cudaEvent_t* ev = t_host.ev.data();
+  cudaError_t e;
+  // the copies start after whatever the caller queued on s
+  if ((e = cudaEventRecord(ev[0], s)) || (e = cudaStreamWaitEvent(t_host.h2d, ev[0], 0)) ||
+      (e = cudaStreamWaitEvent(t_host.d2h, ev[0], 0)))
+    return cuda_fail(e, "stream ordering");
+  const size_t nB = (size_t)(K - 1) * ldb + N;
+  if ((e = cudaMemcpyAsync(t_host.B, B, nB * 4, cudaMemcpyHostToDevice, t_host.h2d)) ||
+      (e = cudaEventRecord(ev[1], t_host.h2d)))
+    return cuda_fail(e, "copy B to device");
+  for (int i = 0; i < npan; ++i) {   // all panel copies in, queued behind B
+    const int64_t r0 = i * tiles_per * 128, r1 = std::min(M, (i + 1) * tiles_per * 128);
+    if (r0 >= r1) break;
+    if ((e = cudaMemcpyAsync(t_host.A + r0 * lda, A + r0 * lda, ((r1 - r0 - 1) * lda + K) * 4,
+                             cudaMemcpyHostToDevice, t_host.h2d)))
+      return cuda_fail(e, "copy A panel to device");
+    if (beta != 0.0f &&
+        (e = cudaMemcpyAsync(t_host.C + r0 * ldc, C + r0 * ldc, ((r1 - r0 - 1) * ldc + N) * 4,
+                             cudaMemcpyHostToDevice, t_host.h2d)))
+      return cuda_fail(e, "copy C panel to device");
+    if ((e = cudaEventRecord(ev[2 + i], t_host.h2d))) return cuda_fail(e, "event");
+  }
+  // B packed once
+  if ((e = cudaStreamWaitEvent(s, ev[1], 0)) ||
+      (e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) ||
+      (e = pack_launch(p->prec, nullptr, 0, K, 1, t_host.B, N, ldb, nullptr, p->amaxB, nullptr,
+                       p->planesB, p->pitch, p->sms, s)))
+    return cuda_fail(e, "pack B");
+  for (int i = 0; i < npan; ++i) {
+    const int64_t t0 = i * tiles_per, t1 = std::min(tiles_m, (i + 1) * tiles_per);
+    if (t0 >= t1) break;
+    const int64_t r0 = t0 * 128, r1 = std::min(M, t1 * 128);
+    if ((e = cudaStreamWaitEvent(s, ev[2 + i], 0)) ||
+        (e = pack_rows_panel_launch(p->prec, t_host.A + r0 * lda, r1 - r0, K, lda, p->amaxA + t0,
+                                    static_cast<char*>(p->planesA) + r0 * p->pitch * prec_elem_bytes(p->prec),
+                                    M * p->pitch, p->pitch, p->sms, s)))
+      return cuda_fail(e, "pack A panel");
+    TcArgs a = p->args;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.C = t_host.C;
+    a.tm0 = (int)t0;
+    a.tiles_m = (int)(t1 - t0);
+    a.num_tiles = a.tiles_m * a.tiles_n;
+    a.num_units = a.num_tiles;   // split_k == 1
+    a.group_m = std::max(1, std::min(a.group_m, a.tiles_m));
+    TcLaunch l = p->launch;
+    l.grid = std::min(a.num_units, p->sms);
+    if ((e = tc_gemm_launch(l, p->tmA, p->tmB, a, s)) || (e = cudaEventRecord(ev[2 + npan + i], s)) ||
+        (e = cudaStreamWaitEvent(t_host.d2h, ev[2 + npan + i], 0)) ||
+        (e = cudaMemcpyAsync(C + r0 * ldc, t_host.C + r0 * ldc, ((r1 - r0 - 1) * ldc + N) * 4,
+                             cudaMemcpyDeviceToHost, t_host.d2h)))
+      return cuda_fail(e, "panel gemm / copy back");
+  }
+  if ((e = cudaStreamSynchronize(t_host.d2h)) || (e = cudaStreamSynchronize(s)))
+    return cuda_fail(e, "synchronize");
+  return GEMM_OK;
+}
+
 gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
                            const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
                            gemm_mode mode, cudaStream_t s) {
@@ -472,8 +570,7 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   int dev = 0;
   cudaGetDevice(&dev);
   if (t_host.dev != dev) {
-    t_host.~HostBuffers();
-    new (&t_host) HostBuffers();
+    t_host.release();
     t_host.dev = dev;
   }
   const bool need_ab = K > 0 && alpha != 0.0f;
@@ -483,6 +580,10 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   if ((st = grow(&t_host.A, &t_host.nA, std::max<size_t>(nA, 1))) != GEMM_OK) return st;
   if ((st = grow(&t_host.B, &t_host.nB, std::max<size_t>(nB, 1))) != GEMM_OK) return st;
   if ((st = grow(&t_host.C, &t_host.nC, nC)) != GEMM_OK) return st;
+  gemm_plan_t p = nullptr;
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
+  if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && M >= 4 * 128)
+    return host_gemm_panels(p, alpha, A, B, beta, C, s);
   cudaError_t e;
   if (need_ab) {
     if ((e = cudaMemcpyAsync(t_host.A, A, nA * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
@@ -494,8 +595,6 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
     if ((e = cudaMemcpyAsync(t_host.C, C, nC * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "copy C to device");
   }
-  gemm_plan_t p = nullptr;
-  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
   if ((st = plan_execute_impl(p, alpha, t_host.A, t_host.B, beta, t_host.C, s)) != GEMM_OK) return st;
   if ((e = cudaMemcpyAsync(C, t_host.C, nC * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "copy C to host");

@@ -86,9 +86,8 @@ template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
                                                 unsigned* __restrict__ amax,
-                                                void* __restrict__ planes, int64_t pitch,
-                                                int64_t r0, int64_t k0) {
-  const int64_t plane = rows * pitch;
+                                                void* __restrict__ planes, int64_t plane,
+                                                int64_t pitch, int64_t r0, int64_t k0) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[r0 / kScaleBlock]));
   float v[4][2][4];
@@ -164,8 +163,8 @@ constexpr int kColTilePitch = 132;
 template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
                                                 int64_t ld, bool vec, unsigned* __restrict__ amax,
-                                                void* __restrict__ planes, int64_t pitch,
-                                                int64_t n0, int64_t k0) {
+                                                void* __restrict__ planes, int64_t plane,
+                                                int64_t pitch, int64_t n0, int64_t k0) {
   __shared__ __align__(16) float tile[64 * kColTilePitch];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned m = 0;
@@ -204,7 +203,6 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
   const int64_t n = n0 + nl;
   if (n < N && k0 + kl < pitch) {
     const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[n / kScaleBlock]));
-    const int64_t plane = N * pitch;
     const int64_t obase = n * pitch + k0 + kl;
     const int64_t avail = pitch - (k0 + kl);   // multiple of 8 (bf16) or 4 (tf32)
     if (TF32) {
@@ -252,6 +250,7 @@ struct PackShape {
   const float* A;
   const float* B;
   int64_t M, N, K, lda, ldb, pitch;
+  int64_t planeA, planeB;   // elements from the hi plane to the lo plane
   bool vecA, vecB;
   unsigned* amaxA;
   unsigned* amaxB;
@@ -269,12 +268,12 @@ __device__ __forceinline__ void first_item(const PackShape& p, int i) {
   const int na = p.first_items_a();
   if (i < na) {
     const int cols = (int)((p.pitch + 255) / 256);
-    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
+    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA, p.pitch,
                                   (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
   } else {
     const int l = i - na;
     const int ncols = (int)((p.N + 127) / 128);
-    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB, p.pitch,
                                   (int64_t)(l % ncols) * 128, (int64_t)(l / ncols) * 64);
   }
 }
@@ -287,14 +286,14 @@ __device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
     if (block_exponent(p.amaxA[i]) == 0) return;   // uniform per CTA
     for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
       for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
-        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.pitch,
+        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA, p.pitch,
                                         r0 + 32 * q, k0);
   } else {
     const int l = i - na;
     const int64_t n0 = (int64_t)l * 128;
     if (block_exponent(p.amaxB[l]) == 0) return;
     for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.pitch,
+      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB, p.pitch,
                                       n0, k0);
   }
 }
@@ -339,6 +338,8 @@ __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, cons
   PackShape p;
   p.A = q.A, p.B = q.B;
   p.M = g.M, p.N = g.N, p.K = g.K, p.lda = g.lda, p.ldb = g.ldb, p.pitch = g.pitch;
+  p.planeA = static_cast<int64_t>(g.M) * g.pitch;
+  p.planeB = static_cast<int64_t>(g.N) * g.pitch;
   p.vecA = (reinterpret_cast<uintptr_t>(q.A) % 16 == 0) && (g.lda % 4 == 0);
   p.vecB = (reinterpret_cast<uintptr_t>(q.B) % 16 == 0) && (g.ldb % 4 == 0);
   p.amaxA = g.amaxA, p.amaxB = g.amaxB;
@@ -386,11 +387,37 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
   PackShape p;
   p.A = A, p.B = B, p.M = A ? M : 0, p.N = B ? N : 0, p.K = K, p.lda = lda, p.ldb = ldb;
   p.pitch = pitch;
+  p.planeA = p.M * pitch;
+  p.planeB = p.N * pitch;
   p.vecA = A && lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
   p.vecB = B && ldb % 4 == 0 && reinterpret_cast<uintptr_t>(B) % 16 == 0;
   p.amaxA = amaxA, p.amaxB = amaxB, p.planesA = planesA, p.planesB = planesB;
   const int64_t first = pack_first_items(p.M, p.N, pitch);
   const int64_t rescale = pack_rescale_items(p.M, p.N, pitch);
+  if (first == 0) return cudaSuccess;
+  if (prec == Prec::TF32) {
+    pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_rescale_kernel<true><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+  } else {
+    pack_first_kernel<false><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_rescale_kernel<false><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
+                                   unsigned* amaxA, void* planesA, int64_t plane_stride,
+                                   int64_t pitch, int sms, cudaStream_t s) {
+  PackShape p;
+  p.A = A, p.B = nullptr, p.M = rows, p.N = 0, p.K = K, p.lda = lda, p.ldb = 1;
+  p.pitch = pitch;
+  p.planeA = plane_stride;
+  p.planeB = 0;
+  p.vecA = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+  p.vecB = false;
+  p.amaxA = amaxA, p.amaxB = nullptr, p.planesA = planesA, p.planesB = nullptr;
+  const int64_t first = pack_first_items(rows, 0, pitch);
+  const int64_t rescale = pack_rescale_items(rows, 0, pitch);
   if (first == 0) return cudaSuccess;
   if (prec == Prec::TF32) {
     pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);

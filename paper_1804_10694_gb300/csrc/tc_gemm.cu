@@ -103,6 +103,7 @@ struct SingleSched {
     w.prob = 0;
     w.ks = u / a->num_tiles;
     raster(t, a->tiles_m, a->tiles_n, a->group_m, w.tm, w.tn);
+    w.tm += a->tm0;
     w.c0 = w.ks * a->chunks_per_split;
     w.c1 = min(w.c0 + a->chunks_per_split, a->chunks_total);
     return w;

@@ -274,3 +274,25 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     A, B = W.uniform(M, K, 1), W.uniform(K, N, 2)
     got = run_gemm("bf16x3", M, N, K, 1.0, A, B, 0.0, np.zeros((M, N), np.float32))
     assert oracle.rel_frob(got, oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("alpha,beta", W.ALPHA_BETA)
+def test_host_buffer_pipelined_panels(mode, alpha, beta):
+    """Host-buffer calls large enough for the row-panel pipeline (B packed
+    once, panels of A and C streamed in and out while others compute)."""
+    M, N, K = 1000, 300, 700
+    A, B, C0 = W.uniform(M, K, 81, ld=K + 5), W.uniform(K, N, 82, ld=N + 3), W.uniform(M, N, 83, ld=N + 1)
+    ref = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
+    C = C0.copy()
+    lib = pkg.load()
+    st = lib.gemm_f32_host(M, N, K, alpha, A.ctypes.data, A.shape[1], B.ctypes.data, B.shape[1],
+                           beta, C.ctypes.data, C.shape[1], pkg.MODES[mode], None)
+    assert st == 0, lib.gemm_last_error()
+    assert oracle.rel_frob(C, ref) <= TOL
+    check_padding_untouched(C0, C, N)
+    # integer inputs stay bit-exact through the pipeline
+    Ai, Bi, Ci = W.integers(M, K, 84), W.integers(K, N, 85), W.integers(M, N, 86)
+    Cg = Ci.copy()
+    pkg.gemm_host(Ai, Bi, Cg, alpha, beta, mode=mode)
+    assert np.array_equal(Cg, oracle.gemm_f64(M, N, K, alpha, Ai, Bi, beta, Ci).astype(np.float32))
