@@ -100,7 +100,12 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
 /* As gemm_f32_ex, but A, B and C are HOST pointers (pageable or pinned): the
  * call copies A, B (and C when beta != 0) to device buffers it keeps per
  * thread, computes, copies C back and synchronizes the stream before
- * returning. */
+ * returning.  Only the M x N (M x K, K x N) elements are copied; padding
+ * beyond a row's length in the host buffers is never written.  With
+ * page-locked A and C, at least 512 rows, no split-K and the environment
+ * variable GEMM_HOST_PANELS (default 8) above 1, B is copied and packed once
+ * and row panels of A and C stream through two copy streams while earlier
+ * panels compute. */
 gemm_status gemm_f32_host(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                           int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                           int64_t ldc, gemm_mode mode, gemm_stream_t stream);

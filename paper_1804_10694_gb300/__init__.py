@@ -247,19 +247,28 @@ class GroupedPlan:
         self._h = h
         self.G = G
 
-    def execute(self, As, Bs, Cs, alphas, betas, stream=None, graph: bool = True):
-        """As, Bs, Cs: sequences of CUDA tensors (or integer device pointers)."""
+    def prepare(self, As, Bs, Cs, alphas, betas):
+        """Marshal the per-problem arguments once (sequences of CUDA tensors
+        or integer device pointers, and scalars); execute() without arguments
+        then reuses them, so that a replay costs one C call."""
         G = self.G
 
         def ptr(x):
             return x if isinstance(x, int) else x.data_ptr()
-        pa = (ctypes.c_void_p * G)(*[ptr(x) for x in As])
-        pb = (ctypes.c_void_p * G)(*[ptr(x) for x in Bs])
-        pc = (ctypes.c_void_p * G)(*[ptr(x) for x in Cs])
-        al = (ctypes.c_float * G)(*[float(a) for a in alphas])
-        be = (ctypes.c_float * G)(*[float(b) for b in betas])
+        self._args = ((ctypes.c_float * G)(*[float(a) for a in alphas]),
+                      (ctypes.c_void_p * G)(*[ptr(x) for x in As]),
+                      (ctypes.c_void_p * G)(*[ptr(x) for x in Bs]),
+                      (ctypes.c_float * G)(*[float(b) for b in betas]),
+                      (ctypes.c_void_p * G)(*[ptr(x) for x in Cs]))
+        return self
+
+    def execute(self, As=None, Bs=None, Cs=None, alphas=None, betas=None, stream=None,
+                graph: bool = True):
+        """Run the group; with no tensors given, the prepared arguments are used."""
+        if As is not None:
+            self.prepare(As, Bs, Cs, alphas, betas)
         fn = self._lib.gemm_grouped_execute if graph else self._lib.gemm_grouped_execute_eager
-        check(fn(self._h, al, pa, pb, be, pc, _stream_handle(stream)))
+        check(fn(self._h, *self._args, _stream_handle(stream)))
 
     def info(self) -> dict:
         bn, kb, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -78,7 +78,8 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   if ((e = cudaMemsetAsync(p->d_amax, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "clear block maxima");
   if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_split_prefix, p->split_total,
-                               p->d_absmax_prefix, p->absmax_total, p->G, p->sms, s)) != cudaSuccess)
+                               p->d_absmax_prefix, p->absmax_total, p->G,
+                               p->d_amax + p->amax_bytes / sizeof(unsigned) - 1, p->sms, s)) != cudaSuccess)
     return cuda_fail(e, "grouped pack launch");
   GroupedArgs a{};
   a.probs = p->d_probs;
@@ -239,7 +240,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     abs_prefix[slot + 1] = abs_prefix[slot] + (pack ? pack_rescale_items(p->M[i], p->N[i], pitch) : 0);
   }
   const size_t off_amax = off;
-  p->amax_bytes = amax_count * sizeof(unsigned);
+  p->amax_bytes = (amax_count + 1) * sizeof(unsigned);   // + the rescale flag (last word)
   off = round256(off + p->amax_bytes);
   const size_t off_probs = off;
   off = round256(off + (size_t)G * sizeof(GroupedProblem));

@@ -76,16 +76,19 @@ cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t l
 // re-splits the blocks needing a power-of-two scale.  The block maxima must
 // be zero on entry.  A (or B) may be null to pack only the other operand.
 // A: M x K (lda) -> planesA [2][M][pitch];  B: K x N (ldb) -> planesB [2][N][pitch].
+// flag: one word, zero on entry like the block maxima, raised by the first
+// pass when a block needs a rescale so the rescale pass returns at once when
+// none does (null: the rescale pass checks every block).
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
-                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, void* planesA,
-                        void* planesB, int64_t pitch, int sms, cudaStream_t s);
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* flag,
+                        void* planesA, void* planesB, int64_t pitch, int sms, cudaStream_t s);
 // A row panel alone: rows [0, rows) of the panel starting at A, written to
 // the planes of the whole matrix at planesA (already offset to the panel's
 // first row) with hi-to-lo plane distance plane_stride elements; amaxA points
 // at the panel's first block (the panel starts on a 128-row boundary).
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
-                                   unsigned* amaxA, void* planesA, int64_t plane_stride,
-                                   int64_t pitch, int sms, cudaStream_t s);
+                                   unsigned* amaxA, unsigned* flag, void* planesA,
+                                   int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s);
 // Work items of the two passes for one problem (grouped prefix sums).
 int pack_first_items(int64_t M, int64_t N, int64_t pitch);
 int pack_rescale_items(int64_t M, int64_t N, int64_t pitch);
@@ -133,6 +136,6 @@ cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a,
 // must have been zeroed.
 cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const GroupedPtrs* ptrs,
                                 const int* first_prefix, int first_total, const int* rescale_prefix,
-                                int rescale_total, int G, int sms, cudaStream_t s);
+                                int rescale_total, int G, unsigned* flag, int sms, cudaStream_t s);
 
 }  // namespace gb

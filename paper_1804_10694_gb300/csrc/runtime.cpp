@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <map>
@@ -280,7 +281,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   size_t off = 0;
   const size_t offA = off; off = align_up(off + bytesA, 256);
   const size_t offB = off; off = align_up(off + bytesB, 256);
-  const size_t offAmax = off; off = align_up(off + (nblkA + nblkB) * sizeof(unsigned), 256);
+  const size_t offAmax = off; off = align_up(off + (nblkA + nblkB + 1) * sizeof(unsigned), 256);
   const size_t offPart = off;
   if (sk > 1) off = align_up(off + (size_t)sk * M * N * sizeof(float), 256);
   p->ws_bytes = off;
@@ -295,7 +296,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->planesB = w + offB;
   p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
   p->amaxB = p->amaxA + nblkA;
-  p->amax_bytes = (nblkA + nblkB) * sizeof(unsigned);
+  p->amax_bytes = (nblkA + nblkB + 1) * sizeof(unsigned);   // + the rescale flag
+  p->rescale_flag = p->amaxB + nblkB;
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
   if ((st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK) return st;
@@ -352,8 +354,8 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   if (prof) cudaEventRecord(ev[0], s);
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
-  if ((e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->planesA,
-                       p->planesB, p->pitch, p->sms, s)) != cudaSuccess)
+  if ((e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
+                       p->planesA, p->planesB, p->pitch, p->sms, s)) != cudaSuccess)
     return cuda_fail(e, "pack launch");
   TcArgs a = p->args;
   a.alpha = alpha;
@@ -477,6 +479,39 @@ static gemm_status grow(float** p, size_t* cap, size_t n) {
   return GEMM_OK;
 }
 
+// rows x cols floats between row-major buffers with leading dimension ld
+// (only the logical matrix moves; padding columns are never touched)
+static cudaError_t copy_rows(float* dst, const float* src, int64_t rows, int64_t cols, int64_t ld,
+                             cudaMemcpyKind kind, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  if (ld == cols) return cudaMemcpyAsync(dst, src, (size_t)rows * cols * 4, kind, s);
+  return cudaMemcpy2DAsync(dst, (size_t)ld * 4, src, (size_t)ld * 4, (size_t)cols * 4, (size_t)rows, kind, s);
+}
+
+// Panels of the host-buffer pipeline (GEMM_HOST_PANELS, default 8; 1 turns
+// the pipeline off).  On 8192^3 with pinned buffers 1/2/4/8 panels took
+// 7.5/5.7/5.0/4.7 ms per call (beta != 0).
+static int host_panels() {
+  static const int n = [] {
+    const char* v = std::getenv("GEMM_HOST_PANELS");
+    const int x = v ? std::atoi(v) : 8;
+    return x < 1 ? 1 : (x > 64 ? 64 : x);
+  }();
+  return n;
+}
+
+// Page-locked (or registered) host memory: only such buffers copy
+// asynchronously, so only they gain from the panel pipeline (pageable copies
+// are staged by the driver and ran slower with more panels).
+static bool page_locked(const void* ptr) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 static gemm_status host_streams(int nevents) {
   cudaError_t e;
   if (!t_host.h2d && (e = cudaStreamCreateWithFlags(&t_host.h2d, cudaStreamNonBlocking)) != cudaSuccess)
@@ -497,7 +532,7 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
                                     float beta, float* C, cudaStream_t s) {
   const int64_t M = p->M, N = p->N, K = p->K, lda = p->lda, ldb = p->ldb, ldc = p->ldc;
   const int64_t tiles_m = (M + 127) / 128;
-  const int npan = (int)std::min<int64_t>(4, tiles_m);
+  const int npan = (int)std::min<int64_t>(host_panels(), tiles_m);
   const int64_t tiles_per = (tiles_m + npan - 1) / npan;
   gemm_status st = host_streams(2 + 2 * npan);
   if (st != GEMM_OK) return st;
@@ -507,27 +542,25 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
   if ((e = cudaEventRecord(ev[0], s)) || (e = cudaStreamWaitEvent(t_host.h2d, ev[0], 0)) ||
       (e = cudaStreamWaitEvent(t_host.d2h, ev[0], 0)))
     return cuda_fail(e, "stream ordering");
-  const size_t nB = (size_t)(K - 1) * ldb + N;
-  if ((e = cudaMemcpyAsync(t_host.B, B, nB * 4, cudaMemcpyHostToDevice, t_host.h2d)) ||
+  if ((e = copy_rows(t_host.B, B, K, N, ldb, cudaMemcpyHostToDevice, t_host.h2d)) ||
       (e = cudaEventRecord(ev[1], t_host.h2d)))
     return cuda_fail(e, "copy B to device");
   for (int i = 0; i < npan; ++i) {   // all panel copies in, queued behind B
     const int64_t r0 = i * tiles_per * 128, r1 = std::min(M, (i + 1) * tiles_per * 128);
     if (r0 >= r1) break;
-    if ((e = cudaMemcpyAsync(t_host.A + r0 * lda, A + r0 * lda, ((r1 - r0 - 1) * lda + K) * 4,
-                             cudaMemcpyHostToDevice, t_host.h2d)))
+    if ((e = copy_rows(t_host.A + r0 * lda, A + r0 * lda, r1 - r0, K, lda, cudaMemcpyHostToDevice,
+                       t_host.h2d)))
       return cuda_fail(e, "copy A panel to device");
-    if (beta != 0.0f &&
-        (e = cudaMemcpyAsync(t_host.C + r0 * ldc, C + r0 * ldc, ((r1 - r0 - 1) * ldc + N) * 4,
-                             cudaMemcpyHostToDevice, t_host.h2d)))
+    if (beta != 0.0f && (e = copy_rows(t_host.C + r0 * ldc, C + r0 * ldc, r1 - r0, N, ldc,
+                                       cudaMemcpyHostToDevice, t_host.h2d)))
       return cuda_fail(e, "copy C panel to device");
     if ((e = cudaEventRecord(ev[2 + i], t_host.h2d))) return cuda_fail(e, "event");
   }
   // B packed once
   if ((e = cudaStreamWaitEvent(s, ev[1], 0)) ||
       (e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) ||
-      (e = pack_launch(p->prec, nullptr, 0, K, 1, t_host.B, N, ldb, nullptr, p->amaxB, nullptr,
-                       p->planesB, p->pitch, p->sms, s)))
+      (e = pack_launch(p->prec, nullptr, 0, K, 1, t_host.B, N, ldb, nullptr, p->amaxB,
+                       p->rescale_flag, nullptr, p->planesB, p->pitch, p->sms, s)))
     return cuda_fail(e, "pack B");
   for (int i = 0; i < npan; ++i) {
     const int64_t t0 = i * tiles_per, t1 = std::min(tiles_m, (i + 1) * tiles_per);
@@ -535,6 +568,7 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     const int64_t r0 = t0 * 128, r1 = std::min(M, t1 * 128);
     if ((e = cudaStreamWaitEvent(s, ev[2 + i], 0)) ||
         (e = pack_rows_panel_launch(p->prec, t_host.A + r0 * lda, r1 - r0, K, lda, p->amaxA + t0,
+                                    p->rescale_flag,
                                     static_cast<char*>(p->planesA) + r0 * p->pitch * prec_elem_bytes(p->prec),
                                     M * p->pitch, p->pitch, p->sms, s)))
       return cuda_fail(e, "pack A panel");
@@ -551,8 +585,8 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     l.grid = std::min(a.num_units, p->sms);
     if ((e = tc_gemm_launch(l, p->tmA, p->tmB, a, s)) || (e = cudaEventRecord(ev[2 + npan + i], s)) ||
         (e = cudaStreamWaitEvent(t_host.d2h, ev[2 + npan + i], 0)) ||
-        (e = cudaMemcpyAsync(C + r0 * ldc, t_host.C + r0 * ldc, ((r1 - r0 - 1) * ldc + N) * 4,
-                             cudaMemcpyDeviceToHost, t_host.d2h)))
+        (e = copy_rows(C + r0 * ldc, t_host.C + r0 * ldc, r1 - r0, N, ldc, cudaMemcpyDeviceToHost,
+                       t_host.d2h)))
       return cuda_fail(e, "panel gemm / copy back");
   }
   if ((e = cudaStreamSynchronize(t_host.d2h)) || (e = cudaStreamSynchronize(s)))
@@ -582,21 +616,22 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   if ((st = grow(&t_host.C, &t_host.nC, nC)) != GEMM_OK) return st;
   gemm_plan_t p = nullptr;
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
-  if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && M >= 4 * 128)
+  if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && host_panels() > 1 &&
+      M >= 4 * 128 && page_locked(A) && page_locked(C))
     return host_gemm_panels(p, alpha, A, B, beta, C, s);
   cudaError_t e;
   if (need_ab) {
-    if ((e = cudaMemcpyAsync(t_host.A, A, nA * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = copy_rows(t_host.A, A, M, K, lda, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "copy A to device");
-    if ((e = cudaMemcpyAsync(t_host.B, B, nB * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = copy_rows(t_host.B, B, K, N, ldb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "copy B to device");
   }
   if (beta != 0.0f) {
-    if ((e = cudaMemcpyAsync(t_host.C, C, nC * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = copy_rows(t_host.C, C, M, N, ldc, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return cuda_fail(e, "copy C to device");
   }
   if ((st = plan_execute_impl(p, alpha, t_host.A, t_host.B, beta, t_host.C, s)) != GEMM_OK) return st;
-  if ((e = cudaMemcpyAsync(C, t_host.C, nC * sizeof(float), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if ((e = copy_rows(C, t_host.C, M, N, ldc, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return cuda_fail(e, "copy C to host");
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "stream synchronize");
   return GEMM_OK;
@@ -777,9 +812,11 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
   if (sms <= 0) return fail(GEMM_ERR_CUDA, "no device");
   cudaError_t e;
   if (!transpose)
-    e = pack_launch(p, X, rows, cols, ld, nullptr, 0, 1, amax, nullptr, planes, nullptr, pitch, sms, s);
+    e = pack_launch(p, X, rows, cols, ld, nullptr, 0, 1, amax, nullptr, nullptr, planes, nullptr, pitch,
+                    sms, s);
   else
-    e = pack_launch(p, nullptr, 0, rows, 1, X, cols, ld, nullptr, amax, nullptr, planes, pitch, sms, s);
+    e = pack_launch(p, nullptr, 0, rows, 1, X, cols, ld, nullptr, amax, nullptr, nullptr, planes, pitch,
+                    sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   return GEMM_OK;
 }

@@ -24,7 +24,8 @@ struct gemm_plan_s {
   void* planesB = nullptr;
   unsigned* amaxA = nullptr;
   unsigned* amaxB = nullptr;
-  size_t amax_bytes = 0;
+  size_t amax_bytes = 0;            // block maxima of A and B plus the rescale flag
+  unsigned* rescale_flag = nullptr;
   float* partial = nullptr;
   CUtensorMap tmA{}, tmB{};
   gb::TcArgs args{};

@@ -61,7 +61,9 @@ __device__ __forceinline__ void split_tf32(float xs, float& hi, float& lo) {
 __device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 
 // CTA-wide max of m folded into *slot (every thread of the CTA calls this).
-__device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
+// When the block's running max leaves the safe range, *flag is raised so that
+// the rescale pass knows it has work (flag may be null: always check).
+__device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot, unsigned* flag) {
   __shared__ unsigned wm[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -70,7 +72,10 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
   if (threadIdx.x == 0) {
     unsigned b = wm[0];
     for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) b = max(b, wm[i]);
-    if (b) atomicMax(slot, b);
+    if (b) {
+      const unsigned old = atomicMax(slot, b);
+      if (flag && block_exponent(max(old, b)) != 0) *flag = 1u;
+    }
   }
   __syncthreads();   // wm is reused by the next tile of a looping launch
 }
@@ -85,7 +90,7 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
 template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
-                                                unsigned* __restrict__ amax,
+                                                unsigned* __restrict__ amax, unsigned* flag,
                                                 void* __restrict__ planes, int64_t plane,
                                                 int64_t pitch, int64_t r0, int64_t k0) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -148,7 +153,7 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
       }
     }
   }
-  if (PASS == kFirst) fold_block_max(m, amax + r0 / kScaleBlock);
+  if (PASS == kFirst) fold_block_max(m, amax + r0 / kScaleBlock, flag);
 }
 
 // ---------------------------------------------------- B: transposing split
@@ -163,8 +168,8 @@ constexpr int kColTilePitch = 132;
 template <bool TF32, Pass PASS>
 __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
                                                 int64_t ld, bool vec, unsigned* __restrict__ amax,
-                                                void* __restrict__ planes, int64_t plane,
-                                                int64_t pitch, int64_t n0, int64_t k0) {
+                                                unsigned* flag, void* __restrict__ planes,
+                                                int64_t plane, int64_t pitch, int64_t n0, int64_t k0) {
   __shared__ __align__(16) float tile[64 * kColTilePitch];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned m = 0;
@@ -236,7 +241,7 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
     }
   }
   if (PASS == kFirst)
-    fold_block_max(m, amax + n0 / kScaleBlock);   // its barriers also guard `tile`
+    fold_block_max(m, amax + n0 / kScaleBlock, flag);   // its barriers also guard `tile`
   else
     __syncthreads();   // the tile is reused by the next item of a looping launch
 }
@@ -251,6 +256,7 @@ struct PackShape {
   const float* B;
   int64_t M, N, K, lda, ldb, pitch;
   int64_t planeA, planeB;   // elements from the hi plane to the lo plane
+  unsigned* flag;           // raised when some block needs a rescale (null: always check)
   bool vecA, vecB;
   unsigned* amaxA;
   unsigned* amaxB;
@@ -268,12 +274,12 @@ __device__ __forceinline__ void first_item(const PackShape& p, int i) {
   const int na = p.first_items_a();
   if (i < na) {
     const int cols = (int)((p.pitch + 255) / 256);
-    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA, p.pitch,
+    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA, p.pitch,
                                   (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
   } else {
     const int l = i - na;
     const int ncols = (int)((p.N + 127) / 128);
-    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB, p.pitch,
+    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.flag, p.planesB, p.planeB, p.pitch,
                                   (int64_t)(l % ncols) * 128, (int64_t)(l / ncols) * 64);
   }
 }
@@ -286,14 +292,14 @@ __device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
     if (block_exponent(p.amaxA[i]) == 0) return;   // uniform per CTA
     for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
       for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
-        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA, p.pitch,
+        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA, p.pitch,
                                         r0 + 32 * q, k0);
   } else {
     const int l = i - na;
     const int64_t n0 = (int64_t)l * 128;
     if (block_exponent(p.amaxB[l]) == 0) return;
     for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB, p.pitch,
+      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.flag, p.planesB, p.planeB, p.pitch,
                                       n0, k0);
   }
 }
@@ -307,6 +313,7 @@ __global__ void pack_first_kernel(const PackShape p) {
 
 template <bool TF32>
 __global__ void pack_rescale_kernel(const PackShape p) {
+  if (p.flag && *p.flag == 0u) return;   // no block out of range
   const int total = p.rescale_items_a() + p.rescale_items_b();
   for (int i = blockIdx.x; i < total; i += gridDim.x) rescale_item<TF32>(p, i);
 }
@@ -350,14 +357,16 @@ __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, cons
 template <bool TF32, Pass PASS>
 __global__ void grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
                                     const GroupedPtrs* __restrict__ ptrs,
-                                    const int* __restrict__ prefix_g, int G) {
+                                    const int* __restrict__ prefix_g, int G, unsigned* flag) {
+  if (PASS == kRescale && *flag == 0u) return;   // no block of any problem out of range
   const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   for (int i = blockIdx.x; i < total; i += gridDim.x) {
     const int g = find_problem(prefix, G, i);
     const GroupedPtrs& q = ptrs[g];
     if (q.alpha == 0.0f) continue;   // A and B are not read when alpha == 0
-    const PackShape p = problem_shape(probs[g], q);
+    PackShape p = problem_shape(probs[g], q);
+    p.flag = flag;
     if (PASS == kFirst)
       first_item<TF32>(p, i - prefix[g]);
     else
@@ -382,9 +391,10 @@ int pack_rescale_items(int64_t M, int64_t N, int64_t pitch) {
 }
 
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
-                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, void* planesA,
-                        void* planesB, int64_t pitch, int sms, cudaStream_t s) {
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* flag,
+                        void* planesA, void* planesB, int64_t pitch, int sms, cudaStream_t s) {
   PackShape p;
+  p.flag = flag;
   p.A = A, p.B = B, p.M = A ? M : 0, p.N = B ? N : 0, p.K = K, p.lda = lda, p.ldb = ldb;
   p.pitch = pitch;
   p.planeA = p.M * pitch;
@@ -406,9 +416,10 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
 }
 
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
-                                   unsigned* amaxA, void* planesA, int64_t plane_stride,
-                                   int64_t pitch, int sms, cudaStream_t s) {
+                                   unsigned* amaxA, unsigned* flag, void* planesA,
+                                   int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s) {
   PackShape p;
+  p.flag = flag;
   p.A = A, p.B = nullptr, p.M = rows, p.N = 0, p.K = K, p.lda = lda, p.ldb = 1;
   p.pitch = pitch;
   p.planeA = plane_stride;
@@ -431,16 +442,16 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
 
 cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const GroupedPtrs* ptrs,
                                 const int* first_prefix, int first_total, const int* rescale_prefix,
-                                int rescale_total, int G, int sms, cudaStream_t s) {
+                                int rescale_total, int G, unsigned* flag, int sms, cudaStream_t s) {
   const size_t dyn = (G + 1) <= 4096 ? static_cast<size_t>(G + 1) * sizeof(int) : 0;
   if (first_total == 0) return cudaSuccess;
   const int gf = grid_for(first_total, sms), gr = grid_for(rescale_total, sms);
   if (prec == Prec::TF32) {
-    grouped_pack_kernel<true, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
-    grouped_pack_kernel<true, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G);
+    grouped_pack_kernel<true, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G, flag);
+    grouped_pack_kernel<true, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G, flag);
   } else {
-    grouped_pack_kernel<false, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
-    grouped_pack_kernel<false, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G);
+    grouped_pack_kernel<false, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G, flag);
+    grouped_pack_kernel<false, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G, flag);
   }
   return cudaGetLastError();
 }

@@ -284,15 +284,25 @@ def test_host_buffer_pipelined_panels(mode, alpha, beta):
     M, N, K = 1000, 300, 700
     A, B, C0 = W.uniform(M, K, 81, ld=K + 5), W.uniform(K, N, 82, ld=N + 3), W.uniform(M, N, 83, ld=N + 1)
     ref = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
-    C = C0.copy()
     lib = pkg.load()
-    st = lib.gemm_f32_host(M, N, K, alpha, A.ctypes.data, A.shape[1], B.ctypes.data, B.shape[1],
-                           beta, C.ctypes.data, C.shape[1], pkg.MODES[mode], None)
-    assert st == 0, lib.gemm_last_error()
-    assert oracle.rel_frob(C, ref) <= TOL
-    check_padding_untouched(C0, C, N)
+
+    def pinned(x):                # the pipeline runs only on page-locked buffers
+        t = torch.empty(x.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = x
+        return t
+
+    for make in (pinned, lambda x: torch.from_numpy(x.copy())):   # pinned, then pageable
+        hA, hB, hC = make(A), make(B), make(C0)
+        st = lib.gemm_f32_host(M, N, K, alpha, hA.data_ptr(), A.shape[1], hB.data_ptr(), B.shape[1],
+                               beta, hC.data_ptr(), C0.shape[1], pkg.MODES[mode], None)
+        assert st == 0, lib.gemm_last_error()
+        C = hC.numpy()
+        assert oracle.rel_frob(C, ref) <= TOL
+        check_padding_untouched(C0, C, N)
     # integer inputs stay bit-exact through the pipeline
     Ai, Bi, Ci = W.integers(M, K, 84), W.integers(K, N, 85), W.integers(M, N, 86)
-    Cg = Ci.copy()
-    pkg.gemm_host(Ai, Bi, Cg, alpha, beta, mode=mode)
-    assert np.array_equal(Cg, oracle.gemm_f64(M, N, K, alpha, Ai, Bi, beta, Ci).astype(np.float32))
+    hA, hB, hC = pinned(Ai), pinned(Bi), pinned(Ci)
+    st = lib.gemm_f32_host(M, N, K, alpha, hA.data_ptr(), K, hB.data_ptr(), N, beta, hC.data_ptr(), N,
+                           pkg.MODES[mode], None)
+    assert st == 0, lib.gemm_last_error()
+    assert np.array_equal(hC.numpy(), oracle.gemm_f64(M, N, K, alpha, Ai, Bi, beta, Ci).astype(np.float32))
