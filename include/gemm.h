@@ -82,6 +82,8 @@ typedef struct {
   int split_k;     /* number of K partitions (partials reduced in fixed order) */
   int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (1..8) */
   int group_m;     /* raster: output tiles walked in groups of this many along M */
+  int fused;       /* 1: A is split inside the gemm kernel (no packed copy of A);
+                    *    0: A is packed into hi/lo planes by a separate pass */
 } gemm_config;
 
 /* ---------------------------------------------------------------- gemm -- */

@@ -17,6 +17,7 @@ feature is written here from its definition, in float64:
   log2 arithmetic intensity, 2MNK / (4 (MK + KN + 2 MN))
   log2 k-chunks per split
   1 for the tf32 mode, else 0
+  1 when A is split inside the gemm kernel, else 0
 
 A k-chunk is 128 bytes of one row: 64 bf16 or 32 tf32 elements.
 """
@@ -51,4 +52,5 @@ def features(M: int, N: int, K: int, cfg: dict, tf32: bool, sms: int) -> list[fl
     ai = 2.0 * M * N * K / (4.0 * (M * K + K * N + 2.0 * M * N))
     return [math.log2(M), math.log2(N), math.log2(K), e["bn"] / 128.0, math.log2(e["split_k"]),
             e["kb"] / 8.0, math.log2(e["group_m"]), math.log2(e["tiles"]), math.log2(1 + waves),
-            fill, padded, math.log2(ai), math.log2(e["per"]), 1.0 if tf32 else 0.0]
+            fill, padded, math.log2(ai), math.log2(e["per"]), 1.0 if tf32 else 0.0,
+            1.0 if cfg.get("fused", 0) else 0.0]

@@ -6,7 +6,7 @@
 // shape, e.g. split-K above the number of k-chunks, are timed once) is run
 // `reps` times after two warm-up executions, each execution timed with CUDA
 // events; the median is recorded.  Results are appended to a CSV file
-// ("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m") that the cost
+// ("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused") that the cost
 // model trains on, and the fastest configuration per shape is kept in an
 // in-memory table (GEMM_SELECT_TABLE).
 #include <cuda_runtime.h>
@@ -42,18 +42,19 @@ EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, i
   e.kb = (int)std::min<int64_t>(c.kb, per);
   e.group_m = (int)std::max<int64_t>(1, std::min<int64_t>(c.group_m, tiles_m));
   e.tiles = tiles_m * ((N + c.block_n - 1) / c.block_n);
+  e.fused = c.fused;
   return e;
 }
 
 std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t K) {
   std::vector<int> out;
-  std::set<std::tuple<int, int, int, int>> seen;
+  std::set<std::tuple<int, int, int, int, int>> seen;
   const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
   gemm_config c;
   for (int id = 0; id < config_count(mode); ++id) {
     config_get(id, &c);
     const EffConfig e = effective_config(c, p, M, N, K);
-    if (seen.insert(std::make_tuple(e.bn, e.split_k, e.kb, e.group_m)).second) out.push_back(id);
+    if (seen.insert(std::make_tuple(e.bn, e.split_k, e.kb, e.group_m, e.fused)).second) out.push_back(id);
   }
   return out;
 }
@@ -278,7 +279,8 @@ gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps
     f = std::fopen(out_path, "a");
     if (!f) return fail(GEMM_ERR_IO, "cannot open %s for appending", out_path);
     std::fseek(f, 0, SEEK_END);
-    if (std::ftell(f) == 0) std::fprintf(f, "M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m\n");
+    if (std::ftell(f) == 0)
+      std::fprintf(f, "M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n");
   }
   gemm_status st = GEMM_OK;
   for (int s = 0; s < G && st == GEMM_OK; ++s) {
@@ -295,8 +297,9 @@ gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps
           if (!f) return;
           gemm_config c;
           config_get(cid, &c);
-          std::fprintf(f, "%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d\n", (long long)M, (long long)N,
-                       (long long)K, (int)mode, cid, ms, c.block_n, c.split_k, c.kb, c.group_m);
+          std::fprintf(f, "%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d,%d\n", (long long)M, (long long)N,
+                       (long long)K, (int)mode, cid, ms, c.block_n, c.split_k, c.kb, c.group_m,
+                       c.fused);
         },
         &best, &best_ms);
     if (f) std::fflush(f);

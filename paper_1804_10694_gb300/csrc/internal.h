@@ -39,22 +39,27 @@ struct TcArgs {
   const unsigned* amaxB;   // per 128-column block of B
   float* partial;          // split-K partial sums [split][M][N], null when split_k == 1
   int* err;
+  // fused-split variant only: A itself (row-major FP32, split inside the kernel)
+  const float* A;
+  int64_t lda;
+  int vecA;                // A 16-byte aligned and lda % 4 == 0: float4 loads
 };
 
 struct TcLaunch {
   int bn;          // tile N (64 or 128)
   Prec prec;       // BF16 or TF32
   int grid;
+  bool fused;      // A split inside the gemm kernel (only B is packed)
 };
 
 // Returns the dynamic shared memory a tensor-core kernel variant needs.
-int tc_smem_bytes(int bn, Prec prec);
+int tc_smem_bytes(int bn, Prec prec, bool fused = false);
 // Bytes of one row per k-chunk of the kernel variant with tile width bn (the
 // swizzle width of its operand tiles: 128, or 64 for bn = 256).
 int tc_chunk_bytes(int bn);
 // Raise the shared-memory limit of a tile-width/precision variant on the
 // current device (call outside stream capture; idempotent).
-cudaError_t tc_prepare(int bn, Prec prec);
+cudaError_t tc_prepare(int bn, Prec prec, bool fused = false);
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s);
 // C = sum_s partial[s] + beta * C over the split-K partial sums (alpha is
@@ -86,6 +91,12 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
 // the planes of the whole matrix at planesA (already offset to the panel's
 // first row) with hi-to-lo plane distance plane_stride elements; amaxA points
 // at the panel's first block (the panel starts on a 128-row boundary).
+// As pack_launch, but A is only scanned for its block maxima (no planes):
+// the fused-split gemm kernel splits A itself while it streams the tiles.
+cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
+                              const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
+                              unsigned* amaxB, unsigned* flag, void* planesB, int64_t pitch, int sms,
+                              cudaStream_t s);
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
                                    unsigned* amaxA, unsigned* flag, void* planesA,
                                    int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s);

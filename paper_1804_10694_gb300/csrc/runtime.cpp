@@ -102,24 +102,28 @@ constexpr int kMaxFoldChunks = 8;
 
 // Candidates of the tensor-core kernels.  The same table serves BF16X3 and
 // TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way).
+// Ids 0..71 pack both operands; ids 72..143 repeat them with A split inside
+// the gemm kernel.
 static const std::vector<gemm_config>& config_table() {
   static const std::vector<gemm_config> table = [] {
     std::vector<gemm_config> t;
     const int splits[] = {1, 2, 3, 4, 6, 8};
     const int kbs[] = {4, 2, 8};
     const int groups[] = {16, 1};
-    for (int bn : {128, 64})
-      for (int sk : splits)
-        for (int kb : kbs)
-          for (int g : groups) {
-            gemm_config c;
-            c.block_n = bn;
-            c.stages = bn == 64 ? 4 : 3;
-            c.split_k = sk;
-            c.kb = kb;
-            c.group_m = g;
-            t.push_back(c);
-          }
+    for (int fused : {0, 1})
+      for (int bn : {128, 64})
+        for (int sk : splits)
+          for (int kb : kbs)
+            for (int g : groups) {
+              gemm_config c;
+              c.block_n = bn;
+              c.stages = fused ? (bn == 64 ? 3 : 2) : (bn == 64 ? 4 : 3);
+              c.split_k = sk;
+              c.kb = kb;
+              c.group_m = g;
+              c.fused = fused;
+              t.push_back(c);
+            }
     return t;
   }();
   return table;
@@ -139,7 +143,8 @@ bool config_get(int id, gemm_config* out) {
 static int find_config(int bn, int sk, int kb, int g) {
   const auto& t = config_table();
   for (int i = 0; i < (int)t.size(); ++i)
-    if (t[i].block_n == bn && t[i].split_k == sk && t[i].kb == kb && t[i].group_m == g) return i;
+    if (t[i].block_n == bn && t[i].split_k == sk && t[i].kb == kb && t[i].group_m == g && !t[i].fused)
+      return i;
   return 0;
 }
 
@@ -199,6 +204,23 @@ static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t r
   if (r != CUDA_SUCCESS)
     return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) rows=%lld K=%lld pitch=%lld",
                 (int)r, (long long)rows, (long long)K, (long long)pitch);
+  return GEMM_OK;
+}
+
+// FP32 A itself for the fused-split kernel: 128-byte-wide boxes (32 floats)
+// of 128 rows, 128-byte swizzle, zero fill outside the matrix.  Needs a
+// 16-byte aligned base and lda % 4 == 0.
+static gemm_status encode_rows_f32(CUtensorMap* map, const float* A, int64_t M, int64_t K, int64_t lda) {
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)M, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(lda * 4), (cuuint64_t)(M * lda * 4)};
+  cuuint32_t box[3] = {32, 128, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(A), dims, strides,
+                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for A, M=%lld K=%lld lda=%lld", (int)r,
+                (long long)M, (long long)K, (long long)lda);
   return GEMM_OK;
 }
 
@@ -273,8 +295,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   const int64_t chunks_kernel = (K + kchunk - 1) / kchunk;
   const int64_t tiles_m = (M + 127) / 128, tiles_n = (N + bn - 1) / bn;
 
-  // workspace: A planes | B planes | amax A | amax B | split-K partials
-  const size_t bytesA = (size_t)2 * M * p->pitch * es;
+  // workspace: A planes (packed variant) | B planes | amax A | amax B | split-K partials
+  const bool fused = p->cfg.fused != 0;
+  const size_t bytesA = fused ? 0 : (size_t)2 * M * p->pitch * es;
   const size_t bytesB = (size_t)2 * N * p->pitch * es;
   const size_t nblkA = (size_t)(M + kScaleBlock - 1) / kScaleBlock;
   const size_t nblkB = (size_t)(N + kScaleBlock - 1) / kScaleBlock;
@@ -292,7 +315,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
                 cudaGetErrorString(e));
   }
   char* w = static_cast<char*>(p->ws);
-  p->planesA = w + offA;
+  p->planesA = fused ? nullptr : w + offA;
   p->planesB = w + offB;
   p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
   p->amaxB = p->amaxA + nblkA;
@@ -300,7 +323,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->rescale_flag = p->amaxB + nblkB;
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
-  if ((st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK) return st;
+  if (!fused && (st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK)
+    return st;
   if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn, sw)) != GEMM_OK) return st;
 
   TcArgs& a = p->args;
@@ -318,10 +342,12 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.amaxB = p->amaxB;
   a.partial = p->partial;
   a.err = dev->err_word;
+  a.lda = lda;
   p->launch.bn = bn;
   p->launch.prec = pr;
   p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
-  if ((e = tc_prepare(bn, pr)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
+  p->launch.fused = fused;
+  if ((e = tc_prepare(bn, pr, fused)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
   *out = p.release();
   return GEMM_OK;
 }
@@ -354,15 +380,31 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   if (prof) cudaEventRecord(ev[0], s);
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
-  if ((e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
-                       p->planesA, p->planesB, p->pitch, p->sms, s)) != cudaSuccess)
-    return cuda_fail(e, "pack launch");
+  if (p->launch.fused)
+    e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
+                          p->planesB, p->pitch, p->sms, s);
+  else
+    e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
+                    p->planesA, p->planesB, p->pitch, p->sms, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   TcArgs a = p->args;
   a.alpha = alpha;
   a.beta = beta;
   a.C = C;
+  a.A = A;
+  a.vecA = (p->lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0) ? 1 : 0;
+  CUtensorMap tmAf;   // fused variant: A staged by TMA when its rows are 16-byte aligned
+  const CUtensorMap* mapA = &p->tmA;
+  if (p->launch.fused) {
+    std::memset(&tmAf, 0, sizeof tmAf);
+    if (a.vecA) {
+      gemm_status st = encode_rows_f32(&tmAf, A, M, K, p->lda);
+      if (st != GEMM_OK) return st;
+    }
+    mapA = &tmAf;
+  }
   if (prof) cudaEventRecord(ev[1], s);
-  if ((e = tc_gemm_launch(p->launch, p->tmA, p->tmB, a, s)) != cudaSuccess)
+  if ((e = tc_gemm_launch(p->launch, *mapA, p->tmB, a, s)) != cudaSuccess)
     return cuda_fail(e, "tensor-core gemm launch");
   if (prof) cudaEventRecord(ev[2], s);
   if (a.split_k > 1) {
@@ -616,7 +658,8 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   if ((st = grow(&t_host.C, &t_host.nC, nC)) != GEMM_OK) return st;
   gemm_plan_t p = nullptr;
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
-  if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && host_panels() > 1 &&
+  if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && !p->launch.fused &&
+      host_panels() > 1 &&
       M >= 4 * 128 && page_locked(A) && page_locked(C))
     return host_gemm_panels(p, alpha, A, B, beta, C, s);
   cudaError_t e;

@@ -21,44 +21,18 @@
 // grouped kernels map a flattened item index to (problem, tile) through
 // prefix sums, so one launch packs every problem of a grouped gemm.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "scale.cuh"
+#include "split_arith.cuh"
 
 namespace gb {
 
 namespace {
 
 enum Pass { kFirst = 0, kRescale = 1 };
-
-// ---------------------------------------------------------------- rounding
-__device__ __forceinline__ float round_tf32_rne(float x) {
-  const unsigned u = __float_as_uint(x);
-  if ((u & 0x7F800000u) == 0x7F800000u) return x;   // Inf / NaN unchanged
-  const unsigned r = (u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
-  return __uint_as_float(r);
-}
-
-struct HiLoBf16 {
-  __nv_bfloat16 hi, lo;
-};
-
-__device__ __forceinline__ HiLoBf16 split_bf16(float xs) {
-  HiLoBf16 o;
-  o.hi = __float2bfloat16_rn(xs);
-  o.lo = isfinite(xs) ? __float2bfloat16_rn(xs - __bfloat162float(o.hi)) : __float2bfloat16_rn(0.0f);
-  return o;
-}
-
-__device__ __forceinline__ void split_tf32(float xs, float& hi, float& lo) {
-  hi = round_tf32_rne(xs);
-  lo = isfinite(xs) ? round_tf32_rne(xs - hi) : 0.0f;
-}
-
-// |x| as an orderable bit pattern (non-negative floats order like their bits;
-// NaN patterns sort above Inf, so a NaN marks the block as non-finite).
-__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
 
 // CTA-wide max of m folded into *slot (every thread of the CTA calls this).
 // When the block's running max leaves the safe range, *flag is raised so that
@@ -246,6 +220,87 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
     __syncthreads();   // the tile is reused by the next item of a looping launch
 }
 
+// ------------------------------------------------ A: block maxima only
+// For the fused-split gemm, which splits A itself: one item is a 128-row
+// block over a span of 64 loads per row (256 floats with float4 loads);
+// thread (x, y) of the 64 x 4 CTA reads load x of rows y, y + 4, ... with
+// eight loads in flight, and the CTA folds one max per item.
+constexpr int kAmaxLoads = 64;
+
+// Rows stored back to back (lda == K, 16-byte aligned): a block is one
+// contiguous run of rows * K floats, streamed as float4 in `parts` pieces.
+__global__ void __launch_bounds__(256) amax_flat_kernel(const float* __restrict__ A, int64_t M,
+                                                        int64_t K, int parts,
+                                                        unsigned* __restrict__ amax, unsigned* flag) {
+  const int64_t nblk = (M + 127) / 128;
+  for (int64_t item = blockIdx.x; item < nblk * parts; item += gridDim.x) {
+    const int64_t b = item / parts;
+    const int part = static_cast<int>(item - b * parts);
+    const int64_t n4 = min(static_cast<int64_t>(128), M - b * 128) * K / 4;   // K % 4 == 0
+    const int64_t per = (n4 + parts - 1) / parts;
+    const int64_t lo = part * per, hi = min(n4, lo + per);
+    const float4* p = reinterpret_cast<const float4*>(A + b * 128 * K);
+    unsigned m = 0;
+    for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += 8 * 256) {
+      float4 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int64_t idx = i0 + 256 * i;
+        v[i] = idx < hi ? __ldg(p + idx) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        m = max(m, max(max(abs_bits(v[i].x), abs_bits(v[i].y)), max(abs_bits(v[i].z), abs_bits(v[i].w))));
+    }
+    fold_block_max(m, amax + b, flag);
+  }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) amax_rows_kernel(const float* __restrict__ A, int64_t M,
+                                                        int64_t K, int64_t lda,
+                                                        unsigned* __restrict__ amax, unsigned* flag) {
+  constexpr int U = VEC ? 4 : 1;   // floats per load
+  constexpr int64_t span = kAmaxLoads * U;
+  const int64_t nblk = (M + 127) / 128, nspan = (K + span - 1) / span;
+  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+  for (int64_t item = blockIdx.x; item < nblk * nspan; item += gridDim.x) {
+    const int64_t b = item / nspan;
+    const int64_t k = (item - b * nspan) * span + static_cast<int64_t>(tx) * U;
+    const int rows = static_cast<int>(min(static_cast<int64_t>(128), M - b * 128));
+    const float* base = A + (b * 128) * lda + k;
+    unsigned m = 0;
+    if (k < K) {
+      for (int r0 = ty; r0 < rows; r0 += 32) {
+        float v[8][U];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = r0 + 4 * i;
+#pragma unroll
+          for (int e = 0; e < U; ++e) v[i][e] = 0.0f;
+          if (r >= rows) continue;
+          const float* p = base + r * lda;
+          if (VEC && k + 4 <= K) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+            const float t[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < U; ++e) v[i][e] = t[e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < U; ++e)
+              if (k + e < K) v[i][e] = __ldg(p + e);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int e = 0; e < U; ++e) m = max(m, abs_bits(v[i][e]));
+      }
+    }
+    fold_block_max(m, amax + b, flag);
+  }
+}
+
 // --------------------------------------------------- tile decomposition
 // First pass: A in 32-row x 256-column tiles, B in 64-k x 128-column tiles.
 // Rescale pass: one item per scale block (128 rows of A or 128 columns of B,
@@ -274,8 +329,8 @@ __device__ __forceinline__ void first_item(const PackShape& p, int i) {
   const int na = p.first_items_a();
   if (i < na) {
     const int cols = (int)((p.pitch + 255) / 256);
-    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA, p.pitch,
-                                  (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
+    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA,
+                                  p.pitch, (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
   } else {
     const int l = i - na;
     const int ncols = (int)((p.N + 127) / 128);
@@ -413,6 +468,38 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
     pack_rescale_kernel<false><<<grid_for(rescale, sms), 256, 0, s>>>(p);
   }
   return cudaGetLastError();
+}
+
+cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
+                              const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
+                              unsigned* amaxB, unsigned* flag, void* planesB, int64_t pitch, int sms,
+                              cudaStream_t s) {
+  if (M > 0 && K > 0) {
+    const bool vec = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+    if (vec && lda == K) {
+      const int64_t nblk = (M + 127) / 128;
+      const int parts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(
+          (4 * static_cast<int64_t>(sms) + nblk - 1) / nblk, (128 * K / 4 + 2047) / 2048)));
+      const int grid = static_cast<int>(std::min<int64_t>(nblk * parts, 8 * static_cast<int64_t>(sms)));
+      amax_flat_kernel<<<grid, 256, 0, s>>>(A, M, K, parts, amaxA, flag);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      return pack_launch(prec, nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, flag, nullptr, planesB,
+                         pitch, sms, s);
+    }
+    const int64_t span = kAmaxLoads * (vec ? 4 : 1);
+    const int64_t items = ((M + 127) / 128) * ((K + span - 1) / span);
+    const int grid = static_cast<int>(std::min<int64_t>(items, 8 * static_cast<int64_t>(sms)));
+    if (vec)
+      amax_rows_kernel<true><<<grid, 256, 0, s>>>(A, M, K, lda, amaxA, flag);
+    else
+      amax_rows_kernel<false><<<grid, 256, 0, s>>>(A, M, K, lda, amaxA, flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // B as in the packed variant
+  return pack_launch(prec, nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, flag, nullptr, planesB, pitch,
+                     sms, s);
 }
 
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,

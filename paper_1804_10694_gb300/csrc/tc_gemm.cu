@@ -24,12 +24,23 @@
 //
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
 // TMEM owner, warps 2..5 = epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+//
+// Fused-split variant (the packing of A moved into the main loop): TMA
+// brings only B's planes.  Copy warps stage 128 x 64 (bf16) or 128 x 32
+// (tf32) FP32 blocks of A in shared memory with cp.async; split warps split
+// them with the packing pass's arithmetic and the block exponent found by a
+// max-only pass over A, and write hi/lo into the stage in the layout a
+// 128-byte-swizzled TMA load would have produced, then arrive on the stage's
+// full barrier (which completes on their arrivals plus B's bytes).  A never
+// exists as planes in memory: its operand traffic is one FP32 read instead
+// of a read, a write and a re-read.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
 #include "ptx.cuh"
 #include "scale.cuh"
+#include "split_arith.cuh"
 
 namespace gb {
 
@@ -39,24 +50,42 @@ namespace gb {
 // this geometry supports) measured 1.1-1.2 PFLOP/s on GB300 against 1.6 for
 // 128, with the 128-byte swizzle (2-deep ring) and with the 64-byte swizzle
 // (4-deep ring) alike, so it is not offered.
-template <int BN, bool TF32>
+template <int BN, bool TF32, bool FUSED = false>
 struct TcCfg {
   static constexpr int BM = 128;
   static constexpr int SW = 128;                       // bytes of one row per k-chunk
   static constexpr int A_PLANE = BM * SW;
   static constexpr int B_PLANE = BN * SW;
   static constexpr int STAGE = 2 * A_PLANE + 2 * B_PLANE;
-  static constexpr int STAGES = BN == 64 ? 4 : BN == 128 ? 3 : 2;
+  // operand ring depth (the fused variant gives room to the staging of A)
+  static constexpr int STAGES = FUSED ? 2 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
   static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
   static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
-  static constexpr int EPI_WG = BN == 256 ? 2 : 1;     // epilogue warpgroups
+  // epilogue warpgroups (two for the fused 128-wide tile: with its extra
+  // warps, one warpgroup holding 128 columns would run out of registers)
+  static constexpr int EPI_WG = (BN == 256 || (FUSED && BN == 128)) ? 2 : 1;
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int TMEM_COLS = 2 * BN;             // two accumulator buffers
   static constexpr int EPI_PITCH = 33;                 // floats per staged row (bank-conflict free)
   static constexpr int EPI_BYTES = 4 * EPI_WG * 32 * EPI_PITCH * 4;   // one 32x32 buffer per epilogue warp
   static constexpr int BAR_BYTES = 256;
-  static constexpr int SMEM = STAGES * STAGE + EPI_BYTES + BAR_BYTES + 1024;
-  static constexpr int THREADS = 64 + 128 * EPI_WG;
+  // fused variant: two staging buffers for one FP32 k-chunk of A each
+  // (128 rows of BK floats, as 128-byte-wide boxes swizzled like a
+  // SWIZZLE_128B TMA load), filled by TMA or cp.async
+  static constexpr int STG_ROW = BK * 4;
+  static constexpr int STG_BYTES = FUSED ? 128 * STG_ROW : 0;
+  // (as deep as shared memory allows: the staging ring is what keeps enough
+  // bytes of A in flight to cover memory latency)
+  static constexpr int STG_STAGES = !FUSED ? 0 : BN == 64 ? (TF32 ? 6 : 3) : (TF32 ? 4 : 2);
+  static constexpr int OFF_STG = STAGES * STAGE;
+  static constexpr int OFF_EPI = OFF_STG + STG_STAGES * STG_BYTES;
+  static constexpr int OFF_BAR = OFF_EPI + EPI_BYTES;
+  static constexpr int SMEM = OFF_BAR + BAR_BYTES + 1024;
+  // fused variant: SPLIT_THREADS threads stage A and split it into the
+  // stage (at most 12 warps in all, which leaves 168 registers a thread)
+  static constexpr int SPLIT0 = 64 + 128 * EPI_WG;
+  static constexpr int SPLIT_THREADS = FUSED ? (BN == 128 ? 64 : 128) : 0;
+  static constexpr int THREADS = SPLIT0 + SPLIT_THREADS;
   static_assert(SMEM <= 232448, "shared memory budget");
   static_assert(TMEM_COLS <= 512, "tensor memory budget");
 };
@@ -77,6 +106,15 @@ struct EpiView {
   const unsigned* amaxB;
   float* partial;
   int split_k;
+};
+
+// Source of A for the fused-split variant.
+struct FusedA {
+  const float* A;
+  int64_t lda;
+  int M, K;
+  bool vec;                 // 16-byte aligned rows: staged by TMA, else by 4-byte cp.async
+  const unsigned* amaxA;    // block maxima from the max-only pass
 };
 
 __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
@@ -116,6 +154,9 @@ struct SingleSched {
     v.amaxA = a->amaxA, v.amaxB = a->amaxB, v.partial = a->partial, v.split_k = a->split_k;
     return v;
   }
+  __device__ FusedA srcA(int) const {
+    return FusedA{a->A, a->lda, a->M, a->K, a->vecA != 0, a->amaxA};
+  }
 };
 
 // Scheduling policy of a grouped launch: units are the tiles of all problems,
@@ -150,9 +191,96 @@ struct GroupedSched {
   }
 };
 
-template <int BN, bool TF32, class Sched>
+// Two floats rounded to bf16 (nearest even) in one instruction: a in the low
+// half, b in the high half.
+__device__ __forceinline__ unsigned cvt_bf16x2(float a, float b) {
+  unsigned d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+  return d;
+}
+
+// Fused variant: split one 16-byte output group (x scaled by sf) into the hi
+// and lo planes of a stage.  Row r of a plane holds 128 bytes; its 16-byte
+// group q sits at position q ^ (r % 8), the 128-byte swizzle.  FINITE: the
+// block holds no Inf/NaN (its max is finite), so the non-finite cases of the
+// split can be skipped and bf16 pairs converted in one instruction; for
+// finite values the result is the same bits as split_bf16 / split_tf32.
+template <bool TF32, int EPG, bool FINITE>
+__device__ __forceinline__ void fused_store(uint8_t* hi_plane, uint8_t* lo_plane, int r, int q,
+                                            const float (&x)[EPG], float sf) {
+  const int off = r * 128 + ((q ^ (r & 7)) << 4);
+  if (FINITE && TF32) {
+    float hv[4], lv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xs = x[j] * sf;
+      const unsigned u = __float_as_uint(xs);
+      hv[j] = __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
+      const unsigned d = __float_as_uint(xs - hv[j]);
+      lv[j] = __uint_as_float((d + 0xFFFu + ((d >> 13) & 1u)) & 0xFFFFE000u);
+    }
+    *reinterpret_cast<float4*>(hi_plane + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    *reinterpret_cast<float4*>(lo_plane + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+  } else if (FINITE) {
+    unsigned hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float a = x[2 * j] * sf, b = x[2 * j + 1] * sf;
+      const unsigned hp = cvt_bf16x2(a, b);
+      const float ha = __uint_as_float(hp << 16), hb = __uint_as_float(hp & 0xFFFF0000u);
+      hw[j] = hp;
+      lw[j] = cvt_bf16x2(a - ha, b - hb);
+    }
+    *reinterpret_cast<uint4*>(hi_plane + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(lo_plane + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  } else if (TF32) {
+    float4 h, l;
+    split_tf32(x[0] * sf, h.x, l.x);
+    split_tf32(x[1] * sf, h.y, l.y);
+    split_tf32(x[2] * sf, h.z, l.z);
+    split_tf32(x[3] * sf, h.w, l.w);
+    *reinterpret_cast<float4*>(hi_plane + off) = h;
+    *reinterpret_cast<float4*>(lo_plane + off) = l;
+  } else {
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const HiLoBf16 t = split_bf16(x[j] * sf);
+      h[j] = t.hi;
+      l[j] = t.lo;
+    }
+    *reinterpret_cast<uint4*>(hi_plane + off) = *reinterpret_cast<const uint4*>(h);
+    *reinterpret_cast<uint4*>(lo_plane + off) = *reinterpret_cast<const uint4*>(l);
+  }
+}
+
+// Fused variant: split rows t, t + NT, ... of a staged chunk (two or one
+// 128-byte-wide boxes, SWIZZLE_128B layout) into the hi/lo planes.
+template <bool TF32, bool FINITE, int NT>
+__device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* hi_plane,
+                                                 uint8_t* lo_plane, int t, float sf) {
+  constexpr int EPG = TF32 ? 4 : 8;   // elements per 16-byte output group
+  constexpr int BOX = 128 * 128;
+#pragma unroll 1
+  for (int r = t; r < 128; r += NT) {
+    float x[8][EPG];
+#pragma unroll
+    for (int g = 0; g < 8; ++g)
+#pragma unroll
+      for (int h = 0; h < EPG / 4; ++h) {
+        const int j = g * (EPG / 4) + h;   // 16-byte unit of the row
+        const float4 v = *reinterpret_cast<const float4*>(sbuf + (j >> 3) * BOX + r * 128 +
+                                                          (((j & 7) ^ (r & 7)) << 4));
+        x[g][4 * h] = v.x, x[g][4 * h + 1] = v.y, x[g][4 * h + 2] = v.z, x[g][4 * h + 3] = v.w;
+      }
+#pragma unroll
+    for (int g = 0; g < 8; ++g) fused_store<TF32, EPG, FINITE>(hi_plane, lo_plane, r, g, x[g], sf);
+  }
+}
+
+template <int BN, bool TF32, class Sched, bool FUSED = false>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
-  using Cfg = TcCfg<BN, TF32>;
+  using Cfg = TcCfg<BN, TF32, FUSED>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -162,16 +290,22 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   const int nunits = sc.units();
   const int kb = sc.kb();
 
-  // barrier block after the stage ring
-  float* epi_buf = reinterpret_cast<float*>(smem + STAGES * Cfg::STAGE);
-  uint8_t* bar_area = smem + STAGES * Cfg::STAGE + Cfg::EPI_BYTES;
-  const uint32_t bar0 = sbase + STAGES * Cfg::STAGE + Cfg::EPI_BYTES;
+  // stage ring | A staging (fused) | epilogue buffers | barrier block
+  float* epi_buf = reinterpret_cast<float*>(smem + Cfg::OFF_EPI);
+  uint8_t* bar_area = smem + Cfg::OFF_BAR;
+  const uint32_t bar0 = sbase + Cfg::OFF_BAR;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
   auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
   const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * (2 * STAGES + 5));
+  // fused variant: staging buffer b holds a copied chunk / is free again
+  constexpr int NSTG = Cfg::STG_STAGES;
+  auto stg_full_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 5 + b); };
+  auto stg_empty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 5 + NSTG + b); };
+  constexpr int NBAR = 2 * STAGES + 5 + 2 * NSTG;
+  static_assert(8 * NBAR + 16 <= Cfg::BAR_BYTES, "barrier block");
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
@@ -179,7 +313,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(full_bar(s), 1);
+      mbar_init(full_bar(s), 1 + Cfg::SPLIT_THREADS / 32);   // producer + one per split warp
       mbar_init(empty_bar(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -187,6 +321,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       mbar_init(acce_bar(b), 128 * Cfg::EPI_WG);
     }
     mbar_init(drain_bar, 1);
+    if constexpr (FUSED) {
+      // a staging buffer fills on one TMA issuer's arrival (plus its bytes)
+      // or on every split thread's cp.async arrival
+      const uint32_t fill_count = sc.srcA(0).vec ? 1u : static_cast<uint32_t>(Cfg::SPLIT_THREADS);
+      for (int b = 0; b < NSTG; ++b) {
+        mbar_init(stg_full_bar(b), fill_count);
+        mbar_init(stg_empty_bar(b), Cfg::SPLIT_THREADS / 32);
+      }
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -201,7 +344,108 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
-    if (lane == 0) {
+    bool fused_tma = false;
+    if constexpr (FUSED) fused_tma = sc.srcA(0).vec;
+    if (lane == 0 && fused_tma) {
+      if constexpr (FUSED) {
+        // Fused variant with A staged by TMA: this thread feeds both rings,
+        // A's staging buffers and B's stages, each as far ahead as its ring
+        // allows, polling both without blocking.
+        constexpr int NSTG_ = Cfg::STG_STAGES;
+        constexpr int BOX = 128 * 128;
+        const uint32_t stg0 = sbase + Cfg::OFF_STG;
+        struct Cur {
+          int u, c;
+          Work w;
+          bool have;
+        };
+        auto first_c = [&](Cur& q, int u0) {
+          q.have = false;
+          for (q.u = u0; q.u < nunits; q.u += gridDim.x) {
+            q.w = sc.work(q.u);
+            if (q.w.c0 < q.w.c1) {
+              q.have = true;
+              q.c = q.w.c0;
+              break;
+            }
+          }
+        };
+        auto adv = [&](Cur& q) {
+          if (++q.c >= q.w.c1) first_c(q, q.u + gridDim.x);
+        };
+        Cur aq{}, bq{};
+        first_c(aq, blockIdx.x);
+        bq = aq;
+        const CUtensorMap* mA = sc.mapA(0);
+        const CUtensorMap* mB = sc.mapB(0);
+        tma_prefetch_desc(mA);
+        tma_prefetch_desc(mB);
+        uint32_t aslot = 0, aph = 0, bstage = 0, bph = 0;
+        uint32_t a_used = 0, a_par = 0, b_used = 0, b_par = 0;   // per buffer: filled once / last parity
+        bool ok = true;
+        uint32_t idle = 0;
+        uint64_t t0 = 0;
+        while (aq.have || bq.have) {
+          bool prog = false;
+          if (aq.have && mbar_test_wait(stg_empty_bar(aslot), aph ^ 1u)) {
+            const uint32_t fb = stg_full_bar(aslot);
+            mbar_arrive_expect_tx(fb, Cfg::STG_BYTES);
+#pragma unroll
+            for (int h = 0; h < Cfg::STG_ROW / 128; ++h)
+              tma_load_3d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, aq.c * Cfg::BK + 32 * h,
+                          aq.w.tm * 128, 0);
+            a_used |= 1u << aslot;
+            a_par = (a_par & ~(1u << aslot)) | (aph << aslot);
+            adv(aq);
+            if (++aslot == NSTG_) {
+              aslot = 0;
+              aph ^= 1u;
+            }
+            prog = true;
+          }
+          if (bq.have && mbar_test_wait(empty_bar(bstage), bph ^ 1u)) {
+            const uint32_t fb = full_bar(bstage);
+            mbar_arrive_expect_tx(fb, 2 * Cfg::B_PLANE);
+            const uint32_t sB = sbase + bstage * Cfg::STAGE + 2 * Cfg::A_PLANE;
+            const int kx = bq.c * Cfg::BK;
+            tma_load_3d(sB, mB, fb, kx, bq.w.tn * BN, 0);
+            tma_load_3d(sB + Cfg::B_PLANE, mB, fb, kx, bq.w.tn * BN, 1);
+            b_used |= 1u << bstage;
+            b_par = (b_par & ~(1u << bstage)) | (bph << bstage);
+            adv(bq);
+            if (++bstage == STAGES) {
+              bstage = 0;
+              bph ^= 1u;
+            }
+            prog = true;
+          }
+          if (prog) {
+            idle = 0;
+            continue;
+          }
+          if (*abort_flag) {
+            ok = false;
+            break;
+          }
+          if (idle++ == 0) {
+            t0 = global_timer_ns();
+          } else if ((idle & 255u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicOr(err, kErrTimeout);
+            ok = false;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (!ok) {
+          // abort: let every copy this thread started land before shared memory is released
+          for (int b = 0; b < NSTG_; ++b)
+            if (a_used & (1u << b)) mbar_wait_drain(stg_full_bar(b), (a_par >> b) & 1u);
+          for (int b = 0; b < STAGES; ++b)
+            if (b_used & (1u << b)) mbar_wait_drain(full_bar(b), (b_par >> b) & 1u);
+        }
+      }
+    } else if (lane == 0) {
       uint32_t stage = 0, phase = 0;
       uint32_t last_phase[STAGES];
       bool issued[STAGES];
@@ -215,7 +459,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         const CUtensorMap* mA = sc.mapA(w.prob);
         const CUtensorMap* mB = sc.mapB(w.prob);
         if (w.prob != last_prob) {
-          tma_prefetch_desc(mA);
+          if (!FUSED) tma_prefetch_desc(mA);
           tma_prefetch_desc(mB);
           last_prob = w.prob;
         }
@@ -225,11 +469,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             break;
           }
           const uint32_t fb = full_bar(stage);
-          mbar_arrive_expect_tx(fb, Cfg::STAGE);
+          mbar_arrive_expect_tx(fb, FUSED ? 2 * Cfg::B_PLANE : Cfg::STAGE);
           const uint32_t sA = sbase + stage * Cfg::STAGE;
           const int kx = c * Cfg::BK;
-          tma_load_3d(sA, mA, fb, kx, w.tm * Cfg::BM, 0);
-          tma_load_3d(sA + Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, 1);
+          if (!FUSED) {
+            tma_load_3d(sA, mA, fb, kx, w.tm * Cfg::BM, 0);
+            tma_load_3d(sA + Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, 1);
+          }
           tma_load_3d(sA + 2 * Cfg::A_PLANE, mB, fb, kx, w.tn * BN, 0);
           tma_load_3d(sA + 2 * Cfg::A_PLANE + Cfg::B_PLANE, mB, fb, kx, w.tn * BN, 1);
           issued[stage] = true;
@@ -313,7 +559,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       }
     }
     __syncwarp();
-  } else {
+  } else if (warp < 2 + 4 * Cfg::EPI_WG) {
     // ------------------------------------------------------------ epilogue
     constexpr int EC = Cfg::EPI_COLS;
     const int q = warp & 3;                 // TMEM lane quadrant of this warp
@@ -450,6 +696,129 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         __syncwarp();
       }
     }
+  } else if constexpr (FUSED) {
+    // ------------------------------------------------------------ A (fused)
+    // FP32 chunks of A (128 rows x BK) are staged in a ring of STG_STAGES
+    // buffers, that many chunks ahead: by the producer thread with one TMA
+    // load per 128-byte-wide box when A's rows are 16-byte aligned, else by
+    // the split threads with 4-byte cp.async copies; both leave the
+    // SWIZZLE_128B layout, row r's 16-byte unit u at u ^ (r % 8).  Split
+    // thread t splits rows t, t + SPLIT_THREADS, ... of a staged chunk into
+    // the stage's hi/lo planes (conflict-free shared accesses on both
+    // sides) and fences its writes for the async proxy; then one lane a
+    // warp arrives on the stage's full barrier and frees the staging
+    // buffer.  The split warps never wait for one another.  Every wait is
+    // bounded.
+    constexpr int UPR = Cfg::STG_ROW / 16;            // 16-byte units per staged row
+    constexpr int BOX = 128 * 128;                    // bytes of one 128-byte-wide staging box
+    const int ct = threadIdx.x - Cfg::SPLIT0;
+    const uint32_t stg0 = sbase + Cfg::OFF_STG;
+    const uint8_t* stg_gen = smem + Cfg::OFF_STG;
+    const bool tma = sc.srcA(0).vec;                  // uniform: the producer stages A by TMA
+
+    // split cursor (sc_) and, when the split threads stage A themselves with
+    // cp.async, fill cursor (fc) over this CTA's (unit, chunk)s
+    struct Cursor {
+      int u, c;
+      Work w;
+      bool have;
+    };
+    auto first = [&](Cursor& q, int u0) {
+      q.have = false;
+      for (q.u = u0; q.u < nunits; q.u += gridDim.x) {
+        q.w = sc.work(q.u);
+        if (q.w.c0 < q.w.c1) {
+          q.have = true;
+          q.c = q.w.c0;
+          break;
+        }
+      }
+    };
+    auto advance = [&](Cursor& q) {
+      if (++q.c >= q.w.c1) first(q, q.u + gridDim.x);
+    };
+    Cursor sc_{}, fc{};
+    first(sc_, blockIdx.x);
+    fc = sc_;
+    // cp.async staging of the fill cursor's chunk into buffer b (4-byte
+    // copies: A's rows are not 16-byte aligned), same layout as the TMA boxes
+    auto fill = [&](int b) {
+      const FusedA src = sc.srcA(fc.w.prob);
+      const int64_t kbase = static_cast<int64_t>(fc.c) * Cfg::BK;
+      for (int i = ct; i < 128 * UPR; i += Cfg::SPLIT_THREADS) {
+        const int r = i / UPR, j = i % UPR;
+        const uint32_t dst = stg0 + b * Cfg::STG_BYTES + (j >> 3) * BOX + r * 128 +
+                             (((j & 7) ^ (r & 7)) << 4);
+        const int64_t row = static_cast<int64_t>(fc.w.tm) * 128 + r;
+        const int64_t k = kbase + 4 * j;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const bool in = row < src.M && k + e < src.K;
+          cp_async_4(dst + 4 * e, in ? src.A + row * src.lda + k + e : src.A, in ? 4u : 0u);
+        }
+      }
+      cp_async_mbar_arrive(stg_full_bar(b));
+      advance(fc);
+    };
+
+    if (!tma) {
+#pragma unroll
+      for (int b = 0; b < NSTG; ++b)
+        if (fc.have) fill(b);
+    }
+    uint32_t stage = 0, phase = 0, slot = 0, sphase = 0;
+    unsigned amax = 0;
+    int last_prob = -1, last_tm = -1;
+    while (sc_.have) {
+      if (sc_.w.prob != last_prob || sc_.w.tm != last_tm) {
+        amax = sc.srcA(sc_.w.prob).amaxA[sc_.w.tm];
+        last_prob = sc_.w.prob;
+        last_tm = sc_.w.tm;
+      }
+      // lane 0 waits for the warp; __syncwarp orders its acquire before the
+      // other lanes' accesses
+      int w_ok = 1;
+      if (lane == 0)
+        w_ok = mbar_wait(stg_full_bar(slot), sphase, abort_flag, err) &&
+               mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, err);
+      if (!__shfl_sync(0xffffffffu, w_ok, 0)) break;
+      const float sf = pow2f(-block_exponent(amax));
+      const bool finite = amax < 0x7F800000u;
+      uint8_t* hi = smem + stage * Cfg::STAGE;
+      const uint8_t* sbuf = stg_gen + slot * Cfg::STG_BYTES;
+      // one branch for the whole chunk, so that the eight groups of a row
+      // form one straight-line block the compiler can interleave
+      if (finite)
+        fused_split_rows<TF32, true, Cfg::SPLIT_THREADS>(sbuf, hi, hi + Cfg::A_PLANE, ct, sf);
+      else
+        fused_split_rows<TF32, false, Cfg::SPLIT_THREADS>(sbuf, hi, hi + Cfg::A_PLANE, ct, sf);
+      // every lane fences its writes for the async proxy; after __syncwarp
+      // lane 0 arrives for the warp (one arrival per warp)
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(full_bar(stage));
+        mbar_arrive(stg_empty_bar(slot));
+      }
+      // cp.async staging: refill this buffer with the chunk STG_STAGES ahead
+      // once every split warp has read it
+      if (!tma && fc.have) {
+        int e_ok = 1;
+        if (lane == 0) e_ok = mbar_wait(stg_empty_bar(slot), sphase, abort_flag, err);
+        if (!__shfl_sync(0xffffffffu, e_ok, 0)) break;
+        fill(slot);
+      }
+      advance(sc_);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+      if (++slot == NSTG) {
+        slot = 0;
+        sphase ^= 1u;
+      }
+    }
+    if (!tma) cp_async_wait_all();   // no copy may land after the shared memory is released
   }
 
   tc_fence_before();
@@ -474,6 +843,16 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32>::THREADS, 1) tc_grouped_kernel
   tc_gemm_body<BN, TF32>(sc);
 }
 
+// Fused variant: tmA maps A itself (FP32, 128-byte-wide boxes of 128 rows)
+// when its rows are 16-byte aligned; otherwise it is unused.
+template <int BN, bool TF32>
+__global__ void __launch_bounds__(TcCfg<BN, TF32, true>::THREADS, 1)
+    tc_gemm_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const TcArgs a) {
+  SingleSched sc{&tmA, &tmB, &a};
+  tc_gemm_body<BN, TF32, SingleSched, true>(sc);
+}
+
 // Split-K fix-up: C = sum_s partial[s] + beta * C, where each partial already
 // holds alpha * (its share of A*B); partials are summed in increasing s (a
 // fixed order, so results do not depend on timing).
@@ -491,7 +870,11 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
   }
 }
 
-int tc_smem_bytes(int bn, Prec prec) {
+int tc_smem_bytes(int bn, Prec prec, bool fused) {
+  if (fused) {
+    if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true, true>::SMEM : TcCfg<128, true, true>::SMEM;
+    return bn == 64 ? TcCfg<64, false, true>::SMEM : TcCfg<128, false, true>::SMEM;
+  }
   if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true>::SMEM : TcCfg<128, true>::SMEM;
   return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
 }
@@ -504,54 +887,71 @@ int tc_chunk_bytes(int bn) {
 // The dynamic shared memory limit of every kernel variant is raised once per
 // device and thread, outside any stream capture: plans call tc_prepare when
 // they are created, launches call it again (a no-op after the first time).
-template <int BN, bool TF32>
+template <int BN, bool TF32, bool FUSED>
 static cudaError_t prepare_variant() {
-  using Cfg = TcCfg<BN, TF32>;
+  using Cfg = TcCfg<BN, TF32, FUSED>;
   static thread_local int configured_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (configured_device != dev) {
-    e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Cfg::SMEM);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32>,
+    if (FUSED) {
+      e = cudaFuncSetAttribute(tc_gemm_fused_kernel<BN, TF32>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    } else {
+      e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               Cfg::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    }
     if (e != cudaSuccess) return e;
     configured_device = dev;
   }
   return cudaSuccess;
 }
 
-cudaError_t tc_prepare(int bn, Prec prec) {
+template <bool FUSED>
+static cudaError_t prepare_fused(int bn, Prec prec) {
   if (prec == Prec::TF32) {
-    if (bn == 64) return prepare_variant<64, true>();
-    if (bn == 128) return prepare_variant<128, true>();
+    if (bn == 64) return prepare_variant<64, true, FUSED>();
+    if (bn == 128) return prepare_variant<128, true, FUSED>();
   } else {
-    if (bn == 64) return prepare_variant<64, false>();
-    if (bn == 128) return prepare_variant<128, false>();
+    if (bn == 64) return prepare_variant<64, false, FUSED>();
+    if (bn == 128) return prepare_variant<128, false, FUSED>();
   }
   return cudaErrorInvalidValue;
 }
 
+cudaError_t tc_prepare(int bn, Prec prec, bool fused) {
+  return fused ? prepare_fused<true>(bn, prec) : prepare_fused<false>(bn, prec);
+}
+
 template <int BN, bool TF32>
-static cudaError_t launch_variant(int grid, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                                  const TcArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, TF32>;
-  cudaError_t e = prepare_variant<BN, TF32>();
-  if (e != cudaSuccess) return e;
-  tc_gemm_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
+                                  const CUtensorMap& tmB, const TcArgs& a, cudaStream_t s) {
+  if (fused) {
+    using Cfg = TcCfg<BN, TF32, true>;
+    cudaError_t e = prepare_variant<BN, TF32, true>();
+    if (e != cudaSuccess) return e;
+    tc_gemm_fused_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+  } else {
+    using Cfg = TcCfg<BN, TF32>;
+    cudaError_t e = prepare_variant<BN, TF32, false>();
+    if (e != cudaSuccess) return e;
+    tc_gemm_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s) {
   if (l.prec == Prec::TF32) {
-    if (l.bn == 64) return launch_variant<64, true>(l.grid, tmA, tmB, a, s);
-    if (l.bn == 128) return launch_variant<128, true>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, true>(l.grid, l.fused, tmA, tmB, a, s);
   } else {
-    if (l.bn == 64) return launch_variant<64, false>(l.grid, tmA, tmB, a, s);
-    if (l.bn == 128) return launch_variant<128, false>(l.grid, tmA, tmB, a, s);
+    if (l.bn == 64) return launch_variant<64, false>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, false>(l.grid, l.fused, tmA, tmB, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -559,7 +959,7 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
 template <int BN, bool TF32>
 static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaStream_t s) {
   using Cfg = TcCfg<BN, TF32>;
-  cudaError_t e = prepare_variant<BN, TF32>();
+  cudaError_t e = prepare_variant<BN, TF32, false>();
   if (e != cudaSuccess) return e;
   tc_grouped_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
   return cudaGetLastError();

@@ -48,7 +48,7 @@ def effective_key(mode, cid, M, N, K):
     per = -(-chunks // sk)
     sk = -(-chunks // per)
     tiles_m = -(-M // 128)
-    return (c["block_n"], sk, min(c["kb"], per), max(1, min(c["group_m"], tiles_m)))
+    return (c["block_n"], sk, min(c["kb"], per), max(1, min(c["group_m"], tiles_m)), c["fused"])
 
 
 def timed_choice(times, mode, cid, shape):
