@@ -61,11 +61,17 @@ void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const g
 
 namespace {
 
+// An ensemble of `members` networks trained from different initial weights
+// on the same data (theta holds their parameters one after another); the
+// prediction is the mean of their outputs, which evens out the run-to-run
+// spread of a single network's choices.
 struct Model {
   bool loaded = false;
+  int members = 0;
   std::vector<float> mean, stdv, theta;
   float ymean = 0.0f, ystd = 1.0f;
 };
+constexpr int kMembers = 5;
 std::mutex g_model_mu;
 Model g_model;
 
@@ -86,14 +92,15 @@ int sm_count() {
 // Device workspace of one forward + backward pass over n samples.
 struct Pass {
   int n = 0;
-  DevBuf X, t, y, Z1, Z2, H1, H2, dZ1T, dZ2T, dy, ones, theta, grad, loss;
+  DevBuf X, t, y, Z1, Z2, H1, H2, dZ1T, dZ2T, dy, ones, theta, grad, loss, part;
   gemm_status alloc(int n_) {
     n = n_;
     const int P = mlp_param_count();
     const size_t nh = (size_t)n * kHidden;
     if (X.alloc((size_t)n * kFeatures) || t.alloc(n) || y.alloc(n) || Z1.alloc(nh) || Z2.alloc(nh) ||
         H1.alloc(nh) || H2.alloc(nh) || dZ1T.alloc(nh) || dZ2T.alloc(nh) || dy.alloc(n) ||
-        ones.alloc(n) || theta.alloc(P) || grad.alloc(P) || loss.alloc(1)) {
+        ones.alloc(n) || theta.alloc(P) || grad.alloc(P) || loss.alloc(1) ||
+        part.alloc((size_t)batch_outer_parts(n) * kHidden * kHidden)) {
       cudaGetLastError();
       return fail(GEMM_ERR_ALLOC, "cost-model buffers for %d samples", n);
     }
@@ -121,14 +128,16 @@ gemm_status loss_and_grad(Pass& ps, bool want_loss, cudaStream_t s) {
   float* gb2 = gW2 + Hd * Hd;
   float* gw3 = gb2 + Hd;
   float* gb3 = gw3 + Hd;
-  // weight gradients: products over the batch with the library's FP32 gemm
-  if ((e = simt_gemm_launch(Hd, F, n, 1.0f, ps.dZ1T.p, n, ps.X.p, F, 0.0f, gW1, F, s)) ||
-      (e = simt_gemm_launch(Hd, 1, n, 1.0f, ps.dZ1T.p, n, ps.ones.p, 1, 0.0f, gb1, 1, s)) ||
-      (e = simt_gemm_launch(Hd, Hd, n, 1.0f, ps.dZ2T.p, n, ps.H1.p, Hd, 0.0f, gW2, Hd, s)) ||
-      (e = simt_gemm_launch(Hd, 1, n, 1.0f, ps.dZ2T.p, n, ps.ones.p, 1, 0.0f, gb2, 1, s)) ||
-      (e = simt_gemm_launch(1, Hd, n, 1.0f, ps.dy.p, n, ps.H2.p, Hd, 0.0f, gw3, Hd, s)) ||
-      (e = simt_gemm_launch(1, 1, n, 1.0f, ps.dy.p, n, ps.ones.p, 1, 0.0f, gb3, 1, s)))
-    return cuda_fail(e, "gradient gemm");
+  // weight gradients: products over the batch (the partials of one product
+  // are summed before the next one overwrites the scratch: same stream)
+  float* pt = ps.part.p;
+  if ((e = batch_outer_launch(ps.dZ1T.p, n, ps.X.p, F, Hd, F, n, pt, gW1, s)) ||
+      (e = batch_outer_launch(ps.dZ1T.p, n, ps.ones.p, 1, Hd, 1, n, pt, gb1, s)) ||
+      (e = batch_outer_launch(ps.dZ2T.p, n, ps.H1.p, Hd, Hd, Hd, n, pt, gW2, s)) ||
+      (e = batch_outer_launch(ps.dZ2T.p, n, ps.ones.p, 1, Hd, 1, n, pt, gb2, s)) ||
+      (e = batch_outer_launch(ps.dy.p, n, ps.H2.p, Hd, 1, Hd, n, pt, gw3, s)) ||
+      (e = batch_outer_launch(ps.dy.p, n, ps.ones.p, 1, 1, 1, n, pt, gb3, s)))
+    return cuda_fail(e, "gradient products");
   return GEMM_OK;
 }
 
@@ -159,14 +168,18 @@ std::vector<float> init_params(uint64_t seed) {
 gemm_status save_model(const Model& m, const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(GEMM_ERR_IO, "cannot write %s", path);
-  std::fprintf(f, "gb300-gemm-costmodel 1\nfeatures %d hidden %d params %d\n", kFeatures, kHidden,
-               (int)m.theta.size());
+  const int P = mlp_param_count();
+  std::fprintf(f, "gb300-gemm-costmodel 2\nfeatures %d hidden %d params %d members %d\n", kFeatures,
+               kHidden, P, m.members);
   std::fprintf(f, "mean");
   for (float v : m.mean) std::fprintf(f, " %.9g", v);
   std::fprintf(f, "\nstd");
   for (float v : m.stdv) std::fprintf(f, " %.9g", v);
-  std::fprintf(f, "\ntarget %.9g %.9g\ntheta", m.ymean, m.ystd);
-  for (float v : m.theta) std::fprintf(f, " %.9g", v);
+  std::fprintf(f, "\ntarget %.9g %.9g", m.ymean, m.ystd);
+  for (int k = 0; k < m.members; ++k) {
+    std::fprintf(f, "\ntheta");
+    for (int i = 0; i < P; ++i) std::fprintf(f, " %.9g", m.theta[(size_t)k * P + i]);
+  }
   std::fprintf(f, "\n");
   const bool ok = std::ferror(f) == 0;
   std::fclose(f);
@@ -182,12 +195,17 @@ gemm_status load_model(const char* path, Model* m) {
     std::fclose(f);
     return fail(GEMM_ERR_IO, "%s: malformed cost-model file (%s)", path, what);
   };
-  if (std::fscanf(f, "%63s %d", tag, &ver) != 2 || std::strcmp(tag, "gb300-gemm-costmodel") || ver != 1)
+  // version 1: one network; version 2: "members K" networks
+  if (std::fscanf(f, "%63s %d", tag, &ver) != 2 || std::strcmp(tag, "gb300-gemm-costmodel") ||
+      (ver != 1 && ver != 2))
     return bad("header");
   if (std::fscanf(f, " features %d hidden %d params %d", &F, &Hd, &P) != 3 || F != kFeatures ||
       Hd != kHidden || P != mlp_param_count())
     return bad("dimensions");
-  m->mean.resize(F), m->stdv.resize(F), m->theta.resize(P);
+  int K = 1;
+  if (ver == 2 && (std::fscanf(f, " members %d", &K) != 1 || K < 1 || K > 64)) return bad("members");
+  m->members = K;
+  m->mean.resize(F), m->stdv.resize(F), m->theta.resize((size_t)K * P);
   if (std::fscanf(f, " %63s", tag) != 1 || std::strcmp(tag, "mean")) return bad("mean");
   for (auto& v : m->mean)
     if (std::fscanf(f, "%f", &v) != 1) return bad("mean values");
@@ -195,9 +213,13 @@ gemm_status load_model(const char* path, Model* m) {
   for (auto& v : m->stdv)
     if (std::fscanf(f, "%f", &v) != 1 || !(v > 0.0f)) return bad("std values");
   if (std::fscanf(f, " target %f %f", &m->ymean, &m->ystd) != 2 || !(m->ystd > 0.0f)) return bad("target");
-  if (std::fscanf(f, " %63s", tag) != 1 || std::strcmp(tag, "theta")) return bad("theta");
-  for (auto& v : m->theta)
-    if (std::fscanf(f, "%f", &v) != 1 || !std::isfinite(v)) return bad("theta values");
+  for (int k = 0; k < K; ++k) {
+    if (std::fscanf(f, " %63s", tag) != 1 || std::strcmp(tag, "theta")) return bad("theta");
+    for (int i = 0; i < P; ++i) {
+      float& v = m->theta[(size_t)k * P + i];
+      if (std::fscanf(f, "%f", &v) != 1 || !std::isfinite(v)) return bad("theta values");
+    }
+  }
   std::fclose(f);
   m->loaded = true;
   return GEMM_OK;
@@ -248,19 +270,25 @@ gemm_status costmodel_pick(gemm_mode mode, int64_t M, int64_t N, int64_t K, int*
     for (int f = 0; f < kFeatures; ++f)
       X[(size_t)i * kFeatures + f] = (X[(size_t)i * kFeatures + f] - m.mean[f]) / m.stdv[f];
   }
+  const int P = mlp_param_count();
   DevBuf dX, dth, dy;
-  if (dX.alloc(X.size()) || dth.alloc(m.theta.size()) || dy.alloc(n)) {
+  if (dX.alloc(X.size()) || dth.alloc(m.theta.size()) || dy.alloc((size_t)n * m.members)) {
     cudaGetLastError();
     return fail(GEMM_ERR_ALLOC, "cost-model prediction buffers");
   }
   cudaError_t e;
   if ((e = cudaMemcpy(dX.p, X.data(), X.size() * 4, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(dth.p, m.theta.data(), m.theta.size() * 4, cudaMemcpyHostToDevice)) ||
-      (e = mlp_forward_launch(dX.p, n, dth.p, dy.p, nullptr, nullptr, nullptr)))
-    return cuda_fail(e, "cost-model forward");
-  std::vector<float> y(n);
-  if ((e = cudaMemcpy(y.data(), dy.p, n * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      (e = cudaMemcpy(dth.p, m.theta.data(), m.theta.size() * 4, cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "cost-model upload");
+  for (int k = 0; k < m.members; ++k)
+    if ((e = mlp_forward_launch(dX.p, n, dth.p + (size_t)k * P, dy.p + (size_t)k * n, nullptr, nullptr,
+                                nullptr)) != cudaSuccess)
+      return cuda_fail(e, "cost-model forward");
+  std::vector<float> ys((size_t)n * m.members), y(n, 0.0f);
+  if ((e = cudaMemcpy(ys.data(), dy.p, ys.size() * 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "cost-model prediction copy");
+  for (int k = 0; k < m.members; ++k)
+    for (int i = 0; i < n; ++i) y[i] += ys[(size_t)k * n + i] / m.members;
   int best = 0;
   for (int i = 1; i < n; ++i)
     if (y[i] < y[best]) best = i;
@@ -377,7 +405,6 @@ gemm_status gemm_costmodel_train(const char* timings_path, int epochs, uint64_t 
   Pass ps;
   if ((st = ps.alloc(n)) != GEMM_OK) return st;
   const int P = mlp_param_count();
-  m.theta = init_params(seed);
   DevBuf mom, var;
   if (mom.alloc(P) || var.alloc(P)) {
     cudaGetLastError();
@@ -385,24 +412,33 @@ gemm_status gemm_costmodel_train(const char* timings_path, int epochs, uint64_t 
   }
   cudaError_t e;
   if ((e = cudaMemcpy(ps.X.p, X.data(), X.size() * 4, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(ps.t.p, t.data(), t.size() * 4, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemcpy(ps.theta.p, m.theta.data(), P * 4, cudaMemcpyHostToDevice)) ||
-      (e = cudaMemset(mom.p, 0, P * 4)) || (e = cudaMemset(var.p, 0, P * 4)))
+      (e = cudaMemcpy(ps.t.p, t.data(), t.size() * 4, cudaMemcpyHostToDevice)))
     return cuda_fail(e, "upload training data");
-  const float lr0 = 3e-3f;
-  for (int step = 1; step <= epochs; ++step) {
-    if ((st = loss_and_grad(ps, false, nullptr)) != GEMM_OK) return st;
-    const double frac = (double)(step - 1) / epochs;
-    const float lr = (float)(lr0 * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
-    if ((e = adam_launch(ps.theta.p, ps.grad.p, mom.p, var.p, P, step, lr, 0.9f, 0.999f, 1e-8f, nullptr)))
-      return cuda_fail(e, "adam");
+  m.members = kMembers;
+  m.theta.assign((size_t)kMembers * P, 0.0f);
+  float loss_sum = 0.0f;
+  for (int k = 0; k < kMembers; ++k) {
+    // member k: its own initial weights, the same data and schedule
+    const std::vector<float> th0 = init_params(splitmix64(seed + 0x632BE59BD9B4E019ull * (uint64_t)k));
+    if ((e = cudaMemcpy(ps.theta.p, th0.data(), P * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(mom.p, 0, P * 4)) || (e = cudaMemset(var.p, 0, P * 4)))
+      return cuda_fail(e, "upload initial weights");
+    const float lr0 = 3e-3f;
+    for (int step = 1; step <= epochs; ++step) {
+      if ((st = loss_and_grad(ps, false, nullptr)) != GEMM_OK) return st;
+      const double frac = (double)(step - 1) / epochs;
+      const float lr = (float)(lr0 * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.14159265358979 * frac))));
+      if ((e = adam_launch(ps.theta.p, ps.grad.p, mom.p, var.p, P, step, lr, 0.9f, 0.999f, 1e-8f, nullptr)))
+        return cuda_fail(e, "adam");
+    }
+    if ((st = loss_and_grad(ps, true, nullptr)) != GEMM_OK) return st;
+    float loss = 0;
+    if ((e = cudaMemcpy(&loss, ps.loss.p, 4, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(m.theta.data() + (size_t)k * P, ps.theta.p, P * 4, cudaMemcpyDeviceToHost)))
+      return cuda_fail(e, "download model");
+    loss_sum += loss;
   }
-  if ((st = loss_and_grad(ps, true, nullptr)) != GEMM_OK) return st;
-  float loss = 0;
-  if ((e = cudaMemcpy(&loss, ps.loss.p, 4, cudaMemcpyDeviceToHost)) ||
-      (e = cudaMemcpy(m.theta.data(), ps.theta.p, P * 4, cudaMemcpyDeviceToHost)))
-    return cuda_fail(e, "download model");
-  if (final_loss) *final_loss = loss;
+  if (final_loss) *final_loss = loss_sum / kMembers;   // mean training loss of the members
   m.loaded = true;
   if (out_model && *out_model && (st = save_model(m, out_model)) != GEMM_OK) return st;
   std::lock_guard<std::mutex> lk(g_model_mu);

@@ -10,8 +10,8 @@
 //             pre-activation gradients dz2 = dy w3 [z2 > 0],
 //             dz1 = W2^T dz2 [z1 > 0], written transposed ([H][n]) next to the
 //             activations h1, h2 ([n][H]); the weight gradients are then
-//             products over the batch, dW = dZ^T H, computed by the library's
-//             own FP32 gemm kernel (costmodel.cpp).
+//             products over the batch, dW = dZ^T H (batch_outer_launch:
+//             per-chunk partials summed in a fixed order).
 //   mse     : one CTA, fixed summation order (deterministic).
 //   adam    : elementwise Adam update (Kingma & Ba, Algorithm 1).
 #include <cuda_runtime.h>
@@ -129,6 +129,65 @@ __global__ void adam_kernel(float* __restrict__ theta, const float* __restrict__
   }
 }
 
+// Products over the batch, out[r][c] = sum_i A[r lda + i] B[i ldb + c]
+// (r < R <= 64, c < C <= 64): CTA p sums samples [p kOuterChunk, ...) into
+// partial p, staging 32 samples of both operands in shared memory per step;
+// a second kernel adds the partials in increasing p (a fixed order, so the
+// gradient does not depend on timing).
+constexpr int kOuterChunk = 512;
+
+__global__ void __launch_bounds__(256) outer_partial_kernel(const float* __restrict__ A, int lda,
+                                                            const float* __restrict__ B, int ldb,
+                                                            int R, int C, int n,
+                                                            float* __restrict__ part) {
+  __shared__ float sA[64][33];
+  __shared__ float sB[32][65];
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.x * kOuterChunk;
+  const int i1 = min(n, i0 + kOuterChunk);
+  const int m = R * C;
+  float acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = 0.0f;
+  for (int s0 = i0; s0 < i1; s0 += 32) {
+    for (int idx = t; idx < R * 32; idx += 256) {
+      const int r = idx >> 5, j = idx & 31;
+      sA[r][j] = s0 + j < i1 ? A[static_cast<int64_t>(r) * lda + s0 + j] : 0.0f;
+    }
+    for (int idx = t; idx < 32 * C; idx += 256) {
+      const int j = idx / C, c = idx - j * C;
+      sB[j][c] = s0 + j < i1 ? B[static_cast<int64_t>(s0 + j) * ldb + c] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int o = t + 256 * k;
+      if (o < m) {
+        const int r = o / C, c = o - r * C;
+        float a = acc[k];
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) a = fmaf(sA[r][j], sB[j][c], a);
+        acc[k] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int o = t + 256 * k;
+    if (o < m) part[static_cast<int64_t>(blockIdx.x) * m + o] = acc[k];
+  }
+}
+
+__global__ void sum_partials_kernel(const float* __restrict__ part, int nparts, int m,
+                                    float* __restrict__ out) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= m) return;
+  float s = 0.0f;
+  for (int p = 0; p < nparts; ++p) s += part[static_cast<int64_t>(p) * m + o];
+  out[o] = s;
+}
+
 __global__ void fill_value_kernel(float* x, int n, float v) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = v;
 }
@@ -168,6 +227,17 @@ cudaError_t adam_launch(float* theta, const float* g, float* m, float* v, int P,
   c1 -= p1;
   c2 -= p2;
   adam_kernel<<<(P + 255) / 256, 256, 0, s>>>(theta, g, m, v, P, lr, b1, b2, eps, (float)c1, (float)c2);
+  return cudaGetLastError();
+}
+
+int batch_outer_parts(int n) { return (n + kOuterChunk - 1) / kOuterChunk; }
+
+cudaError_t batch_outer_launch(const float* A, int lda, const float* B, int ldb, int R, int C, int n,
+                               float* part, float* out, cudaStream_t s) {
+  if (R < 1 || R > 64 || C < 1 || C > 64 || n < 1) return cudaErrorInvalidValue;
+  const int parts = batch_outer_parts(n);
+  outer_partial_kernel<<<parts, 256, 0, s>>>(A, lda, B, ldb, R, C, n, part);
+  sum_partials_kernel<<<(R * C + 255) / 256, 256, 0, s>>>(part, parts, R * C, out);
   return cudaGetLastError();
 }
 

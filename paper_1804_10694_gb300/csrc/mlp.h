@@ -21,5 +21,10 @@ cudaError_t mse_launch(const float* y, const float* t, int n, float* out, cudaSt
 cudaError_t adam_launch(float* theta, const float* g, float* m, float* v, int P, int step, float lr,
                         float b1, float b2, float eps, cudaStream_t s);
 cudaError_t fill_value_launch(float* x, int n, float v, cudaStream_t s);
+// out[r][c] = sum_{i<n} A[r lda + i] B[i ldb + c] for r < R, c < C (both
+// <= 64); part holds batch_outer_parts(n) * R * C floats of scratch.
+int batch_outer_parts(int n);
+cudaError_t batch_outer_launch(const float* A, int lda, const float* B, int ldb, int R, int C, int n,
+                               float* part, float* out, cudaStream_t s);
 
 }  // namespace gb

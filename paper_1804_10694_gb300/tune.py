@@ -6,10 +6,12 @@ model saves.  The paper tunes tile sizes by search (Section VI-A); this is
 that search, its learned replacement and the comparison between them.
 
     python -m paper_1804_10694_gb300.tune --out-dir DIR [--train 700]
-        [--heldout 100] [--reps 5] [--epochs 3000] [--mode bf16x3]
+        [--heldout 100] [--reps 5] [--epochs 6000] [--mode bf16x3]
+        [--reuse-timings DIR2]
 
 Writes DIR/timings_train.csv, DIR/timings_heldout.csv, DIR/costmodel.txt and
-DIR/regret.json.
+DIR/regret.json.  With --reuse-timings the two timing files are copied from
+DIR2 instead of measured (the model is retrained and evaluated on them).
 """
 from __future__ import annotations
 
@@ -70,8 +72,10 @@ def main(argv=None):
     ap.add_argument("--train", type=int, default=700)
     ap.add_argument("--heldout", type=int, default=100)
     ap.add_argument("--reps", type=int, default=5)
-    ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--epochs", type=int, default=6000)
     ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--reuse-timings", default=None,
+                    help="directory with timings_train.csv and timings_heldout.csv to reuse")
     args = ap.parse_args(argv)
 
     import workloads as W
@@ -85,14 +89,19 @@ def main(argv=None):
     train = W.training_shapes(args.train, seed=args.seed)
     held = list(CONV_SHAPES) + W.training_shapes(args.heldout, seed=args.seed + 1)
 
-    t0 = time.time()
-    pkg.autotune(train, mode=args.mode, reps=args.reps, out_path=tpath)
-    t_train = time.time() - t0
-    per_shape_s = []
-    for s in held:
-        t1 = time.time()
-        pkg.autotune([s], mode=args.mode, reps=args.reps, out_path=hpath)
-        per_shape_s.append(time.time() - t1)
+    t_train, per_shape_s = None, []
+    if args.reuse_timings:
+        import shutil
+        shutil.copyfile(os.path.join(args.reuse_timings, "timings_train.csv"), tpath)
+        shutil.copyfile(os.path.join(args.reuse_timings, "timings_heldout.csv"), hpath)
+    else:
+        t0 = time.time()
+        pkg.autotune(train, mode=args.mode, reps=args.reps, out_path=tpath)
+        t_train = time.time() - t0
+        for s in held:
+            t1 = time.time()
+            pkg.autotune([s], mode=args.mode, reps=args.reps, out_path=hpath)
+            per_shape_s.append(time.time() - t1)
     t2 = time.time()
     loss = pkg.costmodel_train(tpath, epochs=args.epochs, seed=args.seed, out_model=mpath)
     t_fit = time.time() - t2
@@ -131,7 +140,7 @@ def main(argv=None):
         "final_train_mse_normalised": loss,
         "autotune_train_seconds": t_train,
         "fit_seconds": t_fit,
-        "exhaustive_seconds_per_heldout_shape_mean": float(np.mean(per_shape_s)),
+        "exhaustive_seconds_per_heldout_shape_mean": float(np.mean(per_shape_s)) if per_shape_s else None,
         "model_predict_seconds_mean": float(np.mean(pred_s)),
         "model_regret_mean": float(mr.mean()),
         "model_regret_median": float(np.median(mr)),

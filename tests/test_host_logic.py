@@ -110,3 +110,20 @@ def test_training_shapes_bounded():
     for m, n, k in shapes:
         assert m * n * k <= 2 ** 37
         assert min(m, n, k) >= 1
+
+
+def test_costmodel_ensemble_file_format(tmp_path):
+    """Version 2 files hold `members` networks (one theta line each); a
+    missing member or a bad member count is rejected."""
+    P = 64 * 15 + 64 + 64 * 64 + 64 + 64 + 1
+    head = ("gb300-gemm-costmodel 2\nfeatures 15 hidden 64 params %d members %%d\nmean %s\nstd %s\n"
+            "target -1.5 2\n" % (P, " ".join(["0"] * 15), " ".join(["1"] * 15)))
+    theta = "theta %s\n" % " ".join(["0.01"] * P)
+    lib = pkg.load()
+    f = tmp_path / "m.txt"
+    f.write_text(head % 3 + theta * 3)
+    assert lib.gemm_costmodel_load(str(f).encode()) == 0
+    f.write_text(head % 3 + theta * 2)
+    assert lib.gemm_costmodel_load(str(f).encode()) == 7
+    f.write_text(head % 0 + theta)
+    assert lib.gemm_costmodel_load(str(f).encode()) == 7
