@@ -288,10 +288,12 @@ int gemm_device_sm_count(void);
  * leading dimension ld, device memory) into hi/lo planes
  * planes[2][rows][pitch] (bf16 for BF16X3, tf32 values in 32-bit containers
  * for TF32X3; pitch = cols rounded up to 8 resp. 4) and writes the per-block
- * max |x| bit patterns to amax[ceil(rows/128)].  `transpose` != 0 treats X as
- * a K x N matrix B and writes planes[2][N][pitch] with
- * amax[ceil(N/128)] (blocks of 128 columns).  All pointers are device
- * pointers; amax must be zeroed by the caller. */
+ * max |x| bit patterns to amax[0 .. nblk), nblk = ceil(rows/128); blocks
+ * outside the safe range are split with their exponent.  `transpose` != 0
+ * treats X as a K x N matrix B and writes planes[2][N][pitch], with
+ * nblk = ceil(N/128) blocks of 128 columns.  amax must hold 2 * nblk words,
+ * zeroed by the caller (the second half counts pack items per block).  All
+ * pointers are device pointers. */
 gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t cols,
                             const float* X, int64_t ld, void* planes, int64_t pitch,
                             unsigned* amax, gemm_stream_t stream);
@@ -305,11 +307,12 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
  * afford the device synchronisation cudaMalloc/cudaFree may imply.  The paper
  * has no counterpart: it is an interface convenience of this library.
  *
- * The call allocates nothing.  Its scratch (packed hi/lo operand planes and
- * block maxima) is a fixed 64 MiB static device array that every GPU which
- * loads this code holds until the process exits; a problem needing more,
- * 4 * (M + N) * roundup(K, 8) bytes plus 4 * (ceil(M/128) + ceil(N/128)) for
- * the maxima (each part rounded up to 256 bytes), is rejected with
+ * The call allocates nothing.  Its scratch (packed hi/lo operand planes,
+ * block maxima and per-block pack counters) is a fixed 64 MiB static device
+ * array that every GPU which loads this code holds until the process exits;
+ * a problem needing more, 4 * (M + N) * roundup(K, 8) bytes plus
+ * 8 * (ceil(M/128) + ceil(N/128)) for the maxima and counters (each part
+ * rounded up to 256 bytes), is rejected with
  * GEMM_ERR_INVALID_ARG (for square problems the limit is about
  * M = N = K = 2896).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first

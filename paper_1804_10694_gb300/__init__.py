@@ -210,10 +210,11 @@ def split_pack(X, mode="bf16x3", transpose: bool = False, stream=None):
     pitch = packed_pitch(m, K)
     dt = torch.bfloat16 if m == 2 else torch.float32
     planes = torch.zeros((2, prow, pitch), dtype=dt, device=X.device)
-    amax = torch.zeros(((prow + 127) // 128,), dtype=torch.int32, device=X.device)
+    nblk = (prow + 127) // 128
+    work = torch.zeros((2 * nblk,), dtype=torch.int32, device=X.device)   # maxima, then counters
     check(load().gemm_split_pack(m, 1 if transpose else 0, rows, cols, px, ld, planes.data_ptr(),
-                                 pitch, amax.data_ptr(), _stream_handle(stream)))
-    return planes, amax
+                                 pitch, work.data_ptr(), _stream_handle(stream)))
+    return planes, work[:nblk]
 
 
 # ------------------------------------------------------------------ grouped

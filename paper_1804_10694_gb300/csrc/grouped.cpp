@@ -37,11 +37,10 @@ struct gemm_grouped_plan_s {
   gb::GroupedProblem* d_probs = nullptr;
   gb::GroupedPtrs* d_ptrs = nullptr;
   gb::GroupedUnit* d_units = nullptr;
-  int* d_absmax_prefix = nullptr;   // rescale-pass items
   int* d_split_prefix = nullptr;
   unsigned* d_amax = nullptr;
   size_t amax_bytes = 0;
-  int num_units = 0, absmax_total = 0, split_total = 0;
+  int num_units = 0, split_total = 0;
   std::vector<gb::GroupedPtrs> h_ptrs, uploaded;
   bool have_uploaded = false;
   cudaStream_t cap_stream = nullptr;
@@ -77,9 +76,8 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   if (p->num_units == 0) return GEMM_OK;
   if ((e = cudaMemsetAsync(p->d_amax, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "clear block maxima");
-  if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_split_prefix, p->split_total,
-                               p->d_absmax_prefix, p->absmax_total, p->G,
-                               p->d_amax + p->amax_bytes / sizeof(unsigned) - 1, p->sms, s)) != cudaSuccess)
+  if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_split_prefix, p->split_total, p->G,
+                               p->sms, s)) != cudaSuccess)
     return cuda_fail(e, "grouped pack launch");
   GroupedArgs a{};
   a.probs = p->d_probs;
@@ -213,7 +211,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   const int es = prec_elem_bytes(pr);
   std::vector<GroupedProblem> hp(G);
   std::vector<size_t> offA(G), offB(G);
-  std::vector<int> tile_prefix(G + 1, 0), abs_prefix(G + 1, 0), spl_prefix(G + 1, 0);
+  std::vector<int> tile_prefix(G + 1, 0), spl_prefix(G + 1, 0);
   size_t off = 0, amax_count = 0;
   std::vector<size_t> amax_off(G);
   for (int slot = 0; slot < G; ++slot) {
@@ -232,15 +230,16 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     off = round256(off + (size_t)2 * std::max<int64_t>(p->M[i], 1) * pitch * es);
     offB[slot] = off;
     off = round256(off + (size_t)2 * std::max<int64_t>(p->N[i], 1) * pitch * es);
+    // per problem: maxima of A's and B's blocks, then one pack counter per block
     amax_off[slot] = amax_count;
-    amax_count += (size_t)(p->M[i] + kScaleBlock - 1) / kScaleBlock + (p->N[i] + kScaleBlock - 1) / kScaleBlock + 2;
+    amax_count += 2 * ((size_t)(p->M[i] + kScaleBlock - 1) / kScaleBlock +
+                       (size_t)(p->N[i] + kScaleBlock - 1) / kScaleBlock);
     tile_prefix[slot + 1] = tile_prefix[slot] + g.tiles_m * g.tiles_n;
     const bool pack = !empty && p->K[i] > 0;
     spl_prefix[slot + 1] = spl_prefix[slot] + (pack ? pack_first_items(p->M[i], p->N[i], pitch) : 0);
-    abs_prefix[slot + 1] = abs_prefix[slot] + (pack ? pack_rescale_items(p->M[i], p->N[i], pitch) : 0);
   }
   const size_t off_amax = off;
-  p->amax_bytes = (amax_count + 1) * sizeof(unsigned);   // + the rescale flag (last word)
+  p->amax_bytes = std::max<size_t>(amax_count, 1) * sizeof(unsigned);
   off = round256(off + p->amax_bytes);
   const size_t off_probs = off;
   off = round256(off + (size_t)G * sizeof(GroupedProblem));
@@ -249,7 +248,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   const size_t off_units = off;
   off = round256(off + (size_t)std::max(tile_prefix[G], 1) * sizeof(GroupedUnit));
   const size_t off_pref = off;
-  off = round256(off + (size_t)2 * (G + 1) * sizeof(int));
+  off = round256(off + (size_t)(G + 1) * sizeof(int));
   p->ws_bytes = off;
   if ((e = cudaMalloc(&p->ws, p->ws_bytes)) != cudaSuccess) {
     cudaGetLastError();
@@ -260,15 +259,17 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   p->d_probs = reinterpret_cast<GroupedProblem*>(w + off_probs);
   p->d_ptrs = reinterpret_cast<GroupedPtrs*>(w + off_ptrs);
   p->d_units = reinterpret_cast<GroupedUnit*>(w + off_units);
-  p->d_absmax_prefix = reinterpret_cast<int*>(w + off_pref);
-  p->d_split_prefix = p->d_absmax_prefix + (G + 1);
+  p->d_split_prefix = reinterpret_cast<int*>(w + off_pref);
   for (int slot = 0; slot < G; ++slot) {
     const int i = p->order[slot];
     GroupedProblem& g = hp[slot];
     g.planesA = w + offA[slot];
     g.planesB = w + offB[slot];
+    const int64_t nbA = (p->M[i] + kScaleBlock - 1) / kScaleBlock, nbB = (p->N[i] + kScaleBlock - 1) / kScaleBlock;
     g.amaxA = p->d_amax + amax_off[slot];
-    g.amaxB = g.amaxA + (p->M[i] + kScaleBlock - 1) / kScaleBlock + 1;
+    g.amaxB = g.amaxA + nbA;
+    g.cntA = g.amaxB + nbB;
+    g.cntB = g.cntA + nbA;
     const int64_t Ki = std::max<int64_t>(p->K[i], 1);
     if ((st = encode_planes_map(&g.tmA, pr, g.planesA, std::max<int64_t>(p->M[i], 1), Ki, g.pitch, 128,
                                 128)) != GEMM_OK)
@@ -279,7 +280,6 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   }
   if ((e = tc_prepare(p->bn, pr)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
   p->num_units = tile_prefix[G];
-  p->absmax_total = abs_prefix[G];
   p->split_total = spl_prefix[G];
   if ((e = cudaMemcpy(p->d_probs, hp.data(), (size_t)G * sizeof(GroupedProblem), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload of the problem table");
@@ -298,14 +298,12 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
       units.push_back(GroupedUnit{slot, first_m + r % rows, r / rows, g.chunks});
     }
   }
-  std::vector<int> pref;
-  pref.insert(pref.end(), abs_prefix.begin(), abs_prefix.end());
-  pref.insert(pref.end(), spl_prefix.begin(), spl_prefix.end());
   if (!units.empty() &&
       (e = cudaMemcpy(p->d_units, units.data(), units.size() * sizeof(GroupedUnit), cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(e, "upload of the unit table");
-  if ((e = cudaMemcpy(p->d_absmax_prefix, pref.data(), pref.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
-    return cuda_fail(e, "upload of the prefix tables");
+  if ((e = cudaMemcpy(p->d_split_prefix, spl_prefix.data(), spl_prefix.size() * sizeof(int),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_fail(e, "upload of the prefix table");
   *out = p.release();
   return GEMM_OK;
 }

@@ -81,28 +81,27 @@ cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t l
 // re-splits the blocks needing a power-of-two scale.  The block maxima must
 // be zero on entry.  A (or B) may be null to pack only the other operand.
 // A: M x K (lda) -> planesA [2][M][pitch];  B: K x N (ldb) -> planesB [2][N][pitch].
-// flag: one word, zero on entry like the block maxima, raised by the first
-// pass when a block needs a rescale so the rescale pass returns at once when
-// none does (null: the rescale pass checks every block).
+// Packing (split.cu), one launch.  amax* hold the block maxima and cnt*
+// one counter per block (items done); both must be zero on entry.  The CTA
+// that completes a block re-splits it with its exponent when the block lies
+// outside the safe range.
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
-                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* flag,
-                        void* planesA, void* planesB, int64_t pitch, int sms, cudaStream_t s);
-// A row panel alone: rows [0, rows) of the panel starting at A, written to
-// the planes of the whole matrix at planesA (already offset to the panel's
-// first row) with hi-to-lo plane distance plane_stride elements; amaxA points
-// at the panel's first block (the panel starts on a 128-row boundary).
-// As pack_launch, but A is only scanned for its block maxima (no planes):
-// the fused-split gemm kernel splits A itself while it streams the tiles.
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA,
+                        unsigned* cntB, void* planesA, void* planesB, int64_t pitch, int sms,
+                        cudaStream_t s);
+// Fused-split preparation, one launch: A's block maxima only (no planes:
+// the gemm kernel splits A itself) and B packed as by pack_launch.
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
-                              unsigned* amaxB, unsigned* flag, void* planesB, int64_t pitch, int sms,
+                              unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
                               cudaStream_t s);
+// A row panel of A (rows rows, starting at a 128-row block) packed into the
+// planes of the whole matrix at planesA (already offset to the panel's
+// first row; plane_stride = elements from the hi plane to the lo plane).
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
-                                   unsigned* amaxA, unsigned* flag, void* planesA,
+                                   unsigned* amaxA, unsigned* cntA, void* planesA,
                                    int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s);
-// Work items of the two passes for one problem (grouped prefix sums).
 int pack_first_items(int64_t M, int64_t N, int64_t pitch);
-int pack_rescale_items(int64_t M, int64_t N, int64_t pitch);
 
 // ------------------------------------------------------------ grouped
 // Static description of one problem of a grouped gemm, device resident
@@ -115,6 +114,8 @@ struct alignas(128) GroupedProblem {
   void* planesB;
   unsigned* amaxA;
   unsigned* amaxB;
+  unsigned* cntA;           // per block: pack items done
+  unsigned* cntB;
   int64_t pitch, lda, ldb, ldc;
   int M, N, K, chunks, tiles_m, tiles_n;
 };
@@ -142,11 +143,9 @@ struct GroupedArgs {
 };
 
 cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s);
-// Both pack passes for every problem (two launches, items found through the
-// prefix sums of pack_first_items / pack_rescale_items); the block maxima
-// must have been zeroed.
+// Packing of every problem in one launch (items found through the prefix
+// sums of pack_first_items); the block maxima and counters must be zero.
 cudaError_t grouped_pack_launch(Prec p, const GroupedProblem* probs, const GroupedPtrs* ptrs,
-                                const int* first_prefix, int first_total, const int* rescale_prefix,
-                                int rescale_total, int G, unsigned* flag, int sms, cudaStream_t s);
+                                const int* first_prefix, int first_total, int G, int sms, cudaStream_t s);
 
 }  // namespace gb

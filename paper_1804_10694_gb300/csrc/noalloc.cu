@@ -135,7 +135,7 @@ extern "C" gemm_status gemm_f32_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, 
   const size_t bytesB = round256((size_t)2 * N * pitch * 2);
   const size_t nblkA = (size_t)(M + kScaleBlock - 1) / kScaleBlock;
   const size_t nblkB = (size_t)(N + kScaleBlock - 1) / kScaleBlock;
-  const size_t bytesAmax = (nblkA + nblkB + 1) * sizeof(unsigned);   // + the rescale flag
+  const size_t bytesAmax = 2 * (nblkA + nblkB) * sizeof(unsigned);   // maxima, then pack counters
   const size_t need = bytesA + bytesB + round256(bytesAmax);
   if (need > kNoAllocScratchBytes)
     return fail(GEMM_ERR_INVALID_ARG,
@@ -157,7 +157,8 @@ extern "C" gemm_status gemm_f32_bf16x3_noalloc(int64_t M, int64_t N, int64_t K, 
   unsigned* amaxB = amaxA + nblkA;
 
   if ((e = cudaMemsetAsync(amaxA, 0, bytesAmax, s)) != cudaSuccess) return cuda_fail(e, "clear block maxima");
-  if ((e = pack_launch(Prec::BF16, A, M, K, lda, B, N, ldb, amaxA, amaxB, amaxB + nblkB, planesA,
+  unsigned* cntA = amaxB + nblkB;
+  if ((e = pack_launch(Prec::BF16, A, M, K, lda, B, N, ldb, amaxA, amaxB, cntA, cntA + nblkA, planesA,
                        planesB, pitch, d->sms, s)) != cudaSuccess)
     return cuda_fail(e, "pack");
 

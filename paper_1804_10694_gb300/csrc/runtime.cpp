@@ -304,7 +304,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   size_t off = 0;
   const size_t offA = off; off = align_up(off + bytesA, 256);
   const size_t offB = off; off = align_up(off + bytesB, 256);
-  const size_t offAmax = off; off = align_up(off + (nblkA + nblkB + 1) * sizeof(unsigned), 256);
+  const size_t offAmax = off; off = align_up(off + 2 * (nblkA + nblkB) * sizeof(unsigned), 256);
   const size_t offPart = off;
   if (sk > 1) off = align_up(off + (size_t)sk * M * N * sizeof(float), 256);
   p->ws_bytes = off;
@@ -319,8 +319,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->planesB = w + offB;
   p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
   p->amaxB = p->amaxA + nblkA;
-  p->amax_bytes = (nblkA + nblkB + 1) * sizeof(unsigned);   // + the rescale flag
-  p->rescale_flag = p->amaxB + nblkB;
+  p->amax_bytes = 2 * (nblkA + nblkB) * sizeof(unsigned);   // maxima, then per-block counters
+  p->cntA = p->amaxB + nblkB;
+  p->cntB = p->cntA + nblkA;
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
   if (!fused && (st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK)
@@ -381,10 +382,10 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
   if (p->launch.fused)
-    e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
+    e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
                           p->planesB, p->pitch, p->sms, s);
   else
-    e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->rescale_flag,
+    e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntA, p->cntB,
                     p->planesA, p->planesB, p->pitch, p->sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   TcArgs a = p->args;
@@ -601,8 +602,8 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
   // B packed once
   if ((e = cudaStreamWaitEvent(s, ev[1], 0)) ||
       (e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) ||
-      (e = pack_launch(p->prec, nullptr, 0, K, 1, t_host.B, N, ldb, nullptr, p->amaxB,
-                       p->rescale_flag, nullptr, p->planesB, p->pitch, p->sms, s)))
+      (e = pack_launch(p->prec, nullptr, 0, K, 1, t_host.B, N, ldb, nullptr, p->amaxB, nullptr,
+                       p->cntB, nullptr, p->planesB, p->pitch, p->sms, s)))
     return cuda_fail(e, "pack B");
   for (int i = 0; i < npan; ++i) {
     const int64_t t0 = i * tiles_per, t1 = std::min(tiles_m, (i + 1) * tiles_per);
@@ -610,7 +611,7 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     const int64_t r0 = t0 * 128, r1 = std::min(M, t1 * 128);
     if ((e = cudaStreamWaitEvent(s, ev[2 + i], 0)) ||
         (e = pack_rows_panel_launch(p->prec, t_host.A + r0 * lda, r1 - r0, K, lda, p->amaxA + t0,
-                                    p->rescale_flag,
+                                    p->cntA + t0,
                                     static_cast<char*>(p->planesA) + r0 * p->pitch * prec_elem_bytes(p->prec),
                                     M * p->pitch, p->pitch, p->sms, s)))
       return cuda_fail(e, "pack A panel");
@@ -854,12 +855,14 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
   const int sms = gemm_device_sm_count();
   if (sms <= 0) return fail(GEMM_ERR_CUDA, "no device");
   cudaError_t e;
+  // amax holds the maxima of nblk blocks followed by their nblk counters
+  const int64_t nblk = ((transpose ? cols : rows) + kScaleBlock - 1) / kScaleBlock;
   if (!transpose)
-    e = pack_launch(p, X, rows, cols, ld, nullptr, 0, 1, amax, nullptr, nullptr, planes, nullptr, pitch,
-                    sms, s);
+    e = pack_launch(p, X, rows, cols, ld, nullptr, 0, 1, amax, nullptr, amax + nblk, nullptr, planes,
+                    nullptr, pitch, sms, s);
   else
-    e = pack_launch(p, nullptr, 0, rows, 1, X, cols, ld, nullptr, amax, nullptr, nullptr, planes, pitch,
-                    sms, s);
+    e = pack_launch(p, nullptr, 0, rows, 1, X, cols, ld, nullptr, amax, nullptr, amax + nblk, nullptr,
+                    planes, pitch, sms, s);
   if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   return GEMM_OK;
 }

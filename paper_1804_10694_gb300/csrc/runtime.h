@@ -24,8 +24,9 @@ struct gemm_plan_s {
   void* planesB = nullptr;
   unsigned* amaxA = nullptr;
   unsigned* amaxB = nullptr;
-  size_t amax_bytes = 0;            // block maxima of A and B plus the rescale flag
-  unsigned* rescale_flag = nullptr;
+  size_t amax_bytes = 0;            // block maxima of A and B, then their pack counters
+  unsigned* cntA = nullptr;
+  unsigned* cntB = nullptr;
   float* partial = nullptr;
   CUtensorMap tmA{}, tmB{};
   gb::TcArgs args{};

@@ -4,25 +4,27 @@
 //     x' = x * 2^-e            (e = block exponent, exponent-field arithmetic)
 //     hi = RN(x'),  lo = RN(x' - hi)
 // with RN round-to-nearest-even to bf16 (hardware conversion) or to tf32
-// (bit arithmetic below; the planes keep tf32 values in 32-bit containers).
+// (bit arithmetic; the planes keep tf32 values in 32-bit containers).
 // A is kept row-major (K contiguous); B is transposed so that both operands
 // are K-major for the tensor-core kernel.  Rows of the planes are padded to
 // a 16-byte pitch with zeros.
 //
 // Blocks: A uses one exponent per 128 rows (all of K), B one per 128 columns
 // (all of K).  Most blocks need no scaling (e = 0, see scale.cuh), so packing
-// takes ONE pass over the operands: it writes the unscaled split and folds
-// max |x| of each block into the block's slot.  A second, cheap pass then
-// re-splits, with their exponent, only the blocks whose max lies outside the
-// safe range; every other CTA of that pass returns after one load.
+// is ONE launch: each item (tile) writes the unscaled split, folds max |x|
+// into its block's slot and counts itself done on the block's counter; the
+// CTA that completes a block thus sees the block's final max and, only if
+// the block lies outside the safe range, re-splits it with its exponent.  No
+// CTA ever waits for another.
 //
 // Every kernel is a thin wrapper around per-tile device functions; the
-// single-problem kernels walk the tiles of A and then of B in one launch, the
-// grouped kernels map a flattened item index to (problem, tile) through
-// prefix sums, so one launch packs every problem of a grouped gemm.
+// single-problem kernel walks the tiles of A and then of B, the grouped
+// kernel maps a flattened item index to (problem, tile) through prefix
+// sums, so one launch packs every problem of a grouped gemm.
 #include <cuda_bf16.h>
-#include <algorithm>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "internal.h"
 #include "scale.cuh"
@@ -34,10 +36,44 @@ namespace {
 
 enum Pass { kFirst = 0, kRescale = 1 };
 
-// CTA-wide max of m folded into *slot (every thread of the CTA calls this).
-// When the block's running max leaves the safe range, *flag is raised so that
-// the rescale pass knows it has work (flag may be null: always check).
-__device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot, unsigned* flag) {
+// End of a run of items of one block processed by this CTA (every thread
+// of the CTA calls this with its max |x| over the run): folds the CTA's max
+// into the block's slot and counts the run's items on the block's counter.
+// Returns, uniformly over the CTA, the block's final max bits when this run
+// completed the block, else 0xFFFFFFFF.  The CTA barrier orders every
+// thread's plane writes before thread 0's device-scope fence, which is
+// cumulative: they and the atomicMax are visible before the completing CTA
+// can observe the count (the pattern of a split-K semaphore).  No CTA waits
+// for another.
+__device__ __forceinline__ unsigned finish_run(unsigned m, unsigned* slot, unsigned* cnt,
+                                               unsigned run, unsigned items) {
+  __shared__ unsigned wm[32];
+  __shared__ unsigned s_done;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned b = wm[0];
+    for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) b = max(b, wm[i]);
+    if (b) atomicMax(slot, b);
+    __threadfence();
+    const unsigned done = atomicAdd(cnt, run) + run;
+    unsigned v = 0xFFFFFFFFu;
+    if (done == items) {
+      __threadfence();
+      v = *reinterpret_cast<const volatile unsigned*>(slot);
+    }
+    s_done = v;
+  }
+  __syncthreads();
+  const unsigned v = s_done;
+  __syncthreads();   // wm and s_done are reused by the next run
+  return v;
+}
+
+// CTA-wide max of m folded into *slot (the max-only pass; no counting).
+__device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
   __shared__ unsigned wm[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -46,12 +82,9 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot, unsig
   if (threadIdx.x == 0) {
     unsigned b = wm[0];
     for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) b = max(b, wm[i]);
-    if (b) {
-      const unsigned old = atomicMax(slot, b);
-      if (flag && block_exponent(max(old, b)) != 0) *flag = 1u;
-    }
+    if (b) atomicMax(slot, b);
   }
-  __syncthreads();   // wm is reused by the next tile of a looping launch
+  __syncthreads();   // wm is reused by the next item
 }
 
 // --------------------------------------------------------- A: row-major split
@@ -62,9 +95,9 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot, unsig
 // bytes are in flight to cover memory latency.  The 32 rows lie in one
 // 128-row block.
 template <bool TF32, Pass PASS>
-__device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int64_t rows,
+__device__ __forceinline__ unsigned split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
-                                                unsigned* __restrict__ amax, unsigned* flag,
+                                                unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t plane,
                                                 int64_t pitch, int64_t r0, int64_t k0) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -127,11 +160,12 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
       }
     }
   }
-  if (PASS == kFirst) fold_block_max(m, amax + r0 / kScaleBlock, flag);
+  return m;   // this thread's max |x| (kFirst; 0 for kRescale)
 }
 
 // ---------------------------------------------------- B: transposing split
-// One CTA handles a 64 (k) x 128 (n) tile.  Load phase: warp w reads k-rows
+// One CTA handles a 64 (k) x 128 (n) tile through the shared `tile`
+// (64 x kColTilePitch floats, declared once by the kernel).  Load phase: warp w reads k-rows
 // w + 8i (i < 8), each lane a float4 of n (512 contiguous bytes per warp and
 // row); all eight loads are issued first, then stored to a shared tile whose
 // 132-float pitch keeps both phases free of bank conflicts.  Write phase:
@@ -140,11 +174,11 @@ __device__ __forceinline__ void split_rows_tile(const float* __restrict__ X, int
 constexpr int kColTilePitch = 132;
 
 template <bool TF32, Pass PASS>
-__device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
+__device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
                                                 int64_t ld, bool vec, unsigned* __restrict__ amax,
-                                                unsigned* flag, void* __restrict__ planes,
-                                                int64_t plane, int64_t pitch, int64_t n0, int64_t k0) {
-  __shared__ __align__(16) float tile[64 * kColTilePitch];
+                                                void* __restrict__ planes, int64_t plane,
+                                                int64_t pitch, int64_t n0, int64_t k0,
+                                                float* __restrict__ tile) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned m = 0;
   {
@@ -214,33 +248,47 @@ __device__ __forceinline__ void split_cols_tile(const float* __restrict__ X, int
       }
     }
   }
-  if (PASS == kFirst)
-    fold_block_max(m, amax + n0 / kScaleBlock, flag);   // its barriers also guard `tile`
-  else
-    __syncthreads();   // the tile is reused by the next item of a looping launch
+  __syncthreads();   // the tile is reused by the next item of a looping launch
+  return m;          // this thread's max |x| (kFirst; 0 for kRescale)
 }
 
 // ------------------------------------------------ A: block maxima only
-// For the fused-split gemm, which splits A itself: one item is a 128-row
-// block over a span of 64 loads per row (256 floats with float4 loads);
-// thread (x, y) of the 64 x 4 CTA reads load x of rows y, y + 4, ... with
-// eight loads in flight, and the CTA folds one max per item.
+// For the fused-split gemm, which splits A itself.  An item is a piece of a
+// 128-row block: a contiguous run of float4 when the rows are stored back to
+// back (lda == K, 16-byte aligned), else a span of 64 loads of every row of
+// the block (thread (x, y) of the 64 x 4 CTA reads load x of rows y, y + 4,
+// ...); eight independent loads a thread are in flight, and the CTA folds
+// one max per item.
 constexpr int kAmaxLoads = 64;
 
-// Rows stored back to back (lda == K, 16-byte aligned): a block is one
-// contiguous run of rows * K floats, streamed as float4 in `parts` pieces.
-__global__ void __launch_bounds__(256) amax_flat_kernel(const float* __restrict__ A, int64_t M,
-                                                        int64_t K, int parts,
-                                                        unsigned* __restrict__ amax, unsigned* flag) {
-  const int64_t nblk = (M + 127) / 128;
-  for (int64_t item = blockIdx.x; item < nblk * parts; item += gridDim.x) {
-    const int64_t b = item / parts;
-    const int part = static_cast<int>(item - b * parts);
-    const int64_t n4 = min(static_cast<int64_t>(128), M - b * 128) * K / 4;   // K % 4 == 0
-    const int64_t per = (n4 + parts - 1) / parts;
+enum AmaxMode { kAmaxFlat = 0, kAmaxRowsVec = 1, kAmaxRowsScalar = 2 };
+
+struct AmaxShape {
+  const float* A;
+  int64_t M, K, lda;
+  int parts;          // flat mode: pieces a block is cut into
+  unsigned* amax;
+};
+
+template <int MODE>
+__device__ __forceinline__ int64_t amax_items(const AmaxShape& a) {
+  const int64_t nblk = (a.M + 127) / 128;
+  if (MODE == kAmaxFlat) return nblk * a.parts;
+  const int64_t span = kAmaxLoads * (MODE == kAmaxRowsVec ? 4 : 1);
+  return nblk * ((a.K + span - 1) / span);
+}
+
+template <int MODE>
+__device__ __forceinline__ void amax_item(const AmaxShape& a, int64_t item) {
+  unsigned m = 0;
+  int64_t b;
+  if (MODE == kAmaxFlat) {
+    b = item / a.parts;
+    const int part = static_cast<int>(item - b * a.parts);
+    const int64_t n4 = min(static_cast<int64_t>(128), a.M - b * 128) * a.K / 4;   // K % 4 == 0
+    const int64_t per = (n4 + a.parts - 1) / a.parts;
     const int64_t lo = part * per, hi = min(n4, lo + per);
-    const float4* p = reinterpret_cast<const float4*>(A + b * 128 * K);
-    unsigned m = 0;
+    const float4* p = reinterpret_cast<const float4*>(a.A + b * 128 * a.K);
     for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += 8 * 256) {
       float4 v[8];
 #pragma unroll
@@ -252,25 +300,16 @@ __global__ void __launch_bounds__(256) amax_flat_kernel(const float* __restrict_
       for (int i = 0; i < 8; ++i)
         m = max(m, max(max(abs_bits(v[i].x), abs_bits(v[i].y)), max(abs_bits(v[i].z), abs_bits(v[i].w))));
     }
-    fold_block_max(m, amax + b, flag);
-  }
-}
-
-template <bool VEC>
-__global__ void __launch_bounds__(256) amax_rows_kernel(const float* __restrict__ A, int64_t M,
-                                                        int64_t K, int64_t lda,
-                                                        unsigned* __restrict__ amax, unsigned* flag) {
-  constexpr int U = VEC ? 4 : 1;   // floats per load
-  constexpr int64_t span = kAmaxLoads * U;
-  const int64_t nblk = (M + 127) / 128, nspan = (K + span - 1) / span;
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
-  for (int64_t item = blockIdx.x; item < nblk * nspan; item += gridDim.x) {
-    const int64_t b = item / nspan;
+  } else {
+    constexpr int U = MODE == kAmaxRowsVec ? 4 : 1;   // floats per load
+    constexpr int64_t span = kAmaxLoads * U;
+    const int64_t nspan = (a.K + span - 1) / span;
+    b = item / nspan;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
     const int64_t k = (item - b * nspan) * span + static_cast<int64_t>(tx) * U;
-    const int rows = static_cast<int>(min(static_cast<int64_t>(128), M - b * 128));
-    const float* base = A + (b * 128) * lda + k;
-    unsigned m = 0;
-    if (k < K) {
+    const int rows = static_cast<int>(min(static_cast<int64_t>(128), a.M - b * 128));
+    const float* base = a.A + (b * 128) * a.lda + k;
+    if (k < a.K) {
       for (int r0 = ty; r0 < rows; r0 += 32) {
         float v[8][U];
 #pragma unroll
@@ -279,8 +318,8 @@ __global__ void __launch_bounds__(256) amax_rows_kernel(const float* __restrict_
 #pragma unroll
           for (int e = 0; e < U; ++e) v[i][e] = 0.0f;
           if (r >= rows) continue;
-          const float* p = base + r * lda;
-          if (VEC && k + 4 <= K) {
+          const float* p = base + r * a.lda;
+          if (U == 4 && k + 4 <= a.K) {
             const float4 q = __ldg(reinterpret_cast<const float4*>(p));
             const float t[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
@@ -288,7 +327,7 @@ __global__ void __launch_bounds__(256) amax_rows_kernel(const float* __restrict_
           } else {
 #pragma unroll
             for (int e = 0; e < U; ++e)
-              if (k + e < K) v[i][e] = __ldg(p + e);
+              if (k + e < a.K) v[i][e] = __ldg(p + e);
           }
         }
 #pragma unroll
@@ -297,80 +336,120 @@ __global__ void __launch_bounds__(256) amax_rows_kernel(const float* __restrict_
           for (int e = 0; e < U; ++e) m = max(m, abs_bits(v[i][e]));
       }
     }
-    fold_block_max(m, amax + b, flag);
   }
+  fold_block_max(m, a.amax + b);
 }
 
 // --------------------------------------------------- tile decomposition
-// First pass: A in 32-row x 256-column tiles, B in 64-k x 128-column tiles.
-// Rescale pass: one item per scale block (128 rows of A or 128 columns of B,
-// all of K); a block that needs no scaling costs one load, one that does is
-// re-split tile by tile.
+// A in 32-row x 256-column tiles (rows_b/32 x ceil(pitch/256) a block), B in
+// 64-k x 128-column tiles (ceil(pitch/64) a block), numbered so that the
+// items of one block are consecutive.  A CTA processes a contiguous range
+// of items, so it meets a block boundary only every few dozen items and
+// folds maxima and counts once per run of one block.
 struct PackShape {
   const float* A;
   const float* B;
   int64_t M, N, K, lda, ldb, pitch;
   int64_t planeA, planeB;   // elements from the hi plane to the lo plane
-  unsigned* flag;           // raised when some block needs a rescale (null: always check)
   bool vecA, vecB;
   unsigned* amaxA;
   unsigned* amaxB;
+  unsigned* cntA;           // per block: items done (zero on entry)
+  unsigned* cntB;
   void* planesA;
   void* planesB;
 
-  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * ((pitch + 255) / 256)); }
-  __device__ int first_items_b() const { return (int)(((N + 127) / 128) * ((pitch + 63) / 64)); }
-  __device__ int rescale_items_a() const { return (int)((M + 127) / 128); }
-  __device__ int rescale_items_b() const { return (int)((N + 127) / 128); }
+  __device__ int cols_a() const { return (int)((pitch + 255) / 256); }
+  __device__ int ktiles_b() const { return (int)((pitch + 63) / 64); }
+  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * cols_a()); }
+  __device__ int first_items_b() const { return (int)(((N + 127) / 128) * ktiles_b()); }
+  __device__ int items() const { return first_items_a() + first_items_b(); }
+  // block of item i: A blocks 0.., then B blocks as -1 - b
+  __device__ int64_t block_of(int i) const {
+    const int na = first_items_a();
+    return i < na ? (int64_t)(i / cols_a()) / 4 : -1 - (int64_t)((i - na) / ktiles_b());
+  }
 };
 
+// Split item i (unscaled); returns this thread's max |x|.
 template <bool TF32>
-__device__ __forceinline__ void first_item(const PackShape& p, int i) {
+__device__ __forceinline__ unsigned first_item(const PackShape& p, int i, float* tile) {
   const int na = p.first_items_a();
   if (i < na) {
-    const int cols = (int)((p.pitch + 255) / 256);
-    split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA,
-                                  p.pitch, (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
+    const int cols = p.cols_a();
+    return split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA,
+                                         p.pitch, (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
+  }
+  const int l = i - na, kt = p.ktiles_b();
+  return split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB,
+                                       p.pitch, (int64_t)(l / kt) * 128, (int64_t)(l % kt) * 64, tile);
+}
+
+// Close a run of `run` items of block `blk` (encoded as in block_of); the
+// CTA that completes an out-of-range block re-splits it with its exponent.
+template <bool TF32>
+__device__ __forceinline__ void finish_block(const PackShape& p, int64_t blk, unsigned m, unsigned run,
+                                             float* tile) {
+  if (blk >= 0) {
+    const int64_t rows_b = min(static_cast<int64_t>(kScaleBlock), p.M - blk * kScaleBlock);
+    const unsigned items = (unsigned)(((rows_b + 31) / 32) * p.cols_a());
+    const unsigned fin = finish_run(m, p.amaxA + blk, p.cntA + blk, run, items);
+    if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
+      for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
+        for (int64_t q = blk * kScaleBlock; q < blk * kScaleBlock + rows_b; q += 32)
+          split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA,
+                                          p.pitch, q, k0);
+    }
   } else {
-    const int l = i - na;
-    const int ncols = (int)((p.N + 127) / 128);
-    split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.flag, p.planesB, p.planeB, p.pitch,
-                                  (int64_t)(l % ncols) * 128, (int64_t)(l / ncols) * 64);
+    const int64_t b = -1 - blk;
+    const unsigned fin = finish_run(m, p.amaxB + b, p.cntB + b, run, (unsigned)p.ktiles_b());
+    if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
+      for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
+        split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB,
+                                        p.pitch, b * 128, k0, tile);
+    }
   }
 }
 
+// Items [i0, i1) of one problem, in runs of one block each.
 template <bool TF32>
-__device__ __forceinline__ void rescale_item(const PackShape& p, int i) {
-  const int na = p.rescale_items_a();
-  if (i < na) {
-    const int64_t r0 = (int64_t)i * 128;
-    if (block_exponent(p.amaxA[i]) == 0) return;   // uniform per CTA
-    for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
-      for (int q = 0; q < 4 && r0 + 32 * q < p.M; ++q)
-        split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.flag, p.planesA, p.planeA, p.pitch,
-                                        r0 + 32 * q, k0);
-  } else {
-    const int l = i - na;
-    const int64_t n0 = (int64_t)l * 128;
-    if (block_exponent(p.amaxB[l]) == 0) return;
-    for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-      split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.flag, p.planesB, p.planeB, p.pitch,
-                                      n0, k0);
+__device__ __forceinline__ void pack_range(const PackShape& p, int i0, int i1, float* tile) {
+  int i = i0;
+  while (i < i1) {
+    const int64_t blk = p.block_of(i);
+    unsigned m = 0, run = 0;
+    do {
+      m = max(m, first_item<TF32>(p, i, tile));
+      ++run;
+      ++i;
+    } while (i < i1 && p.block_of(i) == blk);
+    finish_block<TF32>(p, blk, m, run, tile);
   }
 }
 
 // ------------------------------------------------ single-problem kernels
+// CTA c takes the c-th contiguous share of the items.
 template <bool TF32>
-__global__ void pack_first_kernel(const PackShape p) {
-  const int total = p.first_items_a() + p.first_items_b();
-  for (int i = blockIdx.x; i < total; i += gridDim.x) first_item<TF32>(p, i);
+__global__ void __launch_bounds__(256) pack_first_kernel(const PackShape p) {
+  __shared__ __align__(16) float tile[64 * kColTilePitch];
+  const int total = p.items();
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * per;
+  pack_range<TF32>(p, i0, min(total, i0 + per), tile);
 }
 
-template <bool TF32>
-__global__ void pack_rescale_kernel(const PackShape p) {
-  if (p.flag && *p.flag == 0u) return;   // no block out of range
-  const int total = p.rescale_items_a() + p.rescale_items_b();
-  for (int i = blockIdx.x; i < total; i += gridDim.x) rescale_item<TF32>(p, i);
+// Fused-split preparation in one launch: A's block maxima (grid-stride),
+// then B packed as in pack_first_kernel (p holds B only; a contiguous
+// share of its items per CTA).
+template <bool TF32, int MODE>
+__global__ void __launch_bounds__(256) fused_prep_kernel(const AmaxShape a, const PackShape p) {
+  __shared__ __align__(16) float tile[64 * kColTilePitch];
+  const int64_t na = amax_items<MODE>(a);
+  for (int64_t i = blockIdx.x; i < na; i += gridDim.x) amax_item<MODE>(a, i);
+  const int total = p.items();
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  const int i0 = blockIdx.x * per;
+  pack_range<TF32>(p, i0, min(total, i0 + per), tile);
 }
 
 // ------------------------------------------------------ grouped kernels
@@ -404,28 +483,29 @@ __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, cons
   p.planeB = static_cast<int64_t>(g.N) * g.pitch;
   p.vecA = (reinterpret_cast<uintptr_t>(q.A) % 16 == 0) && (g.lda % 4 == 0);
   p.vecB = (reinterpret_cast<uintptr_t>(q.B) % 16 == 0) && (g.ldb % 4 == 0);
-  p.amaxA = g.amaxA, p.amaxB = g.amaxB;
+  p.amaxA = g.amaxA, p.amaxB = g.amaxB, p.cntA = g.cntA, p.cntB = g.cntB;
   p.planesA = g.planesA, p.planesB = g.planesB;
   return p;
 }
 
-template <bool TF32, Pass PASS>
-__global__ void grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
-                                    const GroupedPtrs* __restrict__ ptrs,
-                                    const int* __restrict__ prefix_g, int G, unsigned* flag) {
-  if (PASS == kRescale && *flag == 0u) return;   // no block of any problem out of range
+template <bool TF32>
+__global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
+                                                           const GroupedPtrs* __restrict__ ptrs,
+                                                           const int* __restrict__ prefix_g, int G) {
+  __shared__ __align__(16) float tile[64 * kColTilePitch];
   const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
-  for (int i = blockIdx.x; i < total; i += gridDim.x) {
+  const int per = (total + gridDim.x - 1) / gridDim.x;
+  int i = blockIdx.x * per;
+  const int iend = min(total, i + per);
+  while (i < iend) {
+    // the part of this CTA's share that lies in problem g
     const int g = find_problem(prefix, G, i);
+    const int e = min(iend, prefix[g + 1]);
     const GroupedPtrs& q = ptrs[g];
-    if (q.alpha == 0.0f) continue;   // A and B are not read when alpha == 0
-    PackShape p = problem_shape(probs[g], q);
-    p.flag = flag;
-    if (PASS == kFirst)
-      first_item<TF32>(p, i - prefix[g]);
-    else
-      rescale_item<TF32>(p, i - prefix[g]);
+    if (q.alpha != 0.0f)   // A and B are not read when alpha == 0 (uniform per CTA)
+      pack_range<TF32>(problem_shape(probs[g], q), i - prefix[g], e - prefix[g], tile);
+    i = e;
   }
 }
 
@@ -434,112 +514,102 @@ int grid_for(int64_t items, int sms) {
   return static_cast<int>(items < cap ? (items > 0 ? items : 1) : cap);
 }
 
-}  // namespace
-
-// Items per problem of the two pack passes (host side, same tiling as above).
-int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
-  return static_cast<int>(((M + 31) / 32) * ((pitch + 255) / 256) + ((N + 127) / 128) * ((pitch + 63) / 64));
-}
-int pack_rescale_items(int64_t M, int64_t N, int64_t pitch) {
-  (void)pitch;
-  return static_cast<int>((M + 127) / 128 + (N + 127) / 128);
-}
-
-cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
-                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* flag,
-                        void* planesA, void* planesB, int64_t pitch, int sms, cudaStream_t s) {
+PackShape make_shape(const float* A, int64_t M, int64_t K, int64_t lda, const float* B, int64_t N,
+                     int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA, unsigned* cntB,
+                     void* planesA, void* planesB, int64_t plane_a, int64_t pitch) {
   PackShape p;
-  p.flag = flag;
   p.A = A, p.B = B, p.M = A ? M : 0, p.N = B ? N : 0, p.K = K, p.lda = lda, p.ldb = ldb;
   p.pitch = pitch;
-  p.planeA = p.M * pitch;
+  p.planeA = plane_a;
   p.planeB = p.N * pitch;
   p.vecA = A && lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
   p.vecB = B && ldb % 4 == 0 && reinterpret_cast<uintptr_t>(B) % 16 == 0;
-  p.amaxA = amaxA, p.amaxB = amaxB, p.planesA = planesA, p.planesB = planesB;
-  const int64_t first = pack_first_items(p.M, p.N, pitch);
-  const int64_t rescale = pack_rescale_items(p.M, p.N, pitch);
+  p.amaxA = amaxA, p.amaxB = amaxB, p.cntA = cntA, p.cntB = cntB;
+  p.planesA = planesA, p.planesB = planesB;
+  return p;
+}
+
+cudaError_t launch_first(Prec prec, const PackShape& p, int sms, cudaStream_t s) {
+  const int64_t first = pack_first_items(p.M, p.N, p.pitch);
   if (first == 0) return cudaSuccess;
-  if (prec == Prec::TF32) {
+  if (prec == Prec::TF32)
     pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
-    pack_rescale_kernel<true><<<grid_for(rescale, sms), 256, 0, s>>>(p);
-  } else {
+  else
     pack_first_kernel<false><<<grid_for(first, sms), 256, 0, s>>>(p);
-    pack_rescale_kernel<false><<<grid_for(rescale, sms), 256, 0, s>>>(p);
-  }
   return cudaGetLastError();
+}
+
+}  // namespace
+
+// Items per problem of the pack launch (host side, same tiling as above).
+int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
+  return static_cast<int>(((M + 31) / 32) * ((pitch + 255) / 256) + ((N + 127) / 128) * ((pitch + 63) / 64));
+}
+
+cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
+                        int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA,
+                        unsigned* cntB, void* planesA, void* planesB, int64_t pitch, int sms,
+                        cudaStream_t s) {
+  const PackShape p = make_shape(A, M, K, lda, B, N, ldb, amaxA, amaxB, cntA, cntB, planesA, planesB,
+                                 (A ? M : 0) * pitch, pitch);
+  return launch_first(prec, p, sms, s);
 }
 
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
-                              unsigned* amaxB, unsigned* flag, void* planesB, int64_t pitch, int sms,
+                              unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
                               cudaStream_t s) {
-  if (M > 0 && K > 0) {
-    const bool vec = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
-    if (vec && lda == K) {
-      const int64_t nblk = (M + 127) / 128;
-      const int parts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(
-          (4 * static_cast<int64_t>(sms) + nblk - 1) / nblk, (128 * K / 4 + 2047) / 2048)));
-      const int grid = static_cast<int>(std::min<int64_t>(nblk * parts, 8 * static_cast<int64_t>(sms)));
-      amax_flat_kernel<<<grid, 256, 0, s>>>(A, M, K, parts, amaxA, flag);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      return pack_launch(prec, nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, flag, nullptr, planesB,
-                         pitch, sms, s);
-    }
-    const int64_t span = kAmaxLoads * (vec ? 4 : 1);
-    const int64_t items = ((M + 127) / 128) * ((K + span - 1) / span);
-    const int grid = static_cast<int>(std::min<int64_t>(items, 8 * static_cast<int64_t>(sms)));
-    if (vec)
-      amax_rows_kernel<true><<<grid, 256, 0, s>>>(A, M, K, lda, amaxA, flag);
-    else
-      amax_rows_kernel<false><<<grid, 256, 0, s>>>(A, M, K, lda, amaxA, flag);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  // B as in the packed variant
-  return pack_launch(prec, nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, flag, nullptr, planesB, pitch,
-                     sms, s);
-}
-
-cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
-                                   unsigned* amaxA, unsigned* flag, void* planesA,
-                                   int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s) {
-  PackShape p;
-  p.flag = flag;
-  p.A = A, p.B = nullptr, p.M = rows, p.N = 0, p.K = K, p.lda = lda, p.ldb = 1;
-  p.pitch = pitch;
-  p.planeA = plane_stride;
-  p.planeB = 0;
-  p.vecA = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
-  p.vecB = false;
-  p.amaxA = amaxA, p.amaxB = nullptr, p.planesA = planesA, p.planesB = nullptr;
-  const int64_t first = pack_first_items(rows, 0, pitch);
-  const int64_t rescale = pack_rescale_items(rows, 0, pitch);
-  if (first == 0) return cudaSuccess;
-  if (prec == Prec::TF32) {
-    pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
-    pack_rescale_kernel<true><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+  const PackShape p = make_shape(nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, nullptr, cntB, nullptr,
+                                 planesB, 0, pitch);
+  AmaxShape a;
+  a.A = A, a.M = M, a.K = K, a.lda = lda, a.amax = amaxA, a.parts = 1;
+  const int64_t nblk = (M + 127) / 128;
+  const bool vec = lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
+  int mode = vec ? kAmaxRowsVec : kAmaxRowsScalar;
+  int64_t na;
+  if (vec && lda == K) {
+    mode = kAmaxFlat;
+    a.parts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(
+        (4 * static_cast<int64_t>(sms) + nblk - 1) / nblk, (128 * K / 4 + 2047) / 2048)));
+    na = nblk * a.parts;
   } else {
-    pack_first_kernel<false><<<grid_for(first, sms), 256, 0, s>>>(p);
-    pack_rescale_kernel<false><<<grid_for(rescale, sms), 256, 0, s>>>(p);
+    const int64_t span = kAmaxLoads * (vec ? 4 : 1);
+    na = nblk * ((K + span - 1) / span);
+  }
+  if (M == 0 || K == 0) na = 0, a.M = 0;
+  const int64_t total = na + pack_first_items(0, p.N, pitch);
+  if (total == 0) return cudaSuccess;
+  const int grid = grid_for(total, sms);
+  if (prec == Prec::TF32) {
+    if (mode == kAmaxFlat) fused_prep_kernel<true, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
+    else if (mode == kAmaxRowsVec) fused_prep_kernel<true, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
+    else fused_prep_kernel<true, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+  } else {
+    if (mode == kAmaxFlat) fused_prep_kernel<false, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
+    else if (mode == kAmaxRowsVec) fused_prep_kernel<false, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
+    else fused_prep_kernel<false, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
   }
   return cudaGetLastError();
 }
 
+cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
+                                   unsigned* amaxA, unsigned* cntA, void* planesA,
+                                   int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s) {
+  const PackShape p = make_shape(A, rows, K, lda, nullptr, 0, 1, amaxA, nullptr, cntA, nullptr, planesA,
+                                 nullptr, plane_stride, pitch);
+  return launch_first(prec, p, sms, s);
+}
+
 cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const GroupedPtrs* ptrs,
-                                const int* first_prefix, int first_total, const int* rescale_prefix,
-                                int rescale_total, int G, unsigned* flag, int sms, cudaStream_t s) {
+                                const int* first_prefix, int first_total, int G, int sms,
+                                cudaStream_t s) {
   const size_t dyn = (G + 1) <= 4096 ? static_cast<size_t>(G + 1) * sizeof(int) : 0;
   if (first_total == 0) return cudaSuccess;
-  const int gf = grid_for(first_total, sms), gr = grid_for(rescale_total, sms);
-  if (prec == Prec::TF32) {
-    grouped_pack_kernel<true, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G, flag);
-    grouped_pack_kernel<true, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G, flag);
-  } else {
-    grouped_pack_kernel<false, kFirst><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G, flag);
-    grouped_pack_kernel<false, kRescale><<<gr, 256, dyn, s>>>(probs, ptrs, rescale_prefix, G, flag);
-  }
+  const int gf = grid_for(first_total, sms);
+  if (prec == Prec::TF32)
+    grouped_pack_kernel<true><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+  else
+    grouped_pack_kernel<false><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
   return cudaGetLastError();
 }
 
