@@ -570,6 +570,22 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       const Work w = wn;
       if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+      {
+        // warm L2 with the part of C this thread will read (beta != 0) while
+        // the unit's main loop still runs: short-K tiles are otherwise bound
+        // by the latency of the epilogue's C loads
+        const EpiView pv = sc.epi(w.prob);
+        const int prow = w.tm * 128 + q * 32 + lane;
+        const int pcol = w.tn * BN + half * EC;
+        if (pv.beta != 0.0f && pv.split_k == 1 && prow < pv.M && pcol < pv.N) {
+          const float* rp = pv.C + static_cast<int64_t>(prow) * pv.ldc + pcol;
+          const int ncols = min(EC, pv.N - pcol);
+#pragma unroll
+          for (int j = 0; j < EC; j += 32)
+            if (j < ncols) prefetch_l2(rp + j);
+          prefetch_l2(rp + ncols - 1);
+        }
+      }
       float S[EC];
       int blk = 0;
       for (int cb = w.c0; cb < w.c1; cb += kb, ++blk) {
