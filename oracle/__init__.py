@@ -12,6 +12,7 @@ Modules:
   split  -- the operand split (power-of-two block scaling, round-to-nearest-even
             to bf16 / tf32, hi/lo planes).
   mlp    -- the cost model's MLP: forward, MSE loss, analytic backward, Adam.
+  conv   -- direct 3x3 convolution (stride 1, zero padding 1), FP64 and exact.
 """
 from .gemm import (build, gemm_f64, gemm_f64_rows, rel_frob, gemm_exact,  # noqa: F401
                    library_path, num_threads)

@@ -27,6 +27,9 @@ import numpy as np
 # 224x224 images (M = output pixels, N = output channels, K = 9 * in channels).
 SQUARE_SWEEP = (1024, 1060, 2048, 4099, 8192)
 CONV_SHAPES = ((50176, 64, 576), (12544, 128, 1152), (3136, 256, 2304))
+# the 3x3 convolution layers behind CONV_SHAPES (batch, H, W, C in, K out):
+# M = batch*H*W output pixels, N = K, K_gemm = 9*C
+CONV3X3_LAYERS = ((1, 224, 224, 64, 64), (1, 112, 112, 128, 128), (1, 56, 56, 256, 256))
 ALPHA_BETA = ((1.0, 0.0), (1.5, 0.5))
 
 CONFIG_SMALL = 0      # 512^3, alpha 1.5, beta 0.5
@@ -136,3 +139,19 @@ def training_shapes(count: int, seed: int, lo: int = 32, hi: int = 65536,
         if math.log2(float(m) * cout * k) <= max_mnk_log2 and m * k <= max_elems:
             out.append((m, cout, k))
     return out
+
+
+def conv_image(batch: int, H: int, W: int, C: int, seed: int, kind: str = "uniform") -> np.ndarray:
+    """NHWC float32 image: iid uniform[-1, 1], or integers in [-8, 8]."""
+    rng = _rng(seed)
+    if kind == "integers":
+        return rng.integers(-8, 9, size=(batch, H, W, C)).astype(np.float32)
+    return rng.uniform(-1.0, 1.0, size=(batch, H, W, C)).astype(np.float32)
+
+
+def conv_filter(C: int, K: int, seed: int, kind: str = "uniform") -> np.ndarray:
+    """RSCK float32 3x3 filter: iid uniform[-1, 1], or integers in [-8, 8]."""
+    rng = _rng(seed)
+    if kind == "integers":
+        return rng.integers(-8, 9, size=(3, 3, C, K)).astype(np.float32)
+    return rng.uniform(-1.0, 1.0, size=(3, 3, C, K)).astype(np.float32)
