@@ -126,6 +126,25 @@ gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64
 gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                                     int64_t ldc, gemm_mode mode, int config_id, gemm_plan_t* out);
 
+/* Direct 3x3 convolution, stride 1, zero padding 1 (the paper benchmarks
+ * convolutions, Section VI), as an implicit gemm: the patch matrix of the
+ * image (M = batch*H*W output pixels by 9*C taps x channels) is never formed;
+ * the fused-split kernel gathers it tile by tile while splitting it.
+ *   out[n][h][w][k] = alpha * sum_{r,s,c} in[n][h+r-1][w+s-1][c] * f[r][s][c][k]
+ *                     + beta * out[n][h][w][k]      (in = 0 outside the image)
+ * Execute with gemm_plan_execute(plan, alpha, in, f, beta, out, stream):
+ *   in:  NHWC FP32 [batch][H][W][C], channels contiguous, 16-byte aligned;
+ *   f:   RSCK FP32 [3][3][C][K] (= the gemm's B, 9C x K row-major);
+ *   out: NHWC FP32 [batch][H][W][K] (= the gemm's C, ld K).
+ * All device memory owned by the caller.  C must be a multiple of 4.  One
+ * power-of-two exponent covers the whole image (its max |x|), B is scaled
+ * per 128 output channels as in the gemm.  config_id < 0 picks a default;
+ * otherwise it must be a fused-split configuration (gemm_config.fused).
+ * Errors: INVALID_ARG (sizes, C % 4, mode, configuration), ALIGNMENT (at
+ * execute: input not 16-byte aligned), ALLOC, CUDA, UNSUPPORTED_DEVICE. */
+gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K,
+                                     gemm_mode mode, int config_id, gemm_plan_t* out);
+
 /* Run the plan: split/pack of A and B, the gemm kernel, and the split-K
  * reduction when split_k > 1, all on `stream`.  No host synchronization, so
  * the call may be captured into a CUDA graph. */

@@ -43,6 +43,10 @@ struct TcArgs {
   const float* A;
   int64_t lda;
   int vecA;                // A 16-byte aligned and lda % 4 == 0: float4 loads
+  // direct 3x3 convolution (fused variant): A is the patch matrix of the NHWC
+  // image at A (conv_H x conv_W x conv_C pixels, zero padding 1), gathered
+  // while staging; one block exponent for the whole image (amaxA[0])
+  int conv, conv_H, conv_W, conv_C;
 };
 
 struct TcLaunch {
@@ -94,7 +98,7 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
                               unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t K_b = -1);
 // A row panel of A (rows rows, starting at a 128-row block) packed into the
 // planes of the whole matrix at planesA (already offset to the panel's
 // first row; plane_stride = elements from the hi plane to the lo plane).

@@ -58,6 +58,11 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 static EncodeTiledFn g_encode = nullptr;
+using EncodeIm2colFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const int*, const int*,
+                                    cuuint32_t, cuuint32_t, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeIm2colFn g_encode_im2col = nullptr;
 
 gemm_status device_state(DeviceState** out, int* dev_out) {
   int dev = 0;
@@ -84,6 +89,15 @@ gemm_status device_state(DeviceState** out, int* dev_out) {
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
       return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled entry point not found");
     g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  if (!g_encode_im2col) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeIm2col", &fn, 12000, cudaEnableDefault, &q);
+    if (e == cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+      g_encode_im2col = reinterpret_cast<EncodeIm2colFn>(fn);
+    else
+      cudaGetLastError();   // the convolution then stages its patches with cp.async
   }
   *out = &d;
   if (dev_out) *dev_out = dev;
@@ -221,6 +235,28 @@ static gemm_status encode_rows_f32(CUtensorMap* map, const float* A, int64_t M, 
   if (r != CUDA_SUCCESS)
     return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for A, M=%lld K=%lld lda=%lld", (int)r,
                 (long long)M, (long long)K, (long long)lda);
+  return GEMM_OK;
+}
+
+// The patch matrix of a 3x3 convolution (stride 1, zero padding 1) over the
+// NHWC image X, for TMA's im2col mode: each load brings 128 consecutive
+// output pixels (row-major over N, H, W, wrapping rows and images) times 32
+// channels of one filter tap, zero outside the image; 128-byte swizzle.  The
+// bounding box corners (-1, -1) and (-1, -1) make the starting pixel of
+// output (h, w) the input pixel (h - 1, w - 1); the tap adds (r, s).
+static gemm_status encode_im2col_3x3(CUtensorMap* map, const float* X, int64_t batch, int64_t H,
+                                     int64_t W, int64_t C) {
+  if (!g_encode_im2col) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "cuTensorMapEncodeIm2col unavailable");
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  cuuint64_t strides[3] = {(cuuint64_t)(C * 4), (cuuint64_t)(W * C * 4), (cuuint64_t)(H * W * C * 4)};
+  const int lower[2] = {-1, -1}, upper[2] = {-1, -1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode_im2col(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(X), dims, strides,
+                               lower, upper, 32, 128, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeIm2col failed (%d)", (int)r);
   return GEMM_OK;
 }
 
@@ -381,7 +417,14 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   if (prof) cudaEventRecord(ev[0], s);
   if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemsetAsync(amax)");
-  if (p->launch.fused)
+  if (p->args.conv) {
+    // one exponent for the whole image: its max, scanned as a single row
+    if (reinterpret_cast<uintptr_t>(A) % 16 != 0)
+      return fail(GEMM_ERR_ALIGNMENT, "the convolution's input image must be 16-byte aligned");
+    const int64_t elems = (int64_t)p->conv_batch * p->args.conv_H * p->args.conv_W * p->args.conv_C;
+    e = pack_fused_launch(p->prec, A, 1, elems, elems, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
+                          p->planesB, p->pitch, p->sms, s, K);
+  } else if (p->launch.fused)
     e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
                           p->planesB, p->pitch, p->sms, s);
   else
@@ -394,12 +437,15 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.C = C;
   a.A = A;
   a.vecA = (p->lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0) ? 1 : 0;
+  if (a.conv)   // TMA im2col staging when every 32-channel box lies in one tap of whole chunks
+    a.vecA = (g_encode_im2col && a.conv_C % (p->prec == Prec::TF32 ? 32 : 64) == 0) ? 1 : 0;
   CUtensorMap tmAf;   // fused variant: A staged by TMA when its rows are 16-byte aligned
   const CUtensorMap* mapA = &p->tmA;
   if (p->launch.fused) {
     std::memset(&tmAf, 0, sizeof tmAf);
     if (a.vecA) {
-      gemm_status st = encode_rows_f32(&tmAf, A, M, K, p->lda);
+      gemm_status st = a.conv ? encode_im2col_3x3(&tmAf, A, p->conv_batch, a.conv_H, a.conv_W, a.conv_C)
+                              : encode_rows_f32(&tmAf, A, M, K, p->lda);
       if (st != GEMM_OK) return st;
     }
     mapA = &tmAf;
@@ -728,6 +774,46 @@ gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda
   if (config_id < 0 && mode != GEMM_MODE_F32_SIMT)
     return fail(GEMM_ERR_INVALID_ARG, "negative configuration id");
   return plan_create_impl(M, N, K, lda, ldb, ldc, mode, config_id, GEMM_SELECT_DEFAULT, out);
+}
+
+gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K,
+                                     gemm_mode mode, int config_id, gemm_plan_t* out) {
+  clear_error();
+  if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
+  *out = nullptr;
+  if (batch < 1 || H < 1 || W < 1 || C < 1 || K < 1)
+    return fail(GEMM_ERR_INVALID_ARG, "convolution sizes must be positive");
+  if (C % 4 != 0) return fail(GEMM_ERR_INVALID_ARG, "input channels C=%lld must be a multiple of 4", (long long)C);
+  if (H > 65535 || W > 65535 || C > (1 << 20) || batch * H * W > INT32_MAX || 9 * C > INT32_MAX)
+    return fail(GEMM_ERR_INVALID_ARG, "convolution too large");
+  if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
+  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
+    return fail(GEMM_ERR_INVALID_ARG, "the convolution runs in BF16X3 or TF32X3 mode");
+  const int64_t M = batch * H * W, Kd = 9 * C;
+  gemm_config c;
+  if (config_id < 0) {
+    // default: the A-splitting kernel, tile width by K, no split, longest fold
+    const int bn = K <= 64 ? 64 : 128;
+    for (int id = 0; id < config_count(mode); ++id) {
+      config_get(id, &c);
+      if (c.fused && c.block_n == bn && c.split_k == 1 && c.kb == 8 && c.group_m == 16) {
+        config_id = id;
+        break;
+      }
+    }
+  } else if (!config_get(config_id, &c) || !c.fused) {
+    return fail(GEMM_ERR_INVALID_ARG, "configuration %d is not a fused-split configuration", config_id);
+  }
+  gemm_plan_t p = nullptr;
+  gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p);
+  if (st != GEMM_OK) return st;
+  p->conv_batch = (int)batch;
+  p->args.conv = 1;
+  p->args.conv_H = (int)H;
+  p->args.conv_W = (int)W;
+  p->args.conv_C = (int)C;
+  *out = p;
+  return GEMM_OK;
 }
 
 gemm_status gemm_plan_execute(gemm_plan_t plan, float alpha, const float* A, const float* B,

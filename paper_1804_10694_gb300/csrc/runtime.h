@@ -27,6 +27,7 @@ struct gemm_plan_s {
   size_t amax_bytes = 0;            // block maxima of A and B, then their pack counters
   unsigned* cntA = nullptr;
   unsigned* cntB = nullptr;
+  int conv_batch = 0;               // direct convolution plans (args.conv): images per call
   float* partial = nullptr;
   CUtensorMap tmA{}, tmB{};
   gb::TcArgs args{};

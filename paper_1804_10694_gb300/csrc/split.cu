@@ -558,9 +558,11 @@ cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
                               unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
-                              cudaStream_t s) {
-  const PackShape p = make_shape(nullptr, 0, K, 1, B, N, ldb, nullptr, amaxB, nullptr, cntB, nullptr,
-                                 planesB, 0, pitch);
+                              cudaStream_t s, int64_t K_b) {
+  // K_b: rows of B when they differ from A's row length (the convolution
+  // scans its image as one M = 1 row of all its elements)
+  const PackShape p = make_shape(nullptr, 0, K_b >= 0 ? K_b : K, 1, B, N, ldb, nullptr, amaxB, nullptr,
+                                 cntB, nullptr, planesB, 0, pitch);
   AmaxShape a;
   a.A = A, a.M = M, a.K = K, a.lda = lda, a.amax = amaxA, a.parts = 1;
   const int64_t nblk = (M + 127) / 128;

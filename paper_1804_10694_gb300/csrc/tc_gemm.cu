@@ -106,6 +106,7 @@ struct EpiView {
   const unsigned* amaxB;
   float* partial;
   int split_k;
+  int amaxA_stride;         // 1: one exponent per 128-row block; 0: one for all of A
 };
 
 // Source of A for the fused-split variant.
@@ -113,8 +114,11 @@ struct FusedA {
   const float* A;
   int64_t lda;
   int M, K;
-  bool vec;                 // 16-byte aligned rows: staged by TMA, else by 4-byte cp.async
+  bool vec;                 // staged by TMA (rows 16-byte aligned; for a convolution,
+                            // im2col boxes of whole taps), else by cp.async
   const unsigned* amaxA;    // block maxima from the max-only pass
+  int amax_stride;          // 1, or 0 when one exponent covers all of A
+  int conv, H, W, C;        // A = patch matrix of an NHWC image (3x3, zero padding 1)
 };
 
 __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
@@ -152,10 +156,12 @@ struct SingleSched {
     EpiView v;
     v.M = a->M, v.N = a->N, v.C = a->C, v.ldc = a->ldc, v.alpha = a->alpha, v.beta = a->beta;
     v.amaxA = a->amaxA, v.amaxB = a->amaxB, v.partial = a->partial, v.split_k = a->split_k;
+    v.amaxA_stride = a->conv ? 0 : 1;
     return v;
   }
   __device__ FusedA srcA(int) const {
-    return FusedA{a->A, a->lda, a->M, a->K, a->vecA != 0, a->amaxA};
+    return FusedA{a->A, a->lda, a->M, a->K, a->vecA != 0, a->amaxA, a->conv ? 0 : 1,
+                  a->conv, a->conv_H, a->conv_W, a->conv_C};
   }
 };
 
@@ -187,6 +193,7 @@ struct GroupedSched {
     EpiView v;
     v.M = p.M, v.N = p.N, v.C = q.C, v.ldc = p.ldc, v.alpha = q.alpha, v.beta = q.beta;
     v.amaxA = p.amaxA, v.amaxB = p.amaxB, v.partial = nullptr, v.split_k = 1;
+    v.amaxA_stride = 1;
     return v;
   }
 };
@@ -378,6 +385,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         bq = aq;
         const CUtensorMap* mA = sc.mapA(0);
         const CUtensorMap* mB = sc.mapB(0);
+        const FusedA fa = sc.srcA(0);
         tma_prefetch_desc(mA);
         tma_prefetch_desc(mB);
         uint32_t aslot = 0, aph = 0, bstage = 0, bph = 0;
@@ -390,10 +398,26 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           if (aq.have && mbar_test_wait(stg_empty_bar(aslot), aph ^ 1u)) {
             const uint32_t fb = stg_full_bar(aslot);
             mbar_arrive_expect_tx(fb, Cfg::STG_BYTES);
+            if (fa.conv) {
+              // patch-matrix boxes: 128 output pixels from the tile's first,
+              // 32 channels of one tap (the host checked C % (32 * boxes) == 0)
+              const int hw = fa.H * fa.W;
+              const int p0 = aq.w.tm * 128;
+              const int n0 = p0 / hw, rem = p0 - n0 * hw;
+              const int h0 = rem / fa.W, w0 = rem - h0 * fa.W;
 #pragma unroll
-            for (int h = 0; h < Cfg::STG_ROW / 128; ++h)
-              tma_load_3d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, aq.c * Cfg::BK + 32 * h,
-                          aq.w.tm * 128, 0);
+              for (int h = 0; h < Cfg::STG_ROW / 128; ++h) {
+                const int k0 = aq.c * Cfg::BK + 32 * h;
+                const int tap = k0 / fa.C, c0 = k0 - tap * fa.C;
+                tma_load_im2col_4d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, c0, w0 - 1, h0 - 1, n0,
+                                   static_cast<uint16_t>(tap % 3), static_cast<uint16_t>(tap / 3));
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < Cfg::STG_ROW / 128; ++h)
+                tma_load_3d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, aq.c * Cfg::BK + 32 * h,
+                            aq.w.tm * 128, 0);
+            }
             a_used |= 1u << aslot;
             a_par = (a_par & ~(1u << aslot)) | (aph << aslot);
             adv(aq);
@@ -629,7 +653,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       // applied before the power of two, so that a result in range is not
       // lost to an overflow of the unscaled sum (the power of two is exact).
       const int col0 = w.tn * BN + half * EC;
-      const int e = block_exponent(v.amaxA[w.tm]) + block_exponent(v.amaxB[col0 / kScaleBlock]);
+      const int e = block_exponent(v.amaxA[w.tm * v.amaxA_stride]) +
+                    block_exponent(v.amaxB[col0 / kScaleBlock]);
       float alpha = v.alpha;
       float beta = v.beta;
       if (v.split_k > 1 || e != 0) {
@@ -761,6 +786,45 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     auto fill = [&](int b) {
       const FusedA src = sc.srcA(fc.w.prob);
       const int64_t kbase = static_cast<int64_t>(fc.c) * Cfg::BK;
+      if (src.conv) {
+        // Patch-matrix gather of a 3x3 convolution: column k = (tap, c),
+        // tap = 3 r + s; row = output pixel (n, h, w) reads the input pixel
+        // (n, h + r - 1, w + s - 1), zero outside.  C % 4 == 0, so a 16-byte
+        // unit is four channels of one tap.  With SPLIT_THREADS a multiple of
+        // UPR, this thread's unit j is fixed and its rows step by RS pixels.
+        static_assert(Cfg::SPLIT_THREADS % UPR == 0, "unit mapping");
+        constexpr int RS = Cfg::SPLIT_THREADS / UPR;
+        const int j = ct % UPR;
+        const int64_t k = kbase + 4 * j;
+        const bool kin = k < src.K;
+        const int tap = kin ? static_cast<int>(k / src.C) : 0;
+        const int c = static_cast<int>(k - static_cast<int64_t>(tap) * src.C);
+        const int dr = tap / 3 - 1, ds = tap % 3 - 1;
+        const int hw = src.H * src.W;
+        int64_t pix = static_cast<int64_t>(fc.w.tm) * 128 + ct / UPR;
+        int n = static_cast<int>(pix / hw);
+        int rem = static_cast<int>(pix - static_cast<int64_t>(n) * hw);
+        int h = rem / src.W, w = rem - h * src.W;
+        for (int r = ct / UPR; r < 128; r += RS) {
+          const uint32_t dst = stg0 + b * Cfg::STG_BYTES + (j >> 3) * BOX + r * 128 +
+                               (((j & 7) ^ (r & 7)) << 4);
+          const int hh = h + dr, ww = w + ds;
+          const bool in = kin && pix < src.M && hh >= 0 && hh < src.H && ww >= 0 && ww < src.W;
+          const float* p = in ? src.A + ((static_cast<int64_t>(n) * src.H + hh) * src.W + ww) * src.C + c
+                              : src.A;
+          cp_async_16(dst, p, in ? 16u : 0u);
+          // next row: RS pixels further
+          pix += RS;
+          w += RS;
+          while (w >= src.W) {
+            w -= src.W;
+            if (++h == src.H) h = 0, ++n;
+          }
+        }
+        cp_async_mbar_arrive(stg_full_bar(b));
+        advance(fc);
+        return;
+      }
       for (int i = ct; i < 128 * UPR; i += Cfg::SPLIT_THREADS) {
         const int r = i / UPR, j = i % UPR;
         const uint32_t dst = stg0 + b * Cfg::STG_BYTES + (j >> 3) * BOX + r * 128 +
@@ -787,7 +851,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     int last_prob = -1, last_tm = -1;
     while (sc_.have) {
       if (sc_.w.prob != last_prob || sc_.w.tm != last_tm) {
-        amax = sc.srcA(sc_.w.prob).amaxA[sc_.w.tm];
+        const FusedA sa = sc.srcA(sc_.w.prob);
+        amax = sa.amaxA[sc_.w.tm * sa.amax_stride];
         last_prob = sc_.w.prob;
         last_tm = sc_.w.tm;
       }

@@ -81,3 +81,16 @@ def test_split_pack_argument_checks():
 def test_build_flags_target_sm103a():
     from paper_1804_10694_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_conv3x3_plan_argument_validation():
+    """Rejected before any device work: channels not a multiple of 4,
+    non-positive sizes, a SIMT mode, a packed configuration id."""
+    import ctypes
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    assert lib.gemm_conv3x3_plan_create(1, 4, 4, 3, 8, 2, -1, ctypes.byref(h)) == 1
+    assert lib.gemm_conv3x3_plan_create(0, 4, 4, 4, 8, 2, -1, ctypes.byref(h)) == 1
+    assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 1, -1, ctypes.byref(h)) == 1
+    packed = next(i for i in range(pkg.config_count("bf16x3")) if not pkg.config_get("bf16x3", i)["fused"])
+    assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 2, packed, ctypes.byref(h)) == 1

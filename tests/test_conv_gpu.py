@@ -1,0 +1,159 @@
+"""Parity of the direct 3x3 convolution (implicit gemm through the
+fused-split kernel) with the convolution oracle, and with the gemm path on an
+explicitly formed patch matrix (same split, same MMAs: bit for bit)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import conv
+import paper_1804_10694_gb300 as pkg
+import workloads as W
+from gpu_helpers import TOL
+
+pytestmark = pytest.mark.gpu
+
+
+def run_conv(x, f, alpha, beta, out0, mode="bf16x3", config_id=None):
+    n, H, Wd, C = x.shape
+    K = f.shape[3]
+    plan = pkg.Conv3x3Plan(n, H, Wd, C, K, mode=mode, config_id=config_id)
+    dx, df, do = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (x, f, out0))
+    plan.execute(dx, df, do, alpha, beta)
+    torch.cuda.synchronize()
+    cid = plan.info()["config_id"]
+    plan.destroy()
+    return do.cpu().numpy(), cid
+
+
+def patches(x):
+    """Patch matrix, row = output pixel, column = (r, s, c)."""
+    n, H, Wd, C = x.shape
+    pad = np.zeros((n, H + 2, Wd + 2, C), np.float32)
+    pad[:, 1:H + 1, 1:Wd + 1] = x
+    cols = [pad[:, r:r + H, s:s + Wd, :].reshape(-1, C) for r in range(3) for s in range(3)]
+    return np.ascontiguousarray(np.concatenate(cols, axis=1))
+
+
+def fused_ids(mode, **want):
+    out = []
+    for i in range(pkg.config_count(mode)):
+        c = pkg.config_get(mode, i)
+        if c["fused"] and all(c[k] == v for k, v in want.items()):
+            out.append(i)
+    return out
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_small_images_match_oracle(mode):
+    x = W.conv_image(2, 9, 13, 8, 101)
+    f = W.conv_filter(8, 12, 102)
+    out0 = W.conv_image(2, 9, 13, 12, 103)
+    ref = conv.conv3x3_f64(x, f, 1.5, 0.5, out0)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode)
+    assert oracle.rel_frob(got.reshape(-1, 12), ref.reshape(-1, 12)) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_integer_images_bit_exact(mode):
+    x = W.conv_image(1, 17, 11, 12, 104, kind="integers")
+    f = W.conv_filter(12, 20, 105, kind="integers")
+    out0 = W.conv_image(1, 17, 11, 20, 106, kind="integers")
+    ref = conv.conv3x3_f64(x, f, 1.5, 0.5, out0).astype(np.float32)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+def test_every_fused_configuration_equals_gemm_on_patch_matrix(mode):
+    """The patch matrix the kernel gathers, formed explicitly and run through
+    the gemm with the same configuration, gives the same bits (uniform data:
+    both use exponent 0)."""
+    x = W.conv_image(2, 11, 7, 16, 107)
+    f = W.conv_filter(16, 40, 108)
+    out0 = W.conv_image(2, 11, 7, 40, 109)
+    P = patches(x)
+    M, Kd, K = P.shape[0], P.shape[1], 40
+    dP, dB = torch.from_numpy(P).cuda(), torch.from_numpy(f.reshape(Kd, K).copy()).cuda()
+    ref = conv.conv3x3_f64(x, f, 1.0, -0.5, out0).reshape(-1, K)
+    for cid in fused_ids(mode):
+        got, _ = run_conv(x, f, 1.0, -0.5, out0, mode, config_id=cid)
+        dC = torch.from_numpy(out0.reshape(-1, K).copy()).cuda()
+        plan = pkg.Plan(M, K, Kd, mode=mode, config_id=cid)
+        plan.execute(dP, dB, dC, 1.0, -0.5)
+        torch.cuda.synchronize()
+        plan.destroy()
+        assert np.array_equal(got.reshape(-1, K).view(np.uint32), dC.cpu().numpy().view(np.uint32)), \
+            pkg.config_get(mode, cid)
+        assert oracle.rel_frob(got.reshape(-1, K), ref) <= TOL
+
+
+@pytest.mark.parametrize("mode,C", [("bf16x3", 64), ("tf32x3", 32), ("bf16x3", 128)])
+def test_im2col_staging_equals_gemm_on_patch_matrix(mode, C):
+    """Channel counts whose chunks are whole taps are staged by TMA's im2col
+    mode (offsets per tap, zero outside the image, rows wrapping across image
+    rows and images); same bits as the gemm on the formed patch matrix."""
+    x = W.conv_image(2, 7, 10, C, 150 + C)
+    f = W.conv_filter(C, 24, 151)
+    out0 = W.conv_image(2, 7, 10, 24, 152)
+    P = patches(x)
+    M, Kd, K = P.shape[0], P.shape[1], 24
+    dP, dB = torch.from_numpy(P).cuda(), torch.from_numpy(f.reshape(Kd, K).copy()).cuda()
+    for cid in fused_ids(mode, group_m=16, kb=4)[::3]:
+        got, _ = run_conv(x, f, 1.5, 0.5, out0, mode, config_id=cid)
+        dC = torch.from_numpy(out0.reshape(-1, K).copy()).cuda()
+        plan = pkg.Plan(M, K, Kd, mode=mode, config_id=cid)
+        plan.execute(dP, dB, dC, 1.5, 0.5)
+        torch.cuda.synchronize()
+        plan.destroy()
+        assert np.array_equal(got.reshape(-1, K).view(np.uint32), dC.cpu().numpy().view(np.uint32)), \
+            pkg.config_get(mode, cid)
+
+
+def test_degenerate_images():
+    # 1x1 images: only the centre tap sees data; a one-pixel-wide image; C = 4, K = 1
+    for (n, H, Wd, C, K) in [(3, 1, 1, 4, 5), (1, 7, 1, 8, 3), (2, 5, 6, 4, 1)]:
+        x = W.conv_image(n, H, Wd, C, 110 + H)
+        f = W.conv_filter(C, K, 120 + Wd)
+        out0 = np.zeros((n, H, Wd, K), np.float32)
+        ref = conv.conv3x3_f64(x, f)
+        got, _ = run_conv(x, f, 1.0, 0.0, out0)
+        assert oracle.rel_frob(got.reshape(-1, K), ref.reshape(-1, K)) <= TOL, (n, H, Wd, C, K)
+
+
+def test_whole_image_exponent_keeps_tiny_inputs():
+    """One power-of-two exponent for the whole image: inputs near 2^-100
+    keep their low parts."""
+    x = W.scaled(W.conv_image(1, 20, 20, 8, 130), -100)
+    f = W.conv_filter(8, 16, 131)
+    ref = conv.conv3x3_f64(x, f)
+    got, _ = run_conv(x, f, 1.0, 0.0, np.zeros((1, 20, 20, 16), np.float32))
+    assert oracle.rel_frob(got.reshape(-1, 16), ref.reshape(-1, 16)) <= TOL
+
+
+@pytest.mark.parametrize("layer", W.CONV3X3_LAYERS)
+def test_full_size_layers_sampled_pixels(layer):
+    n, H, Wd, C, K = layer
+    x = W.conv_image(n, H, Wd, C, 140)
+    f = W.conv_filter(C, K, 141)
+    got, cid = run_conv(x, f, 1.0, 0.0, np.zeros((n, H, Wd, K), np.float32))
+    rng = np.random.default_rng(7)
+    pix = sorted(set(rng.choice(n * H * Wd, 96, replace=False).tolist()) |
+                 {0, Wd - 1, (H - 1) * Wd, H * Wd - 1})
+    ref = conv.conv3x3_pixels_f64(pix, x, f)
+    assert oracle.rel_frob(got.reshape(-1, K)[pix], ref) <= TOL
+
+
+def test_misaligned_image_is_rejected():
+    plan = pkg.Conv3x3Plan(1, 4, 4, 4, 4)
+    buf = torch.zeros(1 + 4 * 4 * 4, device="cuda")
+    f = torch.zeros(3, 3, 4, 4, device="cuda")
+    out = torch.zeros(1, 4, 4, 4, device="cuda")
+    lib = pkg.load()
+    st = lib.gemm_plan_execute(plan._h, 1.0, buf.data_ptr() + 4, f.data_ptr(), 0.0, out.data_ptr(), None)
+    assert st == 2   # GEMM_ERR_ALIGNMENT
+    plan.destroy()
