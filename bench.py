@@ -248,13 +248,15 @@ def other_workloads(model_path: str | None):
     """Secondary measurements on the other workloads (outside the timed
     region; device-filled uniform[-1, 1] data, median of CUDA-event timings):
     the square sweep in all three modes, the conv-as-gemm shapes with the
-    heuristic, the cost model's pick and the exhaustive best, and the
-    512-problem grouped gemm replayed from its CUDA graph."""
+    heuristic, the cost model's pick, the exhaustive best and the best packed
+    and fused-split configurations, the same layers as direct 3x3
+    convolutions, and the 512-problem grouped gemm replayed from its CUDA
+    graph."""
     import torch
     import paper_1804_10694_gb300 as pkg
     import workloads as W
     stream = torch.cuda.current_stream()
-    out = {"sweep": {}, "conv": {}, "grouped": None}
+    out = {"sweep": {}, "conv": {}, "conv_direct": {}, "grouped": None}
     for n in W.SQUARE_SWEEP:
         A = torch.empty(n, n, device="cuda").uniform_(-1, 1)
         B = torch.empty(n, n, device="cuda").uniform_(-1, 1)
@@ -311,6 +313,35 @@ def other_workloads(model_path: str | None):
         simt.destroy()
         out["conv"][f"{M}x{N}x{K}"] = res
         del A, B, C
+    # the same layers as direct 3x3 convolutions (implicit gemm on the NHWC
+    # image: the patch matrix is gathered by TMA im2col loads, never formed)
+    out["conv_direct"] = {}
+    for (nb, H, Wd, Ci, Ko) in W.CONV3X3_LAYERS:
+        x = torch.empty(nb, H, Wd, Ci, device="cuda").uniform_(-1, 1)
+        f = torch.empty(3, 3, Ci, Ko, device="cuda").uniform_(-1, 1)
+        o = torch.empty(nb, H, Wd, Ko, device="cuda")
+        flops = 2.0 * nb * H * Wd * Ko * 9 * Ci
+        res = {}
+        cands = [None] + [i for i in range(pkg.config_count("bf16x3"))
+                          if (lambda c: c["fused"] and c["kb"] == 8 and c["group_m"] == 16
+                              and c["split_k"] <= 3)(pkg.config_get("bf16x3", i))]
+        best = None
+        for cid in cands:
+            plan = pkg.Conv3x3Plan(nb, H, Wd, Ci, Ko, config_id=cid)
+            for _ in range(2):
+                plan.execute(x, f, o, 1.0, 0.0)
+            ms = _median_ms(lambda: [plan.execute(x, f, o, 1.0, 0.0) for _ in range(10)], 5, stream) / 10
+            entry = {"tflops": round(flops / (ms * 1e-3) / 1e12, 2), "ms": round(ms, 4),
+                     "config": pkg.config_get("bf16x3", plan.info()["config_id"]),
+                     "hbm_gbs": round(4.0 * (x.numel() + f.numel() + o.numel()) / (ms * 1e-3) / 1e9, 1)}
+            if cid is None:
+                res["default"] = entry
+            if best is None or ms < best["ms"]:
+                best = entry
+            plan.destroy()
+        res["best"] = best
+        out["conv_direct"][f"{nb}x{H}x{Wd}x{Ci}->{Ko}"] = res
+        del x, f, o
     shapes = W.grouped_shapes()
     As = [torch.empty(m, k, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
     Bs = [torch.empty(k, n, device="cuda").uniform_(-1, 1) for m, n, k in shapes]

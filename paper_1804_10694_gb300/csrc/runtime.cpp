@@ -792,11 +792,18 @@ gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_
   const int64_t M = batch * H * W, Kd = 9 * C;
   gemm_config c;
   if (config_id < 0) {
-    // default: the A-splitting kernel, tile width by K, no split, longest fold
-    const int bn = K <= 64 ? 64 : 128;
+    // default: the fused-split twin of the gemm heuristic's choice for this
+    // shape (tile width by K, split-K when the tiles do not fill the GPU)
+    DeviceState* dev;
+    gemm_status st0 = device_state(&dev, nullptr);
+    if (st0 != GEMM_OK) return st0;
+    const int packed = default_config(mode, M, K, Kd, dev->sms);
+    gemm_config d;
+    config_get(packed, &d);
     for (int id = 0; id < config_count(mode); ++id) {
       config_get(id, &c);
-      if (c.fused && c.block_n == bn && c.split_k == 1 && c.kb == 8 && c.group_m == 16) {
+      if (c.fused && c.block_n == d.block_n && c.split_k == d.split_k && c.kb == d.kb &&
+          c.group_m == d.group_m) {
         config_id = id;
         break;
       }
