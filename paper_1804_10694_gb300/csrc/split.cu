@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "ptx.cuh"
 #include "scale.cuh"
 #include "split_arith.cuh"
 
@@ -436,6 +437,7 @@ __global__ void __launch_bounds__(256) pack_first_kernel(const PackShape p) {
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
   pack_range<TF32>(p, i0, min(total, i0 + per), tile);
+  griddep_launch_dependents();   // the gemm may start its prologue
 }
 
 // Fused-split preparation in one launch: A's block maxima (grid-stride),
@@ -450,6 +452,7 @@ __global__ void __launch_bounds__(256) fused_prep_kernel(const AmaxShape a, cons
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
   pack_range<TF32>(p, i0, min(total, i0 + per), tile);
+  griddep_launch_dependents();
 }
 
 // ------------------------------------------------------ grouped kernels
@@ -507,6 +510,7 @@ __global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem*
       pack_range<TF32>(problem_shape(probs[g], q), i - prefix[g], e - prefix[g], tile);
     i = e;
   }
+  griddep_launch_dependents();
 }
 
 int grid_for(int64_t items, int sms) {

@@ -37,6 +37,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include "internal.h"
 #include "ptx.cuh"
 #include "scale.cuh"
@@ -348,6 +350,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the prologue above overlaps the end of the packing kernel; nothing below
+  // runs before that kernel has completed and its writes are visible
+  griddep_wait();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -939,6 +944,7 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, true>::THREADS, 1)
 // fixed order, so results do not depend on timing).
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
                                      float beta, float* __restrict__ C, int64_t ldc) {
+  griddep_wait();   // launched as a dependent of the gemm kernel
   const int64_t total = static_cast<int64_t>(M) * N;
   const int64_t plane = total;
   for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
@@ -949,6 +955,25 @@ __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __re
     float* cp = C + r * ldc + c;
     *cp = beta != 0.0f ? s + beta * *cp : s;
   }
+}
+
+// Launch with programmatic stream serialization: the kernel may begin (its
+// prologue, up to griddep_wait) while the previous kernel of the stream
+// finishes.
+template <typename... Params, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(Params...), int grid, int threads, int smem,
+                                    cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 int tc_smem_bytes(int bn, Prec prec, bool fused) {
@@ -1015,12 +1040,14 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
     using Cfg = TcCfg<BN, TF32, true>;
     cudaError_t e = prepare_variant<BN, TF32, true>();
     if (e != cudaSuccess) return e;
-    tc_gemm_fused_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+    e = launch_dependent(tc_gemm_fused_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    if (e != cudaSuccess) return e;
   } else {
     using Cfg = TcCfg<BN, TF32>;
     cudaError_t e = prepare_variant<BN, TF32, false>();
     if (e != cudaSuccess) return e;
-    tc_gemm_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(tmA, tmB, a);
+    e = launch_dependent(tc_gemm_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -1042,7 +1069,8 @@ static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaSt
   using Cfg = TcCfg<BN, TF32>;
   cudaError_t e = prepare_variant<BN, TF32, false>();
   if (e != cudaSuccess) return e;
-  tc_grouped_kernel<BN, TF32><<<grid, Cfg::THREADS, Cfg::SMEM, s>>>(a);
+  e = launch_dependent(tc_grouped_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1063,8 +1091,9 @@ cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial,
   int64_t blocks = (total + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  splitk_reduce_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(M, N, splits, partial, beta, C,
-                                                               ldc);
+  cudaError_t e = launch_dependent(splitk_reduce_kernel, static_cast<int>(blocks), 256, 0, s, M, N, splits,
+                                   partial, beta, C, ldc);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
