@@ -99,6 +99,18 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
                         int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                         int64_t ldc, gemm_mode mode, gemm_select sel, gemm_stream_t stream);
 
+/* C = alpha * op(A) op(B) + beta * C with BLAS-style transposes: op(A) is
+ * M x K and op(B) is K x N.  transA != 0: A is stored K x M row-major
+ * (lda >= M), op(A) = A^T; transB != 0: B is stored N x K (ldb >= K),
+ * op(B) = B^T.  The packing pass reads each layout directly (no transposed
+ * copy), so the planes and the results are bit-identical to the
+ * untransposed call on the transposed matrices.  Tensor-core modes only
+ * (F32_SIMT with a transpose is INVALID_ARG); a fused-split configuration
+ * chosen for a transposed A runs as its packed twin. */
+gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                       int64_t ldc, gemm_mode mode, gemm_select sel, gemm_stream_t stream);
+
 /* As gemm_f32_ex, but A, B and C are HOST pointers (pageable or pinned): the
  * call copies A, B (and C when beta != 0) to device buffers it keeps per
  * thread, computes, copies C back and synchronizes the stream before
@@ -125,6 +137,11 @@ gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64
  * gemm_config_count / gemm_config_get). */
 gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                                     int64_t ldc, gemm_mode mode, int config_id, gemm_plan_t* out);
+
+/* As gemm_plan_create, with the transposes of gemm_f32_t. */
+gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int64_t K, int64_t lda,
+                               int64_t ldb, int64_t ldc, gemm_mode mode, gemm_select sel,
+                               gemm_plan_t* out);
 
 /* Direct 3x3 convolution, stride 1, zero padding 1 (the paper benchmarks
  * convolutions, Section VI), as an implicit gemm: the patch matrix of the

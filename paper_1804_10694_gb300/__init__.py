@@ -76,6 +76,12 @@ def gemm_f32_ex(M, N, K, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, mode, 
                              _mode(mode), _select(select), stream))
 
 
+def gemm_f32_t(trans_a, trans_b, M, N, K, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, mode,
+               select, stream):
+    check(load().gemm_f32_t(int(trans_a), int(trans_b), M, N, K, alpha, A_ptr, lda, B_ptr, ldb, beta,
+                            C_ptr, ldc, _mode(mode), _select(select), stream))
+
+
 def gemm_host(A, B, C, alpha: float = 1.0, beta: float = 0.0, mode="auto", stream=None):
     """gemm_f32_host on numpy float32 arrays or pinned CPU torch tensors (C
     updated in place).  The copies to and from the device happen inside the
@@ -107,15 +113,21 @@ class Plan:
     """A gemm plan for one shape (owns its workspace); see gemm_plan_create."""
 
     def __init__(self, M, N, K, lda=None, ldb=None, ldc=None, mode="auto", select="default",
-                 config_id: int | None = None):
+                 config_id: int | None = None, trans_a: bool = False, trans_b: bool = False):
         lib = load()
         self._lib = lib
         self.M, self.N, self.K = M, N, K
-        self.lda = lda if lda is not None else max(K, 1)
-        self.ldb = ldb if ldb is not None else max(N, 1)
+        self.trans_a, self.trans_b = bool(trans_a), bool(trans_b)
+        self.lda = lda if lda is not None else max(M if trans_a else K, 1)
+        self.ldb = ldb if ldb is not None else max(K if trans_b else N, 1)
         self.ldc = ldc if ldc is not None else max(N, 1)
         h = ctypes.c_void_p()
-        if config_id is None:
+        if trans_a or trans_b:
+            if config_id is not None:
+                raise ValueError("transposed plans choose their configuration by `select`")
+            check(lib.gemm_plan_create_t(int(trans_a), int(trans_b), M, N, K, self.lda, self.ldb,
+                                         self.ldc, _mode(mode), _select(select), ctypes.byref(h)))
+        elif config_id is None:
             check(lib.gemm_plan_create(M, N, K, self.lda, self.ldb, self.ldc, _mode(mode),
                                        _select(select), ctypes.byref(h)))
         else:
@@ -124,10 +136,14 @@ class Plan:
         self._h = h
 
     def execute(self, A, B, C, alpha: float = 1.0, beta: float = 0.0, stream=None):
-        pa, M, K, lda = _matrix(A, "A")
-        pb, _, N, ldb = _matrix(B, "B")
-        pc, _, _, ldc = _matrix(C, "C")
-        if (M, N, K) != (self.M, self.N, self.K) or (lda, ldb, ldc) != (self.lda, self.ldb, self.ldc):
+        """A, B as stored (K x M for a transposed A, N x K for a transposed B)."""
+        pa, ra, ca, lda = _matrix(A, "A")
+        pb, rb, cb, ldb = _matrix(B, "B")
+        pc, M, N, ldc = _matrix(C, "C")
+        K = ra if self.trans_a else ca
+        ok = (ca, ra) == (M, K) if self.trans_a else (ra, ca) == (M, K)
+        ok = ok and ((rb, cb) == (N, K) if self.trans_b else (rb, cb) == (K, N))
+        if not ok or (M, N, K) != (self.M, self.N, self.K) or (lda, ldb, ldc) != (self.lda, self.ldb, self.ldc):
             raise ValueError("tensors do not match the plan's shape / leading dimensions")
         check(self._lib.gemm_plan_execute(self._h, alpha, pa, pb, beta, pc, _stream_handle(stream)))
         return C

@@ -37,6 +37,8 @@ SIGNATURES = {
     "gemm_plan_create": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
     "gemm_plan_create_config": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
     "gemm_conv3x3_plan_create": (i32, [i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
+    "gemm_plan_create_t": (i32, [i32, i32, i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
+    "gemm_f32_t": (i32, [i32, i32, i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, i32, vp]),
     "gemm_plan_execute": (i32, [vp, f32, vp, vp, f32, vp, vp]),
     "gemm_plan_info": (i32, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_size_t)]),
     "gemm_plan_destroy": (i32, [vp]),

@@ -89,16 +89,17 @@ cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t l
 // one counter per block (items done); both must be zero on entry.  The CTA
 // that completes a block re-splits it with its exponent when the block lies
 // outside the safe range.
+// transA: A is stored K x M (lda >= M); transB: B is stored N x K (ldb >= K).
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
                         int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA,
                         unsigned* cntB, void* planesA, void* planesB, int64_t pitch, int sms,
-                        cudaStream_t s);
+                        cudaStream_t s, bool transA = false, bool transB = false);
 // Fused-split preparation, one launch: A's block maxima only (no planes:
 // the gemm kernel splits A itself) and B packed as by pack_launch.
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
                               unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
-                              cudaStream_t s, int64_t K_b = -1);
+                              cudaStream_t s, int64_t K_b = -1, bool transB = false);
 // A row panel of A (rows rows, starting at a 128-row block) packed into the
 // planes of the whole matrix at planesA (already offset to the panel's
 // first row; plane_stride = elements from the hi plane to the lo plane).

@@ -260,6 +260,21 @@ static gemm_status encode_im2col_3x3(CUtensorMap* map, const float* X, int64_t b
   return GEMM_OK;
 }
 
+gemm_status validate_shape_t(bool transA, bool transB, int64_t M, int64_t N, int64_t K, int64_t lda,
+                             int64_t ldb, int64_t ldc) {
+  if (M < 0 || N < 0 || K < 0) return fail(GEMM_ERR_INVALID_ARG, "negative size M=%lld N=%lld K=%lld",
+                                           (long long)M, (long long)N, (long long)K);
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX)
+    return fail(GEMM_ERR_INVALID_ARG, "size above 2^31-1");
+  const int64_t row_a = transA ? M : K, row_b = transB ? K : N;
+  if (lda < std::max<int64_t>(row_a, 1))
+    return fail(GEMM_ERR_INVALID_ARG, "lda=%lld < max(%s,1)", (long long)lda, transA ? "M" : "K");
+  if (ldb < std::max<int64_t>(row_b, 1))
+    return fail(GEMM_ERR_INVALID_ARG, "ldb=%lld < max(%s,1)", (long long)ldb, transB ? "K" : "N");
+  if (ldc < std::max<int64_t>(N, 1)) return fail(GEMM_ERR_INVALID_ARG, "ldc=%lld < max(N,1)", (long long)ldc);
+  return GEMM_OK;
+}
+
 gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc) {
   if (M < 0 || N < 0 || K < 0) return fail(GEMM_ERR_INVALID_ARG, "negative size M=%lld N=%lld K=%lld",
                                            (long long)M, (long long)N, (long long)K);
@@ -284,11 +299,14 @@ static gemm_status resolve_mode(gemm_mode mode, const DeviceState& d, gemm_mode*
 }
 
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
-                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out) {
+                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
+                             bool transA, bool transB) {
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
   *out = nullptr;
-  gemm_status st = validate_shape(M, N, K, lda, ldb, ldc);
+  gemm_status st = validate_shape_t(transA, transB, M, N, K, lda, ldb, ldc);
   if (st != GEMM_OK) return st;
+  if ((transA || transB) && mode == GEMM_MODE_F32_SIMT)
+    return fail(GEMM_ERR_INVALID_ARG, "transposed operands need a tensor-core mode");
   DeviceState* dev;
   int devidx;
   if ((st = device_state(&dev, &devidx)) != GEMM_OK) return st;
@@ -297,6 +315,7 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
 
   std::unique_ptr<gemm_plan_s, void (*)(gemm_plan_t)> p(new gemm_plan_s(), plan_destroy_impl);
   p->M = M, p->N = N, p->K = K, p->lda = lda, p->ldb = ldb, p->ldc = ldc;
+  p->transA = transA, p->transB = transB;
   p->mode = m;
   p->device = devidx;
   p->sms = dev->sms;
@@ -313,6 +332,11 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   }
   if (!config_get(config_id, &p->cfg))
     return fail(GEMM_ERR_INVALID_ARG, "configuration id %d out of range", config_id);
+  if (transA && p->cfg.fused) {
+    // the fused kernel stages rows of A: a transposed A runs as the packed twin
+    config_id = find_config(p->cfg.block_n, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
+    config_get(config_id, &p->cfg);
+  }
   p->config_id = config_id;
 
   const Prec pr = p->prec;
@@ -426,10 +450,10 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
                           p->planesB, p->pitch, p->sms, s, K);
   } else if (p->launch.fused)
     e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
-                          p->planesB, p->pitch, p->sms, s);
+                          p->planesB, p->pitch, p->sms, s, -1, p->transB);
   else
     e = pack_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntA, p->cntB,
-                    p->planesA, p->planesB, p->pitch, p->sms, s);
+                    p->planesA, p->planesB, p->pitch, p->sms, s, p->transA, p->transB);
   if (e != cudaSuccess) return cuda_fail(e, "pack launch");
   TcArgs a = p->args;
   a.alpha = alpha;
@@ -482,11 +506,11 @@ void plan_destroy_impl(gemm_plan_t p) {
 struct CacheKey {
   int dev;
   int64_t M, N, K, lda, ldb, ldc;
-  int mode, sel;
+  int mode, sel, trans;
   uintptr_t stream;
   bool operator<(const CacheKey& o) const {
-    return std::tie(dev, M, N, K, lda, ldb, ldc, mode, sel, stream) <
-           std::tie(o.dev, o.M, o.N, o.K, o.lda, o.ldb, o.ldc, o.mode, o.sel, o.stream);
+    return std::tie(dev, M, N, K, lda, ldb, ldc, mode, sel, trans, stream) <
+           std::tie(o.dev, o.M, o.N, o.K, o.lda, o.ldb, o.ldc, o.mode, o.sel, o.trans, o.stream);
   }
   bool operator==(const CacheKey& o) const { return !(*this < o) && !(o < *this); }
 };
@@ -497,10 +521,12 @@ static std::list<CacheKey> g_lru;
 constexpr size_t kCacheMax = 16;
 
 gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
-                        gemm_mode mode, gemm_select sel, cudaStream_t s, gemm_plan_t* out) {
+                        gemm_mode mode, gemm_select sel, cudaStream_t s, gemm_plan_t* out,
+                        bool transA, bool transB) {
   int dev = 0;
   cudaGetDevice(&dev);
-  CacheKey key{dev, M, N, K, lda, ldb, ldc, (int)mode, (int)sel, reinterpret_cast<uintptr_t>(s)};
+  CacheKey key{dev, M, N, K, lda, ldb, ldc, (int)mode, (int)sel, (transA ? 1 : 0) | (transB ? 2 : 0),
+               reinterpret_cast<uintptr_t>(s)};
   std::lock_guard<std::mutex> lk(g_cache_mutex);
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
@@ -510,7 +536,7 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
     return GEMM_OK;
   }
   gemm_plan_t p = nullptr;
-  gemm_status st = plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, &p);
+  gemm_status st = plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, &p, transA, transB);
   if (st != GEMM_OK) return st;
   if (g_cache.size() >= kCacheMax) {
     const CacheKey victim = g_lru.back();
@@ -704,7 +730,8 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   if ((st = grow(&t_host.B, &t_host.nB, std::max<size_t>(nB, 1))) != GEMM_OK) return st;
   if ((st = grow(&t_host.C, &t_host.nC, nC)) != GEMM_OK) return st;
   gemm_plan_t p = nullptr;
-  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p)) != GEMM_OK) return st;
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p, false, false)) != GEMM_OK)
+    return st;
   if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && !p->launch.fused &&
       host_panels() > 1 &&
       M >= 4 * 128 && page_locked(A) && page_locked(C))
@@ -744,8 +771,30 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
   if (!C || (K > 0 && alpha != 0.0f && (!A || !B))) return fail(GEMM_ERR_INVALID_ARG, "null pointer");
   gemm_plan_t p = nullptr;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p)) != GEMM_OK) return st;
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, false, false)) != GEMM_OK) return st;
   return plan_execute_impl(p, alpha, A, B, beta, C, s);
+}
+
+gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
+                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
+                       int64_t ldc, gemm_mode mode, gemm_select sel, gemm_stream_t stream) {
+  clear_error();
+  gemm_status st = validate_shape_t(transA != 0, transB != 0, M, N, K, lda, ldb, ldc);
+  if (st != GEMM_OK) return st;
+  if (M == 0 || N == 0) return GEMM_OK;
+  if (!C || (K > 0 && alpha != 0.0f && (!A || !B))) return fail(GEMM_ERR_INVALID_ARG, "null pointer");
+  gemm_plan_t p = nullptr;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, transA != 0, transB != 0)) != GEMM_OK)
+    return st;
+  return plan_execute_impl(p, alpha, A, B, beta, C, s);
+}
+
+gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int64_t K, int64_t lda,
+                               int64_t ldb, int64_t ldc, gemm_mode mode, gemm_select sel,
+                               gemm_plan_t* out) {
+  clear_error();
+  return plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, out, transA != 0, transB != 0);
 }
 
 gemm_status gemm_f32(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,

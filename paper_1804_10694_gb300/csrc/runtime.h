@@ -10,6 +10,7 @@
 
 struct gemm_plan_s {
   int64_t M = 0, N = 0, K = 0, lda = 0, ldb = 0, ldc = 0;
+  bool transA = false, transB = false;   // A stored K x M, B stored N x K
   gemm_mode mode = GEMM_MODE_F32_SIMT;
   int config_id = -1;
   gemm_config cfg{};
@@ -43,6 +44,8 @@ namespace gb {
 gemm_status fail(gemm_status st, const char* fmt, ...);
 gemm_status cuda_fail(cudaError_t e, const char* what);
 void clear_error();
+gemm_status validate_shape_t(bool transA, bool transB, int64_t M, int64_t N, int64_t K, int64_t lda,
+                             int64_t ldb, int64_t ldc);
 gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc);
 
 int config_count(gemm_mode mode);
@@ -53,7 +56,8 @@ int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, 
                   int64_t ldc, gemm_select sel, int sms);
 
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
-                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out);
+                             gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
+                             bool transA = false, bool transB = false);
 gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const float* B, float beta,
                               float* C, cudaStream_t s);
 void plan_destroy_impl(gemm_plan_t p);

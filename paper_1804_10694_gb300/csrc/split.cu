@@ -342,74 +342,99 @@ __device__ __forceinline__ void amax_item(const AmaxShape& a, int64_t item) {
 }
 
 // --------------------------------------------------- tile decomposition
-// A in 32-row x 256-column tiles (rows_b/32 x ceil(pitch/256) a block), B in
-// 64-k x 128-column tiles (ceil(pitch/64) a block), numbered so that the
-// items of one block are consecutive.  A CTA processes a contiguous range
-// of items, so it meets a block boundary only every few dozen items and
-// folds maxima and counts once per run of one block.
-struct PackShape {
-  const float* A;
-  const float* B;
-  int64_t M, N, K, lda, ldb, pitch;
-  int64_t planeA, planeB;   // elements from the hi plane to the lo plane
-  bool vecA, vecB;
-  unsigned* amaxA;
-  unsigned* amaxB;
-  unsigned* cntA;           // per block: items done (zero on entry)
-  unsigned* cntB;
-  void* planesA;
-  void* planesB;
+// One operand of the pack: its planes hold `rows` rows (M for A, N for B) of
+// K values.  Stored with K contiguous (rows x K, ld >= K: A, or B given
+// transposed) it is split in 32-row x 256-column tiles (rows_b/32 x
+// ceil(pitch/256) a block of 128 rows); stored K x rows (ld >= rows: B, or A
+// given transposed) in 64-k x 128-column tiles that transpose through shared
+// memory (ceil(pitch/64) a block).  Items are numbered so that the items of
+// one block are consecutive.  A CTA processes a contiguous range of items, so
+// it meets a block boundary only every few dozen items and folds maxima and
+// counts once per run of one block.
+struct OpShape {
+  const float* X;
+  int64_t rows, ld;
+  int64_t plane;            // elements from the hi plane to the lo plane
+  bool vec;                 // 16-byte aligned along the contiguous dimension
+  bool kcontig;             // K contiguous in X (row tiles), else column tiles
+  unsigned* amax;           // per block of 128 rows of the planes
+  unsigned* cnt;            // per block: items done (zero on entry)
+  void* planes;
+};
 
-  __device__ int cols_a() const { return (int)((pitch + 255) / 256); }
-  __device__ int ktiles_b() const { return (int)((pitch + 63) / 64); }
-  __device__ int first_items_a() const { return (int)(((M + 31) / 32) * cols_a()); }
-  __device__ int first_items_b() const { return (int)(((N + 127) / 128) * ktiles_b()); }
-  __device__ int items() const { return first_items_a() + first_items_b(); }
-  // block of item i: A blocks 0.., then B blocks as -1 - b
+struct PackShape {
+  OpShape op[2];            // A, B
+  int64_t K, pitch;
+
+  __device__ int ktiles(const OpShape& o) const {
+    return o.kcontig ? (int)((pitch + 255) / 256) : (int)((pitch + 63) / 64);
+  }
+  __device__ int items_of(const OpShape& o) const {
+    if (!o.X || o.rows <= 0) return 0;
+    return (int)((o.kcontig ? (o.rows + 31) / 32 : (o.rows + 127) / 128) * ktiles(o));
+  }
+  __device__ int items() const { return items_of(op[0]) + items_of(op[1]); }
+  __device__ int64_t block_in(const OpShape& o, int l) const {
+    return o.kcontig ? (int64_t)(l / ktiles(o)) / 4 : (int64_t)(l / ktiles(o));
+  }
+  // block of item i: A's blocks 0.., then B's blocks as -1 - b (operands are
+  // selected by branches, never by a runtime index into op[])
   __device__ int64_t block_of(int i) const {
-    const int na = first_items_a();
-    return i < na ? (int64_t)(i / cols_a()) / 4 : -1 - (int64_t)((i - na) / ktiles_b());
+    const int na = items_of(op[0]);
+    return i < na ? block_in(op[0], i) : -1 - block_in(op[1], i - na);
   }
 };
 
-// Split item i (unscaled); returns this thread's max |x|.
+// Split item l of operand o (unscaled); returns this thread's max |x|.
+template <bool TF32>
+__device__ __forceinline__ unsigned op_item(const PackShape& p, const OpShape& o, int l, float* tile) {
+  const int kt = p.ktiles(o);
+  if (o.kcontig)
+    return split_rows_tile<TF32, kFirst>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+                                         (int64_t)(l / kt) * 32, (int64_t)(l % kt) * 256);
+  return split_cols_tile<TF32, kFirst>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+                                       (int64_t)(l / kt) * 128, (int64_t)(l % kt) * 64, tile);
+}
+
 template <bool TF32>
 __device__ __forceinline__ unsigned first_item(const PackShape& p, int i, float* tile) {
-  const int na = p.first_items_a();
-  if (i < na) {
-    const int cols = p.cols_a();
-    return split_rows_tile<TF32, kFirst>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA,
-                                         p.pitch, (int64_t)(i / cols) * 32, (int64_t)(i % cols) * 256);
-  }
-  const int l = i - na, kt = p.ktiles_b();
-  return split_cols_tile<TF32, kFirst>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB,
-                                       p.pitch, (int64_t)(l / kt) * 128, (int64_t)(l % kt) * 64, tile);
+  const int na = p.items_of(p.op[0]);
+  return i < na ? op_item<TF32>(p, p.op[0], i, tile) : op_item<TF32>(p, p.op[1], i - na, tile);
 }
 
 // Close a run of `run` items of block `blk` (encoded as in block_of); the
 // CTA that completes an out-of-range block re-splits it with its exponent.
 template <bool TF32>
-__device__ __forceinline__ void finish_block(const PackShape& p, int64_t blk, unsigned m, unsigned run,
-                                             float* tile) {
-  if (blk >= 0) {
-    const int64_t rows_b = min(static_cast<int64_t>(kScaleBlock), p.M - blk * kScaleBlock);
-    const unsigned items = (unsigned)(((rows_b + 31) / 32) * p.cols_a());
-    const unsigned fin = finish_run(m, p.amaxA + blk, p.cntA + blk, run, items);
+__device__ __forceinline__ void finish_op_block(const PackShape& p, const OpShape& o, int64_t b, unsigned m,
+                                                unsigned run, float* tile) {
+  const int kt = p.ktiles(o);
+  if (o.kcontig) {
+    const int64_t rows_b = min(static_cast<int64_t>(kScaleBlock), o.rows - b * kScaleBlock);
+    const unsigned items = (unsigned)(((rows_b + 31) / 32) * kt);
+    const unsigned fin = finish_run(m, o.amax + b, o.cnt + b, run, items);
     if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
-        for (int64_t q = blk * kScaleBlock; q < blk * kScaleBlock + rows_b; q += 32)
-          split_rows_tile<TF32, kRescale>(p.A, p.M, p.K, p.lda, p.vecA, p.amaxA, p.planesA, p.planeA,
+        for (int64_t q = b * kScaleBlock; q < b * kScaleBlock + rows_b; q += 32)
+          split_rows_tile<TF32, kRescale>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane,
                                           p.pitch, q, k0);
     }
   } else {
-    const int64_t b = -1 - blk;
-    const unsigned fin = finish_run(m, p.amaxB + b, p.cntB + b, run, (unsigned)p.ktiles_b());
+    const unsigned fin = finish_run(m, o.amax + b, o.cnt + b, run, (unsigned)kt);
     if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-        split_cols_tile<TF32, kRescale>(p.B, p.K, p.N, p.ldb, p.vecB, p.amaxB, p.planesB, p.planeB,
-                                        p.pitch, b * 128, k0, tile);
+        split_cols_tile<TF32, kRescale>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+                                        b * 128, k0, tile);
     }
   }
+}
+
+template <bool TF32>
+__device__ __forceinline__ void finish_block(const PackShape& p, int64_t blk, unsigned m, unsigned run,
+                                             float* tile) {
+  if (blk >= 0)
+    finish_op_block<TF32>(p, p.op[0], blk, m, run, tile);
+  else
+    finish_op_block<TF32>(p, p.op[1], -1 - blk, m, run, tile);
 }
 
 // Items [i0, i1) of one problem, in runs of one block each.
@@ -480,14 +505,15 @@ __device__ __forceinline__ const int* stage_prefix(const int* __restrict__ prefi
 
 __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, const GroupedPtrs& q) {
   PackShape p;
-  p.A = q.A, p.B = q.B;
-  p.M = g.M, p.N = g.N, p.K = g.K, p.lda = g.lda, p.ldb = g.ldb, p.pitch = g.pitch;
-  p.planeA = static_cast<int64_t>(g.M) * g.pitch;
-  p.planeB = static_cast<int64_t>(g.N) * g.pitch;
-  p.vecA = (reinterpret_cast<uintptr_t>(q.A) % 16 == 0) && (g.lda % 4 == 0);
-  p.vecB = (reinterpret_cast<uintptr_t>(q.B) % 16 == 0) && (g.ldb % 4 == 0);
-  p.amaxA = g.amaxA, p.amaxB = g.amaxB, p.cntA = g.cntA, p.cntB = g.cntB;
-  p.planesA = g.planesA, p.planesB = g.planesB;
+  p.K = g.K, p.pitch = g.pitch;
+  OpShape& a = p.op[0];
+  a.X = q.A, a.rows = g.M, a.ld = g.lda, a.plane = static_cast<int64_t>(g.M) * g.pitch;
+  a.vec = (reinterpret_cast<uintptr_t>(q.A) % 16 == 0) && (g.lda % 4 == 0);
+  a.kcontig = true, a.amax = g.amaxA, a.cnt = g.cntA, a.planes = g.planesA;
+  OpShape& b = p.op[1];
+  b.X = q.B, b.rows = g.N, b.ld = g.ldb, b.plane = static_cast<int64_t>(g.N) * g.pitch;
+  b.vec = (reinterpret_cast<uintptr_t>(q.B) % 16 == 0) && (g.ldb % 4 == 0);
+  b.kcontig = false, b.amax = g.amaxB, b.cnt = g.cntB, b.planes = g.planesB;
   return p;
 }
 
@@ -518,23 +544,28 @@ int grid_for(int64_t items, int sms) {
   return static_cast<int>(items < cap ? (items > 0 ? items : 1) : cap);
 }
 
-PackShape make_shape(const float* A, int64_t M, int64_t K, int64_t lda, const float* B, int64_t N,
-                     int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA, unsigned* cntB,
-                     void* planesA, void* planesB, int64_t plane_a, int64_t pitch) {
+OpShape make_op(const float* X, int64_t rows, int64_t ld, bool kcontig, unsigned* amax, unsigned* cnt,
+                void* planes, int64_t plane) {
+  OpShape o;
+  o.X = X, o.rows = X ? rows : 0, o.ld = ld, o.plane = plane;
+  o.vec = X && ld % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0;
+  o.kcontig = kcontig, o.amax = amax, o.cnt = cnt, o.planes = planes;
+  return o;
+}
+
+PackShape make_shape(const OpShape& a, const OpShape& b, int64_t K, int64_t pitch) {
   PackShape p;
-  p.A = A, p.B = B, p.M = A ? M : 0, p.N = B ? N : 0, p.K = K, p.lda = lda, p.ldb = ldb;
-  p.pitch = pitch;
-  p.planeA = plane_a;
-  p.planeB = p.N * pitch;
-  p.vecA = A && lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0;
-  p.vecB = B && ldb % 4 == 0 && reinterpret_cast<uintptr_t>(B) % 16 == 0;
-  p.amaxA = amaxA, p.amaxB = amaxB, p.cntA = cntA, p.cntB = cntB;
-  p.planesA = planesA, p.planesB = planesB;
+  p.op[0] = a, p.op[1] = b, p.K = K, p.pitch = pitch;
   return p;
 }
 
+int64_t host_items(const OpShape& o, int64_t pitch) {
+  if (!o.X || o.rows <= 0) return 0;
+  return o.kcontig ? ((o.rows + 31) / 32) * ((pitch + 255) / 256) : ((o.rows + 127) / 128) * ((pitch + 63) / 64);
+}
+
 cudaError_t launch_first(Prec prec, const PackShape& p, int sms, cudaStream_t s) {
-  const int64_t first = pack_first_items(p.M, p.N, p.pitch);
+  const int64_t first = host_items(p.op[0], p.pitch) + host_items(p.op[1], p.pitch);
   if (first == 0) return cudaSuccess;
   if (prec == Prec::TF32)
     pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
@@ -553,20 +584,21 @@ int pack_first_items(int64_t M, int64_t N, int64_t pitch) {
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
                         int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA,
                         unsigned* cntB, void* planesA, void* planesB, int64_t pitch, int sms,
-                        cudaStream_t s) {
-  const PackShape p = make_shape(A, M, K, lda, B, N, ldb, amaxA, amaxB, cntA, cntB, planesA, planesB,
-                                 (A ? M : 0) * pitch, pitch);
+                        cudaStream_t s, bool transA, bool transB) {
+  const PackShape p = make_shape(make_op(A, M, lda, !transA, amaxA, cntA, planesA, M * pitch),
+                                 make_op(B, N, ldb, transB, amaxB, cntB, planesB, N * pitch), K, pitch);
   return launch_first(prec, p, sms, s);
 }
 
 cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda,
                               const float* B, int64_t N, int64_t ldb, unsigned* amaxA,
                               unsigned* amaxB, unsigned* cntB, void* planesB, int64_t pitch, int sms,
-                              cudaStream_t s, int64_t K_b) {
+                              cudaStream_t s, int64_t K_b, bool transB) {
   // K_b: rows of B when they differ from A's row length (the convolution
   // scans its image as one M = 1 row of all its elements)
-  const PackShape p = make_shape(nullptr, 0, K_b >= 0 ? K_b : K, 1, B, N, ldb, nullptr, amaxB, nullptr,
-                                 cntB, nullptr, planesB, 0, pitch);
+  const PackShape p = make_shape(make_op(nullptr, 0, 1, true, nullptr, nullptr, nullptr, 0),
+                                 make_op(B, N, ldb, transB, amaxB, cntB, planesB, N * pitch),
+                                 K_b >= 0 ? K_b : K, pitch);
   AmaxShape a;
   a.A = A, a.M = M, a.K = K, a.lda = lda, a.amax = amaxA, a.parts = 1;
   const int64_t nblk = (M + 127) / 128;
@@ -583,7 +615,7 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
     na = nblk * ((K + span - 1) / span);
   }
   if (M == 0 || K == 0) na = 0, a.M = 0;
-  const int64_t total = na + pack_first_items(0, p.N, pitch);
+  const int64_t total = na + host_items(p.op[1], pitch);
   if (total == 0) return cudaSuccess;
   const int grid = grid_for(total, sms);
   if (prec == Prec::TF32) {
@@ -601,8 +633,8 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
                                    unsigned* amaxA, unsigned* cntA, void* planesA,
                                    int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s) {
-  const PackShape p = make_shape(A, rows, K, lda, nullptr, 0, 1, amaxA, nullptr, cntA, nullptr, planesA,
-                                 nullptr, plane_stride, pitch);
+  const PackShape p = make_shape(make_op(A, rows, lda, true, amaxA, cntA, planesA, plane_stride),
+                                 make_op(nullptr, 0, 1, false, nullptr, nullptr, nullptr, 0), K, pitch);
   return launch_first(prec, p, sms, s);
 }
 

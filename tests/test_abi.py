@@ -94,3 +94,13 @@ def test_conv3x3_plan_argument_validation():
     assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 1, -1, ctypes.byref(h)) == 1
     packed = next(i for i in range(pkg.config_count("bf16x3")) if not pkg.config_get("bf16x3", i)["fused"])
     assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 2, packed, ctypes.byref(h)) == 1
+
+
+def test_transposed_arguments_validated_before_launch():
+    import ctypes
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    # transA: lda must cover M; transB: ldb must cover K; SIMT has no transposed path
+    assert lib.gemm_plan_create_t(1, 0, 100, 50, 40, 99, 50, 50, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create_t(0, 1, 100, 50, 40, 40, 39, 50, 2, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 100, 40, 50, 1, 0, ctypes.byref(h)) == 1
