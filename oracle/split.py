@@ -19,6 +19,9 @@ where the paper is silent (it does not describe this method at all):
 * hi = RN(x'), lo = RN(x' - hi) with RN round-to-nearest-even to bf16 (8-bit
   significand) or tf32 (11-bit significand); x' - hi is an FP32 subtraction.
   A non-finite x' gives hi = x', lo = 0.
+* The BF16x6 mode splits in three: hi, mid = RN(x' - hi), lo =
+  RN((x' - hi) - mid); hi + mid + lo = x' exactly for normal x' (8 + 8 + 8
+  significant bits cover FP32's 24).
 
 All rounding here is written from the IEEE definition on the bit pattern.
 """
@@ -91,15 +94,34 @@ def split_values(xs: np.ndarray, rounder) -> tuple[np.ndarray, np.ndarray]:
     return hi, lo
 
 
+def split3_values(xs: np.ndarray) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Three-way bf16 split of already-scaled FP32 values (the BF16x6 mode):
+    hi = RN(x'), mid = RN(x' - hi), lo = RN((x' - hi) - mid), each
+    difference an FP32 subtraction (exact: the remainders have at most 16 and
+    8 significant bits).  A non-finite x' gives hi = x', mid = lo = 0."""
+    xs = np.asarray(xs, dtype=np.float32)
+    finite = np.isfinite(xs)
+    with np.errstate(invalid="ignore", over="ignore"):
+        hi = round_bf16(xs)
+        r1 = np.where(finite, (xs - hi).astype(np.float32), np.float32(0.0)).astype(np.float32)
+        mid = round_bf16(r1)
+        r2 = (r1 - mid).astype(np.float32)
+        lo = round_bf16(r2)
+    hi = np.where(finite, hi, xs).astype(np.float32)
+    return hi, mid, lo
+
+
 def split_rows(X: np.ndarray, rows: int, cols: int, precision: str):
     """Split a row-major matrix whose rows are grouped in blocks of 128 (the A
     operand; B is passed transposed, i.e. as N x K).  Returns (hi, lo, exps)
-    with hi/lo rows x cols FP32 arrays and one exponent per 128-row block."""
-    rounder = round_bf16 if precision == "bf16" else round_tf32
+    with hi/lo rows x cols FP32 arrays and one exponent per 128-row block;
+    for precision "bf16x6", (hi, mid, lo, exps)."""
+    rounder = round_bf16 if precision in ("bf16", "bf16x6") else round_tf32
     X = np.asarray(X, dtype=np.float32)[:rows, :cols]
     nblk = (rows + BLOCK - 1) // BLOCK
     hi = np.zeros((rows, cols), np.float32)
     lo = np.zeros((rows, cols), np.float32)
+    lo2 = np.zeros((rows, cols), np.float32)
     exps = np.zeros(nblk, np.int32)
     for b in range(nblk):
         blk = X[b * BLOCK:(b + 1) * BLOCK]
@@ -110,7 +132,13 @@ def split_rows(X: np.ndarray, rows: int, cols: int, precision: str):
         exps[b] = e
         with np.errstate(over="ignore", invalid="ignore"):
             scaled = (blk * pow2(-e)).astype(np.float32)
-        h, l = split_values(scaled, rounder)
+        if precision == "bf16x6":
+            h, l, l2 = split3_values(scaled)
+            lo2[b * BLOCK:(b + 1) * BLOCK] = l2
+        else:
+            h, l = split_values(scaled, rounder)
         hi[b * BLOCK:(b + 1) * BLOCK] = h
         lo[b * BLOCK:(b + 1) * BLOCK] = l
+    if precision == "bf16x6":
+        return hi, lo, lo2, exps        # hi, mid, lo
     return hi, lo, exps

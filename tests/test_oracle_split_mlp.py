@@ -205,3 +205,28 @@ def test_adam_first_step_closed_form():
     # second step with the same gradient: m_hat = g, v_hat = g^2 again
     th2, _, _ = mlp.adam_step(th1, g, m, v, 2, lr=0.01)
     assert np.allclose(th2, th1 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-12)
+
+
+def test_split3_is_exact_and_extends_the_two_way_split():
+    """BF16x6 split: three bf16 parts summing exactly to x' (normal values),
+    each part at most half an ulp of the part before, and the first two
+    parts are the two-way split."""
+    from oracle import split
+    import workloads as W
+    x = np.concatenate([W.uniform(64, 64, 11).ravel(), W.wide_range(64, 64, 12, lo=-60, hi=60).ravel(),
+                        np.array([1.0, -1.0, 3.0, 1.0 + 2 ** -23, 65504.0, 2 ** -100], np.float32)])
+    hi, mid, lo = split.split3_values(x)
+    for part in (hi, mid, lo):
+        assert not (part.view(np.uint32) & 0xFFFF).any()          # representable in bf16
+    assert np.array_equal(hi.astype(np.float64) + mid.astype(np.float64) + lo.astype(np.float64),
+                          x.astype(np.float64))
+    def ulp_bf16(v):
+        e = np.floor(np.log2(np.abs(v.astype(np.float64)), where=v != 0, out=np.zeros(v.shape)))
+        return np.where(v != 0, np.ldexp(1.0, (e - 7).astype(int)), 0.0)
+    assert (np.abs(mid) <= ulp_bf16(hi) / 2).all()
+    assert (np.abs(lo) <= ulp_bf16(mid) / 2 + (mid == 0)).all()
+    h2, l2 = split.split_values(x, split.round_bf16)
+    assert np.array_equal(h2, hi) and np.array_equal(l2, mid)
+    # non-finite: hi carries it, the rest is zero
+    h, m, l = split.split3_values(np.array([np.inf, -np.inf, np.nan], np.float32))
+    assert np.isinf(h[:2]).all() and np.isnan(h[2]) and not m.any() and not l.any()
