@@ -14,5 +14,5 @@ Modules:
   mlp    -- the cost model's MLP: forward, MSE loss, analytic backward, Adam.
   conv   -- direct 3x3 convolution (stride 1, zero padding 1), FP64 and exact.
 """
-from .gemm import (build, gemm_f64, gemm_f64_rows, rel_frob, gemm_exact,  # noqa: F401
+from .gemm import (build, gemm_f64, gemm_f64_rows, gemm_f32_seq, rel_frob, gemm_exact,  # noqa: F401
                    library_path, num_threads)

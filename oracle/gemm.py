@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-ffp-contract=off",
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -53,6 +53,9 @@ def _load():
             lib.oracle_gemm_f64_rows.argtypes = [i64, i64, f32, vp, i64, vp, i64,
                                                  f32, vp, i64, vp, i64, vp]
             lib.oracle_gemm_f64_rows.restype = None
+            lib.oracle_gemm_f32_seq.argtypes = [i64, i64, i64, f32, vp, i64, vp, i64,
+                                                f32, vp, i64, vp, i64]
+            lib.oracle_gemm_f32_seq.restype = None
             lib.oracle_rel_frob.argtypes = [i64, i64, vp, i64, vp, i64]
             lib.oracle_rel_frob.restype = ctypes.c_double
             lib.oracle_num_threads.argtypes = []
@@ -113,6 +116,30 @@ def gemm_f64_rows(rows, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndarr
     lib.oracle_gemm_f64_rows(N, K, ctypes.c_float(alpha), _ptr(A), A.shape[1], _ptr(B),
                              B.shape[1], ctypes.c_float(beta), _ptr(C0), ldc,
                              _ptr(rows), len(rows), _ptr(out))
+    return out
+
+
+def gemm_f32_seq(M: int, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndarray,
+                 beta: float, C0: np.ndarray | None) -> np.ndarray:
+    """The definition evaluated in FP32 (k in increasing order, every product
+    and sum rounded to FP32): the accuracy of a plain single-precision gemm,
+    the yardstick of the six-product mode.  M x N float32."""
+    lib = _load()
+    A = _f32(A) if K > 0 and M > 0 else None
+    B = _f32(B) if K > 0 and N > 0 else None
+    ldc = 1
+    if beta != 0.0:
+        C0 = _f32(C0)
+        ldc = C0.shape[1]
+    else:
+        C0 = None
+    out = np.empty((M, N), dtype=np.float32)
+    if M == 0 or N == 0:
+        return out
+    lda = A.shape[1] if A is not None else max(K, 1)
+    ldb = B.shape[1] if B is not None else max(N, 1)
+    lib.oracle_gemm_f32_seq(M, N, K, ctypes.c_float(alpha), _ptr(A), lda, _ptr(B), ldb,
+                            ctypes.c_float(beta), _ptr(C0), ldc, _ptr(out), N)
     return out
 
 

@@ -66,6 +66,39 @@ void oracle_gemm_f64_rows(int64_t N, int64_t K, float alpha,
         oracle_row(rows[r], N, K, da, A, lda, B, ldb, db, C0, ldc, out + r * N);
 }
 
+/* The same definition evaluated in FP32 arithmetic, the accuracy of a plain
+ * single-precision gemm: for each element, acc = 0 and, k in increasing
+ * order, acc = fl(acc + fl(a_ik * b_kj)) (every operation rounded to nearest
+ * FP32, no fused multiply-add: the file is compiled with -ffp-contract=off);
+ * then out = fl(fl(alpha * acc) + fl(beta * c0)), or fl(alpha * acc) when
+ * beta == 0.  Its error against the FP64 result is bounded by the classical
+ * recursive-summation bound gamma_(K+2) * (|alpha| sum_k |a||b| + |beta c0|),
+ * gamma_n = n u / (1 - n u), u = 2^-24.  out is M x N float (ldo). */
+void oracle_gemm_f32_seq(int64_t M, int64_t N, int64_t K, float alpha,
+                         const float* A, int64_t lda, const float* B, int64_t ldb,
+                         float beta, const float* C0, int64_t ldc,
+                         float* out, int64_t ldo)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < M; ++i) {
+        for (int64_t j = 0; j < N; ++j) {
+            float acc = 0.0f;
+            if (alpha != 0.0f) {
+                for (int64_t k = 0; k < K; ++k) {
+                    const float p = A[i * lda + k] * B[k * ldb + j];
+                    acc = acc + p;
+                }
+            }
+            float v = (alpha != 0.0f) ? alpha * acc : 0.0f;
+            if (beta != 0.0f) {
+                const float c = beta * C0[i * ldc + j];
+                v = v + c;
+            }
+            out[i * ldo + j] = v;
+        }
+    }
+}
+
 /* Relative Frobenius error ||got - ref||_F / ||ref||_F, in double.  When the
  * reference is all zero the absolute Frobenius norm of the difference is
  * returned instead.  got is M x N float (ldg), ref M x N double (ldr). */

@@ -166,3 +166,59 @@ def test_golden_worked_example():
     expect = np.array([[float(Fraction(x)) for x in r.split()] for r in vals["C"].split(";")])
     out = oracle.gemm_f64(2, 2, 3, alpha, A, B, beta, C0)
     assert np.array_equal(out, expect)
+
+
+# ------------------------------------------- FP32 evaluation of the definition
+def _gamma(n: int) -> float:
+    u = 2.0 ** -24
+    return n * u / (1.0 - n * u)
+
+
+@pytest.mark.parametrize("gen", ["uniform", "wide"])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (1.5, -0.75), (-2.0, 1.0)])
+def test_f32_seq_within_recursive_summation_bound(gen, alpha, beta):
+    """Every element obeys the classical bound of recursive summation with
+    rounded products, |fl(s) - s| <= gamma_(K+2) (|alpha| sum|a||b| + |beta c|)."""
+    M, N, K = 37, 29, 301
+    f = W.uniform if gen == "uniform" else (lambda r, c, s: W.wide_range(r, c, s, lo=-20, hi=20))
+    A, B, C0 = f(M, K, 31), f(K, N, 32), f(M, N, 33)
+    got = oracle.gemm_f32_seq(M, N, K, alpha, A, B, beta, C0).astype(np.float64)
+    ref = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
+    mag = abs(alpha) * (np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64)))
+    if beta != 0.0:
+        mag += abs(beta) * np.abs(C0.astype(np.float64))
+    assert (np.abs(got - ref) <= _gamma(K + 2) * mag).all()
+
+
+def test_f32_seq_rounds_every_step_in_single_precision():
+    """Not a double computation rounded once: most results differ from the
+    correctly rounded FP64 value, and the error is of the order u sqrt(K)."""
+    M, N, K = 40, 40, 2000
+    A, B = W.uniform(M, K, 41), W.uniform(K, N, 42)
+    got = oracle.gemm_f32_seq(M, N, K, 1.0, A, B, 0.0, None)
+    ref = oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)
+    assert np.mean(got != ref.astype(np.float32)) > 0.5
+    err = oracle.rel_frob(got, ref)
+    assert 2.0 ** -24 < err < 2.0 ** -24 * 8 * np.sqrt(K)
+
+
+def test_f32_seq_sums_in_increasing_k():
+    """2^24 + 1 rounds back to 2^24 (ties to even) before -2^24 cancels it, so
+    the increasing-k sum of [2^24, 1, -2^24] is 0 where the exact value is 1;
+    in the other order the sum would be exact."""
+    A = np.array([[2.0 ** 24, 1.0, -(2.0 ** 24)]], np.float32)
+    B = np.ones((3, 1), np.float32)
+    assert oracle.gemm_f32_seq(1, 1, 3, 1.0, A, B, 0.0, None)[0, 0] == 0.0
+    assert oracle.gemm_f32_seq(1, 1, 3, 1.0, A[:, ::-1].copy(), B, 0.0, None)[0, 0] == 1.0
+    assert oracle.gemm_f64(1, 1, 3, 1.0, A, B, 0.0, None)[0, 0] == 1.0
+
+
+def test_f32_seq_exact_on_integers_and_blas_cases():
+    M, N, K = 30, 20, 50
+    A, B, C0 = W.integers(M, K, 1), W.integers(K, N, 2), W.integers(M, N, 3)
+    got = oracle.gemm_f32_seq(M, N, K, 2.0, A, B, -1.0, C0)
+    assert np.array_equal(got, oracle.gemm_f64(M, N, K, 2.0, A, B, -1.0, C0).astype(np.float32))
+    Cnan = np.full((M, N), np.nan, np.float32)
+    assert np.isfinite(oracle.gemm_f32_seq(M, N, K, 1.0, A, B, 0.0, Cnan)).all()
+    Anan = np.full((M, K), np.nan, np.float32)
+    assert np.array_equal(oracle.gemm_f32_seq(M, N, K, 0.0, Anan, B, 0.5, C0), C0 * np.float32(0.5))
