@@ -8,7 +8,9 @@
  * example and benchmarks as sgemm (Section I; Section VI-A).  The tensor-core
  * modes compute each product as three split-precision tensor-core products
  * (bf16 or tf32 hi/lo parts, FP32 accumulation, per-block power-of-two
- * scaling); the SIMT mode is a plain FP32 CUDA-core kernel.
+ * scaling), or, in BF16X6, as six bf16 products of a three-way split (hi,
+ * mid, lo: hi*hi + hi*mid + mid*hi + hi*lo + mid*mid + lo*hi); the SIMT mode
+ * is a plain FP32 CUDA-core kernel.
  *
  * Conventions for every call below:
  *   - Layout: row-major.  A is M x K with lda >= K, B is K x N with ldb >= N,
@@ -60,7 +62,10 @@ typedef enum {
   GEMM_MODE_AUTO = 0,     /* BF16X3 on sm_103, else error */
   GEMM_MODE_F32_SIMT = 1, /* plain FP32 CUDA-core kernel (reference form) */
   GEMM_MODE_BF16X3 = 2,   /* split-precision bf16 x3 tensor-core kernel */
-  GEMM_MODE_TF32X3 = 3    /* split-precision tf32 x3 tensor-core kernel */
+  GEMM_MODE_TF32X3 = 3,   /* split-precision tf32 x3 tensor-core kernel */
+  GEMM_MODE_BF16X6 = 4    /* three-way bf16 split, six tensor-core products: the
+                           * error of an FP32 dot product at about twice the
+                           * tensor work of BF16X3; packed operands only */
 } gemm_mode;
 
 typedef enum {
@@ -85,6 +90,8 @@ typedef struct {
   int fused;       /* 1: A is split inside the gemm kernel (no packed copy of A);
                     *    0: A is packed into hi/lo planes by a separate pass */
 } gemm_config;
+/* BF16X3 and TF32X3 share one table of 144 entries (ids 72..143 are the
+ * fused twins of ids 0..71); BF16X6 has ids 0..71, each with stages = 2. */
 
 /* ---------------------------------------------------------------- gemm -- */
 
@@ -257,7 +264,10 @@ int gemm_costmodel_feature_count(void);
  * to out[gemm_costmodel_feature_count()]: log2 M, N, K; tile width / 128;
  * log2 split-K; fold length / 8; log2 raster group; log2 tiles; log2(1 +
  * waves); fill of the last wave; padded-work fraction; log2 arithmetic
- * intensity; log2 k-chunks per split; 1 for TF32X3. */
+ * intensity; log2 k-chunks per split; 1 for TF32X3; 1 for a fused
+ * configuration.  BF16X6 is described by the features of BF16X3 (same tiles
+ * and k-chunks): the model is trained on the three-product modes and ranks
+ * the BF16X6 candidates as it ranks their BF16X3 twins. */
 gemm_status gemm_costmodel_features(int64_t M, int64_t N, int64_t K, gemm_mode mode, int config_id,
                                     int sms, float* out);
 
@@ -323,7 +333,8 @@ int gemm_device_sm_count(void);
  * so that it can be checked bit for bit: splits the FP32 matrix X (rows x cols,
  * leading dimension ld, device memory) into hi/lo planes
  * planes[2][rows][pitch] (bf16 for BF16X3, tf32 values in 32-bit containers
- * for TF32X3; pitch = cols rounded up to 8 resp. 4) and writes the per-block
+ * for TF32X3; pitch = cols rounded up to 8 resp. 4; BF16X6 writes three bf16
+ * planes hi, mid, lo, planes[3][rows][pitch]) and writes the per-block
  * max |x| bit patterns to amax[0 .. nblk), nblk = ceil(rows/128); blocks
  * outside the safe range are split with their exponent.  `transpose` != 0
  * treats X as a K x N matrix B and writes planes[2][N][pitch], with

@@ -14,7 +14,7 @@ import ctypes
 from . import _native
 from ._native import GemmConfig, GemmError, check, load  # noqa: F401
 
-MODES = {"auto": 0, "simt": 1, "f32_simt": 1, "bf16x3": 2, "tf32x3": 3}
+MODES = {"auto": 0, "simt": 1, "f32_simt": 1, "bf16x3": 2, "tf32x3": 3, "bf16x6": 4}
 SELECTS = {"default": 0, "model": 1, "table": 2, "exhaustive": 3}
 
 
@@ -210,22 +210,23 @@ def sm_count() -> int:
 
 
 def packed_pitch(mode, K: int) -> int:
-    q = 8 if _mode(mode) == 2 else 4
+    q = 8 if _mode(mode) in (2, 4) else 4
     return (K + q - 1) // q * q
 
 
 def split_pack(X, mode="bf16x3", transpose: bool = False, stream=None):
     """Run the packing stage alone; returns (planes, amax) torch tensors.
-    planes: [2][rows][pitch] (bf16 or float32 holding tf32 values); amax:
-    int32 view of the per-block max |x| bit patterns."""
+    planes: [2][rows][pitch] (bf16 or float32 holding tf32 values; [3][rows]
+    [pitch] bf16 for bf16x6); amax: int32 view of the per-block max |x| bit
+    patterns."""
     import torch
     px, rows, cols, ld = _matrix(X, "X")
     m = _mode(mode)
     K = rows if transpose else cols
     prow = cols if transpose else rows
     pitch = packed_pitch(m, K)
-    dt = torch.bfloat16 if m == 2 else torch.float32
-    planes = torch.zeros((2, prow, pitch), dtype=dt, device=X.device)
+    dt = torch.bfloat16 if m in (2, 4) else torch.float32
+    planes = torch.zeros((3 if m == 4 else 2, prow, pitch), dtype=dt, device=X.device)
     nblk = (prow + 127) // 128
     work = torch.zeros((2 * nblk,), dtype=torch.int32, device=X.device)   # maxima, then counters
     check(load().gemm_split_pack(m, 1 if transpose else 0, rows, cols, px, ld, planes.data_ptr(),

@@ -49,7 +49,7 @@ EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, i
 std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t K) {
   std::vector<int> out;
   std::set<std::tuple<int, int, int, int, int>> seen;
-  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  const Prec p = prec_of_mode(mode);
   gemm_config c;
   for (int id = 0; id < config_count(mode); ++id) {
     config_get(id, &c);
@@ -272,8 +272,7 @@ extern "C" {
 gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps, const char* out_path) {
   clear_error();
   if (G < 0 || (G > 0 && !shapes)) return fail(GEMM_ERR_INVALID_ARG, "bad shape list");
-  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
-    return fail(GEMM_ERR_INVALID_ARG, "autotune needs a tensor-core mode");
+  if (!mode_is_split(mode)) return fail(GEMM_ERR_INVALID_ARG, "autotune needs a tensor-core mode");
   FILE* f = nullptr;
   if (out_path && *out_path) {
     f = std::fopen(out_path, "a");

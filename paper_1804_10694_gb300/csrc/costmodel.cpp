@@ -30,7 +30,7 @@ namespace gb {
 // ------------------------------------------------------------------ features
 void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const gemm_config& c,
                         int sms, float* out) {
-  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  const Prec p = prec_of_mode(mode);
   const EffConfig e = effective_config(c, p, M, N, K);
   const int ck = prec_chunk_elems(p);
   const double chunks = (double)((K + ck - 1) / ck);

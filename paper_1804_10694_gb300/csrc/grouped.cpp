@@ -163,7 +163,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     }
   }
   if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
-  if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
+  if (mode != GEMM_MODE_F32_SIMT && !mode_is_split(mode))
     return fail(GEMM_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -179,7 +179,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
                                                                          grouped_destroy_impl);
   p->G = G;
   p->mode = mode;
-  p->prec = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  p->prec = prec_of_mode(mode);
   p->device = dev;
   p->sms = sms;
   p->M.assign(M, M + G), p->N.assign(N, N + G), p->K.assign(K, K + G);
@@ -227,9 +227,9 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     g.tiles_m = empty ? 0 : (int)((p->M[i] + 127) / 128);
     g.tiles_n = empty ? 0 : (int)((p->N[i] + p->bn - 1) / p->bn);
     offA[slot] = off;
-    off = round256(off + (size_t)2 * std::max<int64_t>(p->M[i], 1) * pitch * es);
+    off = round256(off + (size_t)prec_planes(pr) * std::max<int64_t>(p->M[i], 1) * pitch * es);
     offB[slot] = off;
-    off = round256(off + (size_t)2 * std::max<int64_t>(p->N[i], 1) * pitch * es);
+    off = round256(off + (size_t)prec_planes(pr) * std::max<int64_t>(p->N[i], 1) * pitch * es);
     // per problem: maxima of A's and B's blocks, then one pack counter per block
     amax_off[slot] = amax_count;
     amax_count += 2 * ((size_t)(p->M[i] + kScaleBlock - 1) / kScaleBlock +

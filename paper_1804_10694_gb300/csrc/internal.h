@@ -9,14 +9,19 @@
 namespace gb {
 
 // ---------------------------------------------------------------- precision
-enum class Prec : int { F32 = 0, BF16 = 1, TF32 = 2 };
+// BF16: two bf16 planes (hi, lo), three products; BF16X6: three bf16 planes
+// (hi, mid, lo), six products; TF32: two tf32 planes, three products.
+enum class Prec : int { F32 = 0, BF16 = 1, TF32 = 2, BF16X6 = 3 };
 
-inline int prec_elem_bytes(Prec p) { return p == Prec::BF16 ? 2 : 4; }
+inline bool prec_bf16(Prec p) { return p == Prec::BF16 || p == Prec::BF16X6; }
+inline int prec_elem_bytes(Prec p) { return prec_bf16(p) ? 2 : 4; }
+// Planes each operand is split into.
+inline int prec_planes(Prec p) { return p == Prec::BF16X6 ? 3 : 2; }
 // Elements of one 128-byte k-chunk (one swizzle span) per precision.
-inline int prec_chunk_elems(Prec p) { return p == Prec::BF16 ? 64 : 32; }
+inline int prec_chunk_elems(Prec p) { return prec_bf16(p) ? 64 : 32; }
 // Row pitch of the packed planes: K rounded up so that a row is 16-byte aligned.
 inline int64_t packed_k_pitch(Prec p, int64_t K) {
-  const int64_t q = p == Prec::BF16 ? 8 : 4;
+  const int64_t q = prec_bf16(p) ? 8 : 4;
   return (K + q - 1) / q * q;
 }
 
@@ -51,7 +56,7 @@ struct TcArgs {
 
 struct TcLaunch {
   int bn;          // tile N (64 or 128)
-  Prec prec;       // BF16 or TF32
+  Prec prec;       // BF16, BF16X6 or TF32
   int grid;
   bool fused;      // A split inside the gemm kernel (only B is packed)
 };
@@ -84,7 +89,8 @@ cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t l
 // amaxA; B, transposed: blocks of 128 columns, into amaxB), then a pass that
 // re-splits the blocks needing a power-of-two scale.  The block maxima must
 // be zero on entry.  A (or B) may be null to pack only the other operand.
-// A: M x K (lda) -> planesA [2][M][pitch];  B: K x N (ldb) -> planesB [2][N][pitch].
+// A: M x K (lda) -> planesA [P][M][pitch];  B: K x N (ldb) -> planesB [P][N][pitch],
+// P = prec_planes(prec).
 // Packing (split.cu), one launch.  amax* hold the block maxima and cnt*
 // one counter per block (items done); both must be zero on entry.  The CTA
 // that completes a block re-splits it with its exponent when the block lies
@@ -102,7 +108,7 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
                               cudaStream_t s, int64_t K_b = -1, bool transB = false);
 // A row panel of A (rows rows, starting at a 128-row block) packed into the
 // planes of the whole matrix at planesA (already offset to the panel's
-// first row; plane_stride = elements from the hi plane to the lo plane).
+// first row; plane_stride = elements from one plane to the next).
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,
                                    unsigned* amaxA, unsigned* cntA, void* planesA,
                                    int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s);

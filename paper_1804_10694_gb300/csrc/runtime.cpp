@@ -117,7 +117,9 @@ constexpr int kMaxFoldChunks = 8;
 // Candidates of the tensor-core kernels.  The same table serves BF16X3 and
 // TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way).
 // Ids 0..71 pack both operands; ids 72..143 repeat them with A split inside
-// the gemm kernel.
+// the gemm kernel.  BF16X6 has ids 0..71 only (its kernel reads packed
+// planes of both operands), each with a two-deep ring: a stage holds six
+// planes.
 static const std::vector<gemm_config>& config_table() {
   static const std::vector<gemm_config> table = [] {
     std::vector<gemm_config> t;
@@ -144,6 +146,7 @@ static const std::vector<gemm_config>& config_table() {
 }
 
 int config_count(gemm_mode mode) {
+  if (mode == GEMM_MODE_BF16X6) return (int)config_table().size() / 2;
   return (mode == GEMM_MODE_BF16X3 || mode == GEMM_MODE_TF32X3) ? (int)config_table().size() : 0;
 }
 
@@ -151,6 +154,12 @@ bool config_get(int id, gemm_config* out) {
   const auto& t = config_table();
   if (id < 0 || id >= (int)t.size()) return false;
   *out = t[id];
+  return true;
+}
+
+bool config_get(gemm_mode mode, int id, gemm_config* out) {
+  if (id < 0 || id >= config_count(mode) || !config_get(id, out)) return false;
+  if (mode == GEMM_MODE_BF16X6) out->stages = 2;
   return true;
 }
 
@@ -164,7 +173,7 @@ static int find_config(int bn, int sk, int kb, int g) {
 
 int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
   if (config_count(mode) == 0) return -1;
-  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  const Prec p = prec_of_mode(mode);
   const int bn = N <= 64 ? 64 : 128;
   const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
   const int64_t chunks = (K + prec_chunk_elems(p) - 1) / prec_chunk_elems(p);
@@ -206,12 +215,12 @@ static gemm_status encode_planes(CUtensorMap* map, Prec p, void* base, int64_t r
                                  int64_t pitch, int box_rows, int sw) {
   const int es = prec_elem_bytes(p);
   // the box is one k-chunk wide: sw bytes, the swizzle span of the kernel variant
-  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, 2};
+  cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)prec_planes(p)};
   cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(rows * pitch * es)};
   cuuint32_t box[3] = {(cuuint32_t)(sw / es), (cuuint32_t)box_rows, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUtensorMapDataType dt =
-      p == Prec::BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+      prec_bf16(p) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = g_encode(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         sw == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -288,7 +297,7 @@ gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t
 
 static gemm_status resolve_mode(gemm_mode mode, const DeviceState& d, gemm_mode* out) {
   if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
-  if (mode != GEMM_MODE_F32_SIMT && mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
+  if (mode != GEMM_MODE_F32_SIMT && !mode_is_split(mode))
     return fail(GEMM_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
   if (mode != GEMM_MODE_F32_SIMT && !device_has_tcgen05(d))
     return fail(GEMM_ERR_UNSUPPORTED_DEVICE,
@@ -325,17 +334,17 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
     *out = p.release();
     return GEMM_OK;
   }
-  p->prec = m == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  p->prec = prec_of_mode(m);
   if (config_id < 0) {
     config_id = select_config(m, M, N, K, lda, ldb, ldc, sel, dev->sms);
     if (config_id < 0) return fail(GEMM_ERR_INVALID_ARG, "no configuration for mode");
   }
-  if (!config_get(config_id, &p->cfg))
-    return fail(GEMM_ERR_INVALID_ARG, "configuration id %d out of range", config_id);
+  if (!config_get(m, config_id, &p->cfg))
+    return fail(GEMM_ERR_INVALID_ARG, "configuration id %d out of range for mode %d", config_id, (int)m);
   if (transA && p->cfg.fused) {
     // the fused kernel stages rows of A: a transposed A runs as the packed twin
     config_id = find_config(p->cfg.block_n, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
-    config_get(config_id, &p->cfg);
+    config_get(m, config_id, &p->cfg);
   }
   p->config_id = config_id;
 
@@ -357,8 +366,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
 
   // workspace: A planes (packed variant) | B planes | amax A | amax B | split-K partials
   const bool fused = p->cfg.fused != 0;
-  const size_t bytesA = fused ? 0 : (size_t)2 * M * p->pitch * es;
-  const size_t bytesB = (size_t)2 * N * p->pitch * es;
+  const int np = prec_planes(pr);
+  const size_t bytesA = fused ? 0 : (size_t)np * M * p->pitch * es;
+  const size_t bytesB = (size_t)np * N * p->pitch * es;
   const size_t nblkA = (size_t)(M + kScaleBlock - 1) / kScaleBlock;
   const size_t nblkB = (size_t)(N + kScaleBlock - 1) / kScaleBlock;
   size_t off = 0;
@@ -940,7 +950,7 @@ gemm_status gemm_config_get(gemm_mode mode, int config_id, gemm_config* out) {
   clear_error();
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null output");
   if (config_count(mode) == 0) return fail(GEMM_ERR_INVALID_ARG, "mode has no configurations");
-  if (!config_get(config_id, out)) return fail(GEMM_ERR_INVALID_ARG, "configuration id out of range");
+  if (!config_get(mode, config_id, out)) return fail(GEMM_ERR_INVALID_ARG, "configuration id out of range");
   return GEMM_OK;
 }
 
@@ -980,9 +990,9 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
                             int64_t ld, void* planes, int64_t pitch, unsigned* amax,
                             gemm_stream_t stream) {
   clear_error();
-  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
-    return fail(GEMM_ERR_INVALID_ARG, "split_pack needs BF16X3 or TF32X3");
-  const Prec p = mode == GEMM_MODE_TF32X3 ? Prec::TF32 : Prec::BF16;
+  if (!mode_is_split(mode))
+    return fail(GEMM_ERR_INVALID_ARG, "split_pack needs BF16X3, TF32X3 or BF16X6");
+  const Prec p = prec_of_mode(mode);
   if (rows < 0 || cols < 0 || ld < std::max<int64_t>(cols, 1))
     return fail(GEMM_ERR_INVALID_ARG, "bad split_pack shape");
   if (rows == 0 || cols == 0) return GEMM_OK;

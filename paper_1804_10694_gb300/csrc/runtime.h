@@ -8,6 +8,14 @@
 #include "../../include/gemm.h"
 #include "internal.h"
 
+// Split precision of a tensor-core mode.
+inline gb::Prec prec_of_mode(gemm_mode m) {
+  return m == GEMM_MODE_TF32X3 ? gb::Prec::TF32 : m == GEMM_MODE_BF16X6 ? gb::Prec::BF16X6 : gb::Prec::BF16;
+}
+inline bool mode_is_split(gemm_mode m) {
+  return m == GEMM_MODE_BF16X3 || m == GEMM_MODE_TF32X3 || m == GEMM_MODE_BF16X6;
+}
+
 struct gemm_plan_s {
   int64_t M = 0, N = 0, K = 0, lda = 0, ldb = 0, ldc = 0;
   bool transA = false, transB = false;   // A stored K x M, B stored N x K
@@ -50,6 +58,8 @@ gemm_status validate_shape(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t
 
 int config_count(gemm_mode mode);
 bool config_get(int id, gemm_config* out);
+// The entry as it applies to a mode (false when the id is not one of the mode's).
+bool config_get(gemm_mode mode, int id, gemm_config* out);
 int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms);
 // Configuration for a new plan under a selection policy (tuning code).
 int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,

@@ -4,7 +4,8 @@
 //     x' = x * 2^-e            (e = block exponent, exponent-field arithmetic)
 //     hi = RN(x'),  lo = RN(x' - hi)
 // with RN round-to-nearest-even to bf16 (hardware conversion) or to tf32
-// (bit arithmetic; the planes keep tf32 values in 32-bit containers).
+// (bit arithmetic; the planes keep tf32 values in 32-bit containers); the
+// six-product bf16 mode writes three planes, hi, mid and lo.
 // A is kept row-major (K contiguous); B is transposed so that both operands
 // are K-major for the tensor-core kernel.  Rows of the planes are padded to
 // a 16-byte pitch with zeros.
@@ -95,12 +96,13 @@ __device__ __forceinline__ void fold_block_max(unsigned m, unsigned* slot) {
 // 4l and 4l + 128: its eight loads are issued before any use, so that enough
 // bytes are in flight to cover memory latency.  The 32 rows lie in one
 // 128-row block.
-template <bool TF32, Pass PASS>
+template <Prec PR, Pass PASS>
 __device__ __forceinline__ unsigned split_rows_tile(const float* __restrict__ X, int64_t rows,
                                                 int64_t cols, int64_t ld, bool vec,
                                                 unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t plane,
                                                 int64_t pitch, int64_t r0, int64_t k0) {
+  constexpr bool TF32 = PR == Prec::TF32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[r0 / kScaleBlock]));
   float v[4][2][4];
@@ -147,6 +149,19 @@ __device__ __forceinline__ unsigned split_rows_tile(const float* __restrict__ X,
         split_tf32(x[3] * sc, h.w, l.w);
         *reinterpret_cast<float4*>(P + o) = h;
         *reinterpret_cast<float4*>(P + plane + o) = l;
+      } else if (PR == Prec::BF16X6) {
+        __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+        __align__(8) __nv_bfloat16 h[4], mi[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const Split3Bf16 s = split3_bf16(x[j] * sc);
+          h[j] = s.hi;
+          mi[j] = s.mid;
+          l[j] = s.lo;
+        }
+        *reinterpret_cast<uint2*>(P + o) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(P + plane + o) = *reinterpret_cast<const uint2*>(mi);
+        *reinterpret_cast<uint2*>(P + 2 * plane + o) = *reinterpret_cast<const uint2*>(l);
       } else {
         __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
         __align__(8) __nv_bfloat16 h[4], l[4];
@@ -174,12 +189,13 @@ __device__ __forceinline__ unsigned split_rows_tile(const float* __restrict__ X,
 // The 128 columns are one 128-column block.
 constexpr int kColTilePitch = 132;
 
-template <bool TF32, Pass PASS>
+template <Prec PR, Pass PASS>
 __device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
                                                 int64_t ld, bool vec, unsigned* __restrict__ amax,
                                                 void* __restrict__ planes, int64_t plane,
                                                 int64_t pitch, int64_t n0, int64_t k0,
                                                 float* __restrict__ tile) {
+  constexpr bool TF32 = PR == Prec::TF32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned m = 0;
   {
@@ -231,6 +247,23 @@ __device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X,
         split_tf32(tile[(kl + 4 * g + 3) * kColTilePitch + nl] * sc, h.w, l.w);
         *reinterpret_cast<float4*>(P + obase + 4 * g) = h;
         *reinterpret_cast<float4*>(P + plane + obase + 4 * g) = l;
+      }
+    } else if (PR == Prec::BF16X6) {
+      __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        if (8 * g >= avail) break;
+        __align__(16) __nv_bfloat16 h[8], mi[8], l[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const Split3Bf16 s = split3_bf16(tile[(kl + 8 * g + i) * kColTilePitch + nl] * sc);
+          h[i] = s.hi;
+          mi[i] = s.mid;
+          l[i] = s.lo;
+        }
+        *reinterpret_cast<uint4*>(P + obase + 8 * g) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(P + plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(mi);
+        *reinterpret_cast<uint4*>(P + 2 * plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(l);
       }
     } else {
       __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
@@ -354,7 +387,7 @@ __device__ __forceinline__ void amax_item(const AmaxShape& a, int64_t item) {
 struct OpShape {
   const float* X;
   int64_t rows, ld;
-  int64_t plane;            // elements from the hi plane to the lo plane
+  int64_t plane;            // elements from one plane to the next
   bool vec;                 // 16-byte aligned along the contiguous dimension
   bool kcontig;             // K contiguous in X (row tiles), else column tiles
   unsigned* amax;           // per block of 128 rows of the planes
@@ -386,25 +419,25 @@ struct PackShape {
 };
 
 // Split item l of operand o (unscaled); returns this thread's max |x|.
-template <bool TF32>
+template <Prec PR>
 __device__ __forceinline__ unsigned op_item(const PackShape& p, const OpShape& o, int l, float* tile) {
   const int kt = p.ktiles(o);
   if (o.kcontig)
-    return split_rows_tile<TF32, kFirst>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+    return split_rows_tile<PR, kFirst>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
                                          (int64_t)(l / kt) * 32, (int64_t)(l % kt) * 256);
-  return split_cols_tile<TF32, kFirst>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+  return split_cols_tile<PR, kFirst>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
                                        (int64_t)(l / kt) * 128, (int64_t)(l % kt) * 64, tile);
 }
 
-template <bool TF32>
+template <Prec PR>
 __device__ __forceinline__ unsigned first_item(const PackShape& p, int i, float* tile) {
   const int na = p.items_of(p.op[0]);
-  return i < na ? op_item<TF32>(p, p.op[0], i, tile) : op_item<TF32>(p, p.op[1], i - na, tile);
+  return i < na ? op_item<PR>(p, p.op[0], i, tile) : op_item<PR>(p, p.op[1], i - na, tile);
 }
 
 // Close a run of `run` items of block `blk` (encoded as in block_of); the
 // CTA that completes an out-of-range block re-splits it with its exponent.
-template <bool TF32>
+template <Prec PR>
 __device__ __forceinline__ void finish_op_block(const PackShape& p, const OpShape& o, int64_t b, unsigned m,
                                                 unsigned run, float* tile) {
   const int kt = p.ktiles(o);
@@ -415,60 +448,60 @@ __device__ __forceinline__ void finish_op_block(const PackShape& p, const OpShap
     if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
         for (int64_t q = b * kScaleBlock; q < b * kScaleBlock + rows_b; q += 32)
-          split_rows_tile<TF32, kRescale>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane,
+          split_rows_tile<PR, kRescale>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane,
                                           p.pitch, q, k0);
     }
   } else {
     const unsigned fin = finish_run(m, o.amax + b, o.cnt + b, run, (unsigned)kt);
     if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
-        split_cols_tile<TF32, kRescale>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
+        split_cols_tile<PR, kRescale>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
                                         b * 128, k0, tile);
     }
   }
 }
 
-template <bool TF32>
+template <Prec PR>
 __device__ __forceinline__ void finish_block(const PackShape& p, int64_t blk, unsigned m, unsigned run,
                                              float* tile) {
   if (blk >= 0)
-    finish_op_block<TF32>(p, p.op[0], blk, m, run, tile);
+    finish_op_block<PR>(p, p.op[0], blk, m, run, tile);
   else
-    finish_op_block<TF32>(p, p.op[1], -1 - blk, m, run, tile);
+    finish_op_block<PR>(p, p.op[1], -1 - blk, m, run, tile);
 }
 
 // Items [i0, i1) of one problem, in runs of one block each.
-template <bool TF32>
+template <Prec PR>
 __device__ __forceinline__ void pack_range(const PackShape& p, int i0, int i1, float* tile) {
   int i = i0;
   while (i < i1) {
     const int64_t blk = p.block_of(i);
     unsigned m = 0, run = 0;
     do {
-      m = max(m, first_item<TF32>(p, i, tile));
+      m = max(m, first_item<PR>(p, i, tile));
       ++run;
       ++i;
     } while (i < i1 && p.block_of(i) == blk);
-    finish_block<TF32>(p, blk, m, run, tile);
+    finish_block<PR>(p, blk, m, run, tile);
   }
 }
 
 // ------------------------------------------------ single-problem kernels
 // CTA c takes the c-th contiguous share of the items.
-template <bool TF32>
+template <Prec PR>
 __global__ void __launch_bounds__(256) pack_first_kernel(const PackShape p) {
   __shared__ __align__(16) float tile[64 * kColTilePitch];
   const int total = p.items();
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
-  pack_range<TF32>(p, i0, min(total, i0 + per), tile);
+  pack_range<PR>(p, i0, min(total, i0 + per), tile);
   griddep_launch_dependents();   // the gemm may start its prologue
 }
 
 // Fused-split preparation in one launch: A's block maxima (grid-stride),
 // then B packed as in pack_first_kernel (p holds B only; a contiguous
 // share of its items per CTA).
-template <bool TF32, int MODE>
+template <Prec PR, int MODE>
 __global__ void __launch_bounds__(256) fused_prep_kernel(const AmaxShape a, const PackShape p) {
   __shared__ __align__(16) float tile[64 * kColTilePitch];
   const int64_t na = amax_items<MODE>(a);
@@ -476,7 +509,7 @@ __global__ void __launch_bounds__(256) fused_prep_kernel(const AmaxShape a, cons
   const int total = p.items();
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
-  pack_range<TF32>(p, i0, min(total, i0 + per), tile);
+  pack_range<PR>(p, i0, min(total, i0 + per), tile);
   griddep_launch_dependents();
 }
 
@@ -517,7 +550,7 @@ __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, cons
   return p;
 }
 
-template <bool TF32>
+template <Prec PR>
 __global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
                                                            const GroupedPtrs* __restrict__ ptrs,
                                                            const int* __restrict__ prefix_g, int G) {
@@ -533,7 +566,7 @@ __global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem*
     const int e = min(iend, prefix[g + 1]);
     const GroupedPtrs& q = ptrs[g];
     if (q.alpha != 0.0f)   // A and B are not read when alpha == 0 (uniform per CTA)
-      pack_range<TF32>(problem_shape(probs[g], q), i - prefix[g], e - prefix[g], tile);
+      pack_range<PR>(problem_shape(probs[g], q), i - prefix[g], e - prefix[g], tile);
     i = e;
   }
   griddep_launch_dependents();
@@ -567,10 +600,13 @@ int64_t host_items(const OpShape& o, int64_t pitch) {
 cudaError_t launch_first(Prec prec, const PackShape& p, int sms, cudaStream_t s) {
   const int64_t first = host_items(p.op[0], p.pitch) + host_items(p.op[1], p.pitch);
   if (first == 0) return cudaSuccess;
+  const int grid = grid_for(first, sms);
   if (prec == Prec::TF32)
-    pack_first_kernel<true><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_first_kernel<Prec::TF32><<<grid, 256, 0, s>>>(p);
+  else if (prec == Prec::BF16X6)
+    pack_first_kernel<Prec::BF16X6><<<grid, 256, 0, s>>>(p);
   else
-    pack_first_kernel<false><<<grid_for(first, sms), 256, 0, s>>>(p);
+    pack_first_kernel<Prec::BF16><<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -619,13 +655,15 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
   if (total == 0) return cudaSuccess;
   const int grid = grid_for(total, sms);
   if (prec == Prec::TF32) {
-    if (mode == kAmaxFlat) fused_prep_kernel<true, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
-    else if (mode == kAmaxRowsVec) fused_prep_kernel<true, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
-    else fused_prep_kernel<true, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+    if (mode == kAmaxFlat) fused_prep_kernel<Prec::TF32, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
+    else if (mode == kAmaxRowsVec) fused_prep_kernel<Prec::TF32, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
+    else fused_prep_kernel<Prec::TF32, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+  } else if (prec == Prec::BF16) {
+    if (mode == kAmaxFlat) fused_prep_kernel<Prec::BF16, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
+    else if (mode == kAmaxRowsVec) fused_prep_kernel<Prec::BF16, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
+    else fused_prep_kernel<Prec::BF16, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
   } else {
-    if (mode == kAmaxFlat) fused_prep_kernel<false, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
-    else if (mode == kAmaxRowsVec) fused_prep_kernel<false, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
-    else fused_prep_kernel<false, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+    return cudaErrorInvalidValue;   // the fused kernel splits A in two (three-product modes only)
   }
   return cudaGetLastError();
 }
@@ -645,9 +683,11 @@ cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const Gr
   if (first_total == 0) return cudaSuccess;
   const int gf = grid_for(first_total, sms);
   if (prec == Prec::TF32)
-    grouped_pack_kernel<true><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    grouped_pack_kernel<Prec::TF32><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+  else if (prec == Prec::BF16X6)
+    grouped_pack_kernel<Prec::BF16X6><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
   else
-    grouped_pack_kernel<false><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    grouped_pack_kernel<Prec::BF16><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
   return cudaGetLastError();
 }
 

@@ -1,6 +1,8 @@
 // Split-precision tensor-core gemm for sm_103a: C = alpha * A * B + beta * C
 // with FP32 semantics, computed as three bf16 (or tf32) tensor-core products
-// per k-step, hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory.
+// per k-step, hi*hi + hi*lo + lo*hi, accumulated in FP32 in tensor memory
+// (or, with three bf16 planes hi/mid/lo, as the six products whose plane
+// indices sum to at most two).
 //
 // The paper's gemm recipe (Section I; Section VI-A) is two-level tiling,
 // array packing, register blocking and prefetching, with full tiles kept
@@ -52,22 +54,32 @@ namespace gb {
 // this geometry supports) measured 1.1-1.2 PFLOP/s on GB300 against 1.6 for
 // 128, with the 128-byte swizzle (2-deep ring) and with the 64-byte swizzle
 // (4-deep ring) alike, so it is not offered.
-template <int BN, bool TF32, bool FUSED = false>
+//
+// NP = 3: the six-product bf16 mode, three planes per operand (hi, mid, lo);
+// a stage holds all six, so the ring is two stages deep.  Each accumulator
+// buffer is two BN-column accumulators: hi*hi alone, and the five smaller
+// products.  The tensor core's FP32 accumulation drops low bits of the
+// running sum at every MMA; kept apart, the small products lose bits only
+// relative to their own (2^-8 smaller) sum, and the hi*hi chain is one MMA
+// per k-step instead of six.
+template <int BN, bool TF32, bool FUSED = false, int NP = 2>
 struct TcCfg {
+  static_assert(NP == 2 || (NP == 3 && !TF32 && !FUSED), "three planes: packed bf16 only");
   static constexpr int BM = 128;
   static constexpr int SW = 128;                       // bytes of one row per k-chunk
   static constexpr int A_PLANE = BM * SW;
   static constexpr int B_PLANE = BN * SW;
-  static constexpr int STAGE = 2 * A_PLANE + 2 * B_PLANE;
+  static constexpr int STAGE = NP * A_PLANE + NP * B_PLANE;
   // operand ring depth (the fused variant gives room to the staging of A)
-  static constexpr int STAGES = FUSED ? 2 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+  static constexpr int STAGES = (FUSED || NP == 3) ? 2 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
   static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
   static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
   // epilogue warpgroups (two for the fused 128-wide tile: with its extra
   // warps, one warpgroup holding 128 columns would run out of registers)
   static constexpr int EPI_WG = (BN == 256 || (FUSED && BN == 128)) ? 2 : 1;
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
-  static constexpr int TMEM_COLS = 2 * BN;             // two accumulator buffers
+  static constexpr int ACC_COLS = NP == 3 ? 2 * BN : BN;   // TMEM columns of one accumulator buffer
+  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulator buffers
   static constexpr int EPI_PITCH = 33;                 // floats per staged row (bank-conflict free)
   static constexpr int EPI_BYTES = 4 * EPI_WG * 32 * EPI_PITCH * 4;   // one 32x32 buffer per epilogue warp
   static constexpr int BAR_BYTES = 256;
@@ -225,7 +237,7 @@ __device__ __forceinline__ void fused_store(uint8_t* hi_plane, uint8_t* lo_plane
       const float xs = x[j] * sf;
       const unsigned u = __float_as_uint(xs);
       hv[j] = __uint_as_float((u + 0xFFFu + ((u >> 13) & 1u)) & 0xFFFFE000u);
-      const unsigned d = __float_as_uint(xs - hv[j]);
+      const unsigned d = __float_as_uint(__fsub_rn(xs, hv[j]));
       lv[j] = __uint_as_float((d + 0xFFFu + ((d >> 13) & 1u)) & 0xFFFFE000u);
     }
     *reinterpret_cast<float4*>(hi_plane + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
@@ -238,7 +250,7 @@ __device__ __forceinline__ void fused_store(uint8_t* hi_plane, uint8_t* lo_plane
       const unsigned hp = cvt_bf16x2(a, b);
       const float ha = __uint_as_float(hp << 16), hb = __uint_as_float(hp & 0xFFFF0000u);
       hw[j] = hp;
-      lw[j] = cvt_bf16x2(a - ha, b - hb);
+      lw[j] = cvt_bf16x2(__fsub_rn(a, ha), __fsub_rn(b, hb));
     }
     *reinterpret_cast<uint4*>(hi_plane + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     *reinterpret_cast<uint4*>(lo_plane + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -287,9 +299,9 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
   }
 }
 
-template <int BN, bool TF32, class Sched, bool FUSED = false>
+template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
-  using Cfg = TcCfg<BN, TF32, FUSED>;
+  using Cfg = TcCfg<BN, TF32, FUSED, NP>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -434,8 +446,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           }
           if (bq.have && mbar_test_wait(empty_bar(bstage), bph ^ 1u)) {
             const uint32_t fb = full_bar(bstage);
-            mbar_arrive_expect_tx(fb, 2 * Cfg::B_PLANE);
-            const uint32_t sB = sbase + bstage * Cfg::STAGE + 2 * Cfg::A_PLANE;
+            mbar_arrive_expect_tx(fb, NP * Cfg::B_PLANE);
+            const uint32_t sB = sbase + bstage * Cfg::STAGE + NP * Cfg::A_PLANE;
             const int kx = bq.c * Cfg::BK;
             tma_load_3d(sB, mB, fb, kx, bq.w.tn * BN, 0);
             tma_load_3d(sB + Cfg::B_PLANE, mB, fb, kx, bq.w.tn * BN, 1);
@@ -498,15 +510,16 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             break;
           }
           const uint32_t fb = full_bar(stage);
-          mbar_arrive_expect_tx(fb, FUSED ? 2 * Cfg::B_PLANE : Cfg::STAGE);
+          mbar_arrive_expect_tx(fb, FUSED ? NP * Cfg::B_PLANE : Cfg::STAGE);
           const uint32_t sA = sbase + stage * Cfg::STAGE;
           const int kx = c * Cfg::BK;
           if (!FUSED) {
-            tma_load_3d(sA, mA, fb, kx, w.tm * Cfg::BM, 0);
-            tma_load_3d(sA + Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, 1);
+#pragma unroll
+            for (int z = 0; z < NP; ++z) tma_load_3d(sA + z * Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, z);
           }
-          tma_load_3d(sA + 2 * Cfg::A_PLANE, mB, fb, kx, w.tn * BN, 0);
-          tma_load_3d(sA + 2 * Cfg::A_PLANE + Cfg::B_PLANE, mB, fb, kx, w.tn * BN, 1);
+#pragma unroll
+          for (int z = 0; z < NP; ++z)
+            tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
           issued[stage] = true;
           last_phase[stage] = phase;
           if (++stage == STAGES) {
@@ -539,7 +552,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             break;
           }
           tc_fence_after();
-          const uint32_t d = tmem_base + ab * BN;
+          const uint32_t d = tmem_base + ab * Cfg::ACC_COLS;
           for (int c = cb; c < ce; ++c) {
             if (!mbar_wait(full_bar(stage), phase, abort_flag, err)) {
               ok = false;
@@ -548,7 +561,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             tc_fence_after();
             const uint32_t sAhi = sbase + stage * Cfg::STAGE;
             const uint32_t sAlo = sAhi + Cfg::A_PLANE;
-            const uint32_t sBhi = sAhi + 2 * Cfg::A_PLANE;
+            const uint32_t sBhi = sAhi + NP * Cfg::A_PLANE;
             const uint32_t sBlo = sBhi + Cfg::B_PLANE;
 #pragma unroll
             for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
@@ -558,7 +571,20 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
               const uint64_t dBhi = sdesc_k<Cfg::SW>(sBhi + off);
               const uint64_t dBlo = sdesc_k<Cfg::SW>(sBlo + off);
               const uint32_t acc = (c > cb || kk > 0) ? 1u : 0u;
-              if (TF32) {
+              if constexpr (NP == 3) {
+                // planes 0, 1, 2 = hi, mid, lo; the six products whose
+                // plane indices sum to at most 2: the five smaller ones into
+                // the second accumulator (smallest first), hi*hi into the first
+                const uint32_t d2 = d + BN;
+                const uint64_t dAl2 = sdesc_k<Cfg::SW>(sAhi + 2 * Cfg::A_PLANE + off);
+                const uint64_t dBl2 = sdesc_k<Cfg::SW>(sBhi + 2 * Cfg::B_PLANE + off);
+                umma_bf16(d2, dAl2, dBhi, idesc, acc);
+                umma_bf16(d2, dAlo, dBlo, idesc, 1u);
+                umma_bf16(d2, dAhi, dBl2, idesc, 1u);
+                umma_bf16(d2, dAlo, dBhi, idesc, 1u);
+                umma_bf16(d2, dAhi, dBlo, idesc, 1u);
+                umma_bf16(d, dAhi, dBhi, idesc, acc);
+              } else if (TF32) {
                 umma_tf32(d, dAlo, dBhi, idesc, acc);
                 umma_tf32(d, dAhi, dBlo, idesc, 1u);
                 umma_tf32(d, dAhi, dBhi, idesc, 1u);
@@ -626,7 +652,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         }
         tc_fence_after();
         const uint32_t taddr =
-            tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * BN + half * EC;
+            tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * Cfg::ACC_COLS + half * EC;
 #pragma unroll
         for (int j = 0; j < EC / 32; ++j) {
           uint32_t r[32];
@@ -636,6 +662,13 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) S[j * 32 + i] = __uint_as_float(r[i]);
           } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[j * 32 + i] += __uint_as_float(r[i]);
+          }
+          if constexpr (NP == 3) {
+            // the five smaller products' accumulator, BN columns further on
+            tmem_ld_32x32b_x32(taddr + BN + j * 32, r);
+            tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 32; ++i) S[j * 32 + i] += __uint_as_float(r[i]);
           }
@@ -915,18 +948,19 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   }
 }
 
-template <int BN, bool TF32>
-__global__ void __launch_bounds__(TcCfg<BN, TF32>::THREADS, 1)
+template <int BN, bool TF32, int NP>
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs a) {
   SingleSched sc{&tmA, &tmB, &a};
-  tc_gemm_body<BN, TF32>(sc);
+  tc_gemm_body<BN, TF32, SingleSched, false, NP>(sc);
 }
 
-template <int BN, bool TF32>
-__global__ void __launch_bounds__(TcCfg<BN, TF32>::THREADS, 1) tc_grouped_kernel(const GroupedArgs a) {
+template <int BN, bool TF32, int NP>
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
+    tc_grouped_kernel(const GroupedArgs a) {
   GroupedSched sc{&a};
-  tc_gemm_body<BN, TF32>(sc);
+  tc_gemm_body<BN, TF32, GroupedSched, false, NP>(sc);
 }
 
 // Fused variant: tmA maps A itself (FP32, 128-byte-wide boxes of 128 rows)
@@ -982,6 +1016,8 @@ int tc_smem_bytes(int bn, Prec prec, bool fused) {
     return bn == 64 ? TcCfg<64, false, true>::SMEM : TcCfg<128, false, true>::SMEM;
   }
   if (prec == Prec::TF32) return bn == 64 ? TcCfg<64, true>::SMEM : TcCfg<128, true>::SMEM;
+  if (prec == Prec::BF16X6)
+    return bn == 64 ? TcCfg<64, false, false, 3>::SMEM : TcCfg<128, false, false, 3>::SMEM;
   return bn == 64 ? TcCfg<64, false>::SMEM : TcCfg<128, false>::SMEM;
 }
 
@@ -993,22 +1029,22 @@ int tc_chunk_bytes(int bn) {
 // The dynamic shared memory limit of every kernel variant is raised once per
 // device and thread, outside any stream capture: plans call tc_prepare when
 // they are created, launches call it again (a no-op after the first time).
-template <int BN, bool TF32, bool FUSED>
+template <int BN, bool TF32, bool FUSED, int NP = 2>
 static cudaError_t prepare_variant() {
-  using Cfg = TcCfg<BN, TF32, FUSED>;
+  using Cfg = TcCfg<BN, TF32, FUSED, NP>;
   static thread_local int configured_device = -1;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (configured_device != dev) {
-    if (FUSED) {
+    if constexpr (FUSED) {
       e = cudaFuncSetAttribute(tc_gemm_fused_kernel<BN, TF32>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     } else {
-      e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                Cfg::SMEM);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32>,
+        e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32, NP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     }
     if (e != cudaSuccess) return e;
@@ -1022,6 +1058,10 @@ static cudaError_t prepare_fused(int bn, Prec prec) {
   if (prec == Prec::TF32) {
     if (bn == 64) return prepare_variant<64, true, FUSED>();
     if (bn == 128) return prepare_variant<128, true, FUSED>();
+  } else if (prec == Prec::BF16X6) {
+    if (FUSED) return cudaErrorInvalidValue;   // the fused kernel splits A in two
+    if (bn == 64) return prepare_variant<64, false, false, 3>();
+    if (bn == 128) return prepare_variant<128, false, false, 3>();
   } else {
     if (bn == 64) return prepare_variant<64, false, FUSED>();
     if (bn == 128) return prepare_variant<128, false, FUSED>();
@@ -1033,20 +1073,24 @@ cudaError_t tc_prepare(int bn, Prec prec, bool fused) {
   return fused ? prepare_fused<true>(bn, prec) : prepare_fused<false>(bn, prec);
 }
 
-template <int BN, bool TF32>
+template <int BN, bool TF32, int NP = 2>
 static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
                                   const CUtensorMap& tmB, const TcArgs& a, cudaStream_t s) {
   if (fused) {
-    using Cfg = TcCfg<BN, TF32, true>;
-    cudaError_t e = prepare_variant<BN, TF32, true>();
-    if (e != cudaSuccess) return e;
-    e = launch_dependent(tc_gemm_fused_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
-    if (e != cudaSuccess) return e;
+    if constexpr (NP != 2) {
+      return cudaErrorInvalidValue;
+    } else {
+      using Cfg = TcCfg<BN, TF32, true>;
+      cudaError_t e = prepare_variant<BN, TF32, true>();
+      if (e != cudaSuccess) return e;
+      e = launch_dependent(tc_gemm_fused_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      if (e != cudaSuccess) return e;
+    }
   } else {
-    using Cfg = TcCfg<BN, TF32>;
-    cudaError_t e = prepare_variant<BN, TF32, false>();
+    using Cfg = TcCfg<BN, TF32, false, NP>;
+    cudaError_t e = prepare_variant<BN, TF32, false, NP>();
     if (e != cudaSuccess) return e;
-    e = launch_dependent(tc_gemm_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    e = launch_dependent(tc_gemm_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
@@ -1057,6 +1101,9 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   if (l.prec == Prec::TF32) {
     if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, true>(l.grid, l.fused, tmA, tmB, a, s);
+  } else if (l.prec == Prec::BF16X6) {
+    if (l.bn == 64) return launch_variant<64, false, 3>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, false, 3>(l.grid, l.fused, tmA, tmB, a, s);
   } else {
     if (l.bn == 64) return launch_variant<64, false>(l.grid, l.fused, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, false>(l.grid, l.fused, tmA, tmB, a, s);
@@ -1064,12 +1111,12 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   return cudaErrorInvalidValue;
 }
 
-template <int BN, bool TF32>
+template <int BN, bool TF32, int NP = 2>
 static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, TF32>;
-  cudaError_t e = prepare_variant<BN, TF32, false>();
+  using Cfg = TcCfg<BN, TF32, false, NP>;
+  cudaError_t e = prepare_variant<BN, TF32, false, NP>();
   if (e != cudaSuccess) return e;
-  e = launch_dependent(tc_grouped_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, a);
+  e = launch_dependent(tc_grouped_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -1078,13 +1125,15 @@ cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a,
   if (prec == Prec::TF32) {
     if (bn == 64) return launch_grouped_variant<64, true>(grid, a, s);
     if (bn == 128) return launch_grouped_variant<128, true>(grid, a, s);
+  } else if (prec == Prec::BF16X6) {
+    if (bn == 64) return launch_grouped_variant<64, false, 3>(grid, a, s);
+    if (bn == 128) return launch_grouped_variant<128, false, 3>(grid, a, s);
   } else {
     if (bn == 64) return launch_grouped_variant<64, false>(grid, a, s);
     if (bn == 128) return launch_grouped_variant<128, false>(grid, a, s);
   }
   return cudaErrorInvalidValue;
 }
-
 cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float beta,
                                  float* C, int64_t ldc, cudaStream_t s) {
   const int64_t total = static_cast<int64_t>(M) * N;

@@ -11,7 +11,7 @@ import oracle
 import paper_1804_10694_gb300 as pkg
 import workloads as W
 
-MODES = ("simt", "bf16x3", "tf32x3")
+MODES = ("simt", "bf16x3", "tf32x3", "bf16x6")
 TOL = 1e-5   # relative Frobenius error bound for every result
 
 

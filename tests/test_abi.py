@@ -50,6 +50,15 @@ def test_config_table():
         seen.add(key)
     with pytest.raises(pkg.GemmError):
         pkg.config_get("bf16x3", n)
+    # the six-product mode has the packed half of the table, two stages deep
+    assert pkg.config_count("bf16x6") == n // 2
+    for i in range(n // 2):
+        c6, c3 = pkg.config_get("bf16x6", i), pkg.config_get("bf16x3", i)
+        assert c6["fused"] == 0 and c6["stages"] == 2
+        assert {k: v for k, v in c6.items() if k != "stages"} == \
+            {k: v for k, v in c3.items() if k != "stages"}
+    with pytest.raises(pkg.GemmError):
+        pkg.config_get("bf16x6", n // 2)
 
 
 def test_invalid_arguments_rejected_before_launch():

@@ -276,7 +276,7 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     assert oracle.rel_frob(got, oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None)) <= TOL
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
 @pytest.mark.parametrize("alpha,beta", W.ALPHA_BETA)
 def test_host_buffer_pipelined_panels(mode, alpha, beta):
     """Host-buffer calls large enough for the row-panel pipeline (B packed

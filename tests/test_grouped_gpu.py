@@ -34,7 +34,7 @@ def _run(plan, probs, alphas, betas, graph=True):
     return [c.cpu().numpy() for c in dC]
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "simt"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6", "simt"])
 def test_grouped_small_uneven_against_oracle(mode):
     shapes = [(300, 200, 100), (1, 1, 1), (129, 65, 1000), (64, 64, 64), (0, 5, 5), (7, 300, 0),
               (513, 33, 257), (31, 129, 77), (250, 1024, 40), (5, 0, 9)]
@@ -54,7 +54,7 @@ def test_grouped_small_uneven_against_oracle(mode):
     plan.destroy()
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
 def test_grouped_integer_inputs_bit_exact(mode):
     shapes = W.grouped_shapes(24, seed=77, lo=16, hi=700)
     probs = _problems(shapes, 300, gen=W.integers)

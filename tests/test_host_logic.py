@@ -16,7 +16,7 @@ SHAPES = [(8192, 8192, 8192), (1060, 1060, 1060), (50176, 64, 576), (12544, 128,
           (3136, 256, 2304), (33, 17, 5), (1, 1, 1), (129, 4099, 63), (300, 70, 20000)]
 
 
-@pytest.mark.parametrize("mode,tf32", [("bf16x3", False), ("tf32x3", True)])
+@pytest.mark.parametrize("mode,tf32", [("bf16x3", False), ("tf32x3", True), ("bf16x6", False)])
 def test_features_match_oracle_restatement(mode, tf32):
     n = pkg.config_count(mode)
     assert pkg.costmodel_feature_count() == 15

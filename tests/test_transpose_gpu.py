@@ -25,7 +25,7 @@ def run_t(ta, tb, mode, M, N, K, alpha, As, Bs, beta, C0, select="default"):
     return dC.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
 @pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
 def test_transposes_match_untransposed_bitwise(mode, ta, tb):
     M, N, K = 333, 270, 515
@@ -41,7 +41,7 @@ def test_transposes_match_untransposed_bitwise(mode, ta, tb):
     check_padding_untouched(C0, got, N)
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
 def test_transposed_integer_inputs_bit_exact(mode):
     M, N, K = 300, 200, 700
     A, B, C0 = W.integers(M, K, 204), W.integers(K, N, 205), W.integers(M, N, 206)
@@ -50,7 +50,7 @@ def test_transposed_integer_inputs_bit_exact(mode):
     assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
 def test_transposed_block_scaling(mode):
     """Blocks of 128 rows of A are 128 columns of the stored A^T: the
     transposing pack must scale them as blocks (tiny and mixed blocks)."""
