@@ -124,7 +124,7 @@ gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, 
  * returning.  Only the M x N (M x K, K x N) elements are copied; padding
  * beyond a row's length in the host buffers is never written.  With
  * page-locked A and C, at least 512 rows, no split-K and the environment
- * variable GEMM_HOST_PANELS (default 8) above 1, B is copied and packed once
+ * variable GEMM_HOST_PANELS (default 16) above 1, B is copied and packed once
  * and row panels of A and C stream through two copy streams while earlier
  * panels compute. */
 gemm_status gemm_f32_host(int64_t M, int64_t N, int64_t K, float alpha, const float* A,

@@ -613,13 +613,16 @@ static cudaError_t copy_rows(float* dst, const float* src, int64_t rows, int64_t
   return cudaMemcpy2DAsync(dst, (size_t)ld * 4, src, (size_t)ld * 4, (size_t)cols * 4, (size_t)rows, kind, s);
 }
 
-// Panels of the host-buffer pipeline (GEMM_HOST_PANELS, default 8; 1 turns
-// the pipeline off).  On 8192^3 with pinned buffers 1/2/4/8 panels took
-// 7.5/5.7/5.0/4.7 ms per call (beta != 0).
+// Panels of the host-buffer pipeline (GEMM_HOST_PANELS, default 16; 1 turns
+// the pipeline off).  On 8192^3 with pinned buffers 1/2/4/8/16/32 panels took
+// 7.5/5.7/5.0/4.66/4.53/4.67 ms per call with beta != 0 (4.19/4.25/4.43 ms
+// for 8/16/32 with beta = 0).  The host link carries 211 GB/s host to device
+// alone but 171 + 170 GB/s with both directions busy, so with beta != 0 the
+// floor is about 4.1 ms: the copies back of C panels overlap the copies in.
 static int host_panels() {
   static const int n = [] {
     const char* v = std::getenv("GEMM_HOST_PANELS");
-    const int x = v ? std::atoi(v) : 8;
+    const int x = v ? std::atoi(v) : 16;
     return x < 1 ? 1 : (x > 64 ? 64 : x);
   }();
   return n;
