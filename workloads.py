@@ -30,6 +30,10 @@ CONV_SHAPES = ((50176, 64, 576), (12544, 128, 1152), (3136, 256, 2304))
 # the 3x3 convolution layers behind CONV_SHAPES (batch, H, W, C in, K out):
 # M = batch*H*W output pixels, N = K, K_gemm = 9*C
 CONV3X3_LAYERS = ((1, 224, 224, 64, 64), (1, 112, 112, 128, 128), (1, 56, 56, 256, 256))
+# the paper's Conv benchmark: 512 x 512 images, 16 input and output features,
+# batch 32, filters specialised from 3x3 to 11x11 (batch, H, W, C, K)
+CONV_PAPER_LAYER = (32, 512, 512, 16, 16)
+CONV_FILTER_SIZES = (3, 5, 7, 9, 11)
 ALPHA_BETA = ((1.0, 0.0), (1.5, 0.5))
 
 CONFIG_SMALL = 0      # 512^3, alpha 1.5, beta 0.5
@@ -149,9 +153,10 @@ def conv_image(batch: int, H: int, W: int, C: int, seed: int, kind: str = "unifo
     return rng.uniform(-1.0, 1.0, size=(batch, H, W, C)).astype(np.float32)
 
 
-def conv_filter(C: int, K: int, seed: int, kind: str = "uniform") -> np.ndarray:
-    """RSCK float32 3x3 filter: iid uniform[-1, 1], or integers in [-8, 8]."""
+def conv_filter(C: int, K: int, seed: int, kind: str = "uniform", R: int = 3, S: int = 3) -> np.ndarray:
+    """RSCK float32 R x S filter (3x3 by default): iid uniform[-1, 1], or
+    integers in [-8, 8]."""
     rng = _rng(seed)
     if kind == "integers":
-        return rng.integers(-8, 9, size=(3, 3, C, K)).astype(np.float32)
-    return rng.uniform(-1.0, 1.0, size=(3, 3, C, K)).astype(np.float32)
+        return rng.integers(-8, 9, size=(R, S, C, K)).astype(np.float32)
+    return rng.uniform(-1.0, 1.0, size=(R, S, C, K)).astype(np.float32)
