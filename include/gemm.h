@@ -150,22 +150,32 @@ gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int
                                int64_t ldb, int64_t ldc, gemm_mode mode, gemm_select sel,
                                gemm_plan_t* out);
 
-/* Direct 3x3 convolution, stride 1, zero padding 1 (the paper benchmarks
- * convolutions, Section VI), as an implicit gemm: the patch matrix of the
- * image (M = batch*H*W output pixels by 9*C taps x channels) is never formed;
- * the fused-split kernel gathers it tile by tile while splitting it.
- *   out[n][h][w][k] = alpha * sum_{r,s,c} in[n][h+r-1][w+s-1][c] * f[r][s][c][k]
+/* Direct convolution with an odd R x S filter (1..11 each), stride 1, "same"
+ * zero padding pR = (R-1)/2, pS = (S-1)/2 (the paper benchmarks convolutions
+ * with filters specialised from 3x3 to 11x11, Section VI), as an implicit
+ * gemm: the patch matrix of the image (M = batch*H*W output pixels by R*S*C
+ * taps x channels) is never formed; the fused-split kernel gathers it tile
+ * by tile while splitting it.
+ *   out[n][h][w][k] = alpha * sum_{r,s,c} in[n][h+r-pR][w+s-pS][c] * f[r][s][c][k]
  *                     + beta * out[n][h][w][k]      (in = 0 outside the image)
  * Execute with gemm_plan_execute(plan, alpha, in, f, beta, out, stream):
  *   in:  NHWC FP32 [batch][H][W][C], channels contiguous, 16-byte aligned;
- *   f:   RSCK FP32 [3][3][C][K] (= the gemm's B, 9C x K row-major);
+ *   f:   RSCK FP32 [R][S][C][K] (= the gemm's B, R*S*C x K row-major);
  *   out: NHWC FP32 [batch][H][W][K] (= the gemm's C, ld K).
- * All device memory owned by the caller.  C must be a multiple of 4.  One
+ * All device memory owned by the caller.  C must be a multiple of 4; the
+ * patch tiles are staged by TMA im2col loads when C is a multiple of 16
+ * (boxes of 32 or 16 channels of one tap), else gathered by the kernel's
+ * threads.  One
  * power-of-two exponent covers the whole image (its max |x|), B is scaled
  * per 128 output channels as in the gemm.  config_id < 0 picks a default;
  * otherwise it must be a fused-split configuration (gemm_config.fused).
- * Errors: INVALID_ARG (sizes, C % 4, mode, configuration), ALIGNMENT (at
- * execute: input not 16-byte aligned), ALLOC, CUDA, UNSUPPORTED_DEVICE. */
+ * Errors: INVALID_ARG (sizes, filter sizes, C % 4, mode, configuration),
+ * ALIGNMENT (at execute: input not 16-byte aligned), ALLOC, CUDA,
+ * UNSUPPORTED_DEVICE. */
+gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K, int R,
+                                  int S, gemm_mode mode, int config_id, gemm_plan_t* out);
+
+/* gemm_conv_plan_create with R = S = 3 (zero padding 1). */
 gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K,
                                      gemm_mode mode, int config_id, gemm_plan_t* out);
 

@@ -234,28 +234,28 @@ def split_pack(X, mode="bf16x3", transpose: bool = False, stream=None):
     return planes, work[:nblk]
 
 
-# --------------------------------------------------------- 3x3 convolution
-class Conv3x3Plan(Plan):
-    """Direct 3x3 convolution (stride 1, zero padding 1) as an implicit gemm
-    on NHWC images; see gemm_conv3x3_plan_create."""
+# ------------------------------------------------------------- convolution
+class ConvPlan(Plan):
+    """Direct convolution with an odd R x S filter (stride 1, same zero
+    padding) as an implicit gemm on NHWC images; see gemm_conv_plan_create."""
 
-    def __init__(self, batch, H, W, C, K, mode="bf16x3", config_id: int | None = None):
+    def __init__(self, batch, H, W, C, K, R=3, S=3, mode="bf16x3", config_id: int | None = None):
         lib = load()
         self._lib = lib
-        self.batch, self.H, self.W, self.C, self.K_out = batch, H, W, C, K
-        self.M, self.N, self.K = batch * H * W, K, 9 * C
-        self.lda, self.ldb, self.ldc = 9 * C, K, K
+        self.batch, self.H, self.W, self.C, self.K_out, self.R, self.S = batch, H, W, C, K, R, S
+        self.M, self.N, self.K = batch * H * W, K, R * S * C
+        self.lda, self.ldb, self.ldc = R * S * C, K, K
         h = ctypes.c_void_p()
-        check(lib.gemm_conv3x3_plan_create(batch, H, W, C, K, _mode(mode),
-                                           -1 if config_id is None else int(config_id),
-                                           ctypes.byref(h)))
+        check(lib.gemm_conv_plan_create(batch, H, W, C, K, int(R), int(S), _mode(mode),
+                                        -1 if config_id is None else int(config_id), ctypes.byref(h)))
         self._h = h
 
     def execute(self, x, f, out, alpha: float = 1.0, beta: float = 0.0, stream=None):
-        """x: [batch, H, W, C], f: [3, 3, C, K], out: [batch, H, W, K], all
+        """x: [batch, H, W, C], f: [R, S, C, K], out: [batch, H, W, K], all
         contiguous float32 CUDA tensors."""
         import torch
-        want = {"x": (x, (self.batch, self.H, self.W, self.C)), "f": (f, (3, 3, self.C, self.K_out)),
+        want = {"x": (x, (self.batch, self.H, self.W, self.C)),
+                "f": (f, (self.R, self.S, self.C, self.K_out)),
                 "out": (out, (self.batch, self.H, self.W, self.K_out))}
         for name, (t, shape) in want.items():
             if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
@@ -265,6 +265,13 @@ class Conv3x3Plan(Plan):
         check(self._lib.gemm_plan_execute(self._h, alpha, x.data_ptr(), f.data_ptr(), beta,
                                           out.data_ptr(), _stream_handle(stream)))
         return out
+
+
+class Conv3x3Plan(ConvPlan):
+    """ConvPlan with a 3x3 filter (zero padding 1); see gemm_conv3x3_plan_create."""
+
+    def __init__(self, batch, H, W, C, K, mode="bf16x3", config_id: int | None = None):
+        super().__init__(batch, H, W, C, K, 3, 3, mode, config_id)
 
 
 # ------------------------------------------------------------------ grouped

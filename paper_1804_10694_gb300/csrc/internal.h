@@ -48,10 +48,12 @@ struct TcArgs {
   const float* A;
   int64_t lda;
   int vecA;                // A 16-byte aligned and lda % 4 == 0: float4 loads
-  // direct 3x3 convolution (fused variant): A is the patch matrix of the NHWC
-  // image at A (conv_H x conv_W x conv_C pixels, zero padding 1), gathered
-  // while staging; one block exponent for the whole image (amaxA[0])
-  int conv, conv_H, conv_W, conv_C;
+  // direct convolution (fused variant): A is the patch matrix of the NHWC
+  // image at A (conv_H x conv_W x conv_C pixels) for an odd conv_R x conv_S
+  // filter with same zero padding, gathered while staging; one block
+  // exponent for the whole image (amaxA[0])
+  int conv, conv_H, conv_W, conv_C, conv_R, conv_S;
+  int conv_box_c;          // channels per TMA im2col box (32, or 16), when vecA
 };
 
 struct TcLaunch {

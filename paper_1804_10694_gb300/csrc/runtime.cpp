@@ -247,22 +247,26 @@ static gemm_status encode_rows_f32(CUtensorMap* map, const float* A, int64_t M, 
   return GEMM_OK;
 }
 
-// The patch matrix of a 3x3 convolution (stride 1, zero padding 1) over the
-// NHWC image X, for TMA's im2col mode: each load brings 128 consecutive
-// output pixels (row-major over N, H, W, wrapping rows and images) times 32
-// channels of one filter tap, zero outside the image; 128-byte swizzle.  The
-// bounding box corners (-1, -1) and (-1, -1) make the starting pixel of
-// output (h, w) the input pixel (h - 1, w - 1); the tap adds (r, s).
-static gemm_status encode_im2col_3x3(CUtensorMap* map, const float* X, int64_t batch, int64_t H,
-                                     int64_t W, int64_t C) {
+// The patch matrix of an R x S convolution (stride 1, zero padding (R-1)/2
+// and (S-1)/2) over the NHWC image X, for TMA's im2col mode: each load
+// brings 128 consecutive output pixels (row-major over N, H, W, wrapping
+// rows and images) times box_c channels of one filter tap, zero outside the
+// image; 128-byte swizzle for 32 channels (128-byte rows), 64-byte swizzle
+// for 16 (64-byte rows).  Bounding box corners of -(S-1)/2 (along W) and
+// -(R-1)/2 (along H), lower and upper alike, make the starting pixel of
+// output (h, w) the input pixel (h - (R-1)/2, w - (S-1)/2) and keep H x W
+// starting pixels; the tap adds (r, s).
+static gemm_status encode_im2col(CUtensorMap* map, const float* X, int64_t batch, int64_t H, int64_t W,
+                                 int64_t C, int R, int S, int box_c) {
   if (!g_encode_im2col) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "cuTensorMapEncodeIm2col unavailable");
   cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
   cuuint64_t strides[3] = {(cuuint64_t)(C * 4), (cuuint64_t)(W * C * 4), (cuuint64_t)(H * W * C * 4)};
-  const int lower[2] = {-1, -1}, upper[2] = {-1, -1};
+  const int lower[2] = {-(S / 2), -(R / 2)}, upper[2] = {-(S / 2), -(R / 2)};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode_im2col(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(X), dims, strides,
-                               lower, upper, 32, 128, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               lower, upper, (cuuint32_t)box_c, 128, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               box_c == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeIm2col failed (%d)", (int)r);
@@ -471,14 +475,22 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.C = C;
   a.A = A;
   a.vecA = (p->lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0) ? 1 : 0;
-  if (a.conv)   // TMA im2col staging when every 32-channel box lies in one tap of whole chunks
-    a.vecA = (g_encode_im2col && a.conv_C % (p->prec == Prec::TF32 ? 32 : 64) == 0) ? 1 : 0;
+  if (a.conv) {
+    // TMA im2col staging when C is a multiple of 16: boxes of 32 channels
+    // (128-byte rows) when every k-chunk holds whole taps (C a multiple of
+    // the chunk, so K = R*S*C has no partial chunk), else boxes of 16
+    // (64-byte rows; the kernel variant for them zeroes the part of a last
+    // chunk past K); other channel counts are gathered by the split threads
+    a.vecA = (g_encode_im2col && a.conv_C % 16 == 0) ? 1 : 0;
+    a.conv_box_c = a.conv_C % prec_chunk_elems(p->prec) == 0 ? 32 : 16;
+  }
   CUtensorMap tmAf;   // fused variant: A staged by TMA when its rows are 16-byte aligned
   const CUtensorMap* mapA = &p->tmA;
   if (p->launch.fused) {
     std::memset(&tmAf, 0, sizeof tmAf);
     if (a.vecA) {
-      gemm_status st = a.conv ? encode_im2col_3x3(&tmAf, A, p->conv_batch, a.conv_H, a.conv_W, a.conv_C)
+      gemm_status st = a.conv ? encode_im2col(&tmAf, A, p->conv_batch, a.conv_H, a.conv_W, a.conv_C,
+                                              a.conv_R, a.conv_S, a.conv_box_c)
                               : encode_rows_f32(&tmAf, A, M, K, p->lda);
       if (st != GEMM_OK) return st;
     }
@@ -838,20 +850,27 @@ gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda
   return plan_create_impl(M, N, K, lda, ldb, ldc, mode, config_id, GEMM_SELECT_DEFAULT, out);
 }
 
-gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K,
-                                     gemm_mode mode, int config_id, gemm_plan_t* out) {
+// Largest filter side of the direct convolution (the paper specialises 3x3
+// to 11x11); TMA's im2col corners of a 4-D map reach -128.
+constexpr int kMaxFilter = 11;
+
+gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K, int R,
+                                   int S, gemm_mode mode, int config_id, gemm_plan_t* out) {
   clear_error();
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
   *out = nullptr;
   if (batch < 1 || H < 1 || W < 1 || C < 1 || K < 1)
     return fail(GEMM_ERR_INVALID_ARG, "convolution sizes must be positive");
+  if (R < 1 || S < 1 || R > kMaxFilter || S > kMaxFilter || R % 2 == 0 || S % 2 == 0)
+    return fail(GEMM_ERR_INVALID_ARG, "filter %d x %d: sizes must be odd, 1..%d", R, S, kMaxFilter);
   if (C % 4 != 0) return fail(GEMM_ERR_INVALID_ARG, "input channels C=%lld must be a multiple of 4", (long long)C);
-  if (H > 65535 || W > 65535 || C > (1 << 20) || batch * H * W > INT32_MAX || 9 * C > INT32_MAX)
+  const int64_t taps = (int64_t)R * S;
+  if (H > 65535 || W > 65535 || C > (1 << 20) || batch * H * W > INT32_MAX || taps * C > INT32_MAX)
     return fail(GEMM_ERR_INVALID_ARG, "convolution too large");
   if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
   if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
     return fail(GEMM_ERR_INVALID_ARG, "the convolution runs in BF16X3 or TF32X3 mode");
-  const int64_t M = batch * H * W, Kd = 9 * C;
+  const int64_t M = batch * H * W, Kd = taps * C;
   gemm_config c;
   if (config_id < 0) {
     // default: the fused-split twin of the gemm heuristic's choice for this
@@ -881,8 +900,15 @@ gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_
   p->args.conv_H = (int)H;
   p->args.conv_W = (int)W;
   p->args.conv_C = (int)C;
+  p->args.conv_R = R;
+  p->args.conv_S = S;
   *out = p;
   return GEMM_OK;
+}
+
+gemm_status gemm_conv3x3_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K,
+                                     gemm_mode mode, int config_id, gemm_plan_t* out) {
+  return gemm_conv_plan_create(batch, H, W, C, K, 3, 3, mode, config_id, out);
 }
 
 gemm_status gemm_plan_execute(gemm_plan_t plan, float alpha, const float* A, const float* B,

@@ -132,7 +132,9 @@ struct FusedA {
                             // im2col boxes of whole taps), else by cp.async
   const unsigned* amaxA;    // block maxima from the max-only pass
   int amax_stride;          // 1, or 0 when one exponent covers all of A
-  int conv, H, W, C;        // A = patch matrix of an NHWC image (3x3, zero padding 1)
+  int conv, H, W, C;        // A = patch matrix of an NHWC image (R x S filter, odd
+  int R, S;                 // sizes, zero padding (R-1)/2 and (S-1)/2)
+  int box_c;                // channels per im2col box: 32 (128-byte rows) or 16 (64-byte rows)
 };
 
 __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
@@ -175,7 +177,7 @@ struct SingleSched {
   }
   __device__ FusedA srcA(int) const {
     return FusedA{a->A, a->lda, a->M, a->K, a->vecA != 0, a->amaxA, a->conv ? 0 : 1,
-                  a->conv, a->conv_H, a->conv_W, a->conv_C};
+                  a->conv, a->conv_H, a->conv_W, a->conv_C, a->conv_R, a->conv_S, a->conv_box_c};
   }
 };
 
@@ -275,23 +277,32 @@ __device__ __forceinline__ void fused_store(uint8_t* hi_plane, uint8_t* lo_plane
   }
 }
 
-// Fused variant: split rows t, t + NT, ... of a staged chunk (two or one
-// 128-byte-wide boxes, SWIZZLE_128B layout) into the hi/lo planes.
-template <bool TF32, bool FINITE, int NT>
+// Fused variant: split rows t, t + NT, ... of a staged chunk into the hi/lo
+// planes.  The chunk is a row of boxes of 128 rows each: BW = 128-byte box
+// rows in the SWIZZLE_128B layout (16-byte unit u of row r at u ^ (r % 8)),
+// or BW = 64-byte rows in the SWIZZLE_64B layout (u ^ ((r / 2) % 4)).
+// PARTIAL: only the first `valid` 16-byte units of each row hold data (the
+// last chunk of a convolution whose boxes past K were not loaded); the rest
+// are split as zeros.
+template <bool TF32, bool FINITE, int NT, int BW = 128, bool PARTIAL = false>
 __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* hi_plane,
-                                                 uint8_t* lo_plane, int t, float sf) {
+                                                 uint8_t* lo_plane, int t, float sf, int valid = 0) {
   constexpr int EPG = TF32 ? 4 : 8;   // elements per 16-byte output group
-  constexpr int BOX = 128 * 128;
+  constexpr int UPB = BW / 16;        // 16-byte units per box row
+  constexpr int BOXB = 128 * BW;      // bytes of one box
+  static_assert(BW == 128 || BW == 64, "box width");
 #pragma unroll 1
   for (int r = t; r < 128; r += NT) {
+    const int sw = BW == 128 ? (r & 7) : ((r >> 1) & 3);
     float x[8][EPG];
 #pragma unroll
     for (int g = 0; g < 8; ++g)
 #pragma unroll
       for (int h = 0; h < EPG / 4; ++h) {
         const int j = g * (EPG / 4) + h;   // 16-byte unit of the row
-        const float4 v = *reinterpret_cast<const float4*>(sbuf + (j >> 3) * BOX + r * 128 +
-                                                          (((j & 7) ^ (r & 7)) << 4));
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (!PARTIAL || j < valid)
+          v = *reinterpret_cast<const float4*>(sbuf + (j / UPB) * BOXB + r * BW + (((j % UPB) ^ sw) << 4));
         x[g][4 * h] = v.x, x[g][4 * h + 1] = v.y, x[g][4 * h + 2] = v.z, x[g][4 * h + 3] = v.w;
       }
 #pragma unroll
@@ -299,7 +310,10 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
   }
 }
 
-template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2>
+// FBW (fused variant): row bytes of the staged boxes of A, 128, or 64 for a
+// convolution staged in 16-channel im2col boxes (its own instantiation, so
+// that the 128-byte path keeps its registers).
+template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   using Cfg = TcCfg<BN, TF32, FUSED, NP>;
   constexpr int STAGES = Cfg::STAGES;
@@ -414,22 +428,35 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           bool prog = false;
           if (aq.have && mbar_test_wait(stg_empty_bar(aslot), aph ^ 1u)) {
             const uint32_t fb = stg_full_bar(aslot);
-            mbar_arrive_expect_tx(fb, Cfg::STG_BYTES);
             if (fa.conv) {
               // patch-matrix boxes: 128 output pixels from the tile's first,
-              // 32 channels of one tap (the host checked C % (32 * boxes) == 0)
+              // box_c channels of one tap (the host checked C % box_c == 0);
+              // output (h, w) starts at input (h - (R-1)/2, w - (S-1)/2) and
+              // tap (r, s) = (tap / S, tap % S) adds its offsets.  Boxes of
+              // a last, partial chunk that lie past K are not loaded: the
+              // split warps zero those units.
               const int hw = fa.H * fa.W;
               const int p0 = aq.w.tm * 128;
               const int n0 = p0 / hw, rem = p0 - n0 * hw;
               const int h0 = rem / fa.W, w0 = rem - h0 * fa.W;
+              constexpr int BC = FBW / 4;                       // channels per box
+              constexpr int BOXB = 128 * FBW;                   // bytes of one box
+              constexpr int NBOX = Cfg::STG_ROW / FBW;
+              const int kc0 = aq.c * Cfg::BK;
+              // (32-channel boxes: the host chose them only when K has no partial chunk)
+              const int nval = FBW == 128 ? NBOX : min(NBOX, (fa.K - kc0) / BC);
+              mbar_arrive_expect_tx(fb, nval * BOXB);
 #pragma unroll
-              for (int h = 0; h < Cfg::STG_ROW / 128; ++h) {
-                const int k0 = aq.c * Cfg::BK + 32 * h;
+              for (int h = 0; h < NBOX; ++h) {
+                if (h >= nval) break;
+                const int k0 = kc0 + BC * h;
                 const int tap = k0 / fa.C, c0 = k0 - tap * fa.C;
-                tma_load_im2col_4d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, c0, w0 - 1, h0 - 1, n0,
-                                   static_cast<uint16_t>(tap % 3), static_cast<uint16_t>(tap / 3));
+                const int tr = tap / fa.S, ts = tap - tr * fa.S;
+                tma_load_im2col_4d(stg0 + aslot * Cfg::STG_BYTES + h * BOXB, mA, fb, c0, w0 - fa.S / 2,
+                                   h0 - fa.R / 2, n0, static_cast<uint16_t>(ts), static_cast<uint16_t>(tr));
               }
             } else {
+              mbar_arrive_expect_tx(fb, Cfg::STG_BYTES);
 #pragma unroll
               for (int h = 0; h < Cfg::STG_ROW / 128; ++h)
                 tma_load_3d(stg0 + aslot * Cfg::STG_BYTES + h * BOX, mA, fb, aq.c * Cfg::BK + 32 * h,
@@ -825,9 +852,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       const FusedA src = sc.srcA(fc.w.prob);
       const int64_t kbase = static_cast<int64_t>(fc.c) * Cfg::BK;
       if (src.conv) {
-        // Patch-matrix gather of a 3x3 convolution: column k = (tap, c),
-        // tap = 3 r + s; row = output pixel (n, h, w) reads the input pixel
-        // (n, h + r - 1, w + s - 1), zero outside.  C % 4 == 0, so a 16-byte
+        // Patch-matrix gather of an R x S convolution: column k = (tap, c),
+        // tap = S r + s; row = output pixel (n, h, w) reads the input pixel
+        // (n, h + r - (R-1)/2, w + s - (S-1)/2), zero outside.  C % 4 == 0, so a 16-byte
         // unit is four channels of one tap.  With SPLIT_THREADS a multiple of
         // UPR, this thread's unit j is fixed and its rows step by RS pixels.
         static_assert(Cfg::SPLIT_THREADS % UPR == 0, "unit mapping");
@@ -837,7 +864,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         const bool kin = k < src.K;
         const int tap = kin ? static_cast<int>(k / src.C) : 0;
         const int c = static_cast<int>(k - static_cast<int64_t>(tap) * src.C);
-        const int dr = tap / 3 - 1, ds = tap % 3 - 1;
+        const int dr = tap / src.S - src.R / 2, ds = tap % src.S - src.S / 2;
         const int hw = src.H * src.W;
         int64_t pix = static_cast<int64_t>(fc.w.tm) * 128 + ct / UPR;
         int n = static_cast<int>(pix / hw);
@@ -887,12 +914,14 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     uint32_t stage = 0, phase = 0, slot = 0, sphase = 0;
     unsigned amax = 0;
     int last_prob = -1, last_tm = -1;
+    int kdata = 0;                    // 16-channel boxes: K (boxes past it are not loaded)
     while (sc_.have) {
       if (sc_.w.prob != last_prob || sc_.w.tm != last_tm) {
         const FusedA sa = sc.srcA(sc_.w.prob);
         amax = sa.amaxA[sc_.w.tm * sa.amax_stride];
         last_prob = sc_.w.prob;
         last_tm = sc_.w.tm;
+        kdata = sa.K;
       }
       // lane 0 waits for the warp; __syncwarp orders its acquire before the
       // other lanes' accesses
@@ -907,10 +936,18 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       const uint8_t* sbuf = stg_gen + slot * Cfg::STG_BYTES;
       // one branch for the whole chunk, so that the eight groups of a row
       // form one straight-line block the compiler can interleave
-      if (finite)
-        fused_split_rows<TF32, true, Cfg::SPLIT_THREADS>(sbuf, hi, hi + Cfg::A_PLANE, ct, sf);
-      else
-        fused_split_rows<TF32, false, Cfg::SPLIT_THREADS>(sbuf, hi, hi + Cfg::A_PLANE, ct, sf);
+      constexpr int NT = Cfg::SPLIT_THREADS;
+      uint8_t* lo = hi + Cfg::A_PLANE;
+      if constexpr (FBW == 64) {
+        const int rest = kdata - sc_.c * Cfg::BK;             // elements of the chunk that were loaded
+        const int valid = rest >= Cfg::BK ? UPR : rest / 4;   // 16-byte units per row
+        if (finite) fused_split_rows<TF32, true, NT, 64, true>(sbuf, hi, lo, ct, sf, valid);
+        else fused_split_rows<TF32, false, NT, 64, true>(sbuf, hi, lo, ct, sf, valid);
+      } else if (finite) {
+        fused_split_rows<TF32, true, NT>(sbuf, hi, lo, ct, sf);
+      } else {
+        fused_split_rows<TF32, false, NT>(sbuf, hi, lo, ct, sf);
+      }
       // every lane fences its writes for the async proxy; after __syncwarp
       // lane 0 arrives for the warp (one arrival per warp)
       fence_proxy_async_smem();
@@ -964,13 +1001,14 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
 }
 
 // Fused variant: tmA maps A itself (FP32, 128-byte-wide boxes of 128 rows)
-// when its rows are 16-byte aligned; otherwise it is unused.
-template <int BN, bool TF32>
+// when its rows are 16-byte aligned, or a convolution's image for im2col
+// loads (FBW = 64: boxes of 16 channels); otherwise it is unused.
+template <int BN, bool TF32, int FBW>
 __global__ void __launch_bounds__(TcCfg<BN, TF32, true>::THREADS, 1)
     tc_gemm_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                          const TcArgs a) {
   SingleSched sc{&tmA, &tmB, &a};
-  tc_gemm_body<BN, TF32, SingleSched, true>(sc);
+  tc_gemm_body<BN, TF32, SingleSched, true, 2, FBW>(sc);
 }
 
 // Split-K fix-up: C = sum_s partial[s] + beta * C, where each partial already
@@ -1038,8 +1076,11 @@ static cudaError_t prepare_variant() {
   if (e != cudaSuccess) return e;
   if (configured_device != dev) {
     if constexpr (FUSED) {
-      e = cudaFuncSetAttribute(tc_gemm_fused_kernel<BN, TF32>,
+      e = cudaFuncSetAttribute(tc_gemm_fused_kernel<BN, TF32, 128>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_gemm_fused_kernel<BN, TF32, 64>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     } else {
       e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                Cfg::SMEM);
@@ -1083,7 +1124,10 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
       using Cfg = TcCfg<BN, TF32, true>;
       cudaError_t e = prepare_variant<BN, TF32, true>();
       if (e != cudaSuccess) return e;
-      e = launch_dependent(tc_gemm_fused_kernel<BN, TF32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      if (a.conv && a.vecA && a.conv_box_c == 16)
+        e = launch_dependent(tc_gemm_fused_kernel<BN, TF32, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      else
+        e = launch_dependent(tc_gemm_fused_kernel<BN, TF32, 128>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
       if (e != cudaSuccess) return e;
     }
   } else {

@@ -103,6 +103,11 @@ def test_conv3x3_plan_argument_validation():
     assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 1, -1, ctypes.byref(h)) == 1
     packed = next(i for i in range(pkg.config_count("bf16x3")) if not pkg.config_get("bf16x3", i)["fused"])
     assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 2, packed, ctypes.byref(h)) == 1
+    # R x S filters: odd sizes 1..11 only; BF16X6 has no fused-split kernel
+    for R, S in [(2, 3), (3, 4), (13, 3), (3, 13), (0, 1), (-1, 3)]:
+        assert lib.gemm_conv_plan_create(1, 4, 4, 4, 8, R, S, 2, -1, ctypes.byref(h)) == 1, (R, S)
+        assert b"filter" in lib.gemm_last_error()
+    assert lib.gemm_conv_plan_create(1, 4, 4, 4, 8, 5, 5, 4, -1, ctypes.byref(h)) == 1
 
 
 def test_transposed_arguments_validated_before_launch():

@@ -1,6 +1,7 @@
-"""Parity of the direct 3x3 convolution (implicit gemm through the
-fused-split kernel) with the convolution oracle, and with the gemm path on an
-explicitly formed patch matrix (same split, same MMAs: bit for bit)."""
+"""Parity of the direct convolution (3x3 and other odd R x S filters;
+implicit gemm through the fused-split kernel) with the convolution oracle,
+and with the gemm path on an explicitly formed patch matrix (same split, same
+MMAs: bit for bit)."""
 from __future__ import annotations
 
 import math
@@ -20,8 +21,8 @@ pytestmark = pytest.mark.gpu
 
 def run_conv(x, f, alpha, beta, out0, mode="bf16x3", config_id=None):
     n, H, Wd, C = x.shape
-    K = f.shape[3]
-    plan = pkg.Conv3x3Plan(n, H, Wd, C, K, mode=mode, config_id=config_id)
+    R, S, _, K = f.shape
+    plan = pkg.ConvPlan(n, H, Wd, C, K, R, S, mode=mode, config_id=config_id)
     dx, df, do = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (x, f, out0))
     plan.execute(dx, df, do, alpha, beta)
     torch.cuda.synchronize()
@@ -30,12 +31,13 @@ def run_conv(x, f, alpha, beta, out0, mode="bf16x3", config_id=None):
     return do.cpu().numpy(), cid
 
 
-def patches(x):
+def patches(x, R=3, S=3):
     """Patch matrix, row = output pixel, column = (r, s, c)."""
     n, H, Wd, C = x.shape
-    pad = np.zeros((n, H + 2, Wd + 2, C), np.float32)
-    pad[:, 1:H + 1, 1:Wd + 1] = x
-    cols = [pad[:, r:r + H, s:s + Wd, :].reshape(-1, C) for r in range(3) for s in range(3)]
+    pr, ps = R // 2, S // 2
+    pad = np.zeros((n, H + 2 * pr, Wd + 2 * ps, C), np.float32)
+    pad[:, pr:pr + H, ps:ps + Wd] = x
+    cols = [pad[:, r:r + H, s:s + Wd, :].reshape(-1, C) for r in range(R) for s in range(S)]
     return np.ascontiguousarray(np.concatenate(cols, axis=1))
 
 
@@ -157,3 +159,84 @@ def test_misaligned_image_is_rejected():
     st = lib.gemm_plan_execute(plan._h, 1.0, buf.data_ptr() + 4, f.data_ptr(), 0.0, out.data_ptr(), None)
     assert st == 2   # GEMM_ERR_ALIGNMENT
     plan.destroy()
+
+
+# ------------------------------------------------- other odd filter sizes
+RS = [(1, 1), (5, 5), (7, 3), (3, 9), (11, 11)]
+
+
+@pytest.mark.parametrize("R,S", RS)
+@pytest.mark.parametrize("mode,C", [("bf16x3", 8), ("bf16x3", 64), ("tf32x3", 32), ("bf16x3", 16),
+                                    ("bf16x3", 48), ("tf32x3", 16)])
+def test_rs_filters_match_oracle(R, S, mode, C):
+    """Gathered (C = 8), im2col-staged in 32-channel boxes (whole-tap chunks)
+    and in 16-channel boxes (C = 16, 48: the last chunk is partial when R*S
+    is odd, its boxes past K are not loaded)."""
+    x = W.conv_image(2, 13, 9, C, 160 + R)
+    f = W.conv_filter(C, 20, 161 + S, R=R, S=S)
+    out0 = W.conv_image(2, 13, 9, 20, 162)
+    ref = conv.conv_f64(x, f, 1.5, 0.5, out0)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode)
+    assert oracle.rel_frob(got.reshape(-1, 20), ref.reshape(-1, 20)) <= TOL, (R, S)
+
+
+@pytest.mark.parametrize("R,S,C", [(5, 5, 16), (11, 11, 16), (7, 7, 64)])
+def test_rs_integer_images_bit_exact(R, S, C):
+    x = W.conv_image(1, 15, 12, C, 163, kind="integers")
+    f = W.conv_filter(C, 24, 164, kind="integers", R=R, S=S)
+    out0 = W.conv_image(1, 15, 12, 24, 165, kind="integers")
+    ref = conv.conv_f64(x, f, 1.5, 0.5, out0).astype(np.float32)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("R,S,C", [(5, 5, 64), (7, 3, 64), (11, 11, 64), (5, 5, 12), (5, 5, 16),
+                                   (3, 3, 48), (11, 11, 16), (3, 3, 32)])
+def test_rs_equals_gemm_on_patch_matrix(R, S, C):
+    x = W.conv_image(2, 9, 11, C, 166)
+    f = W.conv_filter(C, 40, 167, R=R, S=S)
+    out0 = W.conv_image(2, 9, 11, 40, 168)
+    P = patches(x, R, S)
+    M, Kd, K = P.shape[0], P.shape[1], 40
+    dP, dB = torch.from_numpy(P).cuda(), torch.from_numpy(f.reshape(Kd, K).copy()).cuda()
+    for cid in fused_ids("bf16x3", group_m=16, kb=4)[::4]:
+        got, _ = run_conv(x, f, 1.0, -0.5, out0, config_id=cid)
+        dC = torch.from_numpy(out0.reshape(-1, K).copy()).cuda()
+        plan = pkg.Plan(M, K, Kd, mode="bf16x3", config_id=cid)
+        plan.execute(dP, dB, dC, 1.0, -0.5)
+        torch.cuda.synchronize()
+        plan.destroy()
+        assert np.array_equal(got.reshape(-1, K).view(np.uint32), dC.cpu().numpy().view(np.uint32)), \
+            (R, S, C, pkg.config_get("bf16x3", cid))
+
+
+@pytest.mark.parametrize("R", W.CONV_FILTER_SIZES[::2])
+def test_paper_conv_layer_sampled_pixels(R):
+    """The paper's Conv layer: 32 images of 512 x 512 x 16, 16 output
+    features, R x R filters; sampled pixels including image corners."""
+    n, H, Wd, C, K = W.CONV_PAPER_LAYER
+    x = W.conv_image(n, H, Wd, C, 170)
+    f = W.conv_filter(C, K, 171, R=R, S=R)
+    got, _ = run_conv(x, f, 1.0, 0.0, np.zeros((n, H, Wd, K), np.float32))
+    rng = np.random.default_rng(R)
+    hw = H * Wd
+    pix = sorted(set(rng.choice(n * hw, 64, replace=False).tolist()) |
+                 {0, Wd - 1, (H - 1) * Wd, hw - 1, (n - 1) * hw, n * hw - 1})
+    ref = conv.conv_pixels_f64(pix, x, f)
+    assert oracle.rel_frob(got.reshape(-1, K)[pix], ref) <= TOL, R
+
+
+@pytest.mark.parametrize("mode,C,R", [("bf16x3", 16, 3), ("bf16x3", 48, 5), ("tf32x3", 16, 3), ("bf16x3", 8, 3)])
+def test_infinite_pixel_reaches_only_its_windows(mode, C, R):
+    """An Inf pixel makes exactly the outputs whose window holds it
+    non-finite: the unloaded part of a partial last chunk is split as zeros,
+    never as pixels of taps past the filter."""
+    x = W.conv_image(1, 12, 10, C, 180)
+    x[0, 5, 5, 3] = np.inf
+    f = W.conv_filter(C, 16, 181, R=R, S=R)
+    ref = conv.conv_f64(x, f).reshape(-1, 16)
+    got, _ = run_conv(x, f, 1.0, 0.0, np.zeros((1, 12, 10, 16), np.float32), mode)
+    got = got.reshape(-1, 16)
+    assert np.array_equal(np.isfinite(got), np.isfinite(ref))
+    rows = np.isfinite(ref).all(axis=1)
+    assert rows.sum() > 0 and oracle.rel_frob(got[rows], ref[rows]) <= TOL
