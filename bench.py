@@ -250,8 +250,8 @@ def other_workloads(model_path: str | None):
     the square sweep in every mode, the conv-as-gemm shapes with the
     heuristic, the cost model's pick, the exhaustive best and the best packed
     and fused-split configurations, the same layers as direct 3x3
-    convolutions, and the 512-problem grouped gemm replayed from its CUDA
-    graph."""
+    convolutions, the paper's Conv layer with filters 3x3 to 11x11, and the
+    512-problem grouped gemm replayed from its CUDA graph."""
     import torch
     import paper_1804_10694_gb300 as pkg
     import workloads as W
@@ -342,6 +342,25 @@ def other_workloads(model_path: str | None):
         res["best"] = best
         out["conv_direct"][f"{nb}x{H}x{Wd}x{Ci}->{Ko}"] = res
         del x, f, o
+    # the paper's Conv benchmark (32 images of 512 x 512 x 16, 16 output
+    # features) and a 64-channel layer, filters 3x3 .. 11x11 (default plans)
+    out["conv_filters"] = {}
+    for (nb, H, Wd, Ci, Ko) in (W.CONV_PAPER_LAYER, (8, 256, 256, 64, 64)):
+        x = torch.empty(nb, H, Wd, Ci, device="cuda").uniform_(-1, 1)
+        o = torch.empty(nb, H, Wd, Ko, device="cuda")
+        res = {}
+        for R in W.CONV_FILTER_SIZES:
+            f = torch.empty(R, R, Ci, Ko, device="cuda").uniform_(-1, 1)
+            plan = pkg.ConvPlan(nb, H, Wd, Ci, Ko, R, R)
+            for _ in range(2):
+                plan.execute(x, f, o, 1.0, 0.0)
+            ms = _median_ms(lambda: plan.execute(x, f, o, 1.0, 0.0), 5, stream)
+            flops = 2.0 * nb * H * Wd * Ko * R * R * Ci
+            res[f"{R}x{R}"] = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
+                               "hbm_gbs": round(4.0 * (x.numel() + f.numel() + o.numel()) / (ms * 1e-3) / 1e9, 1)}
+            plan.destroy()
+        out["conv_filters"][f"{nb}x{H}x{Wd}x{Ci}->{Ko}"] = res
+        del x, o
     shapes = W.grouped_shapes()
     As = [torch.empty(m, k, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
     Bs = [torch.empty(k, n, device="cuda").uniform_(-1, 1) for m, n, k in shapes]
