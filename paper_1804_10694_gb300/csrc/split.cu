@@ -555,6 +555,9 @@ __global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem*
                                                            const GroupedPtrs* __restrict__ ptrs,
                                                            const int* __restrict__ prefix_g, int G) {
   __shared__ __align__(16) float tile[64 * kColTilePitch];
+  // the current problem's shape lives in shared memory: built in registers,
+  // it held 128 registers a thread (two CTAs a SM)
+  __shared__ PackShape shape;
   const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   const int per = (total + gridDim.x - 1) / gridDim.x;
@@ -565,8 +568,12 @@ __global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem*
     const int g = find_problem(prefix, G, i);
     const int e = min(iend, prefix[g + 1]);
     const GroupedPtrs& q = ptrs[g];
-    if (q.alpha != 0.0f)   // A and B are not read when alpha == 0 (uniform per CTA)
-      pack_range<PR>(problem_shape(probs[g], q), i - prefix[g], e - prefix[g], tile);
+    if (q.alpha != 0.0f) {   // A and B are not read when alpha == 0 (uniform per CTA)
+      __syncthreads();       // the previous problem's shape is no longer read
+      if (threadIdx.x == 0) shape = problem_shape(probs[g], q);
+      __syncthreads();
+      pack_range<PR>(shape, i - prefix[g], e - prefix[g], tile);
+    }
     i = e;
   }
   griddep_launch_dependents();
