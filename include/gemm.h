@@ -275,9 +275,7 @@ int gemm_costmodel_feature_count(void);
  * log2 split-K; fold length / 8; log2 raster group; log2 tiles; log2(1 +
  * waves); fill of the last wave; padded-work fraction; log2 arithmetic
  * intensity; log2 k-chunks per split; 1 for TF32X3; 1 for a fused
- * configuration.  BF16X6 is described by the features of BF16X3 (same tiles
- * and k-chunks): the model is trained on the three-product modes and ranks
- * the BF16X6 candidates as it ranks their BF16X3 twins. */
+ * configuration; 1 for BF16X6. */
 gemm_status gemm_costmodel_features(int64_t M, int64_t N, int64_t K, gemm_mode mode, int config_id,
                                     int sms, float* out);
 

@@ -18,6 +18,7 @@ feature is written here from its definition, in float64:
   log2 k-chunks per split
   1 for the tf32 mode, else 0
   1 when A is split inside the gemm kernel, else 0
+  1 for the six-product bf16 mode, else 0
 
 A k-chunk is 128 bytes of one row: 64 bf16 or 32 tf32 elements.
 """
@@ -40,7 +41,7 @@ def effective(block_n: int, split_k: int, kb: int, group_m: int, M: int, N: int,
             "chunk": chunk}
 
 
-def features(M: int, N: int, K: int, cfg: dict, tf32: bool, sms: int) -> list[float]:
+def features(M: int, N: int, K: int, cfg: dict, tf32: bool, sms: int, x6: bool = False) -> list[float]:
     e = effective(cfg["block_n"], cfg["split_k"], cfg["kb"], cfg["group_m"], M, N, K, tf32)
     units = e["tiles"] * e["split_k"]
     waves = units / sms
@@ -53,4 +54,4 @@ def features(M: int, N: int, K: int, cfg: dict, tf32: bool, sms: int) -> list[fl
     return [math.log2(M), math.log2(N), math.log2(K), e["bn"] / 128.0, math.log2(e["split_k"]),
             e["kb"] / 8.0, math.log2(e["group_m"]), math.log2(e["tiles"]), math.log2(1 + waves),
             fill, padded, math.log2(ai), math.log2(e["per"]), 1.0 if tf32 else 0.0,
-            1.0 if cfg.get("fused", 0) else 0.0]
+            1.0 if cfg.get("fused", 0) else 0.0, 1.0 if x6 else 0.0]

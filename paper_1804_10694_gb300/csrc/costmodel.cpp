@@ -57,6 +57,7 @@ void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const g
   out[12] = (float)std::log2((double)e.chunks_per_split);
   out[13] = mode == GEMM_MODE_TF32X3 ? 1.0f : 0.0f;
   out[14] = c.fused ? 1.0f : 0.0f;
+  out[15] = mode == GEMM_MODE_BF16X6 ? 1.0f : 0.0f;   // six products per k-step, three planes
 }
 
 namespace {

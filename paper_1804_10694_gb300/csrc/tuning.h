@@ -22,7 +22,7 @@ bool table_lookup(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, flo
 // when no model is loaded).
 gemm_status costmodel_pick(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);
 
-constexpr int kFeatures = 15;
+constexpr int kFeatures = 16;
 constexpr int kHidden = 64;
 // Input features of the cost model for a (shape, configuration) pair.
 void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const gemm_config& c,

@@ -16,7 +16,7 @@ from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
 
-F = 15   # the library's feature count (checked in the host-logic tests)
+F = 16   # the library's feature count (checked in the host-logic tests)
 H = 64
 
 

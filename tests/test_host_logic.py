@@ -19,19 +19,19 @@ SHAPES = [(8192, 8192, 8192), (1060, 1060, 1060), (50176, 64, 576), (12544, 128,
 @pytest.mark.parametrize("mode,tf32", [("bf16x3", False), ("tf32x3", True), ("bf16x6", False)])
 def test_features_match_oracle_restatement(mode, tf32):
     n = pkg.config_count(mode)
-    assert pkg.costmodel_feature_count() == 15
+    assert pkg.costmodel_feature_count() == 16
     for (M, N, K) in SHAPES:
         for cid in range(0, n, 5):
             cfg = pkg.config_get(mode, cid)
             for sms in (152, 148):
                 got = pkg.costmodel_features(M, N, K, mode, cid, sms)
-                ref = np.array(ofeat.features(M, N, K, cfg, tf32, sms))
+                ref = np.array(ofeat.features(M, N, K, cfg, tf32, sms, x6=(mode == "bf16x6")))
                 assert np.allclose(got, ref, rtol=1e-5, atol=1e-5), (M, N, K, cfg, got, ref)
 
 
 def test_features_reject_bad_arguments():
     lib = pkg.load()
-    out = np.zeros(15, np.float32)
+    out = np.zeros(16, np.float32)
     assert lib.gemm_costmodel_features(0, 4, 4, 2, 0, 152, out.ctypes.data) == 1
     assert lib.gemm_costmodel_features(4, 4, 4, 1, 0, 152, out.ctypes.data) == 1   # SIMT
     assert lib.gemm_costmodel_features(4, 4, 4, 2, 10 ** 6, 152, out.ctypes.data) == 1
@@ -41,25 +41,25 @@ def test_costmodel_load_rejects_missing_and_corrupt_files(tmp_path):
     lib = pkg.load()
     assert lib.gemm_costmodel_load(str(tmp_path / "missing.txt").encode()) == 7
     bad = tmp_path / "bad.txt"
-    bad.write_text("gb300-gemm-costmodel 1\nfeatures 15 hidden 64 params 5\n")
+    bad.write_text("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params 5\n")
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
     assert b"malformed" in lib.gemm_last_error()
     bad.write_text("not a model\n")
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
     # truncated theta
-    P = 64 * 15 + 64 + 64 * 64 + 64 + 64 + 1
-    txt = ("gb300-gemm-costmodel 1\nfeatures 15 hidden 64 params %d\nmean %s\nstd %s\n"
-           "target 0 1\ntheta %s\n" % (P, " ".join(["0"] * 15), " ".join(["1"] * 15),
+    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+    txt = ("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params %d\nmean %s\nstd %s\n"
+           "target 0 1\ntheta %s\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16),
                                        " ".join(["0.5"] * (P - 3))))
     bad.write_text(txt)
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
 
 
 def test_costmodel_load_accepts_well_formed_file(tmp_path):
-    P = 64 * 15 + 64 + 64 * 64 + 64 + 64 + 1
+    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
     good = tmp_path / "good.txt"
-    good.write_text("gb300-gemm-costmodel 1\nfeatures 15 hidden 64 params %d\nmean %s\nstd %s\n"
-                    "target -1.5 2\ntheta %s\n" % (P, " ".join(["0"] * 15), " ".join(["1"] * 15),
+    good.write_text("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params %d\nmean %s\nstd %s\n"
+                    "target -1.5 2\ntheta %s\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16),
                                                    " ".join(["0.01"] * P)))
     assert pkg.load().gemm_costmodel_load(str(good).encode()) == 0
 
@@ -115,9 +115,9 @@ def test_training_shapes_bounded():
 def test_costmodel_ensemble_file_format(tmp_path):
     """Version 2 files hold `members` networks (one theta line each); a
     missing member or a bad member count is rejected."""
-    P = 64 * 15 + 64 + 64 * 64 + 64 + 64 + 1
-    head = ("gb300-gemm-costmodel 2\nfeatures 15 hidden 64 params %d members %%d\nmean %s\nstd %s\n"
-            "target -1.5 2\n" % (P, " ".join(["0"] * 15), " ".join(["1"] * 15)))
+    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+    head = ("gb300-gemm-costmodel 2\nfeatures 16 hidden 64 params %d members %%d\nmean %s\nstd %s\n"
+            "target -1.5 2\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16)))
     theta = "theta %s\n" % " ".join(["0.01"] * P)
     lib = pkg.load()
     f = tmp_path / "m.txt"
