@@ -86,17 +86,15 @@ cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const
 cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t ldc, cudaStream_t s);
 
 // ------------------------------------------------------------ split / pack
-// Both operands in two launches: a first pass writing the unscaled hi/lo
-// planes and the per-block max |x| bit patterns (A: blocks of 128 rows, into
-// amaxA; B, transposed: blocks of 128 columns, into amaxB), then a pass that
-// re-splits the blocks needing a power-of-two scale.  The block maxima must
-// be zero on entry.  A (or B) may be null to pack only the other operand.
+// Packing (split.cu), both operands in one launch: the unscaled planes and
+// the per-block max |x| bit patterns (A: blocks of 128 rows, into amaxA; B,
+// transposed: blocks of 128 columns, into amaxB); amax* hold the block
+// maxima and cnt* one counter per block (items done), both zero on entry.
+// The CTA that completes a block re-splits it with its exponent when the
+// block lies outside the safe range.  A (or B) may be null to pack only the
+// other operand.
 // A: M x K (lda) -> planesA [P][M][pitch];  B: K x N (ldb) -> planesB [P][N][pitch],
 // P = prec_planes(prec).
-// Packing (split.cu), one launch.  amax* hold the block maxima and cnt*
-// one counter per block (items done); both must be zero on entry.  The CTA
-// that completes a block re-splits it with its exponent when the block lies
-// outside the safe range.
 // transA: A is stored K x M (lda >= M); transB: B is stored N x K (ldb >= K).
 cudaError_t pack_launch(Prec prec, const float* A, int64_t M, int64_t K, int64_t lda, const float* B,
                         int64_t N, int64_t ldb, unsigned* amaxA, unsigned* amaxB, unsigned* cntA,
