@@ -109,11 +109,11 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
 /* C = alpha * op(A) op(B) + beta * C with BLAS-style transposes: op(A) is
  * M x K and op(B) is K x N.  transA != 0: A is stored K x M row-major
  * (lda >= M), op(A) = A^T; transB != 0: B is stored N x K (ldb >= K),
- * op(B) = B^T.  The packing pass reads each layout directly (no transposed
- * copy), so the planes and the results are bit-identical to the
- * untransposed call on the transposed matrices.  Tensor-core modes only
- * (F32_SIMT with a transpose is INVALID_ARG); a fused-split configuration
- * chosen for a transposed A runs as its packed twin. */
+ * op(B) = B^T.  The packing pass (tensor-core modes) and the F32_SIMT
+ * kernel's tile loads read each layout directly (no transposed copy), so the
+ * results are bit-identical to the untransposed call on the transposed
+ * matrices; a fused-split configuration chosen for a transposed A runs as
+ * its packed twin. */
 gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
                        const float* A, int64_t lda, const float* B, int64_t ldb, float beta, float* C,
                        int64_t ldc, gemm_mode mode, gemm_select sel, gemm_stream_t stream);

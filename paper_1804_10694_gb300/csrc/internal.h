@@ -79,9 +79,10 @@ cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial,
                                  float* C, int64_t ldc, cudaStream_t s);
 
 // ------------------------------------------------------------ SIMT kernel
+// transA: A stored K x M (lda >= M); transB: B stored N x K (ldb >= K).
 cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                              int64_t lda, const float* B, int64_t ldb, float beta, float* C,
-                             int64_t ldc, cudaStream_t s);
+                             int64_t ldc, cudaStream_t s, bool transA = false, bool transB = false);
 // C = beta * C (K == 0 or alpha == 0), C write-only when beta == 0.
 cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t ldc, cudaStream_t s);
 

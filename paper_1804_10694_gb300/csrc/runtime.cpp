@@ -318,8 +318,6 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   *out = nullptr;
   gemm_status st = validate_shape_t(transA, transB, M, N, K, lda, ldb, ldc);
   if (st != GEMM_OK) return st;
-  if ((transA || transB) && mode == GEMM_MODE_F32_SIMT)
-    return fail(GEMM_ERR_INVALID_ARG, "transposed operands need a tensor-core mode");
   DeviceState* dev;
   int devidx;
   if ((st = device_state(&dev, &devidx)) != GEMM_OK) return st;
@@ -446,7 +444,8 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   }
   if (!A || !B) return fail(GEMM_ERR_INVALID_ARG, "null A or B");
   if (p->mode == GEMM_MODE_F32_SIMT) {
-    if ((e = simt_gemm_launch(M, N, K, alpha, A, p->lda, B, p->ldb, beta, C, p->ldc, s)) != cudaSuccess)
+    if ((e = simt_gemm_launch(M, N, K, alpha, A, p->lda, B, p->ldb, beta, C, p->ldc, s, p->transA,
+                              p->transB)) != cudaSuccess)
       return cuda_fail(e, "simt gemm launch");
     return GEMM_OK;
   }

@@ -7,7 +7,10 @@
 // per thread.  Full tiles (all 128 rows and columns in range, k-slice
 // complete) take unpredicated, vectorised loads when the leading dimensions
 // allow it; partial tiles predicate every access.  The full/partial choice is
-// uniform per CTA, so it introduces no divergence.
+// uniform per CTA, so it introduces no divergence.  TA / TB: A stored K x M
+// (lda >= M), B stored N x K (ldb >= K); the slices are loaded along the
+// stored rows and land in the same shared-memory layout, so the arithmetic
+// (and its order) is that of the untransposed kernel.
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -23,48 +26,61 @@ struct Frag {
   float b[4];
 };
 
-// Load the A slice (128 rows x 8 k) and B slice (8 k x 128 cols) of one k-step
-// into registers.  Thread t loads A row t/2, k (t%2)*4..+3 and B k-row t/32,
-// columns (t%32)*4..+3.
+// Four consecutive floats of a stored row (row r, columns c..c+3), in range
+// when r < rows and c + i < cols.
 template <bool FULL, bool VEC>
+__device__ __forceinline__ void load4(float (&v)[4], const float* __restrict__ X, int64_t ld,
+                                      int64_t r, int64_t c, int64_t rows, int64_t cols) {
+  if (FULL && VEC) {
+    const float4 q = *reinterpret_cast<const float4*>(X + r * ld + c);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else if (FULL) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = X[r * ld + c + i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = (r < rows && c + i < cols) ? X[r * ld + c + i] : 0.0f;
+  }
+}
+
+// Load the A slice (128 rows x 8 k) and B slice (8 k x 128 cols) of one k-step
+// into registers, along the stored rows.  A row-major: thread t loads row t/2,
+// k (t%2)*4..+3; A stored K x M: k-row t/32, m (t%32)*4..+3.  B row-major:
+// k-row t/32, columns (t%32)*4..+3; B stored N x K: column t/2, k (t%2)*4..+3.
+template <bool FULL, bool VEC, bool TA, bool TB>
 __device__ __forceinline__ void load_slice(Frag& f, const float* __restrict__ A, int64_t lda,
                                            const float* __restrict__ B, int64_t ldb, int64_t M,
                                            int64_t N, int64_t K, int64_t m0, int64_t n0,
                                            int64_t k0, int tid) {
-  const int ar = tid >> 1, ak = (tid & 1) * 4;
-  const int bk = tid >> 5, bn = (tid & 31) * 4;
-  const int64_t grow = m0 + ar, gka = k0 + ak;
-  const int64_t gkb = k0 + bk, gcol = n0 + bn;
-  if (FULL && VEC) {
-    const float4 va = *reinterpret_cast<const float4*>(A + grow * lda + gka);
-    f.a[0] = va.x, f.a[1] = va.y, f.a[2] = va.z, f.a[3] = va.w;
-    const float4 vb = *reinterpret_cast<const float4*>(B + gkb * ldb + gcol);
-    f.b[0] = vb.x, f.b[1] = vb.y, f.b[2] = vb.z, f.b[3] = vb.w;
-  } else if (FULL) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      f.a[i] = A[grow * lda + gka + i];
-      f.b[i] = B[gkb * ldb + gcol + i];
-    }
+  const int hi2 = tid >> 1, lo2 = (tid & 1) * 4;
+  const int hi32 = tid >> 5, lo32 = (tid & 31) * 4;
+  if (TA) load4<FULL, VEC>(f.a, A, lda, k0 + hi32, m0 + lo32, K, M);
+  else load4<FULL, VEC>(f.a, A, lda, m0 + hi2, k0 + lo2, M, K);
+  if (TB) load4<FULL, VEC>(f.b, B, ldb, n0 + hi2, k0 + lo2, N, K);
+  else load4<FULL, VEC>(f.b, B, ldb, k0 + hi32, n0 + lo32, K, N);
+}
+
+// Into shared memory, As[k][m] and Bs[k][n] whatever the stored layout.
+template <bool TA, bool TB>
+__device__ __forceinline__ void store_slice(const Frag& f, float (*As)[BM], float (*Bs)[BN],
+                                            int tid) {
+  const int hi2 = tid >> 1, lo2 = (tid & 1) * 4;
+  const int hi32 = tid >> 5, lo32 = (tid & 31) * 4;
+  if (TA) {
+    *reinterpret_cast<float4*>(&As[hi32][lo32]) = make_float4(f.a[0], f.a[1], f.a[2], f.a[3]);
   } else {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      f.a[i] = (grow < M && gka + i < K) ? A[grow * lda + gka + i] : 0.0f;
-      f.b[i] = (gkb < K && gcol + i < N) ? B[gkb * ldb + gcol + i] : 0.0f;
-    }
+    for (int i = 0; i < 4; ++i) As[lo2 + i][hi2] = f.a[i];
+  }
+  if (TB) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Bs[lo2 + i][hi2] = f.b[i];
+  } else {
+    *reinterpret_cast<float4*>(&Bs[hi32][lo32]) = make_float4(f.b[0], f.b[1], f.b[2], f.b[3]);
   }
 }
 
-__device__ __forceinline__ void store_slice(const Frag& f, float (*As)[BM], float (*Bs)[BN],
-                                            int tid) {
-  const int ar = tid >> 1, ak = (tid & 1) * 4;
-  const int bk = tid >> 5, bn = (tid & 31) * 4;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) As[ak + i][ar] = f.a[i];
-  *reinterpret_cast<float4*>(&Bs[bk][bn]) = make_float4(f.b[0], f.b[1], f.b[2], f.b[3]);
-}
-
-template <bool FULL, bool VEC>
+template <bool FULL, bool VEC, bool TA, bool TB>
 __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, float alpha,
                                           const float* __restrict__ A, int64_t lda,
                                           const float* __restrict__ B, int64_t ldb, float beta,
@@ -84,10 +100,10 @@ __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, float
   const int64_t ksteps = (K + BKs - 1) / BKs;
   Frag f;
   if (kfull > 0)
-    load_slice<FULL, VEC>(f, A, lda, B, ldb, M, N, K, m0, n0, 0, tid);
+    load_slice<FULL, VEC, TA, TB>(f, A, lda, B, ldb, M, N, K, m0, n0, 0, tid);
   else
-    load_slice<false, false>(f, A, lda, B, ldb, M, N, K, m0, n0, 0, tid);
-  store_slice(f, As[0], Bs[0], tid);
+    load_slice<false, false, TA, TB>(f, A, lda, B, ldb, M, N, K, m0, n0, 0, tid);
+  store_slice<TA, TB>(f, As[0], Bs[0], tid);
   __syncthreads();
 
   for (int64_t ks = 0; ks < ksteps; ++ks) {
@@ -95,9 +111,9 @@ __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, float
     const bool has_next = ks + 1 < ksteps;
     if (has_next) {
       if (ks + 1 < kfull)
-        load_slice<FULL, VEC>(f, A, lda, B, ldb, M, N, K, m0, n0, (ks + 1) * BKs, tid);
+        load_slice<FULL, VEC, TA, TB>(f, A, lda, B, ldb, M, N, K, m0, n0, (ks + 1) * BKs, tid);
       else
-        load_slice<false, false>(f, A, lda, B, ldb, M, N, K, m0, n0, (ks + 1) * BKs, tid);
+        load_slice<false, false, TA, TB>(f, A, lda, B, ldb, M, N, K, m0, n0, (ks + 1) * BKs, tid);
     }
 #pragma unroll
     for (int k = 0; k < BKs; ++k) {
@@ -113,7 +129,7 @@ __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, float
         for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
     }
     if (has_next) {
-      store_slice(f, As[cur ^ 1], Bs[cur ^ 1], tid);
+      store_slice<TA, TB>(f, As[cur ^ 1], Bs[cur ^ 1], tid);
       __syncthreads();
     }
   }
@@ -152,7 +168,7 @@ __device__ __forceinline__ void gemm_tile(int64_t M, int64_t N, int64_t K, float
   }
 }
 
-template <bool VEC>
+template <bool VEC, bool TA, bool TB>
 __global__ void __launch_bounds__(THREADS) simt_gemm_kernel(int64_t M, int64_t N, int64_t K,
                                                             float alpha, const float* A,
                                                             int64_t lda, const float* B,
@@ -161,9 +177,20 @@ __global__ void __launch_bounds__(THREADS) simt_gemm_kernel(int64_t M, int64_t N
   const int64_t m0 = static_cast<int64_t>(blockIdx.y) * BM;
   const int64_t n0 = static_cast<int64_t>(blockIdx.x) * BN;
   if (m0 + BM <= M && n0 + BN <= N)
-    gemm_tile<true, VEC>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, m0, n0, cvec);
+    gemm_tile<true, VEC, TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, m0, n0, cvec);
   else
-    gemm_tile<false, VEC>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, m0, n0, cvec);
+    gemm_tile<false, VEC, TA, TB>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, m0, n0, cvec);
+}
+
+template <bool TA, bool TB>
+cudaError_t simt_launch(dim3 grid, bool vec, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                        bool cvec, cudaStream_t s) {
+  if (vec)
+    simt_gemm_kernel<true, TA, TB><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec);
+  else
+    simt_gemm_kernel<false, TA, TB><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec);
+  return cudaGetLastError();
 }
 
 __global__ void scale_c_kernel(int64_t M, int64_t N, float beta, float* C, int64_t ldc) {
@@ -179,18 +206,17 @@ __global__ void scale_c_kernel(int64_t M, int64_t N, float beta, float* C, int64
 
 cudaError_t simt_gemm_launch(int64_t M, int64_t N, int64_t K, float alpha, const float* A,
                              int64_t lda, const float* B, int64_t ldb, float beta, float* C,
-                             int64_t ldc, cudaStream_t s) {
+                             int64_t ldc, cudaStream_t s, bool transA, bool transB) {
   const dim3 grid(static_cast<unsigned>((N + BN - 1) / BN), static_cast<unsigned>((M + BM - 1) / BM));
   if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
   const bool vec = (lda % 4 == 0) && (ldb % 4 == 0) &&
                    (reinterpret_cast<uintptr_t>(A) % 16 == 0) &&
                    (reinterpret_cast<uintptr_t>(B) % 16 == 0);
   const bool cvec = (ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0);
-  if (vec)
-    simt_gemm_kernel<true><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec);
-  else
-    simt_gemm_kernel<false><<<grid, THREADS, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec);
-  return cudaGetLastError();
+  if (transA && transB) return simt_launch<true, true>(grid, vec, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec, s);
+  if (transA) return simt_launch<true, false>(grid, vec, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec, s);
+  if (transB) return simt_launch<false, true>(grid, vec, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec, s);
+  return simt_launch<false, false>(grid, vec, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cvec, s);
 }
 
 cudaError_t scale_c_launch(int64_t M, int64_t N, float beta, float* C, int64_t ldc, cudaStream_t s) {

@@ -114,7 +114,8 @@ def test_transposed_arguments_validated_before_launch():
     import ctypes
     lib = pkg.load()
     h = ctypes.c_void_p()
-    # transA: lda must cover M; transB: ldb must cover K; SIMT has no transposed path
+    # transA: lda must cover M; transB: ldb must cover K (every mode, SIMT included)
     assert lib.gemm_plan_create_t(1, 0, 100, 50, 40, 99, 50, 50, 2, 0, ctypes.byref(h)) == 1
     assert lib.gemm_plan_create_t(0, 1, 100, 50, 40, 40, 39, 50, 2, 0, ctypes.byref(h)) == 1
-    assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 100, 40, 50, 1, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 99, 40, 50, 1, 0, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 100, 39, 50, 1, 0, ctypes.byref(h)) == 1

@@ -25,7 +25,7 @@ def run_t(ta, tb, mode, M, N, K, alpha, As, Bs, beta, C0, select="default"):
     return dC.cpu().numpy()
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6", "simt"])
 @pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
 def test_transposes_match_untransposed_bitwise(mode, ta, tb):
     M, N, K = 333, 270, 515
@@ -41,7 +41,7 @@ def test_transposes_match_untransposed_bitwise(mode, ta, tb):
     check_padding_untouched(C0, got, N)
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6", "simt"])
 def test_transposed_integer_inputs_bit_exact(mode):
     M, N, K = 300, 200, 700
     A, B, C0 = W.integers(M, K, 204), W.integers(K, N, 205), W.integers(M, N, 206)
@@ -76,3 +76,17 @@ def test_transposed_plan_and_model_selection():
         torch.cuda.synchronize()
         assert oracle.rel_frob(dC.cpu().numpy(), ref) <= TOL
         plan.destroy()
+
+
+@pytest.mark.parametrize("ta,tb", [(1, 0), (0, 1), (1, 1)])
+def test_simt_transposes_on_ragged_and_unaligned_shapes(ta, tb):
+    """The SIMT kernel's partial tiles and scalar loads with transposed
+    layouts: odd leading dimensions, edges in every dimension."""
+    for (M, N, K) in [(129, 131, 37), (1, 300, 9), (257, 1, 130), (5, 7, 3)]:
+        A, B = W.uniform(M, K, 220 + M), W.uniform(K, N, 221 + N)
+        C0 = W.uniform(M, N, 222, ld=N + 1)
+        As = W._with_ld(np.ascontiguousarray(A.T), M + 1, np.nan) if ta else A
+        Bs = W._with_ld(np.ascontiguousarray(B.T), K + 3, np.nan) if tb else B
+        got = run_t(ta, tb, "simt", M, N, K, 1.5, As, Bs, -0.5, C0)
+        assert oracle.rel_frob(got, oracle.gemm_f64(M, N, K, 1.5, A, B, -0.5, C0)) <= TOL, (M, N, K)
+        check_padding_untouched(C0, got, N)
