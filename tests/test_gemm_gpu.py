@@ -306,3 +306,27 @@ def test_host_buffer_pipelined_panels(mode, alpha, beta):
                            pkg.MODES[mode], None)
     assert st == 0, lib.gemm_last_error()
     assert np.array_equal(hC.numpy(), oracle.gemm_f64(M, N, K, alpha, Ai, Bi, beta, Ci).astype(np.float32))
+
+
+# ------------------------------------------------------- extreme shapes
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6", "simt"])
+def test_tall_skinny_many_row_tiles(mode):
+    """M of 2^21 + 37 rows (16385 row tiles, a ragged last one), N and K
+    just past a tile edge: checked on sampled rows."""
+    M, N, K = (1 << 21) + 37, 65, 129
+    A, B, C0 = W.uniform(M, K, 301), W.uniform(K, N, 302), W.uniform(M, N, 303)
+    got = run_gemm(mode, M, N, K, 1.5, A, B, 0.5, C0)
+    rows = sample_rows(M, 40, seed=5)
+    ref = oracle.gemm_f64_rows(rows, N, K, 1.5, A, B, 0.5, C0)
+    assert rel_err_rows(got, rows, ref, N) <= TOL
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+def test_long_k(mode):
+    """K = 2^17 + 5: 2049 k-chunks of bf16 (4097 of tf32), folded from TMEM
+    every few chunks; a ragged last chunk."""
+    M, N, K = 130, 131, (1 << 17) + 5
+    A, B, C0 = W.uniform(M, K, 304), W.uniform(K, N, 305), W.uniform(M, N, 306)
+    ref = oracle.gemm_f64(M, N, K, 1.0, A, B, -1.0, C0)
+    got = run_gemm(mode, M, N, K, 1.0, A, B, -1.0, C0)
+    assert oracle.rel_frob(got, ref) <= TOL
