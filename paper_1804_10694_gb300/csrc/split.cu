@@ -181,13 +181,19 @@ __device__ __forceinline__ unsigned split_rows_tile(const float* __restrict__ X,
 
 // ---------------------------------------------------- B: transposing split
 // One CTA handles a 64 (k) x 128 (n) tile through the shared `tile`
-// (64 x kColTilePitch floats, declared once by the kernel).  Load phase: warp w reads k-rows
-// w + 8i (i < 8), each lane a float4 of n (512 contiguous bytes per warp and
-// row); all eight loads are issued first, then stored to a shared tile whose
-// 132-float pitch keeps both phases free of bank conflicts.  Write phase:
-// thread t writes 32 consecutive k of output row n = t % 128 (k half t / 128).
+// (64 x 128 floats, declared once by the kernel).  Element (k, n) sits at
+// tile[k * 128 + (n ^ col_swizzle(k))]: the XOR moves whole 4-float groups,
+// so that both phases are free of bank conflicts (bf16; 2-way for tf32).
+// Load phase: warp w reads k-rows w + 8i (i < 8), each lane a float4 of n
+// (512 contiguous bytes per warp and row); all eight loads are issued first,
+// then stored to the tile as float4.  Write phase: output row n's 64-k
+// segment of a plane is 128 bytes (bf16) or 256 (tf32); UPR = 8 or 16
+// threads write it as whole 16-byte units, so that a warp stores complete
+// rows (4 or 2 per instruction) instead of one 16-byte piece of 32 rows.
 // The 128 columns are one 128-column block.
-constexpr int kColTilePitch = 132;
+constexpr int kColTileFloats = 64 * 128;
+
+__device__ __forceinline__ int col_swizzle(int k) { return ((k >> 3) & 7) << 2; }
 
 template <Prec PR, Pass PASS>
 __device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X, int64_t K, int64_t N,
@@ -218,7 +224,8 @@ __device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X,
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      *reinterpret_cast<float4*>(&tile[(w + 8 * i) * kColTilePitch + 4 * lane]) = v[i];
+      const int kr = w + 8 * i;
+      *reinterpret_cast<float4*>(&tile[kr * 128 + ((4 * lane) ^ col_swizzle(kr))]) = v[i];
       if (PASS == kFirst) {
         m = max(m, abs_bits(v[i].x));
         m = max(m, abs_bits(v[i].y));
@@ -228,58 +235,54 @@ __device__ __forceinline__ unsigned split_cols_tile(const float* __restrict__ X,
     }
   }
   __syncthreads();
-  const int nl = threadIdx.x & 127;
-  const int kl = (threadIdx.x >> 7) * 32;
-  const int64_t n = n0 + nl;
-  if (n < N && k0 + kl < pitch) {
+  constexpr int VPU = TF32 ? 4 : 8;          // values per 16-byte output unit
+  constexpr int UPR = 64 / VPU;              // threads per output row segment
+  constexpr int RPP = 256 / UPR;             // output rows per pass
+  const int kl = (threadIdx.x % UPR) * VPU;  // first k of this thread's unit (tile row)
+  const int rloc = threadIdx.x / UPR;
+  const bool kin = k0 + kl < pitch;          // pitch is a multiple of VPU: units are whole
+#pragma unroll 1
+  for (int nl = rloc; nl < 128; nl += RPP) {
+    const int64_t n = n0 + nl;
+    if (n >= N || !kin) continue;
     const float sc = PASS == kFirst ? 1.0f : pow2f(-block_exponent(amax[n / kScaleBlock]));
-    const int64_t obase = n * pitch + k0 + kl;
-    const int64_t avail = pitch - (k0 + kl);   // multiple of 8 (bf16) or 4 (tf32)
+    float x[VPU];
+#pragma unroll
+    for (int i = 0; i < VPU; ++i) x[i] = tile[(kl + i) * 128 + (nl ^ col_swizzle(kl + i))] * sc;
+    const int64_t o = n * pitch + k0 + kl;
     if (TF32) {
       float* P = static_cast<float*>(planes);
-#pragma unroll
-      for (int g = 0; g < 8; ++g) {
-        if (4 * g >= avail) break;
-        float4 h, l;
-        split_tf32(tile[(kl + 4 * g + 0) * kColTilePitch + nl] * sc, h.x, l.x);
-        split_tf32(tile[(kl + 4 * g + 1) * kColTilePitch + nl] * sc, h.y, l.y);
-        split_tf32(tile[(kl + 4 * g + 2) * kColTilePitch + nl] * sc, h.z, l.z);
-        split_tf32(tile[(kl + 4 * g + 3) * kColTilePitch + nl] * sc, h.w, l.w);
-        *reinterpret_cast<float4*>(P + obase + 4 * g) = h;
-        *reinterpret_cast<float4*>(P + plane + obase + 4 * g) = l;
-      }
+      float4 h, l;
+      split_tf32(x[0], h.x, l.x);
+      split_tf32(x[1], h.y, l.y);
+      split_tf32(x[2], h.z, l.z);
+      split_tf32(x[3], h.w, l.w);
+      *reinterpret_cast<float4*>(P + o) = h;
+      *reinterpret_cast<float4*>(P + plane + o) = l;
     } else if (PR == Prec::BF16X6) {
       __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+      __align__(16) __nv_bfloat16 h[8], mi[8], l[8];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        if (8 * g >= avail) break;
-        __align__(16) __nv_bfloat16 h[8], mi[8], l[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const Split3Bf16 s = split3_bf16(tile[(kl + 8 * g + i) * kColTilePitch + nl] * sc);
-          h[i] = s.hi;
-          mi[i] = s.mid;
-          l[i] = s.lo;
-        }
-        *reinterpret_cast<uint4*>(P + obase + 8 * g) = *reinterpret_cast<const uint4*>(h);
-        *reinterpret_cast<uint4*>(P + plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(mi);
-        *reinterpret_cast<uint4*>(P + 2 * plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(l);
+      for (int i = 0; i < 8; ++i) {
+        const Split3Bf16 t = split3_bf16(x[i]);
+        h[i] = t.hi;
+        mi[i] = t.mid;
+        l[i] = t.lo;
       }
+      *reinterpret_cast<uint4*>(P + o) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(P + plane + o) = *reinterpret_cast<const uint4*>(mi);
+      *reinterpret_cast<uint4*>(P + 2 * plane + o) = *reinterpret_cast<const uint4*>(l);
     } else {
       __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+      __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-      for (int g = 0; g < 4; ++g) {
-        if (8 * g >= avail) break;
-        __align__(16) __nv_bfloat16 h[8], l[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const HiLoBf16 s = split_bf16(tile[(kl + 8 * g + i) * kColTilePitch + nl] * sc);
-          h[i] = s.hi;
-          l[i] = s.lo;
-        }
-        *reinterpret_cast<uint4*>(P + obase + 8 * g) = *reinterpret_cast<const uint4*>(h);
-        *reinterpret_cast<uint4*>(P + plane + obase + 8 * g) = *reinterpret_cast<const uint4*>(l);
+      for (int i = 0; i < 8; ++i) {
+        const HiLoBf16 t = split_bf16(x[i]);
+        h[i] = t.hi;
+        l[i] = t.lo;
       }
+      *reinterpret_cast<uint4*>(P + o) = *reinterpret_cast<const uint4*>(h);
+      *reinterpret_cast<uint4*>(P + plane + o) = *reinterpret_cast<const uint4*>(l);
     }
   }
   __syncthreads();   // the tile is reused by the next item of a looping launch
@@ -487,10 +490,11 @@ __device__ __forceinline__ void pack_range(const PackShape& p, int i0, int i1, f
 }
 
 // ------------------------------------------------ single-problem kernels
-// CTA c takes the c-th contiguous share of the items.
+// CTA c takes the c-th contiguous share of the items.  Four CTAs a SM (at
+// most 64 registers a thread).
 template <Prec PR>
-__global__ void __launch_bounds__(256) pack_first_kernel(const PackShape p) {
-  __shared__ __align__(16) float tile[64 * kColTilePitch];
+__global__ void __launch_bounds__(256, 4) pack_first_kernel(const PackShape p) {
+  __shared__ __align__(16) float tile[kColTileFloats];
   const int total = p.items();
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
@@ -502,8 +506,8 @@ __global__ void __launch_bounds__(256) pack_first_kernel(const PackShape p) {
 // then B packed as in pack_first_kernel (p holds B only; a contiguous
 // share of its items per CTA).
 template <Prec PR, int MODE>
-__global__ void __launch_bounds__(256) fused_prep_kernel(const AmaxShape a, const PackShape p) {
-  __shared__ __align__(16) float tile[64 * kColTilePitch];
+__global__ void __launch_bounds__(256, 4) fused_prep_kernel(const AmaxShape a, const PackShape p) {
+  __shared__ __align__(16) float tile[kColTileFloats];
   const int64_t na = amax_items<MODE>(a);
   for (int64_t i = blockIdx.x; i < na; i += gridDim.x) amax_item<MODE>(a, i);
   const int total = p.items();
@@ -551,10 +555,10 @@ __device__ __forceinline__ PackShape problem_shape(const GroupedProblem& g, cons
 }
 
 template <Prec PR>
-__global__ void __launch_bounds__(256) grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
+__global__ void __launch_bounds__(256, 3) grouped_pack_kernel(const GroupedProblem* __restrict__ probs,
                                                            const GroupedPtrs* __restrict__ ptrs,
                                                            const int* __restrict__ prefix_g, int G) {
-  __shared__ __align__(16) float tile[64 * kColTilePitch];
+  __shared__ __align__(16) float tile[kColTileFloats];
   // the current problem's shape lives in shared memory: built in registers,
   // it held 128 registers a thread (two CTAs a SM)
   __shared__ PackShape shape;
