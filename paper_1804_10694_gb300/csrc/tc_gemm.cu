@@ -652,16 +652,20 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
       const Work w = wn;
       if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+      // The unit's epilogue values and block exponents are loaded before its
+      // accumulator is waited for (the pack has completed: every role passed
+      // griddep_wait), and L2 is warmed with the part of C this thread will
+      // read (beta != 0): their latency overlaps the unit's main loop, which
+      // short-K tiles (grouped problems) do not cover otherwise.
+      const EpiView v = sc.epi(w.prob);
+      const int col0 = w.tn * BN + half * EC;
+      const int e = block_exponent(v.amaxA[w.tm * v.amaxA_stride]) +
+                    block_exponent(v.amaxB[col0 / kScaleBlock]);
       {
-        // warm L2 with the part of C this thread will read (beta != 0) while
-        // the unit's main loop still runs: short-K tiles are otherwise bound
-        // by the latency of the epilogue's C loads
-        const EpiView pv = sc.epi(w.prob);
         const int prow = w.tm * 128 + q * 32 + lane;
-        const int pcol = w.tn * BN + half * EC;
-        if (pv.beta != 0.0f && pv.split_k == 1 && prow < pv.M && pcol < pv.N) {
-          const float* rp = pv.C + static_cast<int64_t>(prow) * pv.ldc + pcol;
-          const int ncols = min(EC, pv.N - pcol);
+        if (v.beta != 0.0f && v.split_k == 1 && prow < v.M && col0 < v.N) {
+          const float* rp = v.C + static_cast<int64_t>(prow) * v.ldc + col0;
+          const int ncols = min(EC, v.N - col0);
 #pragma unroll
           for (int j = 0; j < EC; j += 32)
             if (j < ncols) prefetch_l2(rp + j);
@@ -706,7 +710,6 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         if (ab == 0) aphase ^= 1u;
       }
       if (!ok) break;
-      const EpiView v = sc.epi(w.prob);
       if (blk == 0 || v.alpha == 0.0f) {
         // K == 0 or alpha == 0 (grouped problems only): C = beta * C; the
         // planes of such a problem are not packed, so their TMEM sum is unused
@@ -717,9 +720,6 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
       // applied before the power of two, so that a result in range is not
       // lost to an overflow of the unscaled sum (the power of two is exact).
-      const int col0 = w.tn * BN + half * EC;
-      const int e = block_exponent(v.amaxA[w.tm * v.amaxA_stride]) +
-                    block_exponent(v.amaxB[col0 / kScaleBlock]);
       float alpha = v.alpha;
       float beta = v.beta;
       if (v.split_k > 1 || e != 0) {
