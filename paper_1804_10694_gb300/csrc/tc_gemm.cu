@@ -739,10 +739,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       // Two store paths, chosen per 32-column chunk and uniform per warp.
       // Aligned rows and a full chunk: each thread stores its own row with
       // float4 accesses (C loads of the chunk issued first).  Otherwise
-      // (unaligned ldc, partial chunk or rows): the warp stages the 32x32
-      // chunk of its rows (lane = row) in a padded shared buffer, then walks
-      // it one row at a time (lane = column), so that every global access of
-      // the warp covers 128 contiguous bytes of one row whatever the alignment.
+      // (unaligned ldc, partial chunk or rows): the warp brings the 32x32
+      // chunk of C into a padded shared buffer by cp.async (lane = column,
+      // every row in flight at once; beta != 0), combines it with its sums
+      // there (lane = row), then walks the buffer one row at a time (lane =
+      // column), so that every global access of the warp covers 128
+      // contiguous bytes of one row whatever the alignment.
       float* buf = epi_buf + (warp - 2) * 32 * Cfg::EPI_PITCH;
       const int row0 = w.tm * 128 + q * 32;
       const int nrows = min(32, v.M - row0);
@@ -777,26 +779,40 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           }
           continue;
         }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) buf[lane * Cfg::EPI_PITCH + i] = S[j * 32 + i];
-        __syncwarp();
         const bool col_ok = cb + lane < v.N;
         float* base = dst + static_cast<int64_t>(row0) * ldd + cb + lane;
-#pragma unroll
-        for (int r0 = 0; r0 < 32; r0 += 8) {
-          float old[8];
-#pragma unroll
-          for (int rr = 0; rr < 8; ++rr) {
-            const int r = r0 + rr;
-            old[rr] = (beta != 0.0f && col_ok && r < nrows) ? base[r * ldd] : 0.0f;
+        if (beta != 0.0f) {
+          // the chunk of C comes into the buffer by 4-byte cp.async copies
+          // (lane = column, each row 128 contiguous bytes), all 32 rows in
+          // flight at once, then combines with the row-held sums in place
+          const float* src = base;
+          uint32_t sdst = smem_u32(&buf[lane]);
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            const bool in = col_ok && r < nrows;
+            cp_async_4(sdst, in ? src : dst, in ? 4u : 0u);
+            src += ldd;
+            sdst += Cfg::EPI_PITCH * 4;
           }
+          cp_async_commit();
+          cp_async_wait_all();
+          __syncwarp();
 #pragma unroll
-          for (int rr = 0; rr < 8; ++rr) {
-            const int r = r0 + rr;
-            if (col_ok && r < nrows) {
-              const float sv = buf[r * Cfg::EPI_PITCH + lane];
-              base[r * ldd] = beta != 0.0f ? fmaf(alpha, sv, beta * old[rr]) : alpha * sv;
-            }
+          for (int i = 0; i < 32; ++i) {
+            float* bp = &buf[lane * Cfg::EPI_PITCH + i];
+            *bp = fmaf(alpha, S[j * 32 + i], beta * *bp);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) buf[lane * Cfg::EPI_PITCH + i] = alpha * S[j * 32 + i];
+        }
+        __syncwarp();
+        {
+          float* out = base;
+#pragma unroll 4
+          for (int r = 0; r < 32; ++r) {
+            if (col_ok && r < nrows) *out = buf[r * Cfg::EPI_PITCH + lane];
+            out += ldd;
           }
         }
         __syncwarp();
