@@ -15,8 +15,8 @@
 //     along K); each tile's k-loop streams 128-byte k-chunks of the four
 //     planes through a STAGES-deep shared-memory ring filled by TMA;
 //   * register blocking -> tensor memory: one elected thread issues
-//     tcgen05.mma into a TMEM accumulator (two buffers, so the epilogue of one
-//     accumulation block overlaps the MMAs of the next);
+//     tcgen05.mma into a TMEM accumulator (up to four buffers, so that the
+//     epilogue of one accumulation block overlaps the MMAs of the next ones);
 //   * full vs partial tiles: TMA zero-fills the out-of-range part of edge
 //     tiles on load, so the main loop never branches; only the epilogue
 //     masks rows/columns, and full tiles take a vectorised store path;
@@ -79,7 +79,10 @@ struct TcCfg {
   static constexpr int EPI_WG = (BN == 256 || (FUSED && BN == 128)) ? 2 : 1;
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int ACC_COLS = NP == 3 ? 2 * BN : BN;   // TMEM columns of one accumulator buffer
-  static constexpr int TMEM_COLS = 2 * ACC_COLS;       // two accumulator buffers
+  // accumulator buffers: as many as TMEM holds, up to four, so that the MMA
+  // thread runs ahead of the epilogue across short-K tiles
+  static constexpr int NACC = 512 / ACC_COLS >= 4 ? 4 : 512 / ACC_COLS;
+  static constexpr int TMEM_COLS = NACC * ACC_COLS;
   static constexpr int EPI_PITCH = 33;                 // floats per staged row (bank-conflict free)
   static constexpr int EPI_BYTES = 4 * EPI_WG * 32 * EPI_PITCH * 4;   // one 32x32 buffer per epilogue warp
   static constexpr int BAR_BYTES = 256;
@@ -331,14 +334,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   const uint32_t bar0 = sbase + Cfg::OFF_BAR;
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+  constexpr int NACC = Cfg::NACC;
   auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
-  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 4);
+  auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + NACC + b); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * STAGES + 2 * NACC);
   // fused variant: staging buffer b holds a copied chunk / is free again
   constexpr int NSTG = Cfg::STG_STAGES;
-  auto stg_full_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 5 + b); };
-  auto stg_empty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 5 + NSTG + b); };
-  constexpr int NBAR = 2 * STAGES + 5 + 2 * NSTG;
+  auto stg_full_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + b); };
+  auto stg_empty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + NSTG + b); };
+  constexpr int NBAR = 2 * STAGES + 2 * NACC + 1 + 2 * NSTG;
   static_assert(8 * NBAR + 16 <= Cfg::BAR_BYTES, "barrier block");
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -351,7 +355,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       mbar_init(full_bar(s), 1 + Cfg::SPLIT_THREADS / 32);   // producer + one per split warp
       mbar_init(empty_bar(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NACC; ++b) {
       mbar_init(accf_bar(b), 1);
       mbar_init(acce_bar(b), 128 * Cfg::EPI_WG);
     }
@@ -630,8 +634,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           }
           if (!ok) break;
           umma_commit(accf_bar(ab));
-          ab ^= 1u;
-          if (ab == 0) aphase ^= 1u;
+          if (++ab == NACC) {
+            ab = 0;
+            aphase ^= 1u;
+          }
         }
       }
       if (any) {
@@ -706,8 +712,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         }
         tc_fence_before();
         mbar_arrive(acce_bar(ab));
-        ab ^= 1u;
-        if (ab == 0) aphase ^= 1u;
+        if (++ab == NACC) {
+          ab = 0;
+          aphase ^= 1u;
+        }
       }
       if (!ok) break;
       if (blk == 0 || v.alpha == 0.0f) {
