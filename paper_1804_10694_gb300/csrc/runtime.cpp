@@ -553,6 +553,7 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
   if (it != g_cache.end()) {
     g_lru.remove(key);
     g_lru.push_front(key);
+    ++it->second->cache_users;
     *out = it->second;
     return GEMM_OK;
   }
@@ -562,16 +563,41 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
   if (g_cache.size() >= kCacheMax) {
     const CacheKey victim = g_lru.back();
     g_lru.pop_back();
-    // the victim may still be in use on its stream: wait for the device first
-    cudaDeviceSynchronize();
-    plan_destroy_impl(g_cache[victim]);
+    gemm_plan_t v = g_cache[victim];
     g_cache.erase(victim);
+    if (v->cache_users == 0) {
+      // the victim may still be in use on its stream: wait for the device first
+      cudaDeviceSynchronize();
+      plan_destroy_impl(v);
+    } else {
+      v->cache_evicted = true;   // another call holds it: its last holder destroys it
+    }
   }
   g_cache[key] = p;
   g_lru.push_front(key);
+  ++p->cache_users;
   *out = p;
   return GEMM_OK;
 }
+
+void release_cached_plan(gemm_plan_t p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_cache_mutex);
+  if (--p->cache_users == 0 && p->cache_evicted) {
+    cudaDeviceSynchronize();   // its launches may still be queued
+    plan_destroy_impl(p);
+  }
+}
+
+// Holds a plan of the internal cache for the duration of one call, so that
+// another thread's insertion cannot destroy it meanwhile.
+struct CachedPlanUse {
+  gemm_plan_t p;
+  explicit CachedPlanUse(gemm_plan_t plan) : p(plan) {}
+  ~CachedPlanUse() { release_cached_plan(p); }
+  CachedPlanUse(const CachedPlanUse&) = delete;
+  CachedPlanUse& operator=(const CachedPlanUse&) = delete;
+};
 
 // ----------------------------------------------------- host-buffer entry
 // gemm_f32_host keeps per-thread device copies of A, B, C and two copy
@@ -756,6 +782,7 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   gemm_plan_t p = nullptr;
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p, false, false)) != GEMM_OK)
     return st;
+  const CachedPlanUse hold(p);
   if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && !p->launch.fused &&
       host_panels() > 1 &&
       M >= 4 * 128 && page_locked(A) && page_locked(C))
@@ -796,6 +823,7 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
   gemm_plan_t p = nullptr;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, false, false)) != GEMM_OK) return st;
+  const CachedPlanUse hold(p);
   return plan_execute_impl(p, alpha, A, B, beta, C, s);
 }
 
@@ -811,6 +839,7 @@ gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, transA != 0, transB != 0)) != GEMM_OK)
     return st;
+  const CachedPlanUse hold(p);
   return plan_execute_impl(p, alpha, A, B, beta, C, s);
 }
 

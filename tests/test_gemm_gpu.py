@@ -330,3 +330,59 @@ def test_long_k(mode):
     ref = oracle.gemm_f64(M, N, K, 1.0, A, B, -1.0, C0)
     got = run_gemm(mode, M, N, K, 1.0, A, B, -1.0, C0)
     assert oracle.rel_frob(got, ref) <= TOL
+
+
+# ------------------------------------------------------------ concurrency
+def test_concurrent_host_threads_and_streams():
+    """Four host threads call the library at once (the calls release the
+    GIL), each on its own stream with its own shapes and modes, through the
+    cached-plan entry point and the host-buffer entry point: every result
+    matches the oracle (plan cache and per-thread buffers are thread-safe),
+    while a fifth thread pushes plans out of the cache."""
+    import threading
+    jobs = [("bf16x3", 300, 260, 333), ("tf32x3", 129, 257, 1060), ("bf16x6", 520, 390, 700),
+            ("simt", 257, 129, 65)]
+    errors, results = [], {}
+
+    def work(t, mode, M, N, K):
+        try:
+            stream = torch.cuda.Stream()
+            A, B, C0 = W.uniform(M, K, 400 + t), W.uniform(K, N, 410 + t), W.uniform(M, N, 420 + t)
+            ref = oracle.gemm_f64(M, N, K, 1.5, A, B, 0.5, C0)
+            for rep in range(3):
+                with torch.cuda.stream(stream):
+                    dA, dB, dC = dev(A), dev(B), dev(C0)
+                    pkg.gemm(dA, dB, dC, 1.5, 0.5, mode=mode, stream=stream)
+                stream.synchronize()
+                results[(t, rep, "dev")] = oracle.rel_frob(dC.cpu().numpy(), ref)
+                hC = C0.copy()
+                pkg.gemm_host(torch.from_numpy(A), torch.from_numpy(B), torch.from_numpy(hC), 1.5, 0.5,
+                              mode=mode)
+                results[(t, rep, "host")] = oracle.rel_frob(hC, ref)
+        except Exception as e:   # surfaced below
+            errors.append((t, repr(e)))
+
+    def churn():
+        # 24 distinct shapes through the 16-plan cache: evictions while the
+        # other threads hold their plans
+        try:
+            for i in range(24):
+                M, N, K = 64 + 8 * i, 72, 40 + 4 * i
+                A, B = W.uniform(M, K, 500 + i), W.uniform(K, N, 530 + i)
+                dC = torch.zeros(M, N, device="cuda")
+                pkg.gemm(dev(A), dev(B), dC, 1.0, 0.0, mode="bf16x3")
+                torch.cuda.synchronize()
+                results[("churn", i)] = oracle.rel_frob(dC.cpu().numpy(),
+                                                        oracle.gemm_f64(M, N, K, 1.0, A, B, 0.0, None))
+        except Exception as e:
+            errors.append(("churn", repr(e)))
+
+    threads = [threading.Thread(target=work, args=(t, *job)) for t, job in enumerate(jobs)]
+    threads.append(threading.Thread(target=churn))
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    assert len(results) == 4 * 3 * 2 + 24
+    assert all(err <= TOL for err in results.values()), results
