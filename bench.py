@@ -508,6 +508,8 @@ def run_ours(args, world, rank, local):
                     "peak_kind": f"{pk_kind} bf16 dense {'sustained (sw_power_cap during the loop)' if capped else 'burst'}" + (
                         " x 1.1/2.25 (nominal tf32/bf16 ratio)" if args.mode == "tf32x3" else ""),
                     "frac_of_burst": round(achieved / (pk["bf16_tflops"] * (1.1 / 2.25 if args.mode == "tf32x3" else 1.0)), 4),
+                    # the spec sheet's dense peak (2250 TFLOP/s bf16, 1100 tf32), for reference
+                    "frac_of_spec": round(achieved / (1100.0 if args.mode == "tf32x3" else 2250.0), 4),
                     "algorithmic_flops_per_launch": tensor_flops,
                     "kernel_ms": round(main_ms, 4), "pack_ms": round(pack_ms, 4),
                     "fp32_equiv_tflops_kernel": round(flops / (main_ms * 1e-3) / 1e12, 1),
