@@ -602,12 +602,14 @@ def run_reference(args, world, rank):
     import oracle
     A, B, C0 = inputs()
     n = SIZE
-    # bounded sample per step: enough rows for about 4 s of CPU work
+    # bounded sample per step: the whole run (warm-up and timed steps) takes
+    # about two minutes of CPU work, at most 4 s a step
     probe_rows = [0, 1, 2, 3]
     t0 = time.perf_counter()
     oracle.gemm_f64_rows(probe_rows, n, n, ALPHA, A, B, BETA, C0)
     per_row = max((time.perf_counter() - t0) / len(probe_rows), 1e-4)
-    rows_per_step = int(max(8, min(1024, 4.0 / per_row)))
+    step_budget_s = min(4.0, 120.0 / max(1, args.steps + args.warmup))
+    rows_per_step = int(max(8, min(1024, step_budget_s / per_row)))
     rows = list(range(rows_per_step))
     for _ in range(args.warmup):
         oracle.gemm_f64_rows(rows[:8], n, n, ALPHA, A, B, BETA, C0)
