@@ -62,7 +62,7 @@ namespace gb {
 // running sum at every MMA; kept apart, the small products lose bits only
 // relative to their own (2^-8 smaller) sum, and the hi*hi chain is one MMA
 // per k-step instead of six.
-template <int BN, bool TF32, bool FUSED = false, int NP = 2>
+template <int BN, bool TF32, bool FUSED = false, int NP = 2, bool WIDE_EPI = false>
 struct TcCfg {
   static_assert(NP == 2 || (NP == 3 && !TF32 && !FUSED), "three planes: packed bf16 only");
   static constexpr int BM = 128;
@@ -74,9 +74,13 @@ struct TcCfg {
   static constexpr int STAGES = (FUSED || NP == 3) ? 2 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
   static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
   static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
-  // epilogue warpgroups (two for the fused 128-wide tile: with its extra
-  // warps, one warpgroup holding 128 columns would run out of registers)
-  static constexpr int EPI_WG = (BN == 256 || (FUSED && BN == 128)) ? 2 : 1;
+  // epilogue warpgroups: two for the 128-wide tiles of the fused variant
+  // (with its extra warps, one warpgroup holding 128 columns would run out of
+  // registers) and of the grouped launch (WIDE_EPI: its tiles are short in K,
+  // so the epilogue, at half the time per tile with each thread draining 64
+  // columns, is what the MMAs wait for); one elsewhere (at long K the
+  // epilogue hides behind the MMAs, and the extra warps cost about 2% there)
+  static constexpr int EPI_WG = (BN == 256 || (BN == 128 && (FUSED || WIDE_EPI))) ? 2 : 1;
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int ACC_COLS = NP == 3 ? 2 * BN : BN;   // TMEM columns of one accumulator buffer
   // accumulator buffers: as many as TMEM holds, up to four, so that the MMA
@@ -152,6 +156,7 @@ __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int grou
 
 // Scheduling policy of one gemm: units are (split, tile) pairs.
 struct SingleSched {
+  static constexpr bool kWideEpilogue = false;
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
   const TcArgs* a;
@@ -196,6 +201,7 @@ struct SingleSched {
 // each problem's tiles in grouped raster order); the table gives a unit's
 // problem, tile coordinates and k-chunk count in one 16-byte load.
 struct GroupedSched {
+  static constexpr bool kWideEpilogue = true;
   const GroupedArgs* a;
   __device__ int l2_hints() const { return 0; }   // problems of every shape: no priority
   __device__ int units() const { return a->num_units; }
@@ -326,7 +332,7 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
 // that the 128-byte path keeps its registers).
 template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
-  using Cfg = TcCfg<BN, TF32, FUSED, NP>;
+  using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kWideEpilogue>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -1039,7 +1045,7 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
 }
 
 template <int BN, bool TF32, int NP>
-__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, true>::THREADS, 1)
     tc_grouped_kernel(const GroupedArgs a) {
   GroupedSched sc{&a};
   tc_gemm_body<BN, TF32, GroupedSched, false, NP>(sc);
@@ -1131,7 +1137,8 @@ static cudaError_t prepare_variant() {
                                Cfg::SMEM);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32, NP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TcCfg<BN, TF32, false, NP, true>::SMEM);
     }
     if (e != cudaSuccess) return e;
     configured_device = dev;
@@ -1202,7 +1209,7 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
 
 template <int BN, bool TF32, int NP = 2>
 static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, TF32, false, NP>;
+  using Cfg = TcCfg<BN, TF32, false, NP, true>;
   cudaError_t e = prepare_variant<BN, TF32, false, NP>();
   if (e != cudaSuccess) return e;
   e = launch_dependent(tc_grouped_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, a);
