@@ -55,8 +55,12 @@ def parse_args():
                    help="explicit tile configuration for --kernel-only (default: heuristic)")
     p.add_argument("--kernel-only", action="store_true",
                    help="only warm-up and timed plan executions (for ncu captures)")
-    p.add_argument("--case", default="square", choices=("square", "grouped", "conv"),
-                   help="workload of --kernel-only (square M=N=K=size, or the 512 grouped problems)")
+    p.add_argument("--case", default="square", choices=("square", "grouped", "conv", "conv_layer"),
+                   help="workload of --kernel-only (square M=N=K=size, the 512 grouped problems, the "
+                        "first conv-as-gemm shape, or the paper's Conv layer as a direct convolution)")
+    p.add_argument("--conv-batch", type=int, default=32,
+                   help="images of the conv_layer case (512 x 512 x 16 -> 16 each)")
+    p.add_argument("--conv-r", type=int, default=3, help="filter side of the conv_layer case")
     p.add_argument("--no-other-workloads", action="store_true",
                    help="skip the secondary measurements of the other workloads")
     p.add_argument("--costmodel", default=os.path.join(ROOT, "paper_1804_10694_gb300", "data",
@@ -195,6 +199,23 @@ def run_kernel_only(args, local):
         pkg.device_error()
         gp.destroy()
         print(json.dumps({"kernel_only": True, "case": "grouped", "executions": args.warmup + args.steps}))
+        return
+    if args.case == "conv_layer":
+        import workloads as W
+        _, H, Wd, C, K = W.CONV_PAPER_LAYER
+        n, R = args.conv_batch, args.conv_r
+        x = torch.empty(n, H, Wd, C, device="cuda").uniform_(-1, 1)
+        f = torch.empty(R, R, C, K, device="cuda").uniform_(-1, 1)
+        out = torch.empty(n, H, Wd, K, device="cuda")
+        plan = pkg.ConvPlan(n, H, Wd, C, K, R, R, mode=args.mode, config_id=args.config_id)
+        for _ in range(args.warmup + args.steps):
+            plan.execute(x, f, out)
+        torch.cuda.synchronize()
+        pkg.device_error()
+        info = plan.info()
+        plan.destroy()
+        print(json.dumps({"kernel_only": True, "case": "conv_layer", "images": n, "R": R, "mode": args.mode,
+                          "config_id": info["config_id"], "executions": args.warmup + args.steps}))
         return
     if args.case == "conv":
         # the first conv-as-gemm shape, 50176 x 64 x 576 (alpha 1, beta 0)

@@ -48,12 +48,15 @@ struct TcArgs {
   const float* A;
   int64_t lda;
   int vecA;                // A 16-byte aligned and lda % 4 == 0: float4 loads
-  // direct convolution (fused variant): A is the patch matrix of the NHWC
-  // image at A (conv_H x conv_W x conv_C pixels) for an odd conv_R x conv_S
-  // filter with same zero padding, gathered while staging; one block
-  // exponent for the whole image (amaxA[0])
-  int conv, conv_H, conv_W, conv_C, conv_R, conv_S;
-  int conv_box_c;          // channels per TMA im2col box (32, or 16), when vecA
+  // direct convolution: A is the patch matrix of the NHWC image at A
+  // (conv_N images of conv_H x conv_W x conv_C pixels) for an odd conv_R x
+  // conv_S filter with same zero padding; one block exponent for the whole
+  // image (amaxA[0]).  Fused variant: gathered from the FP32 image while
+  // staging.  Packed variant (conv_C % 16 == 0, bf16 planes): the image is
+  // split once into planes stacked as 2 conv_N images, and the kernel loads
+  // 16-channel im2col boxes of them (plane z = images z conv_N ...).
+  int conv, conv_N, conv_H, conv_W, conv_C, conv_R, conv_S;
+  int conv_box_c;          // fused variant: channels per TMA im2col box (32, or 16), when vecA
 };
 
 struct TcLaunch {
@@ -114,6 +117,11 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
                                    unsigned* amaxA, unsigned* cntA, void* planesA,
                                    int64_t plane_stride, int64_t pitch, int sms, cudaStream_t s);
 int pack_first_items(int64_t M, int64_t N, int64_t pitch);
+// Packed convolution: split the NHWC image X (elems FP32 values, elems % 4
+// == 0, X 16-byte aligned) into bf16 planes [plane][elems] under one exponent
+// from its max |x|, folded into amax[0] (zero on entry).  Two launches.
+cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigned* amax, void* planes,
+                               int sms, cudaStream_t s);
 
 // ------------------------------------------------------------ grouped
 // Static description of one problem of a grouped gemm, device resident

@@ -309,6 +309,18 @@ __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
   return d;
 }
 
+// And for the 32-byte swizzle: rows of 32 bytes (one MMA's K slice of bf16),
+// 8-row atoms of 256 bytes (stride-dimension offset 256), swizzle mode 6.
+__device__ __forceinline__ uint64_t sdesc_k_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(256 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(6) << 61;
+  return d;
+}
+
 template <int SW>
 __device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr) {
   static_assert(SW == 128 || SW == 64, "swizzle width");

@@ -273,6 +273,30 @@ static gemm_status encode_im2col(CUtensorMap* map, const float* X, int64_t batch
   return GEMM_OK;
 }
 
+// The same patch matrix over the bf16 planes of a split image (packed
+// convolution): the planes are stacked as planes x batch images of H x W x C
+// values, and each load brings 128 output pixels times box_c channels of one
+// tap: 64 (128-byte rows, 128-byte swizzle) or 16 (32-byte rows, 32-byte
+// swizzle); plane z's pixels are images z batch onward, whose zero padding
+// TMA supplies image by image.
+static gemm_status encode_im2col_planes(CUtensorMap* map, const void* planes, int planes_n, int64_t batch,
+                                        int64_t H, int64_t W, int64_t C, int R, int S, int box_c) {
+  if (!g_encode_im2col) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "cuTensorMapEncodeIm2col unavailable");
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(planes_n * batch)};
+  cuuint64_t strides[3] = {(cuuint64_t)(C * 2), (cuuint64_t)(W * C * 2), (cuuint64_t)(H * W * C * 2)};
+  const int lower[2] = {-(S / 2), -(R / 2)}, upper[2] = {-(S / 2), -(R / 2)};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode_im2col(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(planes), dims,
+                               strides, lower, upper, (cuuint32_t)box_c, 128, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               box_c == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(GEMM_ERR_CUDA, "cuTensorMapEncodeIm2col failed (%d) for the image planes", (int)r);
+  return GEMM_OK;
+}
+
 gemm_status validate_shape_t(bool transA, bool transB, int64_t M, int64_t N, int64_t K, int64_t lda,
                              int64_t ldb, int64_t ldc) {
   if (M < 0 || N < 0 || K < 0) return fail(GEMM_ERR_INVALID_ARG, "negative size M=%lld N=%lld K=%lld",
@@ -313,7 +337,7 @@ static gemm_status resolve_mode(gemm_mode mode, const DeviceState& d, gemm_mode*
 
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
                              gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
-                             bool transA, bool transB) {
+                             bool transA, bool transB, int64_t conv_image_elems) {
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
   *out = nullptr;
   gemm_status st = validate_shape_t(transA, transB, M, N, K, lda, ldb, ldc);
@@ -369,7 +393,10 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   // workspace: A planes (packed variant) | B planes | amax A | amax B | split-K partials
   const bool fused = p->cfg.fused != 0;
   const int np = prec_planes(pr);
-  const size_t bytesA = fused ? 0 : (size_t)np * M * p->pitch * es;
+  const bool conv_packed = conv_image_elems >= 0 && !fused;
+  const size_t bytesA = fused ? 0
+                        : conv_packed ? (size_t)np * conv_image_elems * es
+                                      : (size_t)np * M * p->pitch * es;
   const size_t bytesB = (size_t)np * N * p->pitch * es;
   const size_t nblkA = (size_t)(M + kScaleBlock - 1) / kScaleBlock;
   const size_t nblkB = (size_t)(N + kScaleBlock - 1) / kScaleBlock;
@@ -396,7 +423,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->cntB = p->cntA + nblkA;
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
-  if (!fused && (st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK)
+  // (a packed convolution's A map, over the image planes, is made by its creator)
+  if (!fused && !conv_packed &&
+      (st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK)
     return st;
   if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn, sw)) != GEMM_OK) return st;
 
@@ -459,8 +488,16 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
     if (reinterpret_cast<uintptr_t>(A) % 16 != 0)
       return fail(GEMM_ERR_ALIGNMENT, "the convolution's input image must be 16-byte aligned");
     const int64_t elems = (int64_t)p->conv_batch * p->args.conv_H * p->args.conv_W * p->args.conv_C;
-    e = pack_fused_launch(p->prec, A, 1, elems, elems, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
-                          p->planesB, p->pitch, p->sms, s, K);
+    if (!p->launch.fused) {
+      // packed: the image split once into planes, then B packed alone
+      e = image_split_launch(p->prec, A, elems, p->amaxA, p->planesA, p->sms, s);
+      if (e == cudaSuccess)
+        e = pack_launch(p->prec, nullptr, 0, K, K, B, N, p->ldb, p->amaxA, p->amaxB, p->cntA, p->cntB,
+                        nullptr, p->planesB, p->pitch, p->sms, s);
+    } else {
+      e = pack_fused_launch(p->prec, A, 1, elems, elems, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
+                            p->planesB, p->pitch, p->sms, s, K);
+    }
   } else if (p->launch.fused)
     e = pack_fused_launch(p->prec, A, M, K, p->lda, B, N, p->ldb, p->amaxA, p->amaxB, p->cntB,
                           p->planesB, p->pitch, p->sms, s, -1, p->transB);
@@ -474,7 +511,7 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.C = C;
   a.A = A;
   a.vecA = (p->lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0) ? 1 : 0;
-  if (a.conv) {
+  if (a.conv && p->launch.fused) {
     // TMA im2col staging when C is a multiple of 16: boxes of 32 channels
     // (128-byte rows) when every k-chunk holds whole taps (C a multiple of
     // the chunk, so K = R*S*C has no partial chunk), else boxes of 16
@@ -896,35 +933,67 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   if (H > 65535 || W > 65535 || C > (1 << 20) || batch * H * W > INT32_MAX || taps * C > INT32_MAX)
     return fail(GEMM_ERR_INVALID_ARG, "convolution too large");
   if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
-  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3)
-    return fail(GEMM_ERR_INVALID_ARG, "the convolution runs in BF16X3 or TF32X3 mode");
+  if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3 && mode != GEMM_MODE_BF16X6)
+    return fail(GEMM_ERR_INVALID_ARG, "the convolution runs in BF16X3, TF32X3 or BF16X6 mode");
+  // Packed path (bf16 modes, C a multiple of 16): the image is split once
+  // into planes and the kernel loads 16-channel im2col boxes of them.
+  // Fused path (the other cases): the FP32 patches are staged and split
+  // inside the kernel, once per tap.
+  const bool pack_shape = mode != GEMM_MODE_TF32X3 && C % 16 == 0;
+  if (mode == GEMM_MODE_BF16X6 && !pack_shape)
+    return fail(GEMM_ERR_INVALID_ARG, "the BF16X6 convolution needs C a multiple of 16 (C=%lld)",
+                (long long)C);
   const int64_t M = batch * H * W, Kd = taps * C;
   gemm_config c;
+  if (config_id >= 0) {
+    if (!config_get(mode, config_id, &c))
+      return fail(GEMM_ERR_INVALID_ARG, "configuration %d out of range", config_id);
+    if (!c.fused && !pack_shape)
+      return fail(GEMM_ERR_INVALID_ARG,
+                  "configuration %d is packed: the convolution runs packed only in a bf16 mode with C "
+                  "a multiple of 16", config_id);
+  }
+  DeviceState* dev;
+  gemm_status st0 = device_state(&dev, nullptr);   // also resolves the tensor-map encoders
+  if (st0 != GEMM_OK) return st0;
+  const bool can_pack = pack_shape && g_encode_im2col != nullptr;
+  if (!can_pack && (mode == GEMM_MODE_BF16X6 || (config_id >= 0 && !c.fused)))
+    return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "the packed convolution needs TMA im2col tensor maps");
   if (config_id < 0) {
-    // default: the fused-split twin of the gemm heuristic's choice for this
-    // shape (tile width by K, split-K when the tiles do not fill the GPU)
-    DeviceState* dev;
-    gemm_status st0 = device_state(&dev, nullptr);
-    if (st0 != GEMM_OK) return st0;
-    const int packed = default_config(mode, M, K, Kd, dev->sms);
+    // default: the gemm heuristic's choice for this shape (tile width by K,
+    // split-K when the tiles do not fill the GPU), as its packed or its
+    // fused-split twin
+    const int guess = default_config(mode, M, K, Kd, dev->sms);
     gemm_config d;
-    config_get(packed, &d);
+    config_get(mode, guess, &d);
+    const bool want_fused = !can_pack;
     for (int id = 0; id < config_count(mode); ++id) {
-      config_get(id, &c);
-      if (c.fused && c.block_n == d.block_n && c.split_k == d.split_k && c.kb == d.kb &&
-          c.group_m == d.group_m) {
+      config_get(mode, id, &c);
+      if ((c.fused != 0) == want_fused && c.block_n == d.block_n && c.split_k == d.split_k &&
+          c.kb == d.kb && c.group_m == d.group_m) {
         config_id = id;
         break;
       }
     }
-  } else if (!config_get(config_id, &c) || !c.fused) {
-    return fail(GEMM_ERR_INVALID_ARG, "configuration %d is not a fused-split configuration", config_id);
+    if (config_id < 0) return fail(GEMM_ERR_INVALID_ARG, "no configuration for the convolution");
   }
+  config_get(mode, config_id, &c);
+  const bool packed_conv = !c.fused;
+  const int64_t elems = batch * H * W * C;
   gemm_plan_t p = nullptr;
-  gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p);
+  gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p, false,
+                                    false, packed_conv ? elems : -1);
   if (st != GEMM_OK) return st;
+  const int box_c = C % 64 == 0 ? 64 : 16;   // packed: channels per im2col box
+  if (packed_conv && (st = encode_im2col_planes(&p->tmA, p->planesA, prec_planes(p->prec), batch, H, W, C, R,
+                                                S, box_c)) != GEMM_OK) {
+    plan_destroy_impl(p);
+    return st;
+  }
   p->conv_batch = (int)batch;
   p->args.conv = 1;
+  p->args.conv_N = (int)batch;
+  p->args.conv_box_c = packed_conv ? box_c : 0;
   p->args.conv_H = (int)H;
   p->args.conv_W = (int)W;
   p->args.conv_C = (int)C;

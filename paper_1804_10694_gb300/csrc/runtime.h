@@ -69,9 +69,12 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms);
 int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                   int64_t ldc, gemm_select sel, int sms);
 
+// conv_image_elems >= 0: a packed convolution, whose A planes hold the
+// split image (that many elements a plane) instead of M x pitch rows
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
                              gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
-                             bool transA = false, bool transB = false);
+                             bool transA = false, bool transB = false,
+                             int64_t conv_image_elems = -1);
 gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const float* B, float beta,
                               float* C, cudaStream_t s);
 void plan_destroy_impl(gemm_plan_t p);

@@ -586,6 +586,69 @@ __global__ void __launch_bounds__(256, 4) grouped_pack_kernel(const GroupedProbl
   griddep_launch_dependents();
 }
 
+// ------------------------------------------- convolution image, split once
+// The packed convolution splits its NHWC image once, element by element,
+// into bf16 planes [plane][elems] (plane z = hi, mid, lo), under one
+// exponent for the whole image.  kFirst splits unscaled and folds max |x|
+// into amax[0]; kRescale, launched after it, reads the final max and returns
+// at once when the exponent is 0 (the usual case), else re-splits every
+// element with it.  Four float4 loads a thread are in flight per iteration.
+template <Prec PR, Pass PASS>
+__global__ void __launch_bounds__(256) image_split_kernel(const float4* __restrict__ X, int64_t n4,
+                                                           unsigned* __restrict__ amax,
+                                                           __nv_bfloat16* __restrict__ P, int64_t plane) {
+  float sc = 1.0f;
+  if (PASS == kRescale) {
+    const int e = block_exponent(*amax);
+    if (e == 0) return;
+    sc = pow2f(-e);
+  }
+  unsigned m = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n4; i0 += 4 * stride) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * stride;
+      v[u] = i < n4 ? X[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i >= n4) break;
+      const float x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+      if (PASS == kFirst) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) m = max(m, abs_bits(x[j]));
+      }
+      if (PR == Prec::BF16X6) {
+        __align__(8) __nv_bfloat16 h[4], mi[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const Split3Bf16 t = split3_bf16(x[j] * sc);
+          h[j] = t.hi;
+          mi[j] = t.mid;
+          l[j] = t.lo;
+        }
+        *reinterpret_cast<uint2*>(P + 4 * i) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(P + plane + 4 * i) = *reinterpret_cast<const uint2*>(mi);
+        *reinterpret_cast<uint2*>(P + 2 * plane + 4 * i) = *reinterpret_cast<const uint2*>(l);
+      } else {
+        __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const HiLoBf16 t = split_bf16(x[j] * sc);
+          h[j] = t.hi;
+          l[j] = t.lo;
+        }
+        *reinterpret_cast<uint2*>(P + 4 * i) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(P + plane + 4 * i) = *reinterpret_cast<const uint2*>(l);
+      }
+    }
+  }
+  if (PASS == kFirst) fold_block_max(m, amax);
+}
+
 int grid_for(int64_t items, int sms) {
   const int64_t cap = static_cast<int64_t>(sms) * 8;
   return static_cast<int>(items < cap ? (items > 0 ? items : 1) : cap);
@@ -688,6 +751,25 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
   const PackShape p = make_shape(make_op(A, rows, lda, true, amaxA, cntA, planesA, plane_stride),
                                  make_op(nullptr, 0, 1, false, nullptr, nullptr, nullptr, 0), K, pitch);
   return launch_first(prec, p, sms, s);
+}
+
+cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigned* amax, void* planes,
+                               int sms, cudaStream_t s) {
+  if (prec != Prec::BF16 && prec != Prec::BF16X6) return cudaErrorInvalidValue;
+  if (elems % 4 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0) return cudaErrorInvalidValue;
+  const int64_t n4 = elems / 4;
+  if (n4 == 0) return cudaSuccess;
+  const int grid = grid_for((n4 + 1023) / 1024, sms);
+  const float4* X4 = reinterpret_cast<const float4*>(X);
+  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
+  if (prec == Prec::BF16X6) {
+    image_split_kernel<Prec::BF16X6, kFirst><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16X6, kRescale><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+  } else {
+    image_split_kernel<Prec::BF16, kFirst><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16, kRescale><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const GroupedPtrs* ptrs,

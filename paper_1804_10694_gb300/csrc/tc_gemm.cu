@@ -142,6 +142,7 @@ struct FusedA {
   int conv, H, W, C;        // A = patch matrix of an NHWC image (R x S filter, odd
   int R, S;                 // sizes, zero padding (R-1)/2 and (S-1)/2)
   int box_c;                // channels per im2col box: 32 (128-byte rows) or 16 (64-byte rows)
+  int N;                    // images (the packed variant's plane z starts at image z N)
 };
 
 __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
@@ -192,7 +193,8 @@ struct SingleSched {
   }
   __device__ FusedA srcA(int) const {
     return FusedA{a->A, a->lda, a->M, a->K, a->vecA != 0, a->amaxA, a->conv ? 0 : 1,
-                  a->conv, a->conv_H, a->conv_W, a->conv_C, a->conv_R, a->conv_S, a->conv_box_c};
+                  a->conv, a->conv_H, a->conv_W, a->conv_C, a->conv_R, a->conv_S, a->conv_box_c,
+                  a->conv_N};
   }
 };
 
@@ -330,9 +332,22 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
 // FBW (fused variant): row bytes of the staged boxes of A, 128, or 64 for a
 // convolution staged in 16-channel im2col boxes (its own instantiation, so
 // that the 128-byte path keeps its registers).
-template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128>
+// CONVA != 0: the packed convolution.  A is the patch matrix of the image's
+// bf16 planes, loaded as im2col boxes of CONVA channels of one tap; B's
+// planes are packed as usual.  CONVA = 64 (C a multiple of 64): one box of
+// 128-byte rows a plane and chunk, laid out as a packed A plane (128-byte
+// swizzle).  CONVA = 16: four boxes of 32-byte rows (32-byte swizzle), k-step
+// kk of a chunk being the 4 KB sub-tile kk of each A plane, read by MMA
+// descriptors of the 32-byte swizzle; boxes of a last, partial chunk past K
+// are neither loaded nor multiplied.
+template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128,
+          int CONVA = 0>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kWideEpilogue>;
+  static_assert(CONVA == 0 || ((CONVA == 16 || CONVA == 64) && !FUSED && !TF32),
+                "packed convolution: bf16 planes, 16- or 64-channel boxes");
+  constexpr bool CB16 = CONVA == 16;
+  constexpr int CBOX = 128 * 32;   // bytes of one 16-channel bf16 im2col box
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -551,16 +566,61 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           tma_prefetch_desc(mB);
           last_prob = w.prob;
         }
+        int cn0 = 0, ch0 = 0, cw0 = 0;   // CONVA: image, row and column of the tile's first pixel
+        if constexpr (CONVA != 0) {
+          const FusedA fa = sc.srcA(0);
+          const int hw = fa.H * fa.W;
+          const int p0 = w.tm * 128;
+          cn0 = p0 / hw;
+          const int rem = p0 - cn0 * hw;
+          ch0 = rem / fa.W;
+          cw0 = rem - ch0 * fa.W;
+        }
         for (int c = w.c0; c < w.c1; ++c) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, err)) {
             ok = false;
             break;
           }
           const uint32_t fb = full_bar(stage);
-          mbar_arrive_expect_tx(fb, FUSED ? NP * Cfg::B_PLANE : Cfg::STAGE);
           const uint32_t sA = sbase + stage * Cfg::STAGE;
           const int kx = c * Cfg::BK;
-          if (hints) {
+          if constexpr (CONVA == 64) {
+            // one box a plane: 128 output pixels from the tile's first
+            // (output (h, w) starts at input (h - (R-1)/2, w - (S-1)/2); tap
+            // (r, s) adds its offsets) times the chunk's 64 channels, all of
+            // one tap (C % 64 == 0, so K has no partial chunk)
+            const FusedA fa = sc.srcA(0);
+            mbar_arrive_expect_tx(fb, Cfg::STAGE);
+            const int tap = kx / fa.C, c0 = kx - tap * fa.C;
+            const int tr = tap / fa.S, ts = tap - tr * fa.S;
+#pragma unroll
+            for (int z = 0; z < NP; ++z)
+              tma_load_im2col_4d(sA + z * Cfg::A_PLANE, mA, fb, c0, cw0 - fa.S / 2, ch0 - fa.R / 2,
+                                 cn0 + z * fa.N, static_cast<uint16_t>(ts), static_cast<uint16_t>(tr));
+#pragma unroll
+            for (int z = 0; z < NP; ++z)
+              tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
+          } else if constexpr (CB16) {
+            // boxes: the same pixels times 16 channels of one tap, one per k-step
+            const FusedA fa = sc.srcA(0);
+            const int nval = min(Cfg::KSTEPS, (fa.K - kx) / 16);
+            mbar_arrive_expect_tx(fb, NP * (nval * CBOX + Cfg::B_PLANE));
+            for (int h = 0; h < Cfg::KSTEPS; ++h) {
+              if (h >= nval) break;
+              const int k0 = kx + 16 * h;
+              const int tap = k0 / fa.C, c0 = k0 - tap * fa.C;
+              const int tr = tap / fa.S, ts = tap - tr * fa.S;
+#pragma unroll
+              for (int z = 0; z < NP; ++z)
+                tma_load_im2col_4d(sA + z * Cfg::A_PLANE + h * CBOX, mA, fb, c0, cw0 - fa.S / 2,
+                                   ch0 - fa.R / 2, cn0 + z * fa.N, static_cast<uint16_t>(ts),
+                                   static_cast<uint16_t>(tr));
+            }
+#pragma unroll
+            for (int z = 0; z < NP; ++z)
+              tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
+          } else if (hints) {
+            mbar_arrive_expect_tx(fb, FUSED ? NP * Cfg::B_PLANE : Cfg::STAGE);
             if (!FUSED) {
 #pragma unroll
               for (int z = 0; z < NP; ++z)
@@ -570,6 +630,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             for (int z = 0; z < NP; ++z)
               tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
           } else {
+            mbar_arrive_expect_tx(fb, FUSED ? NP * Cfg::B_PLANE : Cfg::STAGE);
             if (!FUSED) {
 #pragma unroll
               for (int z = 0; z < NP; ++z) tma_load_3d(sA + z * Cfg::A_PLANE, mA, fb, kx, w.tm * Cfg::BM, z);
@@ -596,6 +657,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f32acc(TF32, 128, BN);
+      int convK = 0;   // 16-channel boxes: K of the patch matrix
+      if constexpr (CB16) convK = sc.srcA(0).K;
       uint32_t stage = 0, phase = 0, ab = 0, aphase = 0;
       bool ok = true;
       bool any = false;
@@ -621,11 +684,14 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             const uint32_t sAlo = sAhi + Cfg::A_PLANE;
             const uint32_t sBhi = sAhi + NP * Cfg::A_PLANE;
             const uint32_t sBlo = sBhi + Cfg::B_PLANE;
+            // 16-channel boxes: k-steps of this chunk inside K (its boxes that were loaded)
+            const int kv = CB16 ? min(Cfg::KSTEPS, (convK - c * Cfg::BK) / 16) : Cfg::KSTEPS;
 #pragma unroll
             for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
+              if (CB16 && kk >= kv) break;
               const uint32_t off = kk * 32;   // 32 bytes = one MMA's K slice
-              const uint64_t dAhi = sdesc_k<Cfg::SW>(sAhi + off);
-              const uint64_t dAlo = sdesc_k<Cfg::SW>(sAlo + off);
+              const uint64_t dAhi = CB16 ? sdesc_k_sw32(sAhi + kk * CBOX) : sdesc_k<Cfg::SW>(sAhi + off);
+              const uint64_t dAlo = CB16 ? sdesc_k_sw32(sAlo + kk * CBOX) : sdesc_k<Cfg::SW>(sAlo + off);
               const uint64_t dBhi = sdesc_k<Cfg::SW>(sBhi + off);
               const uint64_t dBlo = sdesc_k<Cfg::SW>(sBlo + off);
               const uint32_t acc = (c > cb || kk > 0) ? 1u : 0u;
@@ -634,7 +700,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
                 // plane indices sum to at most 2: the five smaller ones into
                 // the second accumulator (smallest first), hi*hi into the first
                 const uint32_t d2 = d + BN;
-                const uint64_t dAl2 = sdesc_k<Cfg::SW>(sAhi + 2 * Cfg::A_PLANE + off);
+                const uint64_t dAl2 = CB16 ? sdesc_k_sw32(sAhi + 2 * Cfg::A_PLANE + kk * CBOX)
+                                            : sdesc_k<Cfg::SW>(sAhi + 2 * Cfg::A_PLANE + off);
                 const uint64_t dBl2 = sdesc_k<Cfg::SW>(sBhi + 2 * Cfg::B_PLANE + off);
                 umma_bf16(d2, dAl2, dBhi, idesc, acc);
                 umma_bf16(d2, dAlo, dBlo, idesc, 1u);
@@ -1044,6 +1111,16 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
   tc_gemm_body<BN, TF32, SingleSched, false, NP>(sc);
 }
 
+// Packed convolution: A's planes loaded as im2col boxes (CB channels) of
+// the split image.
+template <int BN, int NP, int CB>
+__global__ void __launch_bounds__(TcCfg<BN, false, false, NP>::THREADS, 1)
+    tc_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcArgs a) {
+  SingleSched sc{&tmA, &tmB, &a};
+  tc_gemm_body<BN, false, SingleSched, false, NP, 128, CB>(sc);
+}
+
 template <int BN, bool TF32, int NP>
 __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, true>::THREADS, 1)
     tc_grouped_kernel(const GroupedArgs a) {
@@ -1139,6 +1216,14 @@ static cudaError_t prepare_variant() {
         e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32, NP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TcCfg<BN, TF32, false, NP, true>::SMEM);
+      if constexpr (!TF32) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg::SMEM);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   Cfg::SMEM);
+      }
     }
     if (e != cudaSuccess) return e;
     configured_device = dev;
@@ -1186,7 +1271,16 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
     using Cfg = TcCfg<BN, TF32, false, NP>;
     cudaError_t e = prepare_variant<BN, TF32, false, NP>();
     if (e != cudaSuccess) return e;
-    e = launch_dependent(tc_gemm_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    if (a.conv) {
+      // packed convolution: tmA maps the split image's planes for im2col loads
+      if constexpr (TF32) return cudaErrorInvalidValue;
+      else if (a.conv_box_c == 64)
+        e = launch_dependent(tc_conv_kernel<BN, NP, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      else
+        e = launch_dependent(tc_conv_kernel<BN, NP, 16>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    } else {
+      e = launch_dependent(tc_gemm_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();

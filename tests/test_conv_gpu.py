@@ -1,7 +1,9 @@
-"""Parity of the direct convolution (3x3 and other odd R x S filters;
-implicit gemm through the fused-split kernel) with the convolution oracle,
-and with the gemm path on an explicitly formed patch matrix (same split, same
-MMAs: bit for bit)."""
+"""Parity of the direct convolution (3x3 and other odd R x S filters, as an
+implicit gemm) with the convolution oracle, and with the gemm path on an
+explicitly formed patch matrix (same split, same MMAs: bit for bit).  Two
+paths: packed (bf16 modes, C a multiple of 16: the image split once into
+planes, 16-channel im2col boxes of them) and fused-split (the FP32 patches
+staged and split inside the kernel)."""
 from __future__ import annotations
 
 import math
@@ -48,6 +50,21 @@ def fused_ids(mode, **want):
         if c["fused"] and all(c[k] == v for k, v in want.items()):
             out.append(i)
     return out
+
+
+def packed_ids(mode, **want):
+    out = []
+    for i in range(pkg.config_count(mode)):
+        c = pkg.config_get(mode, i)
+        if not c["fused"] and all(c[k] == v for k, v in want.items()):
+            out.append(i)
+    return out
+
+
+def path_config(path, mode="bf16x3"):
+    """None (the default path) or the first fused configuration of the
+    default tile shape."""
+    return None if path == "default" else fused_ids(mode, block_n=64, group_m=16, kb=4, split_k=1)[0]
 
 
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
@@ -168,15 +185,17 @@ RS = [(1, 1), (5, 5), (7, 3), (3, 9), (11, 11)]
 @pytest.mark.parametrize("R,S", RS)
 @pytest.mark.parametrize("mode,C", [("bf16x3", 8), ("bf16x3", 64), ("tf32x3", 32), ("bf16x3", 16),
                                     ("bf16x3", 48), ("tf32x3", 16)])
-def test_rs_filters_match_oracle(R, S, mode, C):
-    """Gathered (C = 8), im2col-staged in 32-channel boxes (whole-tap chunks)
-    and in 16-channel boxes (C = 16, 48: the last chunk is partial when R*S
-    is odd, its boxes past K are not loaded)."""
+@pytest.mark.parametrize("path", ["default", "fused"])
+def test_rs_filters_match_oracle(R, S, mode, C, path):
+    """Default path: packed for the bf16 mode with C = 16, 48, 64 (the last
+    chunk is partial when R*S*C is not a multiple of 64: its boxes past K are
+    neither loaded nor multiplied).  Fused path: gathered (C = 8), staged by
+    im2col in 32-channel boxes (whole-tap chunks) and in 16-channel boxes."""
     x = W.conv_image(2, 13, 9, C, 160 + R)
     f = W.conv_filter(C, 20, 161 + S, R=R, S=S)
     out0 = W.conv_image(2, 13, 9, 20, 162)
     ref = conv.conv_f64(x, f, 1.5, 0.5, out0)
-    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode, config_id=path_config(path, mode))
     assert oracle.rel_frob(got.reshape(-1, 20), ref.reshape(-1, 20)) <= TOL, (R, S)
 
 
@@ -226,17 +245,87 @@ def test_paper_conv_layer_sampled_pixels(R):
     assert oracle.rel_frob(got.reshape(-1, K)[pix], ref) <= TOL, R
 
 
+@pytest.mark.parametrize("path", ["default", "fused"])
 @pytest.mark.parametrize("mode,C,R", [("bf16x3", 16, 3), ("bf16x3", 48, 5), ("tf32x3", 16, 3), ("bf16x3", 8, 3)])
-def test_infinite_pixel_reaches_only_its_windows(mode, C, R):
+def test_infinite_pixel_reaches_only_its_windows(mode, C, R, path):
     """An Inf pixel makes exactly the outputs whose window holds it
-    non-finite: the unloaded part of a partial last chunk is split as zeros,
-    never as pixels of taps past the filter."""
+    non-finite: the unloaded part of a partial last chunk is split as zeros
+    (fused) or not multiplied (packed), never taken from taps past the
+    filter or from stale shared memory."""
     x = W.conv_image(1, 12, 10, C, 180)
     x[0, 5, 5, 3] = np.inf
     f = W.conv_filter(C, 16, 181, R=R, S=R)
     ref = conv.conv_f64(x, f).reshape(-1, 16)
-    got, _ = run_conv(x, f, 1.0, 0.0, np.zeros((1, 12, 10, 16), np.float32), mode)
+    got, _ = run_conv(x, f, 1.0, 0.0, np.zeros((1, 12, 10, 16), np.float32), mode,
+                      config_id=path_config(path, mode))
     got = got.reshape(-1, 16)
     assert np.array_equal(np.isfinite(got), np.isfinite(ref))
     rows = np.isfinite(ref).all(axis=1)
     assert rows.sum() > 0 and oracle.rel_frob(got[rows], ref[rows]) <= TOL
+
+
+# ----------------------------------------------------------- packed path
+def test_packed_path_is_the_default_where_it_applies():
+    for mode, C, fused in [("bf16x3", 16, False), ("bf16x3", 48, False), ("bf16x6", 32, False),
+                           ("bf16x3", 8, True), ("bf16x3", 12, True), ("tf32x3", 16, True)]:
+        plan = pkg.ConvPlan(1, 6, 5, C, 8, 3, 3, mode=mode)
+        cid = plan.info()["config_id"]
+        plan.destroy()
+        assert pkg.config_get(mode, cid)["fused"] == int(fused), (mode, C)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("R,S,C", [(3, 3, 16), (5, 5, 16), (3, 3, 48), (7, 3, 64), (1, 1, 32)])
+def test_packed_configurations_equal_gemm_on_patch_matrix(mode, R, S, C):
+    """The packed kernel multiplies the split image's planes through im2col
+    boxes; the gemm on the formed patch matrix, same configuration, splits
+    the same values and issues the same MMAs in the same order (uniform data:
+    exponent 0 for both): same bits, for tile widths 64 and 128, folds and
+    split-K."""
+    x = W.conv_image(2, 9, 11, C, 190 + C)
+    f = W.conv_filter(C, 40, 191, R=R, S=S)
+    out0 = W.conv_image(2, 9, 11, 40, 192)
+    P = patches(x, R, S)
+    M, Kd, K = P.shape[0], P.shape[1], 40
+    dP, dB = torch.from_numpy(P).cuda(), torch.from_numpy(f.reshape(Kd, K).copy()).cuda()
+    ref = conv.conv_f64(x, f, 1.0, -0.5, out0).reshape(-1, K)
+    for cid in packed_ids(mode)[::5]:
+        got, _ = run_conv(x, f, 1.0, -0.5, out0, mode, config_id=cid)
+        dC = torch.from_numpy(out0.reshape(-1, K).copy()).cuda()
+        plan = pkg.Plan(M, K, Kd, mode=mode, config_id=cid)
+        plan.execute(dP, dB, dC, 1.0, -0.5)
+        torch.cuda.synchronize()
+        plan.destroy()
+        assert np.array_equal(got.reshape(-1, K).view(np.uint32), dC.cpu().numpy().view(np.uint32)), \
+            (R, S, C, pkg.config_get(mode, cid))
+        assert oracle.rel_frob(got.reshape(-1, K), ref) <= TOL
+
+
+@pytest.mark.parametrize("shift", [-100, 60])
+def test_packed_image_exponent_rescales(shift):
+    """An image outside [2^-48, 2^48) takes the whole-image exponent: the
+    second split pass re-splits it scaled, so tiny inputs keep their low
+    parts and large ones do not overflow bf16 products."""
+    x = W.scaled(W.conv_image(1, 20, 20, 16, 193), shift)
+    f = W.conv_filter(16, 16, 194)
+    ref = conv.conv_f64(x, f)
+    got, cid = run_conv(x, f, 1.0, 0.0, np.zeros((1, 20, 20, 16), np.float32))
+    assert not pkg.config_get("bf16x3", cid)["fused"]
+    assert oracle.rel_frob(got.reshape(-1, 16), ref.reshape(-1, 16)) <= TOL
+
+
+@pytest.mark.parametrize("R,C", [(3, 16), (11, 16), (5, 32)])
+def test_packed_bf16x6_integer_and_uniform(R, C):
+    xi = W.conv_image(2, 10, 13, C, 195, kind="integers")
+    fi = W.conv_filter(C, 24, 196, kind="integers", R=R, S=R)
+    oi = W.conv_image(2, 10, 13, 24, 197, kind="integers")
+    got, _ = run_conv(xi, fi, 1.5, 0.5, oi, "bf16x6")
+    assert np.array_equal(got, conv.conv_f64(xi, fi, 1.5, 0.5, oi).astype(np.float32))
+    x = W.conv_image(2, 10, 13, C, 198)
+    f = W.conv_filter(C, 24, 199, R=R, S=R)
+    ref = conv.conv_f64(x, f).reshape(-1, 24)
+    e6 = oracle.rel_frob(run_conv(x, f, 1.0, 0.0, np.zeros((2, 10, 13, 24), np.float32), "bf16x6")[0]
+                         .reshape(-1, 24), ref)
+    e3 = oracle.rel_frob(run_conv(x, f, 1.0, 0.0, np.zeros((2, 10, 13, 24), np.float32), "bf16x3")[0]
+                         .reshape(-1, 24), ref)
+    assert e6 <= TOL and e6 * 3.0 < e3, (e6, e3)
