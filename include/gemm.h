@@ -154,24 +154,32 @@ gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int
  * zero padding pR = (R-1)/2, pS = (S-1)/2 (the paper benchmarks convolutions
  * with filters specialised from 3x3 to 11x11, Section VI), as an implicit
  * gemm: the patch matrix of the image (M = batch*H*W output pixels by R*S*C
- * taps x channels) is never formed; the fused-split kernel gathers it tile
- * by tile while splitting it.
+ * taps x channels) is never formed.
  *   out[n][h][w][k] = alpha * sum_{r,s,c} in[n][h+r-pR][w+s-pS][c] * f[r][s][c][k]
  *                     + beta * out[n][h][w][k]      (in = 0 outside the image)
  * Execute with gemm_plan_execute(plan, alpha, in, f, beta, out, stream):
  *   in:  NHWC FP32 [batch][H][W][C], channels contiguous, 16-byte aligned;
  *   f:   RSCK FP32 [R][S][C][K] (= the gemm's B, R*S*C x K row-major);
  *   out: NHWC FP32 [batch][H][W][K] (= the gemm's C, ld K).
- * All device memory owned by the caller.  C must be a multiple of 4; the
- * patch tiles are staged by TMA im2col loads when C is a multiple of 16
- * (boxes of 32 or 16 channels of one tap), else gathered by the kernel's
- * threads.  One
- * power-of-two exponent covers the whole image (its max |x|), B is scaled
- * per 128 output channels as in the gemm.  config_id < 0 picks a default;
- * otherwise it must be a fused-split configuration (gemm_config.fused).
- * Errors: INVALID_ARG (sizes, filter sizes, C % 4, mode, configuration),
- * ALIGNMENT (at execute: input not 16-byte aligned), ALLOC, CUDA,
- * UNSUPPORTED_DEVICE. */
+ * All device memory owned by the caller.  Modes BF16X3, TF32X3, BF16X6
+ * (AUTO = BF16X3).  Two paths, chosen by the configuration:
+ *   packed (a configuration with fused == 0; bf16 modes, C a multiple of
+ *     16): each execution splits the image once into bf16 planes in the
+ *     plan's workspace (planes x batch*H*W*C values), and the kernel loads
+ *     the patch tiles from them by TMA im2col boxes of one tap (64 channels
+ *     when C is a multiple of 64, else 16);
+ *   fused-split (fused == 1; BF16X3 and TF32X3, C a multiple of 4): the
+ *     kernel stages FP32 patch tiles (TMA im2col boxes of 32 or 16 channels
+ *     when C is a multiple of 16, else gathered by its threads) and splits
+ *     them itself.
+ * config_id < 0 picks the default: packed where it applies (BF16X6 has no
+ * fused-split kernel), else fused-split.  One power-of-two exponent covers
+ * the whole image (its max |x|); B is scaled per 128 output channels as in
+ * the gemm.
+ * Errors: INVALID_ARG (sizes, filter sizes, C % 4, mode, a packed
+ * configuration where the packed path does not apply), ALIGNMENT (at
+ * execute: input not 16-byte aligned), ALLOC, CUDA, UNSUPPORTED_DEVICE (no
+ * tcgen05, or no im2col tensor maps for a packed plan). */
 gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C, int64_t K, int R,
                                   int S, gemm_mode mode, int config_id, gemm_plan_t* out);
 

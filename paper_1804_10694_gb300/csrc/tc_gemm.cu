@@ -566,7 +566,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           tma_prefetch_desc(mB);
           last_prob = w.prob;
         }
-        int cn0 = 0, ch0 = 0, cw0 = 0;   // CONVA: image, row and column of the tile's first pixel
+        // CONVA: image, row and column of the tile's first pixel; channel, tap
+        // column and tap row of the next box, stepped box by box (no
+        // divisions on the issuing thread's path: they were its bottleneck)
+        int cn0 = 0, ch0 = 0, cw0 = 0, bc = 0, bs = 0, br = 0;
         if constexpr (CONVA != 0) {
           const FusedA fa = sc.srcA(0);
           const int hw = fa.H * fa.W;
@@ -575,6 +578,11 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           const int rem = p0 - cn0 * hw;
           ch0 = rem / fa.W;
           cw0 = rem - ch0 * fa.W;
+          const int k0 = w.c0 * Cfg::BK;
+          const int tap = k0 / fa.C;
+          bc = k0 - tap * fa.C;
+          br = tap / fa.S;
+          bs = tap - br * fa.S;
         }
         for (int c = w.c0; c < w.c1; ++c) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, err)) {
@@ -591,12 +599,14 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             // one tap (C % 64 == 0, so K has no partial chunk)
             const FusedA fa = sc.srcA(0);
             mbar_arrive_expect_tx(fb, Cfg::STAGE);
-            const int tap = kx / fa.C, c0 = kx - tap * fa.C;
-            const int tr = tap / fa.S, ts = tap - tr * fa.S;
 #pragma unroll
             for (int z = 0; z < NP; ++z)
-              tma_load_im2col_4d(sA + z * Cfg::A_PLANE, mA, fb, c0, cw0 - fa.S / 2, ch0 - fa.R / 2,
-                                 cn0 + z * fa.N, static_cast<uint16_t>(ts), static_cast<uint16_t>(tr));
+              tma_load_im2col_4d(sA + z * Cfg::A_PLANE, mA, fb, bc, cw0 - fa.S / 2, ch0 - fa.R / 2,
+                                 cn0 + z * fa.N, static_cast<uint16_t>(bs), static_cast<uint16_t>(br));
+            if ((bc += 64) == fa.C) {
+              bc = 0;
+              if (++bs == fa.S) bs = 0, ++br;
+            }
 #pragma unroll
             for (int z = 0; z < NP; ++z)
               tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
@@ -607,14 +617,15 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             mbar_arrive_expect_tx(fb, NP * (nval * CBOX + Cfg::B_PLANE));
             for (int h = 0; h < Cfg::KSTEPS; ++h) {
               if (h >= nval) break;
-              const int k0 = kx + 16 * h;
-              const int tap = k0 / fa.C, c0 = k0 - tap * fa.C;
-              const int tr = tap / fa.S, ts = tap - tr * fa.S;
 #pragma unroll
               for (int z = 0; z < NP; ++z)
-                tma_load_im2col_4d(sA + z * Cfg::A_PLANE + h * CBOX, mA, fb, c0, cw0 - fa.S / 2,
-                                   ch0 - fa.R / 2, cn0 + z * fa.N, static_cast<uint16_t>(ts),
-                                   static_cast<uint16_t>(tr));
+                tma_load_im2col_4d(sA + z * Cfg::A_PLANE + h * CBOX, mA, fb, bc, cw0 - fa.S / 2,
+                                   ch0 - fa.R / 2, cn0 + z * fa.N, static_cast<uint16_t>(bs),
+                                   static_cast<uint16_t>(br));
+              if ((bc += 16) == fa.C) {
+                bc = 0;
+                if (++bs == fa.S) bs = 0, ++br;
+              }
             }
 #pragma unroll
             for (int z = 0; z < NP; ++z)
