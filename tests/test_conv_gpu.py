@@ -329,3 +329,19 @@ def test_packed_bf16x6_integer_and_uniform(R, C):
     e3 = oracle.rel_frob(run_conv(x, f, 1.0, 0.0, np.zeros((2, 10, 13, 24), np.float32), "bf16x3")[0]
                          .reshape(-1, 24), ref)
     assert e6 <= TOL and e6 * 3.0 < e3, (e6, e3)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("n,H,Wd,C,K,R", [(3, 5, 7, 32, 200, 3), (1, 1, 1, 16, 8, 5), (2, 1, 9, 64, 130, 3),
+                                          (1, 17, 3, 48, 64, 7)])
+def test_packed_wide_outputs_and_small_images(mode, n, H, Wd, C, K, R):
+    """Several output-channel tiles (K = 200, 130), 1x1 and one-row images
+    (taps almost all in the padding), 64-channel boxes next to 16-channel
+    ones."""
+    x = W.conv_image(n, H, Wd, C, 200 + C)
+    f = W.conv_filter(C, K, 201, R=R, S=R)
+    out0 = W.conv_image(n, H, Wd, K, 202)
+    ref = conv.conv_f64(x, f, 1.5, 0.5, out0).reshape(-1, K)
+    got, cid = run_conv(x, f, 1.5, 0.5, out0, mode)
+    assert not pkg.config_get(mode, cid)["fused"]
+    assert oracle.rel_frob(got.reshape(-1, K), ref) <= TOL
