@@ -165,9 +165,11 @@ gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int
  * (AUTO = BF16X3).  Two paths, chosen by the configuration:
  *   packed (a configuration with fused == 0; bf16 modes, C a multiple of
  *     16): each execution splits the image once into bf16 planes in the
- *     plan's workspace (planes x batch*H*W*C values), and the kernel loads
- *     the patch tiles from them by TMA im2col boxes of one tap (64 channels
- *     when C is a multiple of 64, else 16);
+ *     plan's workspace (planes x batch*H*W*C values; for BF16X3 with C not
+ *     a multiple of 64 the two planes are interleaved by 16-channel groups),
+ *     and the kernel loads the patch tiles from them by TMA im2col boxes of
+ *     one tap (64 channels when C is a multiple of 64, else one 16-channel
+ *     group: its hi and lo together, or one plane's for BF16X6);
  *   fused-split (fused == 1; BF16X3 and TF32X3, C a multiple of 4): the
  *     kernel stages FP32 patch tiles (TMA im2col boxes of 32 or 16 channels
  *     when C is a multiple of 16, else gathered by its threads) and splits

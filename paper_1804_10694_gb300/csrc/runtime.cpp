@@ -278,18 +278,24 @@ static gemm_status encode_im2col(CUtensorMap* map, const float* X, int64_t batch
 // values, and each load brings 128 output pixels times box_c channels of one
 // tap: 64 (128-byte rows, 128-byte swizzle) or 16 (32-byte rows, 32-byte
 // swizzle); plane z's pixels are images z batch onward, whose zero padding
-// TMA supplies image by image.
+// TMA supplies image by image.  box_c = 32: the two planes interleaved by
+// 16-channel groups, one image of 2C channels, boxes of one group's hi and
+// lo (64-byte rows, 64-byte swizzle).
 static gemm_status encode_im2col_planes(CUtensorMap* map, const void* planes, int planes_n, int64_t batch,
                                         int64_t H, int64_t W, int64_t C, int R, int S, int box_c) {
   if (!g_encode_im2col) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "cuTensorMapEncodeIm2col unavailable");
-  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(planes_n * batch)};
-  cuuint64_t strides[3] = {(cuuint64_t)(C * 2), (cuuint64_t)(W * C * 2), (cuuint64_t)(H * W * C * 2)};
+  const bool ilv = box_c == 32;
+  const int64_t Ct = ilv ? 2 * C : C;   // channels of one stacked image
+  cuuint64_t dims[4] = {(cuuint64_t)Ct, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(ilv ? batch : planes_n * batch)};
+  cuuint64_t strides[3] = {(cuuint64_t)(Ct * 2), (cuuint64_t)(W * Ct * 2), (cuuint64_t)(H * W * Ct * 2)};
   const int lower[2] = {-(S / 2), -(R / 2)}, upper[2] = {-(S / 2), -(R / 2)};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = g_encode_im2col(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(planes), dims,
                                strides, lower, upper, (cuuint32_t)box_c, 128, estr,
                                CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               box_c == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_32B,
+                               box_c == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                               : box_c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
@@ -490,7 +496,7 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
     const int64_t elems = (int64_t)p->conv_batch * p->args.conv_H * p->args.conv_W * p->args.conv_C;
     if (!p->launch.fused) {
       // packed: the image split once into planes, then B packed alone
-      e = image_split_launch(p->prec, A, elems, p->amaxA, p->planesA, p->sms, s);
+      e = image_split_launch(p->prec, A, elems, p->amaxA, p->planesA, p->sms, s, p->args.conv_box_c == 32);
       if (e == cudaSuccess)
         e = pack_launch(p->prec, nullptr, 0, K, K, B, N, p->ldb, p->amaxA, p->amaxB, p->cntA, p->cntB,
                         nullptr, p->planesB, p->pitch, p->sms, s);
@@ -984,7 +990,8 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p, false,
                                     false, packed_conv ? elems : -1);
   if (st != GEMM_OK) return st;
-  const int box_c = C % 64 == 0 ? 64 : 16;   // packed: channels per im2col box
+  // packed: channels per im2col box (32: the two planes interleaved)
+  const int box_c = C % 64 == 0 ? 64 : prec_planes(prec_of_mode(mode)) == 2 ? 32 : 16;
   if (packed_conv && (st = encode_im2col_planes(&p->tmA, p->planesA, prec_planes(p->prec), batch, H, W, C, R,
                                                 S, box_c)) != GEMM_OK) {
     plan_destroy_impl(p);

@@ -588,15 +588,19 @@ __global__ void __launch_bounds__(256, 4) grouped_pack_kernel(const GroupedProbl
 
 // ------------------------------------------- convolution image, split once
 // The packed convolution splits its NHWC image once, element by element,
-// into bf16 planes [plane][elems] (plane z = hi, mid, lo), under one
+// into bf16 planes [plane][elems] (plane z = hi, mid, lo), or (ILV, two
+// planes) into one image of twice the channels whose 16-channel groups hold
+// hi then lo: element e = 16 g + j of a pixel's channels goes to 32 g + j
+// (hi) and 32 g + 16 + j (lo), i.e. index 2e - (e mod 16) and 16 more.  One
 // exponent for the whole image.  kFirst splits unscaled and folds max |x|
 // into amax[0]; kRescale, launched after it, reads the final max and returns
 // at once when the exponent is 0 (the usual case), else re-splits every
 // element with it.  Four float4 loads a thread are in flight per iteration.
-template <Prec PR, Pass PASS>
+template <Prec PR, Pass PASS, bool ILV>
 __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restrict__ X, int64_t n4,
                                                            unsigned* __restrict__ amax,
                                                            __nv_bfloat16* __restrict__ P, int64_t plane) {
+  static_assert(!ILV || PR == Prec::BF16, "interleaved layout: two planes");
   float sc = 1.0f;
   if (PASS == kRescale) {
     const int e = block_exponent(*amax);
@@ -641,8 +645,11 @@ __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restri
           h[j] = t.hi;
           l[j] = t.lo;
         }
-        *reinterpret_cast<uint2*>(P + 4 * i) = *reinterpret_cast<const uint2*>(h);
-        *reinterpret_cast<uint2*>(P + plane + 4 * i) = *reinterpret_cast<const uint2*>(l);
+        const int64_t e = 4 * i;
+        const int64_t oh = ILV ? 2 * e - (e & 15) : e;
+        const int64_t ol = ILV ? oh + 16 : plane + e;
+        *reinterpret_cast<uint2*>(P + oh) = *reinterpret_cast<const uint2*>(h);
+        *reinterpret_cast<uint2*>(P + ol) = *reinterpret_cast<const uint2*>(l);
       }
     }
   }
@@ -754,8 +761,9 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
 }
 
 cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigned* amax, void* planes,
-                               int sms, cudaStream_t s) {
+                               int sms, cudaStream_t s, bool interleave) {
   if (prec != Prec::BF16 && prec != Prec::BF16X6) return cudaErrorInvalidValue;
+  if (interleave && (prec != Prec::BF16 || elems % 16 != 0)) return cudaErrorInvalidValue;
   if (elems % 4 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0) return cudaErrorInvalidValue;
   const int64_t n4 = elems / 4;
   if (n4 == 0) return cudaSuccess;
@@ -763,11 +771,14 @@ cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigne
   const float4* X4 = reinterpret_cast<const float4*>(X);
   __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
   if (prec == Prec::BF16X6) {
-    image_split_kernel<Prec::BF16X6, kFirst><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
-    image_split_kernel<Prec::BF16X6, kRescale><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16X6, kFirst, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16X6, kRescale, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+  } else if (interleave) {
+    image_split_kernel<Prec::BF16, kFirst, true><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16, kRescale, true><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
   } else {
-    image_split_kernel<Prec::BF16, kFirst><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
-    image_split_kernel<Prec::BF16, kRescale><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16, kFirst, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::BF16, kRescale, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
   }
   return cudaGetLastError();
 }

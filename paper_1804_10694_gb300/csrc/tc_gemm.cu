@@ -333,21 +333,29 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
 // convolution staged in 16-channel im2col boxes (its own instantiation, so
 // that the 128-byte path keeps its registers).
 // CONVA != 0: the packed convolution.  A is the patch matrix of the image's
-// bf16 planes, loaded as im2col boxes of CONVA channels of one tap; B's
-// planes are packed as usual.  CONVA = 64 (C a multiple of 64): one box of
-// 128-byte rows a plane and chunk, laid out as a packed A plane (128-byte
-// swizzle).  CONVA = 16: four boxes of 32-byte rows (32-byte swizzle), k-step
-// kk of a chunk being the 4 KB sub-tile kk of each A plane, read by MMA
-// descriptors of the 32-byte swizzle; boxes of a last, partial chunk past K
-// are neither loaded nor multiplied.
+// bf16 planes, loaded as im2col boxes of one tap; B's planes are packed as
+// usual.  CONVA = 64 (C a multiple of 64): one box of 64 channels (128-byte
+// rows) a plane and chunk, laid out as a packed A plane (128-byte swizzle).
+// CONVA = 32 (two planes): the planes are interleaved by 16-channel groups
+// (hi then lo of a group, 64 bytes a pixel), and a chunk is four boxes of
+// one group each, 64-byte rows in the 64-byte swizzle: k-step kk reads box
+// kk, hi at its rows' first 32 bytes and lo at their last.  CONVA = 16 (any
+// plane count): four boxes of 16 channels a plane, 32-byte rows in the
+// 32-byte swizzle, k-step kk being the 4 KB sub-tile kk of each A plane.
+// With 16-channel groups, boxes of a last, partial chunk past K are neither
+// loaded nor multiplied.
 template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128,
           int CONVA = 0>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kWideEpilogue>;
-  static_assert(CONVA == 0 || ((CONVA == 16 || CONVA == 64) && !FUSED && !TF32),
-                "packed convolution: bf16 planes, 16- or 64-channel boxes");
+  static_assert(CONVA == 0 ||
+                    ((CONVA == 16 || CONVA == 64 || (CONVA == 32 && NP == 2)) && !FUSED && !TF32),
+                "packed convolution: bf16 planes, 16-, 32- (interleaved) or 64-channel boxes");
   constexpr bool CB16 = CONVA == 16;
+  constexpr bool CB32 = CONVA == 32;
+  constexpr bool CGRP = CB16 || CB32;   // k-steps are 16-channel groups of one tap
   constexpr int CBOX = 128 * 32;   // bytes of one 16-channel bf16 im2col box
+  constexpr int IBOX = 128 * 64;   // bytes of one interleaved hi|lo box
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -610,6 +618,25 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
 #pragma unroll
             for (int z = 0; z < NP; ++z)
               tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
+          } else if constexpr (CB32) {
+            // boxes: the same pixels times one 16-channel group of one tap,
+            // hi and lo interleaved (channel 2c of the interleaved image),
+            // one per k-step
+            const FusedA fa = sc.srcA(0);
+            const int nval = min(Cfg::KSTEPS, (fa.K - kx) / 16);
+            mbar_arrive_expect_tx(fb, nval * IBOX + NP * Cfg::B_PLANE);
+            for (int h = 0; h < Cfg::KSTEPS; ++h) {
+              if (h >= nval) break;
+              tma_load_im2col_4d(sA + h * IBOX, mA, fb, 2 * bc, cw0 - fa.S / 2, ch0 - fa.R / 2, cn0,
+                                 static_cast<uint16_t>(bs), static_cast<uint16_t>(br));
+              if ((bc += 16) == fa.C) {
+                bc = 0;
+                if (++bs == fa.S) bs = 0, ++br;
+              }
+            }
+#pragma unroll
+            for (int z = 0; z < NP; ++z)
+              tma_load_3d(sA + NP * Cfg::A_PLANE + z * Cfg::B_PLANE, mB, fb, kx, w.tn * BN, z);
           } else if constexpr (CB16) {
             // boxes: the same pixels times 16 channels of one tap, one per k-step
             const FusedA fa = sc.srcA(0);
@@ -669,7 +696,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_f32acc(TF32, 128, BN);
       int convK = 0;   // 16-channel boxes: K of the patch matrix
-      if constexpr (CB16) convK = sc.srcA(0).K;
+      if constexpr (CGRP) convK = sc.srcA(0).K;
       uint32_t stage = 0, phase = 0, ab = 0, aphase = 0;
       bool ok = true;
       bool any = false;
@@ -696,13 +723,17 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             const uint32_t sBhi = sAhi + NP * Cfg::A_PLANE;
             const uint32_t sBlo = sBhi + Cfg::B_PLANE;
             // 16-channel boxes: k-steps of this chunk inside K (its boxes that were loaded)
-            const int kv = CB16 ? min(Cfg::KSTEPS, (convK - c * Cfg::BK) / 16) : Cfg::KSTEPS;
+            const int kv = CGRP ? min(Cfg::KSTEPS, (convK - c * Cfg::BK) / 16) : Cfg::KSTEPS;
 #pragma unroll
             for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
-              if (CB16 && kk >= kv) break;
+              if (CGRP && kk >= kv) break;
               const uint32_t off = kk * 32;   // 32 bytes = one MMA's K slice
-              const uint64_t dAhi = CB16 ? sdesc_k_sw32(sAhi + kk * CBOX) : sdesc_k<Cfg::SW>(sAhi + off);
-              const uint64_t dAlo = CB16 ? sdesc_k_sw32(sAlo + kk * CBOX) : sdesc_k<Cfg::SW>(sAlo + off);
+              const uint64_t dAhi = CB32   ? sdesc_k_sw64(sAhi + kk * IBOX)
+                                    : CB16 ? sdesc_k_sw32(sAhi + kk * CBOX)
+                                           : sdesc_k<Cfg::SW>(sAhi + off);
+              const uint64_t dAlo = CB32   ? sdesc_k_sw64(sAhi + kk * IBOX + 32)
+                                    : CB16 ? sdesc_k_sw32(sAlo + kk * CBOX)
+                                           : sdesc_k<Cfg::SW>(sAlo + off);
               const uint64_t dBhi = sdesc_k<Cfg::SW>(sBhi + off);
               const uint64_t dBlo = sdesc_k<Cfg::SW>(sBlo + off);
               const uint32_t acc = (c > cb || kk > 0) ? 1u : 0u;
@@ -1234,6 +1265,11 @@ static cudaError_t prepare_variant() {
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    Cfg::SMEM);
+        if constexpr (NP == 2) {
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 32>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        }
       }
     }
     if (e != cudaSuccess) return e;
@@ -1287,6 +1323,12 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
       if constexpr (TF32) return cudaErrorInvalidValue;
       else if (a.conv_box_c == 64)
         e = launch_dependent(tc_conv_kernel<BN, NP, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      else if (a.conv_box_c == 32) {
+        if constexpr (NP == 2)
+          e = launch_dependent(tc_conv_kernel<BN, NP, 32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+        else
+          return cudaErrorInvalidValue;
+      }
       else
         e = launch_dependent(tc_conv_kernel<BN, NP, 16>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
     } else {
