@@ -3,7 +3,8 @@
 // autotuner's own timings, predicts log execution time from shape and
 // configuration features, so that a configuration can be chosen (argmin over
 // the candidates) without timing them.  Exhaustive tuning stays available as
-// the fallback and as the judge of the model's regret.
+// the fallback and as the reference that the model's regret is measured
+// against.
 //
 // Training runs on the GPU with the library's kernels: forward and per-sample
 // backward kernels (mlp.cu), weight gradients as dZ^T H products by the
