@@ -163,19 +163,20 @@ gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int
  *   out: NHWC FP32 [batch][H][W][K] (= the gemm's C, ld K).
  * All device memory owned by the caller.  Modes BF16X3, TF32X3, BF16X6
  * (AUTO = BF16X3).  Two paths, chosen by the configuration:
- *   packed (a configuration with fused == 0; bf16 modes, C a multiple of
- *     16): each execution splits the image once into bf16 planes in the
- *     plan's workspace (planes x batch*H*W*C values; for BF16X3 with C not
- *     a multiple of 64 the two planes are interleaved by 16-channel groups),
- *     and the kernel loads the patch tiles from them by TMA im2col boxes of
- *     one tap (64 channels when C is a multiple of 64, else one 16-channel
- *     group: its hi and lo together, or one plane's for BF16X6);
+ *   packed (a configuration with fused == 0; C a multiple of 16): each
+ *     execution splits the image once into planes in the plan's workspace
+ *     (planes x batch*H*W*C values; for BF16X3 with C not a multiple of 64,
+ *     and always for TF32X3, the two planes interleaved by 16-channel
+ *     groups), and the kernel loads the patch tiles from them by TMA im2col
+ *     boxes of one tap (64 channels for BF16X3/BF16X6 when C is a multiple
+ *     of 64, else one 16-channel group: its hi and lo together, or one
+ *     plane's for BF16X6);
  *   fused-split (fused == 1; BF16X3 and TF32X3, C a multiple of 4): the
  *     kernel stages FP32 patch tiles (TMA im2col boxes of 32 or 16 channels
  *     when C is a multiple of 16, else gathered by its threads) and splits
  *     them itself.
- * config_id < 0 picks the default: packed where it applies (BF16X6 has no
- * fused-split kernel), else fused-split.  One power-of-two exponent covers
+ * config_id < 0 picks the default: packed where it applies (C a multiple of
+ * 16; BF16X6 has no fused-split kernel), else fused-split.  One power-of-two exponent covers
  * the whole image (its max |x|); B is scaled per 128 output channels as in
  * the gemm.
  * Errors: INVALID_ARG (sizes, filter sizes, C % 4, mode, a packed

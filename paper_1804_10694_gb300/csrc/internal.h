@@ -119,7 +119,7 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
 int pack_first_items(int64_t M, int64_t N, int64_t pitch);
 // Packed convolution: split the NHWC image X (elems FP32 values, elems % 4
 // == 0, X 16-byte aligned) into bf16 planes [plane][elems], or (interleave,
-// BF16 only, C % 16 == 0) one image whose 16-channel groups hold hi then lo,
+// BF16 or TF32, C % 16 == 0) one image whose 16-channel groups hold hi then lo,
 // under one exponent from its max |x|, folded into amax[0] (zero on entry).
 // Two launches.
 cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigned* amax, void* planes,

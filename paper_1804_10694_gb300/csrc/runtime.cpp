@@ -281,21 +281,25 @@ static gemm_status encode_im2col(CUtensorMap* map, const float* X, int64_t batch
 // TMA supplies image by image.  box_c = 32: the two planes interleaved by
 // 16-channel groups, one image of 2C channels, boxes of one group's hi and
 // lo (64-byte rows, 64-byte swizzle).
-static gemm_status encode_im2col_planes(CUtensorMap* map, const void* planes, int planes_n, int64_t batch,
-                                        int64_t H, int64_t W, int64_t C, int R, int S, int box_c) {
+static gemm_status encode_im2col_planes(CUtensorMap* map, Prec prec, const void* planes, int planes_n,
+                                        int64_t batch, int64_t H, int64_t W, int64_t C, int R, int S,
+                                        int box_c) {
   if (!g_encode_im2col) return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "cuTensorMapEncodeIm2col unavailable");
   const bool ilv = box_c == 32;
   const int64_t Ct = ilv ? 2 * C : C;   // channels of one stacked image
+  const int64_t es = prec_elem_bytes(prec);
+  const int64_t box_bytes = box_c * es;   // 32, 64 or 128: the swizzle span
   cuuint64_t dims[4] = {(cuuint64_t)Ct, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(ilv ? batch : planes_n * batch)};
-  cuuint64_t strides[3] = {(cuuint64_t)(Ct * 2), (cuuint64_t)(W * Ct * 2), (cuuint64_t)(H * W * Ct * 2)};
+  cuuint64_t strides[3] = {(cuuint64_t)(Ct * es), (cuuint64_t)(W * Ct * es), (cuuint64_t)(H * W * Ct * es)};
   const int lower[2] = {-(S / 2), -(R / 2)}, upper[2] = {-(S / 2), -(R / 2)};
   cuuint32_t estr[4] = {1, 1, 1, 1};
-  CUresult r = g_encode_im2col(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(planes), dims,
+  CUresult r = g_encode_im2col(map, prec_bf16(prec) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               4, const_cast<void*>(planes), dims,
                                strides, lower, upper, (cuuint32_t)box_c, 128, estr,
                                CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               box_c == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
-                               : box_c == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                             : CU_TENSOR_MAP_SWIZZLE_32B,
+                               box_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                               : box_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                 : CU_TENSOR_MAP_SWIZZLE_32B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
@@ -941,11 +945,11 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
   if (mode != GEMM_MODE_BF16X3 && mode != GEMM_MODE_TF32X3 && mode != GEMM_MODE_BF16X6)
     return fail(GEMM_ERR_INVALID_ARG, "the convolution runs in BF16X3, TF32X3 or BF16X6 mode");
-  // Packed path (bf16 modes, C a multiple of 16): the image is split once
-  // into planes and the kernel loads 16-channel im2col boxes of them.
-  // Fused path (the other cases): the FP32 patches are staged and split
-  // inside the kernel, once per tap.
-  const bool pack_shape = mode != GEMM_MODE_TF32X3 && C % 16 == 0;
+  // Packed path (C a multiple of 16): the image is split once into planes
+  // and the kernel loads im2col boxes of them.  Fused path (the other
+  // cases): the FP32 patches are staged and split inside the kernel, once
+  // per tap.
+  const bool pack_shape = C % 16 == 0;
   if (mode == GEMM_MODE_BF16X6 && !pack_shape)
     return fail(GEMM_ERR_INVALID_ARG, "the BF16X6 convolution needs C a multiple of 16 (C=%lld)",
                 (long long)C);
@@ -956,8 +960,8 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
       return fail(GEMM_ERR_INVALID_ARG, "configuration %d out of range", config_id);
     if (!c.fused && !pack_shape)
       return fail(GEMM_ERR_INVALID_ARG,
-                  "configuration %d is packed: the convolution runs packed only in a bf16 mode with C "
-                  "a multiple of 16", config_id);
+                  "configuration %d is packed: the convolution runs packed only with C a multiple of 16",
+                  config_id);
   }
   DeviceState* dev;
   gemm_status st0 = device_state(&dev, nullptr);   // also resolves the tensor-map encoders
@@ -990,10 +994,12 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p, false,
                                     false, packed_conv ? elems : -1);
   if (st != GEMM_OK) return st;
-  // packed: channels per im2col box (32: the two planes interleaved)
-  const int box_c = C % 64 == 0 ? 64 : prec_planes(prec_of_mode(mode)) == 2 ? 32 : 16;
-  if (packed_conv && (st = encode_im2col_planes(&p->tmA, p->planesA, prec_planes(p->prec), batch, H, W, C, R,
-                                                S, box_c)) != GEMM_OK) {
+  // packed: channels per im2col box (32: the two planes interleaved by
+  // 16-channel groups, the only layout of tf32 planes)
+  const Prec pr = prec_of_mode(mode);
+  const int box_c = pr == Prec::TF32 ? 32 : C % 64 == 0 ? 64 : prec_planes(pr) == 2 ? 32 : 16;
+  if (packed_conv && (st = encode_im2col_planes(&p->tmA, p->prec, p->planesA, prec_planes(p->prec), batch, H,
+                                                W, C, R, S, box_c)) != GEMM_OK) {
     plan_destroy_impl(p);
     return st;
   }

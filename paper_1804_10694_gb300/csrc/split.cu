@@ -589,18 +589,20 @@ __global__ void __launch_bounds__(256, 4) grouped_pack_kernel(const GroupedProbl
 // ------------------------------------------- convolution image, split once
 // The packed convolution splits its NHWC image once, element by element,
 // into bf16 planes [plane][elems] (plane z = hi, mid, lo), or (ILV, two
-// planes) into one image of twice the channels whose 16-channel groups hold
-// hi then lo: element e = 16 g + j of a pixel's channels goes to 32 g + j
-// (hi) and 32 g + 16 + j (lo), i.e. index 2e - (e mod 16) and 16 more.  One
-// exponent for the whole image.  kFirst splits unscaled and folds max |x|
+// planes: bf16, or tf32 values in 32-bit words) into one image of twice the
+// channels whose 16-channel groups hold hi then lo: element e = 16 g + j of
+// a pixel's channels goes to 32 g + j (hi) and 32 g + 16 + j (lo), i.e.
+// index 2e - (e mod 16) and 16 more.  One exponent for the whole image.  kFirst splits unscaled and folds max |x|
 // into amax[0]; kRescale, launched after it, reads the final max and returns
 // at once when the exponent is 0 (the usual case), else re-splits every
 // element with it.  Four float4 loads a thread are in flight per iteration.
 template <Prec PR, Pass PASS, bool ILV>
 __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restrict__ X, int64_t n4,
                                                            unsigned* __restrict__ amax,
-                                                           __nv_bfloat16* __restrict__ P, int64_t plane) {
-  static_assert(!ILV || PR == Prec::BF16, "interleaved layout: two planes");
+                                                           void* __restrict__ planes, int64_t plane) {
+  static_assert(PR != Prec::F32 && (ILV ? PR != Prec::BF16X6 : PR != Prec::TF32),
+                "interleaved: two planes (bf16 or tf32); planar: bf16");
+  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
   float sc = 1.0f;
   if (PASS == kRescale) {
     const int e = block_exponent(*amax);
@@ -625,7 +627,17 @@ __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restri
 #pragma unroll
         for (int j = 0; j < 4; ++j) m = max(m, abs_bits(x[j]));
       }
-      if (PR == Prec::BF16X6) {
+      if (PR == Prec::TF32) {
+        float4 h, l;
+        split_tf32(x[0] * sc, h.x, l.x);
+        split_tf32(x[1] * sc, h.y, l.y);
+        split_tf32(x[2] * sc, h.z, l.z);
+        split_tf32(x[3] * sc, h.w, l.w);
+        const int64_t e = 4 * i;
+        float* Pf = static_cast<float*>(planes);
+        *reinterpret_cast<float4*>(Pf + 2 * e - (e & 15)) = h;
+        *reinterpret_cast<float4*>(Pf + 2 * e - (e & 15) + 16) = l;
+      } else if (PR == Prec::BF16X6) {
         __align__(8) __nv_bfloat16 h[4], mi[4], l[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -762,15 +774,18 @@ cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int6
 
 cudaError_t image_split_launch(Prec prec, const float* X, int64_t elems, unsigned* amax, void* planes,
                                int sms, cudaStream_t s, bool interleave) {
-  if (prec != Prec::BF16 && prec != Prec::BF16X6) return cudaErrorInvalidValue;
-  if (interleave && (prec != Prec::BF16 || elems % 16 != 0)) return cudaErrorInvalidValue;
+  if (prec == Prec::F32) return cudaErrorInvalidValue;
+  if (interleave ? (prec == Prec::BF16X6 || elems % 16 != 0) : prec == Prec::TF32) return cudaErrorInvalidValue;
   if (elems % 4 != 0 || reinterpret_cast<uintptr_t>(X) % 16 != 0) return cudaErrorInvalidValue;
   const int64_t n4 = elems / 4;
   if (n4 == 0) return cudaSuccess;
   const int grid = grid_for((n4 + 1023) / 1024, sms);
   const float4* X4 = reinterpret_cast<const float4*>(X);
-  __nv_bfloat16* P = static_cast<__nv_bfloat16*>(planes);
-  if (prec == Prec::BF16X6) {
+  void* P = planes;
+  if (prec == Prec::TF32) {
+    image_split_kernel<Prec::TF32, kFirst, true><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+    image_split_kernel<Prec::TF32, kRescale, true><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
+  } else if (prec == Prec::BF16X6) {
     image_split_kernel<Prec::BF16X6, kFirst, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
     image_split_kernel<Prec::BF16X6, kRescale, false><<<grid, 256, 0, s>>>(X4, n4, amax, P, elems);
   } else if (interleave) {

@@ -337,9 +337,11 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
 // usual.  CONVA = 64 (C a multiple of 64): one box of 64 channels (128-byte
 // rows) a plane and chunk, laid out as a packed A plane (128-byte swizzle).
 // CONVA = 32 (two planes): the planes are interleaved by 16-channel groups
-// (hi then lo of a group, 64 bytes a pixel), and a chunk is four boxes of
-// one group each, 64-byte rows in the 64-byte swizzle: k-step kk reads box
-// kk, hi at its rows' first 32 bytes and lo at their last.  CONVA = 16 (any
+// (hi then lo of a group), and a box is one group: for bf16 64-byte rows in
+// the 64-byte swizzle, four boxes a chunk, k-step kk reading box kk (hi at
+// its rows' first 32 bytes, lo at their last); for tf32 128-byte rows in the
+// 128-byte swizzle, two boxes a chunk, k-step kk reading box kk / 2 at
+// 32 (kk mod 2) (hi) and 64 more (lo).  CONVA = 16 (any
 // plane count): four boxes of 16 channels a plane, 32-byte rows in the
 // 32-byte swizzle, k-step kk being the 4 KB sub-tile kk of each A plane.
 // With 16-channel groups, boxes of a last, partial chunk past K are neither
@@ -348,14 +350,15 @@ template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FB
           int CONVA = 0>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kWideEpilogue>;
-  static_assert(CONVA == 0 ||
-                    ((CONVA == 16 || CONVA == 64 || (CONVA == 32 && NP == 2)) && !FUSED && !TF32),
-                "packed convolution: bf16 planes, 16-, 32- (interleaved) or 64-channel boxes");
+  static_assert(CONVA == 0 || (!FUSED && ((CONVA == 32 && NP == 2) || ((CONVA == 16 || CONVA == 64) && !TF32))),
+                "packed convolution: 32 (interleaved planes), or bf16 16- or 64-channel boxes");
   constexpr bool CB16 = CONVA == 16;
   constexpr bool CB32 = CONVA == 32;
-  constexpr bool CGRP = CB16 || CB32;   // k-steps are 16-channel groups of one tap
+  constexpr bool CGRP = CB16 || CB32;   // k-steps lie in 16-channel groups of one tap
   constexpr int CBOX = 128 * 32;   // bytes of one 16-channel bf16 im2col box
-  constexpr int IBOX = 128 * 64;   // bytes of one interleaved hi|lo box
+  constexpr int IBOX = TF32 ? 128 * 128 : 128 * 64;   // bytes of one interleaved hi|lo box
+  constexpr int GSTEPS = TF32 ? 2 : 1;                // k-steps per 16-channel group
+  constexpr int KELEM = TF32 ? 8 : 16;                // elements per k-step
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -623,9 +626,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             // hi and lo interleaved (channel 2c of the interleaved image),
             // one per k-step
             const FusedA fa = sc.srcA(0);
-            const int nval = min(Cfg::KSTEPS, (fa.K - kx) / 16);
+            const int nval = min(Cfg::KSTEPS / GSTEPS, (fa.K - kx) / 16);
             mbar_arrive_expect_tx(fb, nval * IBOX + NP * Cfg::B_PLANE);
-            for (int h = 0; h < Cfg::KSTEPS; ++h) {
+            for (int h = 0; h < Cfg::KSTEPS / GSTEPS; ++h) {
               if (h >= nval) break;
               tma_load_im2col_4d(sA + h * IBOX, mA, fb, 2 * bc, cw0 - fa.S / 2, ch0 - fa.R / 2, cn0,
                                  static_cast<uint16_t>(bs), static_cast<uint16_t>(br));
@@ -722,16 +725,18 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             const uint32_t sAlo = sAhi + Cfg::A_PLANE;
             const uint32_t sBhi = sAhi + NP * Cfg::A_PLANE;
             const uint32_t sBlo = sBhi + Cfg::B_PLANE;
-            // 16-channel boxes: k-steps of this chunk inside K (its boxes that were loaded)
-            const int kv = CGRP ? min(Cfg::KSTEPS, (convK - c * Cfg::BK) / 16) : Cfg::KSTEPS;
+            // 16-channel groups: k-steps of this chunk inside K (its boxes that were loaded)
+            const int kv = CGRP ? min(Cfg::KSTEPS, (convK - c * Cfg::BK) / KELEM) : Cfg::KSTEPS;
 #pragma unroll
             for (int kk = 0; kk < Cfg::KSTEPS; ++kk) {
               if (CGRP && kk >= kv) break;
               const uint32_t off = kk * 32;   // 32 bytes = one MMA's K slice
-              const uint64_t dAhi = CB32   ? sdesc_k_sw64(sAhi + kk * IBOX)
+              // interleaved box of this k-step and the hi part's offset in its rows
+              const uint32_t ib = sAhi + (kk / GSTEPS) * IBOX + (kk % GSTEPS) * 32;
+              const uint64_t dAhi = CB32   ? (TF32 ? sdesc_k_sw128(ib) : sdesc_k_sw64(ib))
                                     : CB16 ? sdesc_k_sw32(sAhi + kk * CBOX)
                                            : sdesc_k<Cfg::SW>(sAhi + off);
-              const uint64_t dAlo = CB32   ? sdesc_k_sw64(sAhi + kk * IBOX + 32)
+              const uint64_t dAlo = CB32   ? (TF32 ? sdesc_k_sw128(ib + 64) : sdesc_k_sw64(ib + 32))
                                     : CB16 ? sdesc_k_sw32(sAlo + kk * CBOX)
                                            : sdesc_k<Cfg::SW>(sAlo + off);
               const uint64_t dBhi = sdesc_k<Cfg::SW>(sBhi + off);
@@ -1155,12 +1160,12 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
 
 // Packed convolution: A's planes loaded as im2col boxes (CB channels) of
 // the split image.
-template <int BN, int NP, int CB>
-__global__ void __launch_bounds__(TcCfg<BN, false, false, NP>::THREADS, 1)
+template <int BN, bool TF32, int NP, int CB>
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
     tc_conv_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcArgs a) {
   SingleSched sc{&tmA, &tmB, &a};
-  tc_gemm_body<BN, false, SingleSched, false, NP, 128, CB>(sc);
+  tc_gemm_body<BN, TF32, SingleSched, false, NP, 128, CB>(sc);
 }
 
 template <int BN, bool TF32, int NP>
@@ -1260,16 +1265,16 @@ static cudaError_t prepare_variant() {
                                  TcCfg<BN, TF32, false, NP, true>::SMEM);
       if constexpr (!TF32) {
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg::SMEM);
+          e = cudaFuncSetAttribute(tc_conv_kernel<BN, false, NP, 16>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
         if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   Cfg::SMEM);
-        if constexpr (NP == 2) {
-          if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(tc_conv_kernel<BN, NP, 32>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-        }
+          e = cudaFuncSetAttribute(tc_conv_kernel<BN, false, NP, 64>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+      }
+      if constexpr (NP == 2) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(tc_conv_kernel<BN, TF32, NP, 32>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
       }
     }
     if (e != cudaSuccess) return e;
@@ -1320,17 +1325,18 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
     if (e != cudaSuccess) return e;
     if (a.conv) {
       // packed convolution: tmA maps the split image's planes for im2col loads
-      if constexpr (TF32) return cudaErrorInvalidValue;
-      else if (a.conv_box_c == 64)
-        e = launch_dependent(tc_conv_kernel<BN, NP, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
-      else if (a.conv_box_c == 32) {
+      if (a.conv_box_c == 32) {
         if constexpr (NP == 2)
-          e = launch_dependent(tc_conv_kernel<BN, NP, 32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+          e = launch_dependent(tc_conv_kernel<BN, TF32, NP, 32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
         else
           return cudaErrorInvalidValue;
+      } else if constexpr (TF32) {
+        return cudaErrorInvalidValue;   // tf32 planes are always interleaved
+      } else if (a.conv_box_c == 64) {
+        e = launch_dependent(tc_conv_kernel<BN, false, NP, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      } else {
+        e = launch_dependent(tc_conv_kernel<BN, false, NP, 16>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
       }
-      else
-        e = launch_dependent(tc_conv_kernel<BN, NP, 16>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
     } else {
       e = launch_dependent(tc_gemm_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
     }

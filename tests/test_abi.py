@@ -95,7 +95,7 @@ def test_build_flags_target_sm103a():
 def test_conv3x3_plan_argument_validation():
     """Rejected before any device work: channels not a multiple of 4,
     non-positive sizes, a SIMT mode, a packed configuration id where the
-    packed convolution does not apply (C not a multiple of 16, TF32X3)."""
+    packed convolution does not apply (C not a multiple of 16)."""
     import ctypes
     lib = pkg.load()
     h = ctypes.c_void_p()
@@ -105,7 +105,7 @@ def test_conv3x3_plan_argument_validation():
     packed = next(i for i in range(pkg.config_count("bf16x3")) if not pkg.config_get("bf16x3", i)["fused"])
     assert lib.gemm_conv3x3_plan_create(1, 4, 4, 4, 8, 2, packed, ctypes.byref(h)) == 1
     packed_tf32 = next(i for i in range(pkg.config_count("tf32x3")) if not pkg.config_get("tf32x3", i)["fused"])
-    assert lib.gemm_conv3x3_plan_create(1, 4, 4, 16, 8, 3, packed_tf32, ctypes.byref(h)) == 1
+    assert lib.gemm_conv3x3_plan_create(1, 4, 4, 24, 8, 3, packed_tf32, ctypes.byref(h)) == 1
     assert b"packed" in lib.gemm_last_error()
     # R x S filters: odd sizes 1..11 only; BF16X6 runs packed only (C % 16 == 0)
     for R, S in [(2, 3), (3, 4), (13, 3), (3, 13), (0, 1), (-1, 3)]:

@@ -267,14 +267,15 @@ def test_infinite_pixel_reaches_only_its_windows(mode, C, R, path):
 # ----------------------------------------------------------- packed path
 def test_packed_path_is_the_default_where_it_applies():
     for mode, C, fused in [("bf16x3", 16, False), ("bf16x3", 48, False), ("bf16x6", 32, False),
-                           ("bf16x3", 8, True), ("bf16x3", 12, True), ("tf32x3", 16, True)]:
+                           ("tf32x3", 16, False), ("tf32x3", 64, False),
+                           ("bf16x3", 8, True), ("bf16x3", 12, True), ("tf32x3", 24, True)]:
         plan = pkg.ConvPlan(1, 6, 5, C, 8, 3, 3, mode=mode)
         cid = plan.info()["config_id"]
         plan.destroy()
         assert pkg.config_get(mode, cid)["fused"] == int(fused), (mode, C)
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6", "tf32x3"])
 @pytest.mark.parametrize("R,S,C", [(3, 3, 16), (5, 5, 16), (3, 3, 48), (7, 3, 64), (1, 1, 32)])
 def test_packed_configurations_equal_gemm_on_patch_matrix(mode, R, S, C):
     """The packed kernel multiplies the split image's planes through im2col
@@ -301,16 +302,17 @@ def test_packed_configurations_equal_gemm_on_patch_matrix(mode, R, S, C):
         assert oracle.rel_frob(got.reshape(-1, K), ref) <= TOL
 
 
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("shift", [-100, 60])
-def test_packed_image_exponent_rescales(shift):
+def test_packed_image_exponent_rescales(shift, mode):
     """An image outside [2^-48, 2^48) takes the whole-image exponent: the
     second split pass re-splits it scaled, so tiny inputs keep their low
-    parts and large ones do not overflow bf16 products."""
+    parts and large ones do not overflow the products."""
     x = W.scaled(W.conv_image(1, 20, 20, 16, 193), shift)
     f = W.conv_filter(16, 16, 194)
     ref = conv.conv_f64(x, f)
-    got, cid = run_conv(x, f, 1.0, 0.0, np.zeros((1, 20, 20, 16), np.float32))
-    assert not pkg.config_get("bf16x3", cid)["fused"]
+    got, cid = run_conv(x, f, 1.0, 0.0, np.zeros((1, 20, 20, 16), np.float32), mode)
+    assert not pkg.config_get(mode, cid)["fused"]
     assert oracle.rel_frob(got.reshape(-1, 16), ref.reshape(-1, 16)) <= TOL
 
 
@@ -331,7 +333,7 @@ def test_packed_bf16x6_integer_and_uniform(R, C):
     assert e6 <= TOL and e6 * 3.0 < e3, (e6, e3)
 
 
-@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6", "tf32x3"])
 @pytest.mark.parametrize("n,H,Wd,C,K,R", [(3, 5, 7, 32, 200, 3), (1, 1, 1, 16, 8, 5), (2, 1, 9, 64, 130, 3),
                                           (1, 17, 3, 48, 64, 7)])
 def test_packed_wide_outputs_and_small_images(mode, n, H, Wd, C, K, R):
