@@ -388,8 +388,10 @@ def other_workloads(model_path: str | None):
                 plan.execute(x, f, o, 1.0, 0.0)
             ms = _median_ms(lambda: plan.execute(x, f, o, 1.0, 0.0), 5, stream)
             flops = 2.0 * nb * H * Wd * Ko * R * R * Ci
+            cfg = pkg.config_get("bf16x3", plan.info()["config_id"])
             res[f"{R}x{R}"] = {"ms": round(ms, 4), "tflops": round(flops / (ms * 1e-3) / 1e12, 2),
-                               "hbm_gbs": round(4.0 * (x.numel() + f.numel() + o.numel()) / (ms * 1e-3) / 1e9, 1)}
+                               "hbm_gbs": round(4.0 * (x.numel() + f.numel() + o.numel()) / (ms * 1e-3) / 1e9, 1),
+                               "path": "fused-split" if cfg["fused"] else "packed"}
             plan.destroy()
         out["conv_filters"][f"{nb}x{H}x{Wd}x{Ci}->{Ko}"] = res
         del x, o
