@@ -57,6 +57,7 @@ struct TcArgs {
   // 16-channel im2col boxes of them (plane z = images z conv_N ...).
   int conv, conv_N, conv_H, conv_W, conv_C, conv_R, conv_S;
   int conv_box_c;          // fused variant: channels per TMA im2col box (32, or 16), when vecA
+  int* unit_ctr;           // packed convolution: units taken so far (zero before the launch)
 };
 
 struct TcLaunch {

@@ -413,7 +413,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   size_t off = 0;
   const size_t offA = off; off = align_up(off + bytesA, 256);
   const size_t offB = off; off = align_up(off + bytesB, 256);
-  const size_t offAmax = off; off = align_up(off + 2 * (nblkA + nblkB) * sizeof(unsigned), 256);
+  // maxima and pack counters of both operands, then one unit counter (the
+  // packed convolution's dynamic tile order), all cleared by one memset
+  const size_t offAmax = off; off = align_up(off + (2 * (nblkA + nblkB) + 1) * sizeof(unsigned), 256);
   const size_t offPart = off;
   if (sk > 1) off = align_up(off + (size_t)sk * M * N * sizeof(float), 256);
   p->ws_bytes = off;
@@ -428,9 +430,10 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->planesB = w + offB;
   p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
   p->amaxB = p->amaxA + nblkA;
-  p->amax_bytes = 2 * (nblkA + nblkB) * sizeof(unsigned);   // maxima, then per-block counters
+  p->amax_bytes = (2 * (nblkA + nblkB) + 1) * sizeof(unsigned);   // maxima, per-block counters, unit counter
   p->cntA = p->amaxB + nblkB;
   p->cntB = p->cntA + nblkA;
+  p->unit_ctr = reinterpret_cast<int*>(p->cntB + nblkB);
   p->partial = sk > 1 ? reinterpret_cast<float*>(w + offPart) : nullptr;
 
   // (a packed convolution's A map, over the image planes, is made by its creator)
@@ -1007,6 +1010,7 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   p->args.conv = 1;
   p->args.conv_N = (int)batch;
   p->args.conv_box_c = packed_conv ? box_c : 0;
+  p->args.unit_ctr = packed_conv ? p->unit_ctr : nullptr;
   p->args.conv_H = (int)H;
   p->args.conv_W = (int)W;
   p->args.conv_C = (int)C;

@@ -36,6 +36,7 @@ struct gemm_plan_s {
   size_t amax_bytes = 0;            // block maxima of A and B, then their pack counters
   unsigned* cntA = nullptr;
   unsigned* cntB = nullptr;
+  int* unit_ctr = nullptr;          // after the counters: the packed convolution's unit counter
   int conv_batch = 0;               // direct convolution plans (args.conv): images per call
   float* partial = nullptr;
   CUtensorMap tmA{}, tmB{};

@@ -89,7 +89,7 @@ struct TcCfg {
   static constexpr int TMEM_COLS = NACC * ACC_COLS;
   static constexpr int EPI_PITCH = 33;                 // floats per staged row (bank-conflict free)
   static constexpr int EPI_BYTES = 4 * EPI_WG * 32 * EPI_PITCH * 4;   // one 32x32 buffer per epilogue warp
-  static constexpr int BAR_BYTES = 256;
+  static constexpr int BAR_BYTES = 512;
   // fused variant: two staging buffers for one FP32 k-chunk of A each
   // (128 rows of BK floats, as 128-byte-wide boxes swizzled like a
   // SWIZZLE_128B TMA load), filled by TMA or cp.async
@@ -171,6 +171,7 @@ struct SingleSched {
   // wave only, doubled the DRAM reads: its column blocks left L2 before the
   // wave's other CTAs had read them)
   __device__ int l2_hints() const { return a->group_m > 1 ? 1 : 0; }
+  __device__ int* unit_ctr() const { return a->unit_ctr; }
   __device__ Work work(int u) const {
     Work w;
     const int t = u % a->num_tiles;
@@ -206,6 +207,7 @@ struct GroupedSched {
   static constexpr bool kWideEpilogue = true;
   const GroupedArgs* a;
   __device__ int l2_hints() const { return 0; }   // problems of every shape: no priority
+  __device__ int* unit_ctr() const { return nullptr; }
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
@@ -383,9 +385,22 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   auto stg_full_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + b); };
   auto stg_empty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 * NACC + 1 + NSTG + b); };
   constexpr int NBAR = 2 * STAGES + 2 * NACC + 1 + 2 * NSTG;
-  static_assert(8 * NBAR + 16 <= Cfg::BAR_BYTES, "barrier block");
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  // DYN (the packed convolution): units are taken from a per-launch counter
+  // as a CTA becomes ready for one, instead of every gridDim.x-th, so that
+  // SMs that run faster take more tiles (with a static order the SMs of the
+  // 16-channel convolution finished up to a third apart).  The producer
+  // takes each unit (one unit ahead, so that the atomic's latency overlaps a
+  // unit of loads) and publishes it in a shared-memory queue, which the MMA
+  // thread and the epilogue warps read in the same order; -1 ends it.
+  constexpr bool DYN = CONVA != 0;
+  constexpr int QD = 8;
+  int* const q_unit = reinterpret_cast<int*>(bar_area + 8 * NBAR + 16);
+  const uint32_t qbar0 = bar0 + 8u * NBAR + 16u + 4u * QD;
+  auto qfull_bar = [&](int s) { return qbar0 + 8u * s; };
+  auto qempty_bar = [&](int s) { return qbar0 + 8u * (QD + s); };
+  static_assert(8 * NBAR + 16 + 4 * QD + 16 * QD <= Cfg::BAR_BYTES, "barrier block");
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -400,6 +415,12 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       mbar_init(acce_bar(b), 128 * Cfg::EPI_WG);
     }
     mbar_init(drain_bar, 1);
+    if constexpr (DYN) {
+      for (int s = 0; s < QD; ++s) {
+        mbar_init(qfull_bar(s), 1);                         // the producer
+        mbar_init(qempty_bar(s), 1 + 4 * Cfg::EPI_WG);      // the MMA thread, one per epilogue warp
+      }
+    }
     if constexpr (FUSED) {
       // a staging buffer fills on one TMA issuer's arrival (plus its bytes)
       // or on every split thread's cp.async arrival
@@ -567,9 +588,23 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       bool ok = true;
       int last_prob = -1;
       Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
-      for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Work w = wn;                         // next unit's entry loads early
-        if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+      int qk = 0, u_pre = 0;   // DYN: units published; the next unit, taken one unit ahead
+      auto publish = [&](int u) -> bool {   // DYN: unit u (or the end) into the queue
+        if constexpr (DYN) {
+          const int s = qk % QD;
+          if (!mbar_wait(qempty_bar(s), ((qk / QD) & 1) ^ 1u, abort_flag, err)) return false;
+          q_unit[s] = u < nunits ? u : -1;
+          mbar_arrive(qfull_bar(s));
+          ++qk;
+        }
+        return true;
+      };
+      int u0 = static_cast<int>(blockIdx.x);
+      if constexpr (DYN) u0 = atomicAdd(sc.unit_ctr(), 1);
+      for (int u = u0; ok && (ok = publish(u)) && u < nunits; u = DYN ? u_pre : u + static_cast<int>(gridDim.x)) {
+        if constexpr (DYN) u_pre = atomicAdd(sc.unit_ctr(), 1);
+        const Work w = DYN ? sc.work(u) : wn;      // next unit's entry loads early
+        if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         const CUtensorMap* mA = sc.mapA(w.prob);
         const CUtensorMap* mB = sc.mapB(w.prob);
         if (w.prob != last_prob) {
@@ -704,9 +739,25 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       bool ok = true;
       bool any = false;
       Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
-      for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-        const Work w = wn;
-        if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+      int qk = 0;   // DYN: units read from the queue
+      auto take = [&]() -> int {   // DYN: the next unit from the queue (-1: the end, or an abort)
+        int u = -1;
+        if constexpr (DYN) {
+          const int s = qk % QD;
+          if (!mbar_wait(qfull_bar(s), (qk / QD) & 1, abort_flag, err)) {
+            ok = false;
+            return -1;
+          }
+          u = q_unit[s];
+          mbar_arrive(qempty_bar(s));
+          ++qk;
+        }
+        return u;
+      };
+      for (int u = DYN ? take() : static_cast<int>(blockIdx.x); ok && u >= 0 && u < nunits;
+           u = DYN ? take() : u + static_cast<int>(gridDim.x)) {
+        const Work w = DYN ? sc.work(u) : wn;
+        if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         for (int cb = w.c0; ok && cb < w.c1; cb += kb) {
           const int ce = min(cb + kb, w.c1);
           if (!mbar_wait(acce_bar(ab), aphase ^ 1u, abort_flag, err)) {
@@ -796,9 +847,27 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     uint32_t ab = 0, aphase = 0;
     bool ok = true;
     Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
-    for (int u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-      const Work w = wn;
-      if (u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+    int qk = 0;   // DYN: units read from the queue
+    auto take = [&]() -> int {   // DYN, whole warp: the next unit from the queue (-1: end or abort)
+      int u = -1;
+      if constexpr (DYN) {
+        const int s = qk % QD;
+        const bool waited = mbar_wait(qfull_bar(s), (qk / QD) & 1, abort_flag, err);
+        if (!__all_sync(0xffffffffu, waited)) {
+          ok = false;
+          return -1;
+        }
+        u = q_unit[s];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(qempty_bar(s));
+        ++qk;
+      }
+      return u;
+    };
+    for (int u = DYN ? take() : static_cast<int>(blockIdx.x); ok && u >= 0 && u < nunits;
+         u = DYN ? take() : u + static_cast<int>(gridDim.x)) {
+      const Work w = DYN ? sc.work(u) : wn;
+      if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
       // The unit's epilogue values and block exponents are loaded before its
       // accumulator is waited for (the pack has completed: every role passed
       // griddep_wait), and L2 is warmed with the part of C this thread will
