@@ -38,6 +38,7 @@ struct gemm_grouped_plan_s {
   gb::GroupedPtrs* d_ptrs = nullptr;
   gb::GroupedUnit* d_units = nullptr;
   int* d_split_prefix = nullptr;
+  size_t amax_count = 0;          // words of block maxima and counters (the unit counter follows)
   unsigned* d_amax = nullptr;
   size_t amax_bytes = 0;
   int num_units = 0, split_total = 0;
@@ -88,6 +89,7 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   a.kb = p->kb;
   a.group_m = p->group_m;
   a.err = p->err;
+  a.unit_ctr = reinterpret_cast<int*>(p->d_amax + p->amax_count);
   const int grid = std::min(p->num_units, p->sms);
   if ((e = tc_grouped_launch(p->bn, p->prec, grid, a, s)) != cudaSuccess)
     return cuda_fail(e, "grouped tensor-core launch");
@@ -238,8 +240,11 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     const bool pack = !empty && p->K[i] > 0;
     spl_prefix[slot + 1] = spl_prefix[slot] + (pack ? pack_first_items(p->M[i], p->N[i], pitch) : 0);
   }
+  // block maxima and pack counters of every problem, then the launch's unit
+  // counter (its dynamic tile order), all cleared by one memset
   const size_t off_amax = off;
-  p->amax_bytes = std::max<size_t>(amax_count, 1) * sizeof(unsigned);
+  p->amax_bytes = (amax_count + 1) * sizeof(unsigned);
+  p->amax_count = amax_count;
   off = round256(off + p->amax_bytes);
   const size_t off_probs = off;
   off = round256(off + (size_t)G * sizeof(GroupedProblem));

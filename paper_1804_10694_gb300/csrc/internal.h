@@ -163,6 +163,7 @@ struct GroupedArgs {
   const GroupedUnit* units;   // num_units entries, problems longest-K first
   int G, num_units, kb, group_m;
   int* err;
+  int* unit_ctr;              // units taken so far (zero before the launch)
 };
 
 cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s);

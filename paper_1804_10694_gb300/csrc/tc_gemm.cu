@@ -158,6 +158,7 @@ __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int grou
 // Scheduling policy of one gemm: units are (split, tile) pairs.
 struct SingleSched {
   static constexpr bool kWideEpilogue = false;
+  static constexpr bool kDynamic = false;     // (the packed convolution takes units dynamically)
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
   const TcArgs* a;
@@ -205,9 +206,10 @@ struct SingleSched {
 // problem, tile coordinates and k-chunk count in one 16-byte load.
 struct GroupedSched {
   static constexpr bool kWideEpilogue = true;
+  static constexpr bool kDynamic = true;      // problems of every size: units taken dynamically
   const GroupedArgs* a;
   __device__ int l2_hints() const { return 0; }   // problems of every shape: no priority
-  __device__ int* unit_ctr() const { return nullptr; }
+  __device__ int* unit_ctr() const { return a->unit_ctr; }
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
@@ -387,20 +389,25 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   constexpr int NBAR = 2 * STAGES + 2 * NACC + 1 + 2 * NSTG;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_area + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  // DYN (the packed convolution): units are taken from a per-launch counter
-  // as a CTA becomes ready for one, instead of every gridDim.x-th, so that
-  // SMs that run faster take more tiles (with a static order the SMs of the
-  // 16-channel convolution finished up to a third apart).  The producer
-  // takes each unit (one unit ahead, so that the atomic's latency overlaps a
-  // unit of loads) and publishes it in a shared-memory queue, which the MMA
-  // thread and the epilogue warps read in the same order; -1 ends it.
-  constexpr bool DYN = CONVA != 0;
+  // DYN (the packed convolution, the grouped launch): units are taken from a
+  // per-launch counter as a CTA becomes ready for one, instead of every
+  // gridDim.x-th, so that SMs that run faster, or got shorter units, take
+  // more (with a static order the SMs of the 16-channel convolution finished
+  // up to a third apart).  The producer takes each unit (one unit ahead, so
+  // that the atomic's latency overlaps a unit of loads), and publishes it
+  // with its work entry in a shared-memory queue, which the MMA thread and
+  // the epilogue warps read in the same order; -1 ends it.
+  constexpr bool DYN = CONVA != 0 || Sched::kDynamic;
   constexpr int QD = 8;
   int* const q_unit = reinterpret_cast<int*>(bar_area + 8 * NBAR + 16);
-  const uint32_t qbar0 = bar0 + 8u * NBAR + 16u + 4u * QD;
+  Work* const q_work = reinterpret_cast<Work*>(bar_area + 8 * NBAR + 16 + 4 * QD);
+  const uint32_t qbar0 = bar0 + 8u * NBAR + 16u + 4u * QD + static_cast<uint32_t>(sizeof(Work)) * QD;
   auto qfull_bar = [&](int s) { return qbar0 + 8u * s; };
   auto qempty_bar = [&](int s) { return qbar0 + 8u * (QD + s); };
-  static_assert(8 * NBAR + 16 + 4 * QD + 16 * QD <= Cfg::BAR_BYTES, "barrier block");
+  static_assert((16 + 4 * QD + sizeof(Work) * QD) % 8 == 0, "queue barriers 8-byte aligned");
+  static_assert(8 * NBAR + 16 + (DYN ? 4 * QD + static_cast<int>(sizeof(Work)) * QD + 16 * QD : 0) <=
+                    Cfg::BAR_BYTES,
+                "barrier block");
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -589,21 +596,26 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       int last_prob = -1;
       Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
       int qk = 0, u_pre = 0;   // DYN: units published; the next unit, taken one unit ahead
+      Work wd{};               // DYN: the work entry of the unit to publish next
       auto publish = [&](int u) -> bool {   // DYN: unit u (or the end) into the queue
         if constexpr (DYN) {
           const int s = qk % QD;
           if (!mbar_wait(qempty_bar(s), ((qk / QD) & 1) ^ 1u, abort_flag, err)) return false;
           q_unit[s] = u < nunits ? u : -1;
+          q_work[s] = wd;
           mbar_arrive(qfull_bar(s));
           ++qk;
         }
         return true;
       };
       int u0 = static_cast<int>(blockIdx.x);
-      if constexpr (DYN) u0 = atomicAdd(sc.unit_ctr(), 1);
+      if constexpr (DYN) {
+        u0 = atomicAdd(sc.unit_ctr(), 1);
+        if (u0 < nunits) wd = sc.work(u0);
+      }
       for (int u = u0; ok && (ok = publish(u)) && u < nunits; u = DYN ? u_pre : u + static_cast<int>(gridDim.x)) {
         if constexpr (DYN) u_pre = atomicAdd(sc.unit_ctr(), 1);
-        const Work w = DYN ? sc.work(u) : wn;      // next unit's entry loads early
+        const Work w = DYN ? wd : wn;              // next unit's entry loads early
         if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         const CUtensorMap* mA = sc.mapA(w.prob);
         const CUtensorMap* mB = sc.mapB(w.prob);
@@ -722,6 +734,10 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             phase ^= 1u;
           }
         }
+        // DYN: the next unit's entry, loaded while this unit's last stages fill
+        if constexpr (DYN) {
+          if (u_pre < nunits) wd = sc.work(u_pre);
+        }
       }
       if (!ok) {
         // abort: let every copy this thread started land before shared memory is released
@@ -740,6 +756,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       bool any = false;
       Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
       int qk = 0;   // DYN: units read from the queue
+      Work wq{};    // DYN: the work entry read with the unit
       auto take = [&]() -> int {   // DYN: the next unit from the queue (-1: the end, or an abort)
         int u = -1;
         if constexpr (DYN) {
@@ -749,6 +766,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             return -1;
           }
           u = q_unit[s];
+          wq = q_work[s];
           mbar_arrive(qempty_bar(s));
           ++qk;
         }
@@ -756,7 +774,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
       };
       for (int u = DYN ? take() : static_cast<int>(blockIdx.x); ok && u >= 0 && u < nunits;
            u = DYN ? take() : u + static_cast<int>(gridDim.x)) {
-        const Work w = DYN ? sc.work(u) : wn;
+        const Work w = DYN ? wq : wn;
         if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
         for (int cb = w.c0; ok && cb < w.c1; cb += kb) {
           const int ce = min(cb + kb, w.c1);
@@ -848,6 +866,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     bool ok = true;
     Work wn = nunits > 0 ? sc.work(min(static_cast<int>(blockIdx.x), nunits - 1)) : Work{};
     int qk = 0;   // DYN: units read from the queue
+    Work wq{};    // DYN: the work entry read with the unit
     auto take = [&]() -> int {   // DYN, whole warp: the next unit from the queue (-1: end or abort)
       int u = -1;
       if constexpr (DYN) {
@@ -858,6 +877,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
           return -1;
         }
         u = q_unit[s];
+        wq = q_work[s];
         __syncwarp();
         if (lane == 0) mbar_arrive(qempty_bar(s));
         ++qk;
@@ -866,7 +886,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     };
     for (int u = DYN ? take() : static_cast<int>(blockIdx.x); ok && u >= 0 && u < nunits;
          u = DYN ? take() : u + static_cast<int>(gridDim.x)) {
-      const Work w = DYN ? sc.work(u) : wn;
+      const Work w = DYN ? wq : wn;
       if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
       // The unit's epilogue values and block exponents are loaded before its
       // accumulator is waited for (the pack has completed: every role passed
