@@ -258,27 +258,49 @@ gemm_status gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
 
 /* ------------------------------------------------------------ autotuning -- */
 
-/* Autotune (paper Section VI-A: tile sizes chosen by search): for each of the
- * G shapes (M, N, K triples, tight leading dimensions) time every distinct
- * candidate configuration of `mode` on synthetic uniform data, `reps` CUDA-
- * event-timed executions after two warm-ups, median.  Appends one CSV row per
- * (shape, configuration) to out_path ("M,N,K,mode,config_id,median_ms,
- * block_n,split_k,kb,group_m"; header written to a new file; NULL = no file)
- * and records the fastest configuration per shape in the process-wide table
- * used by GEMM_SELECT_TABLE.  Synchronises the device. */
+/* Autotune (the paper chooses tile sizes by search, Section VI-A; the
+ * candidate table and this call are this library's): for each of the G
+ * shapes, given as G rows of six numbers (M, N, K, lda, ldb, ldc) in
+ * `shapes` (G x 6 int64, row-major; leading dimensions as for gemm_f32_ex),
+ * time every distinct candidate configuration of `mode` on synthetic uniform
+ * data stored with those leading dimensions, `reps` CUDA-event-timed
+ * executions after two warm-ups, median.  Leading dimensions are part of a
+ * shape because they select code paths (TMA or cp.async staging of A, float4
+ * or staged stores of C).  Appends one CSV row per (shape, configuration) to
+ * out_path ("M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,
+ * group_m,fused"; header written to a new file; an existing file must carry
+ * that header, else GEMM_ERR_IO; NULL = no file) and records the fastest
+ * configuration per shape in the process-wide table used by
+ * GEMM_SELECT_TABLE, keyed by all six numbers.  Errors: INVALID_ARG (a bad
+ * shape, before anything runs), IO, ALLOC, CUDA.  Synchronises the device. */
 gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps, const char* out_path);
 
-/* Load timing rows (the CSV above) into the tuned table. */
+/* Load timing rows (the CSV above; rows of the earlier 11-column format
+ * without leading dimensions are read as tight shapes) into the tuned table. */
 gemm_status gemm_autotune_load(const char* path);
 
-/* Fastest configuration and its median time for a shape in the tuned table
- * (GEMM_ERR_INVALID_ARG if the shape was never tuned). */
-gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, gemm_mode mode, int* config_id,
-                               float* ms);
+/* Fastest configuration and its median time for a shape (sizes and leading
+ * dimensions) in the tuned table (GEMM_ERR_INVALID_ARG if it was never
+ * tuned). */
+gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                               gemm_mode mode, int* config_id, float* ms);
+
+/* The configuration id a plan created now would get for this shape under
+ * policy `sel` (defined by this library, like the policies themselves):
+ * DEFAULT = the built-in heuristic, TABLE = the tuned table's entry for the
+ * exact six numbers (else the heuristic), MODEL = the loaded cost model's
+ * argmin (runs on the GPU; else the heuristic), EXHAUSTIVE = time every
+ * candidate now.  -1 for F32_SIMT or an empty problem.  DEFAULT and TABLE
+ * need no device (the heuristic assumes 152 SMs without one). */
+gemm_status gemm_select_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                               gemm_mode mode, gemm_select sel, int* config_id);
 
 /* ------------------------------------------------------------ cost model -- */
 
-/* Number of input features of the cost model (14). */
+/* Number of input features of the cost model (16).  The cost model, its
+ * features and its training are this library's (the learned replacement of
+ * the paper's tile-size search, Section VI-A); they have no paper passage of
+ * their own. */
 int gemm_costmodel_feature_count(void);
 
 /* Features of one (shape, configuration) pair for an `sms`-SM device, written
@@ -333,9 +355,10 @@ int gemm_config_default(gemm_mode mode, int64_t M, int64_t N, int64_t K);
  * thread's next library call. */
 const char* gemm_last_error(void);
 
-/* Reads and clears the current device's kernel error word: GEMM_OK, or
- * GEMM_ERR_TIMEOUT if a kernel abandoned a pipeline wait.  Synchronizes the
- * device. */
+/* Reads and clears the current device's kernel error words (the regular
+ * entry points' word and, if it ran on this device, the allocation-free
+ * path's own word): GEMM_OK, or GEMM_ERR_TIMEOUT if a kernel abandoned a
+ * pipeline wait since the last call.  Synchronizes the device. */
 gemm_status gemm_device_error(void);
 
 /* Self-test of failure detection: launches one kernel whose pipeline wait can
@@ -382,7 +405,11 @@ gemm_status gemm_split_pack(gemm_mode mode, int transpose, int64_t rows, int64_t
  * GEMM_ERR_INVALID_ARG (for square problems the limit is about
  * M = N = K = 2896).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array and each call
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device, do not call this entry point
+ * on that device again.  A pipeline wait that gives up in this path's kernel
+ * is recorded in its own device error word, read and cleared by
+ * gemm_device_error().  All calls share the array and each call
  * overwrites it, so calls that overlap on the GPU (other streams, other host
  * threads) race.  Pointers, layout, special cases and errors are as for
  * gemm_f32_ex; no split-K is used and the call never synchronises. */

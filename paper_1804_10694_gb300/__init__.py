@@ -348,10 +348,22 @@ class GroupedPlan:
 
 
 # --------------------------------------------------------- tuning and model
+def _shape6(s):
+    """(M, N, K) with tight leading dimensions, or (M, N, K, lda, ldb, ldc)."""
+    s = [int(x) for x in s]
+    if len(s) == 3:
+        M, N, K = s
+        return [M, N, K, max(K, 1), max(N, 1), max(N, 1)]
+    if len(s) == 6:
+        return s
+    raise ValueError(f"a shape is (M, N, K) or (M, N, K, lda, ldb, ldc), got {s}")
+
+
 def autotune(shapes, mode="bf16x3", reps: int = 5, out_path: str | None = None):
-    """Time every distinct configuration of each (M, N, K) shape; rows are
-    appended to out_path (CSV) and the best per shape enters the tuned table."""
-    flat = [int(x) for s in shapes for x in s]
+    """Time every distinct configuration of each shape ((M, N, K) with tight
+    leading dimensions, or (M, N, K, lda, ldb, ldc)); rows are appended to
+    out_path (CSV) and the best per shape enters the tuned table."""
+    flat = [x for s in shapes for x in _shape6(s)]
     arr = _i64_array(flat) if flat else None
     check(load().gemm_autotune(arr, len(shapes), _mode(mode), int(reps),
                                out_path.encode() if out_path else None))
@@ -361,10 +373,23 @@ def autotune_load(path: str):
     check(load().gemm_autotune_load(path.encode()))
 
 
-def autotune_best(M, N, K, mode="bf16x3"):
+def autotune_best(M, N, K, mode="bf16x3", lda=None, ldb=None, ldc=None):
+    M, N, K, lda_, ldb_, ldc_ = _shape6((M, N, K))
     cid, ms = ctypes.c_int(), ctypes.c_float()
-    check(load().gemm_autotune_best(M, N, K, _mode(mode), ctypes.byref(cid), ctypes.byref(ms)))
+    check(load().gemm_autotune_best(M, N, K, lda if lda is not None else lda_,
+                                    ldb if ldb is not None else ldb_, ldc if ldc is not None else ldc_,
+                                    _mode(mode), ctypes.byref(cid), ctypes.byref(ms)))
     return cid.value, ms.value
+
+
+def select_config(M, N, K, mode="bf16x3", select="default", lda=None, ldb=None, ldc=None) -> int:
+    """Configuration id a plan would get under a selection policy."""
+    M, N, K, lda_, ldb_, ldc_ = _shape6((M, N, K))
+    cid = ctypes.c_int()
+    check(load().gemm_select_config(M, N, K, lda if lda is not None else lda_,
+                                    ldb if ldb is not None else ldb_, ldc if ldc is not None else ldc_,
+                                    _mode(mode), _select(select), ctypes.byref(cid)))
+    return cid.value
 
 
 def costmodel_feature_count() -> int:

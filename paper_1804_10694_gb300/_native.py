@@ -65,7 +65,9 @@ SIGNATURES = {
     "gemm_grouped_plan_destroy": (i32, [vp]),
     "gemm_autotune": (i32, [vp, i32, i32, i32, cp]),
     "gemm_autotune_load": (i32, [cp]),
-    "gemm_autotune_best": (i32, [i64, i64, i64, i32, ctypes.POINTER(i32), ctypes.POINTER(f32)]),
+    "gemm_autotune_best": (i32, [i64, i64, i64, i64, i64, i64, i32, ctypes.POINTER(i32),
+                                 ctypes.POINTER(f32)]),
+    "gemm_select_config": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(i32)]),
     "gemm_costmodel_feature_count": (i32, []),
     "gemm_costmodel_features": (i32, [i64, i64, i64, i32, i32, i32, vp]),
     "gemm_costmodel_train": (i32, [cp, i32, u64, cp, ctypes.POINTER(f32)]),

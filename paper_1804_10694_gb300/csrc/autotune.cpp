@@ -5,10 +5,13 @@
 // DISTINCT effective configuration (candidates that behave identically on the
 // shape, e.g. split-K above the number of k-chunks, are timed once) is run
 // `reps` times after two warm-up executions, each execution timed with CUDA
-// events; the median is recorded.  Results are appended to a CSV file
-// ("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused") that the cost
-// model trains on, and the fastest configuration per shape is kept in an
-// in-memory table (GEMM_SELECT_TABLE).
+// events; the median is recorded.  A shape is (M, N, K) with its leading
+// dimensions (lda, ldb, ldc): they choose code paths (TMA or cp.async
+// staging of A in the fused kernel, float4 or staged stores of C), so they
+// are part of what is tuned.  Results are appended to a CSV file
+// ("M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused")
+// that the cost model trains on, and the fastest configuration per shape is
+// kept in an in-memory table (GEMM_SELECT_TABLE), keyed by all six numbers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,33 +64,53 @@ std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t 
 
 // -------------------------------------------------------------- tuned table
 namespace {
+using TableKey = std::tuple<int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t>;
 std::mutex g_table_mu;
-std::map<std::tuple<int, int64_t, int64_t, int64_t>, std::pair<int, float>> g_table;
+std::map<TableKey, std::pair<int, float>> g_table;
 
-void table_offer(gemm_mode mode, int64_t M, int64_t N, int64_t K, int cid, float ms) {
+void table_offer(gemm_mode mode, const Shape6& sh, int cid, float ms) {
   std::lock_guard<std::mutex> lk(g_table_mu);
-  auto key = std::make_tuple((int)mode, M, N, K);
+  const TableKey key = std::make_tuple((int)mode, sh.M, sh.N, sh.K, sh.lda, sh.ldb, sh.ldc);
   auto it = g_table.find(key);
   if (it == g_table.end() || ms < it->second.second) g_table[key] = {cid, ms};
 }
 }  // namespace
 
-bool table_lookup(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms) {
+bool table_lookup(gemm_mode mode, const Shape6& sh, int* cid, float* ms) {
   std::lock_guard<std::mutex> lk(g_table_mu);
-  auto it = g_table.find(std::make_tuple((int)mode, M, N, K));
+  auto it = g_table.find(std::make_tuple((int)mode, sh.M, sh.N, sh.K, sh.lda, sh.ldb, sh.ldc));
   if (it == g_table.end()) return false;
   if (cid) *cid = it->second.first;
   if (ms) *ms = it->second.second;
   return true;
 }
 
+int parse_timing_row(const char* line, TimingRow* r) {
+  int commas = 0;
+  for (const char* c = line; *c; ++c) commas += *c == ',';
+  long long M, N, K, lda, ldb, ldc;
+  if (commas == 13) {
+    if (std::sscanf(line, "%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,%f", &M, &N, &K, &lda, &ldb, &ldc,
+                    &r->mode, &r->cid, &r->ms) != 9)
+      return 0;
+  } else if (commas == 10) {
+    // rows written before leading dimensions were part of a shape: tight
+    if (std::sscanf(line, "%lld,%lld,%lld,%d,%d,%f", &M, &N, &K, &r->mode, &r->cid, &r->ms) != 6) return 0;
+    lda = K, ldb = N, ldc = N;
+  } else {
+    return 0;
+  }
+  r->sh = Shape6{M, N, K, lda, ldb, ldc};
+  return 1;
+}
+
 // ------------------------------------------------------------------- timing
 // Median time of `reps` executions of a plan with the given configuration.
-gemm_status time_config(int64_t M, int64_t N, int64_t K, gemm_mode mode, int cid, const float* A,
-                        const float* B, float* C, int reps, float* median_ms) {
+gemm_status time_config(const Shape6& sh, gemm_mode mode, int cid, const float* A, const float* B,
+                        float* C, int reps, float* median_ms) {
   gemm_plan_t p = nullptr;
-  gemm_status st = plan_create_impl(M, N, K, std::max<int64_t>(K, 1), std::max<int64_t>(N, 1),
-                                    std::max<int64_t>(N, 1), mode, cid, GEMM_SELECT_DEFAULT, &p);
+  gemm_status st = plan_create_impl(sh.M, sh.N, sh.K, sh.lda, sh.ldb, sh.ldc, mode, cid,
+                                    GEMM_SELECT_DEFAULT, &p);
   if (st != GEMM_OK) return st;
   reps = std::max(1, reps);
   std::vector<cudaEvent_t> ev(2 * reps, nullptr);
@@ -128,18 +151,21 @@ struct DeviceInputs {
   }
 };
 
-gemm_status make_inputs(int64_t M, int64_t N, int64_t K, uint64_t seed, DeviceInputs* in) {
+gemm_status make_inputs(const Shape6& sh, uint64_t seed, DeviceInputs* in) {
+  // storage of row-major matrices with leading dimensions: (rows - 1) * ld + cols
+  const size_t na = (size_t)std::max<int64_t>((sh.M - 1) * sh.lda + sh.K, 1);
+  const size_t nb = (size_t)std::max<int64_t>((sh.K - 1) * sh.ldb + sh.N, 1);
+  const size_t nc = (size_t)std::max<int64_t>((sh.M - 1) * sh.ldc + sh.N, 1);
   cudaError_t e;
-  if ((e = cudaMalloc(&in->A, (size_t)std::max<int64_t>(M * K, 1) * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&in->B, (size_t)std::max<int64_t>(K * N, 1) * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&in->C, (size_t)std::max<int64_t>(M * N, 1) * 4)) != cudaSuccess) {
+  if ((e = cudaMalloc(&in->A, na * 4)) != cudaSuccess || (e = cudaMalloc(&in->B, nb * 4)) != cudaSuccess ||
+      (e = cudaMalloc(&in->C, nc * 4)) != cudaSuccess) {
     cudaGetLastError();
-    return fail(GEMM_ERR_ALLOC, "tuning inputs for %lldx%lldx%lld do not fit", (long long)M,
-                (long long)N, (long long)K);
+    return fail(GEMM_ERR_ALLOC, "tuning inputs for %lldx%lldx%lld do not fit", (long long)sh.M,
+                (long long)sh.N, (long long)sh.K);
   }
-  if ((e = fill_uniform_launch(in->A, (size_t)(M * K), seed, nullptr)) != cudaSuccess ||
-      (e = fill_uniform_launch(in->B, (size_t)(K * N), seed + 1, nullptr)) != cudaSuccess ||
-      (e = fill_uniform_launch(in->C, (size_t)(M * N), seed + 2, nullptr)) != cudaSuccess)
+  if ((e = fill_uniform_launch(in->A, na, seed, nullptr)) != cudaSuccess ||
+      (e = fill_uniform_launch(in->B, nb, seed + 1, nullptr)) != cudaSuccess ||
+      (e = fill_uniform_launch(in->C, nc, seed + 2, nullptr)) != cudaSuccess)
     return cuda_fail(e, "fill tuning inputs");
   return GEMM_OK;
 }
@@ -148,19 +174,19 @@ gemm_status make_inputs(int64_t M, int64_t N, int64_t K, uint64_t seed, DeviceIn
 
 // Time every distinct configuration of one shape; calls `row` for each.
 template <class RowFn>
-gemm_status tune_shape(int64_t M, int64_t N, int64_t K, gemm_mode mode, int reps, RowFn row,
-                       int* best_cid, float* best_ms) {
+gemm_status tune_shape(const Shape6& sh, gemm_mode mode, int reps, RowFn row, int* best_cid,
+                       float* best_ms) {
   DeviceInputs in;
-  gemm_status st = make_inputs(M, N, K, 0x5EEDull + (uint64_t)(M * 31 + N * 17 + K), &in);
+  gemm_status st = make_inputs(sh, 0x5EEDull + (uint64_t)(sh.M * 31 + sh.N * 17 + sh.K), &in);
   if (st != GEMM_OK) return st;
   *best_cid = -1;
   *best_ms = 0.0f;
-  for (int cid : distinct_configs(mode, M, N, K)) {
+  for (int cid : distinct_configs(mode, sh.M, sh.N, sh.K)) {
     float ms = 0.0f;
-    st = time_config(M, N, K, mode, cid, in.A, in.B, in.C, reps, &ms);
+    st = time_config(sh, mode, cid, in.A, in.B, in.C, reps, &ms);
     if (st != GEMM_OK) return st;
     row(cid, ms);
-    table_offer(mode, M, N, K, cid, ms);
+    table_offer(mode, sh, cid, ms);
     if (*best_cid < 0 || ms < *best_ms) *best_cid = cid, *best_ms = ms;
   }
   return GEMM_OK;
@@ -168,18 +194,18 @@ gemm_status tune_shape(int64_t M, int64_t N, int64_t K, gemm_mode mode, int reps
 
 int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                   int64_t ldc, gemm_select sel, int sms) {
-  (void)lda, (void)ldb, (void)ldc;
+  const Shape6 sh{M, N, K, lda, ldb, ldc};
   int cid = -1;
   float ms = 0.0f;
   switch (sel) {
     case GEMM_SELECT_TABLE:
-      if (table_lookup(mode, M, N, K, &cid, &ms)) return cid;
+      if (table_lookup(mode, sh, &cid, &ms)) return cid;
       break;
     case GEMM_SELECT_MODEL:
       if (costmodel_pick(mode, M, N, K, &cid, &ms) == GEMM_OK && cid >= 0) return cid;
       break;
     case GEMM_SELECT_EXHAUSTIVE: {
-      if (tune_shape(M, N, K, mode, 5, [](int, float) {}, &cid, &ms) == GEMM_OK && cid >= 0) return cid;
+      if (tune_shape(sh, mode, 5, [](int, float) {}, &cid, &ms) == GEMM_OK && cid >= 0) return cid;
       break;
     }
     default:
@@ -273,31 +299,44 @@ gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps
   clear_error();
   if (G < 0 || (G > 0 && !shapes)) return fail(GEMM_ERR_INVALID_ARG, "bad shape list");
   if (!mode_is_split(mode)) return fail(GEMM_ERR_INVALID_ARG, "autotune needs a tensor-core mode");
+  for (int s = 0; s < G; ++s) {
+    const int64_t* r = shapes + 6 * s;
+    gemm_status st = validate_shape(r[0], r[1], r[2], r[3], r[4], r[5]);
+    if (st != GEMM_OK) return fail(st, "shape %d: %s", s, gemm_last_error());
+  }
   FILE* f = nullptr;
   if (out_path && *out_path) {
+    // an existing file must hold rows of this format (its header names lda)
+    if (FILE* old = std::fopen(out_path, "r")) {
+      char head[512] = {0};
+      const bool has = std::fgets(head, sizeof head, old) != nullptr;
+      std::fclose(old);
+      if (has && !std::strstr(head, "lda"))
+        return fail(GEMM_ERR_IO, "%s holds timing rows without leading dimensions; use a new file",
+                    out_path);
+    }
     f = std::fopen(out_path, "a");
     if (!f) return fail(GEMM_ERR_IO, "cannot open %s for appending", out_path);
     std::fseek(f, 0, SEEK_END);
     if (std::ftell(f) == 0)
-      std::fprintf(f, "M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n");
+      std::fprintf(f, "M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n");
   }
   gemm_status st = GEMM_OK;
   for (int s = 0; s < G && st == GEMM_OK; ++s) {
-    const int64_t M = shapes[3 * s], N = shapes[3 * s + 1], K = shapes[3 * s + 2];
-    if ((st = validate_shape(M, N, K, std::max<int64_t>(K, 1), std::max<int64_t>(N, 1),
-                             std::max<int64_t>(N, 1))) != GEMM_OK)
-      break;
-    if (M == 0 || N == 0 || K == 0) continue;
+    const int64_t* r = shapes + 6 * s;
+    const Shape6 sh{r[0], r[1], r[2], r[3], r[4], r[5]};
+    if (sh.M == 0 || sh.N == 0 || sh.K == 0) continue;
     int best = -1;
     float best_ms = 0;
     st = tune_shape(
-        M, N, K, mode, reps,
+        sh, mode, reps,
         [&](int cid, float ms) {
           if (!f) return;
           gemm_config c;
           config_get(cid, &c);
-          std::fprintf(f, "%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d,%d\n", (long long)M, (long long)N,
-                       (long long)K, (int)mode, cid, ms, c.block_n, c.split_k, c.kb, c.group_m,
+          std::fprintf(f, "%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d,%d\n", (long long)sh.M,
+                       (long long)sh.N, (long long)sh.K, (long long)sh.lda, (long long)sh.ldb,
+                       (long long)sh.ldc, (int)mode, cid, ms, c.block_n, c.split_k, c.kb, c.group_m,
                        c.fused);
         },
         &best, &best_ms);
@@ -315,12 +354,10 @@ gemm_status gemm_autotune_load(const char* path) {
   char line[512];
   int rows = 0;
   while (std::fgets(line, sizeof line, f)) {
-    long long M, N, K;
-    int mode, cid;
-    float ms;
-    if (std::sscanf(line, "%lld,%lld,%lld,%d,%d,%f", &M, &N, &K, &mode, &cid, &ms) != 6) continue;
-    if (cid < 0 || cid >= config_count((gemm_mode)mode)) continue;
-    table_offer((gemm_mode)mode, M, N, K, cid, ms);
+    TimingRow r;
+    if (!parse_timing_row(line, &r)) continue;
+    if (r.cid < 0 || r.cid >= config_count((gemm_mode)r.mode)) continue;
+    table_offer((gemm_mode)r.mode, r.sh, r.cid, r.ms);
     ++rows;
   }
   std::fclose(f);
@@ -328,12 +365,37 @@ gemm_status gemm_autotune_load(const char* path) {
   return GEMM_OK;
 }
 
-gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, gemm_mode mode, int* config_id,
-                               float* ms) {
+gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                               gemm_mode mode, int* config_id, float* ms) {
   clear_error();
-  if (!table_lookup(mode, M, N, K, config_id, ms))
+  if (!table_lookup(mode, Shape6{M, N, K, lda, ldb, ldc}, config_id, ms))
     return fail(GEMM_ERR_INVALID_ARG, "shape not in the tuned table");
   return GEMM_OK;
+}
+
+gemm_status gemm_select_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
+                               gemm_mode mode, gemm_select sel, int* config_id) {
+  clear_error();
+  if (!config_id) return fail(GEMM_ERR_INVALID_ARG, "null output");
+  gemm_status st = validate_shape(M, N, K, lda, ldb, ldc);
+  if (st != GEMM_OK) return st;
+  if (mode == GEMM_MODE_AUTO) mode = GEMM_MODE_BF16X3;
+  if (mode != GEMM_MODE_F32_SIMT && !mode_is_split(mode))
+    return fail(GEMM_ERR_INVALID_ARG, "unknown mode %d", (int)mode);
+  if (mode == GEMM_MODE_F32_SIMT || M == 0 || N == 0 || K == 0) {
+    *config_id = -1;
+    return GEMM_OK;
+  }
+  // the SM count of the current device; the heuristic assumes 152 without one
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  *config_id = select_config(mode, M, N, K, lda, ldb, ldc, sel, sms);
+  clear_error();
+  return *config_id >= 0 ? GEMM_OK : fail(GEMM_ERR_INVALID_ARG, "no configuration for mode");
 }
 
 }  // extern "C"

@@ -238,12 +238,12 @@ gemm_status read_timings(const char* path, std::vector<Row>* rows) {
   if (!f) return fail(GEMM_ERR_IO, "cannot open %s", path);
   char line[512];
   while (std::fgets(line, sizeof line, f)) {
+    TimingRow t;
+    if (!parse_timing_row(line, &t)) continue;
     Row r;
-    long long M, N, K;
-    if (std::sscanf(line, "%lld,%lld,%lld,%d,%d,%f", &M, &N, &K, &r.mode, &r.cid, &r.ms) != 6) continue;
-    if (M <= 0 || N <= 0 || K <= 0 || !(r.ms > 0.0f)) continue;
+    r.M = t.sh.M, r.N = t.sh.N, r.K = t.sh.K, r.mode = t.mode, r.cid = t.cid, r.ms = t.ms;
+    if (r.M <= 0 || r.N <= 0 || r.K <= 0 || !(r.ms > 0.0f)) continue;
     if (r.cid < 0 || r.cid >= config_count((gemm_mode)r.mode)) continue;
-    r.M = M, r.N = N, r.K = K;
     rows->push_back(r);
   }
   std::fclose(f);

@@ -17,6 +17,11 @@
 // device address, so the first call on each device (with that device
 // current) asks the runtime for the address with cudaGetSymbolAddress and
 // keeps it; that first call should therefore come before any stream capture.
+// The kept address belongs to the device's context as it was then: after a
+// cudaDeviceReset (or any re-creation of the primary context) it is stale,
+// so this path must not be called on that device again in the process.
+// A pipeline wait that gives up in this path's gemm kernel is recorded in
+// this path's own error word, which gemm_device_error() reads and clears.
 // All calls share the one array and each call overwrites it (the block
 // maxima are cleared at the start of every call): calls whose work overlaps
 // on the GPU -- two streams, or two host threads -- race on it.
@@ -38,8 +43,10 @@ namespace gb {
 
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
 
-// The scratch array and this path's own pipeline-timeout word (no kernel of
-// this file reads it back: the call never synchronises).
+// The scratch array and this path's own pipeline-timeout word.  The call
+// never synchronises, so it never reads the word itself: gemm_device_error()
+// reads and clears it (through noalloc_take_error below) together with the
+// regular entry points' word.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static __device__ int g_noalloc_error_word;
 
@@ -109,6 +116,22 @@ gemm_status encode(CUtensorMap* map, void* base, int64_t rows, int64_t K, int64_
 }
 
 }  // namespace
+
+cudaError_t noalloc_take_error(int dev, int* value) {
+  *value = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (dev < 0 || dev >= 64 || !g_dev[dev].ready) return cudaSuccess;   // never ran here
+  }
+  // copies to and from the symbol of the current device: nothing is allocated
+  cudaError_t e = cudaMemcpyFromSymbol(value, g_noalloc_error_word, sizeof(int));
+  if (e == cudaSuccess && *value != 0) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbol(g_noalloc_error_word, &zero, sizeof(int));
+  }
+  return e;
+}
+
 }  // namespace gb
 
 using namespace gb;

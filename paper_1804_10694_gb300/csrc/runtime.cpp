@@ -1109,17 +1109,24 @@ const char* gemm_last_error(void) { return t_last_error.c_str(); }
 gemm_status gemm_device_error(void) {
   clear_error();
   DeviceState* d;
-  gemm_status st = device_state(&d, nullptr);
+  int dev = 0;
+  gemm_status st = device_state(&d, &dev);
   if (st != GEMM_OK) return st;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
-  int v = 0;
+  int v = 0, vn = 0;
   if ((e = cudaMemcpy(&v, d->err_word, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e, "read error word");
+  // the allocation-free entry point keeps its own word (it allocates nothing)
+  if ((e = noalloc_take_error(dev, &vn)) != cudaSuccess)
+    return cuda_fail(e, "read the allocation-free path's error word");
   if (v != 0) {
     cudaMemset(d->err_word, 0, sizeof(int));
     return fail(GEMM_ERR_TIMEOUT, "a kernel abandoned a pipeline wait (error word %d)", v);
   }
+  if (vn != 0)
+    return fail(GEMM_ERR_TIMEOUT,
+                "a kernel of the allocation-free path abandoned a pipeline wait (error word %d)", vn);
   return GEMM_OK;
 }
 

@@ -82,6 +82,10 @@ void plan_destroy_impl(gemm_plan_t p);
 
 // The current device's kernel error word (allocated on first use).
 gemm_status device_err_word(int** out);
+// Reads and clears the allocation-free path's kernel error word of device
+// `dev`, which must be the current device (value 0 if that path never ran
+// there).  Allocates nothing.
+cudaError_t noalloc_take_error(int dev, int* value);
 // 3-D tensor map over hi/lo planes [2][rows][pitch] with box {sw bytes of K,
 // box_rows, 1} and the sw-byte swizzle (128 or 64).
 gemm_status encode_planes_map(CUtensorMap* map, Prec p, void* base, int64_t rows, int64_t K,

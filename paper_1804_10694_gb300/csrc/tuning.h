@@ -17,7 +17,20 @@ struct EffConfig {
 EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, int64_t K);
 // Candidate ids with pairwise different effective configurations on the shape.
 std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t K);
-bool table_lookup(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);
+// A tuned shape: sizes and leading dimensions.
+struct Shape6 {
+  int64_t M, N, K, lda, ldb, ldc;
+};
+bool table_lookup(gemm_mode mode, const Shape6& sh, int* cid, float* ms);
+// One row of an autotuner CSV file (rows without leading dimensions, from
+// files written before they were part of a shape, read as tight); 0 if the
+// line is not a timing row.
+struct TimingRow {
+  Shape6 sh;
+  int mode, cid;
+  float ms;
+};
+int parse_timing_row(const char* line, TimingRow* r);
 // Cost-model argmin over the distinct configurations (GEMM_ERR_INVALID_ARG
 // when no model is loaded).
 gemm_status costmodel_pick(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);

@@ -67,19 +67,26 @@ def _read_rows(path):
 
 
 def test_autotune_table_and_table_selection(tmp_path):
+    """Shapes carry leading dimensions: the tight 640 x 384 x 1000 and the same
+    sizes with ldc = N + 3 (staged stores of C) are tuned and looked up
+    apart."""
     path = str(tmp_path / "timings.csv")
-    shapes = [(640, 384, 1000), (96, 2000, 300), (3000, 64, 5000)]
+    shapes = [(640, 384, 1000, 1000, 384, 384), (640, 384, 1000, 1000, 384, 387),
+              (96, 2000, 300, 300, 2000, 2000), (3000, 64, 5000, 5001, 64, 64)]
     pkg.autotune(shapes, mode="bf16x3", reps=3, out_path=path)
     rows = _read_rows(path)
-    for (M, N, K) in shapes:
-        mine = [r for r in rows if (int(r["M"]), int(r["N"]), int(r["K"])) == (M, N, K)]
+    for sh in shapes:
+        mine = [r for r in rows
+                if tuple(int(r[k]) for k in ("M", "N", "K", "lda", "ldb", "ldc")) == sh]
         assert len(mine) >= 2
         ids = {int(r["config_id"]) for r in mine}
         assert len(ids) == len(mine)          # every distinct configuration timed once
         best = min(mine, key=lambda r: float(r["median_ms"]))
-        cid, ms = pkg.autotune_best(M, N, K, "bf16x3")
+        M, N, K, lda, ldb, ldc = sh
+        cid, ms = pkg.autotune_best(M, N, K, "bf16x3", lda=lda, ldb=ldb, ldc=ldc)
         assert cid == int(best["config_id"])
-        plan = pkg.Plan(M, N, K, mode="bf16x3", select="table")
+        assert pkg.select_config(M, N, K, "bf16x3", "table", lda=lda, ldb=ldb, ldc=ldc) == cid
+        plan = pkg.Plan(M, N, K, lda, ldb, ldc, mode="bf16x3", select="table")
         assert plan.info()["config_id"] == cid
         plan.destroy()
 
@@ -90,18 +97,18 @@ def _regret(table, shape, cid):
 
 
 def test_trained_model_beats_the_untrained_heuristic(tmp_path):
-    """Train on the autotuner's timings of 48 shapes, then compare, on 12
-    held-out shapes timed exhaustively, the regret of the model's pick with
-    the regret of the built-in heuristic's pick."""
-    train = W.training_shapes(48, seed=11, hi=8192, max_mnk_log2=33.0)
-    held = W.training_shapes(12, seed=12, hi=8192, max_mnk_log2=33.0)
+    """Train on the autotuner's timings of 120 shapes, then compare, on 24
+    held-out shapes timed exhaustively, the mean regret of the model's pick
+    with that of the built-in heuristic's pick: the model must be better."""
+    train = W.training_shapes(120, seed=11, hi=8192, max_mnk_log2=33.0)
+    held = W.training_shapes(24, seed=12, hi=8192, max_mnk_log2=33.0)
     tpath, hpath = str(tmp_path / "train.csv"), str(tmp_path / "held.csv")
     pkg.autotune(train, mode="bf16x3", reps=3, out_path=tpath)
     pkg.autotune(held, mode="bf16x3", reps=3, out_path=hpath)
     loss = pkg.costmodel_train(tpath, epochs=1500, seed=1, out_model=str(tmp_path / "m.txt"))
     assert np.isfinite(loss) and loss < 0.5            # normalised MSE
     table = {}
-    for r in _read_rows(hpath):
+    for r in _read_rows(hpath):   # tight shapes: keyed by the sizes
         table.setdefault((int(r["M"]), int(r["N"]), int(r["K"])), {})[int(r["config_id"])] = float(r["median_ms"])
     model_regret, default_regret = [], []
     for s in held:
@@ -110,7 +117,7 @@ def test_trained_model_beats_the_untrained_heuristic(tmp_path):
         default_regret.append(_regret(table, tuple(s), _canonical(table[tuple(s)], s)))
     m, d = float(np.mean(model_regret)), float(np.mean(default_regret))
     print(f"held-out mean regret: model {m:.3f}, heuristic {d:.3f}")
-    assert m <= max(d, 0.05)
+    assert m < d, (m, d)
     # the loaded model drives GEMM_SELECT_MODEL
     pkg.costmodel_load(str(tmp_path / "m.txt"))
     plan = pkg.Plan(*held[0], mode="bf16x3", select="model")

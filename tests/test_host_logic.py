@@ -68,13 +68,51 @@ def test_autotune_table_file_parsing(tmp_path):
     lib = pkg.load()
     assert lib.gemm_autotune_load(str(tmp_path / "none.csv").encode()) == 7
     f = tmp_path / "t.csv"
-    f.write_text("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m\n"
-                 "777,555,333,2,3,0.5,128,1,2,1\n777,555,333,2,7,0.25,128,2,2,1\n"
-                 "777,555,333,2,99999,0.01,0,0,0,0\ngarbage line\n")
+    f.write_text("M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n"
+                 "777,555,333,333,555,555,2,3,0.5,128,1,2,1,0\n"
+                 "777,555,333,333,555,555,2,7,0.25,128,2,2,1,0\n"
+                 "777,555,333,333,555,555,2,99999,0.01,0,0,0,0,0\ngarbage line\n")
     assert lib.gemm_autotune_load(str(f).encode()) == 0
     assert pkg.autotune_best(777, 555, 333, "bf16x3") == (7, 0.25)
     with pytest.raises(pkg.GemmError):
         pkg.autotune_best(777, 555, 334, "bf16x3")
+    # rows of the earlier format (no leading dimensions) are tight shapes
+    g = tmp_path / "old.csv"
+    g.write_text("M,N,K,mode,config_id,median_ms,block_n,split_k,kb,group_m\n"
+                 "901,503,207,2,11,0.75,128,1,2,1,0\n")
+    assert lib.gemm_autotune_load(str(g).encode()) == 0
+    assert pkg.autotune_best(901, 503, 207, "bf16x3", lda=207, ldb=503, ldc=503) == (11, 0.75)
+
+
+def test_table_selection_keys_on_leading_dimensions(tmp_path):
+    """A shape is (M, N, K, lda, ldb, ldc): the tuned table holds a tight
+    shape and the same sizes with ldc = N + 3 apart, and GEMM_SELECT_TABLE
+    picks each one's own best configuration (no device needed)."""
+    M, N, K = 1200, 650, 900
+    f = tmp_path / "lds.csv"
+    f.write_text("M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n"
+                 f"{M},{N},{K},{K},{N},{N},2,5,0.40,128,1,2,1,0\n"
+                 f"{M},{N},{K},{K},{N},{N},2,9,0.30,128,2,2,1,0\n"
+                 f"{M},{N},{K},{K},{N},{N + 3},2,9,0.50,128,2,2,1,0\n"
+                 f"{M},{N},{K},{K},{N},{N + 3},2,41,0.45,64,1,2,1,0\n")
+    pkg.autotune_load(str(f))
+    assert pkg.autotune_best(M, N, K, "bf16x3") == (9, pytest.approx(0.30))
+    assert pkg.autotune_best(M, N, K, "bf16x3", ldc=N + 3) == (41, pytest.approx(0.45))
+    assert pkg.select_config(M, N, K, "bf16x3", "table") == 9
+    assert pkg.select_config(M, N, K, "bf16x3", "table", ldc=N + 3) == 41
+    # an untuned leading dimension falls back to the heuristic
+    assert pkg.select_config(M, N, K, "bf16x3", "table", lda=K + 1) == \
+        pkg.select_config(M, N, K, "bf16x3", "default")
+    assert pkg.select_config(M, N, K, "simt", "table") == -1
+    with pytest.raises(pkg.GemmError):
+        pkg.select_config(M, N, K, "bf16x3", "table", ldc=N - 1)
+
+
+def test_autotune_rejects_bad_shapes_before_running():
+    lib = pkg.load()
+    bad = (ctypes.c_int64 * 6)(64, 64, 64, 63, 64, 64)      # lda < K
+    assert lib.gemm_autotune(bad, 1, 2, 3, None) == 1
+    assert b"shape 0" in lib.gemm_last_error()
 
 
 def test_grouped_plan_argument_validation():
