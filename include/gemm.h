@@ -97,7 +97,14 @@ typedef struct {
 
 /* C = alpha*A*B + beta*C on the default stream, mode AUTO, default tiles.
  * Definition: paper Section I.  Plans are created and cached internally per
- * (shape, leading dimensions, mode, stream). */
+ * (shape, leading dimensions, mode, stream); the cache holds 16 plans, and a
+ * plan it drops is destroyed once its last execution has completed (polled
+ * with an event on later calls: no call waits on the device).  Creating or
+ * dropping a cached plan allocates or frees device memory, so a call that
+ * would do either while its stream is being captured into a graph fails with
+ * GEMM_ERR_INVALID_ARG: make the call once before the capture, or capture
+ * an explicit plan (gemm_plan_create / gemm_plan_execute), which also keeps
+ * the captured workspace alive for as long as the graph needs it. */
 gemm_status gemm_f32(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
                      const float* B, int64_t ldb, float beta, float* C, int64_t ldc);
 

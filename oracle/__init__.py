@@ -15,4 +15,4 @@ Modules:
   conv   -- direct 3x3 convolution (stride 1, zero padding 1), FP64 and exact.
 """
 from .gemm import (build, gemm_f64, gemm_f64_rows, gemm_f32_seq, rel_frob, gemm_exact,  # noqa: F401
-                   library_path, num_threads)
+                   library_path, num_threads, set_num_threads, product_f64, axpby_f64)

@@ -53,11 +53,15 @@ def _load():
             lib.oracle_gemm_f64_rows.argtypes = [i64, i64, f32, vp, i64, vp, i64,
                                                  f32, vp, i64, vp, i64, vp]
             lib.oracle_gemm_f64_rows.restype = None
+            lib.oracle_axpby_f64.argtypes = [i64, i64, f32, vp, i64, f32, vp, i64, vp, i64]
+            lib.oracle_axpby_f64.restype = None
             lib.oracle_gemm_f32_seq.argtypes = [i64, i64, i64, f32, vp, i64, vp, i64,
                                                 f32, vp, i64, vp, i64]
             lib.oracle_gemm_f32_seq.restype = None
             lib.oracle_rel_frob.argtypes = [i64, i64, vp, i64, vp, i64]
             lib.oracle_rel_frob.restype = ctypes.c_double
+            lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_num_threads.restype = None
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -119,6 +123,34 @@ def gemm_f64_rows(rows, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndarr
     return out
 
 
+def product_f64(M: int, N: int, K: int, A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """The sums sum_k A[i][k] * B[k][j] in double (M x N): gemm_f64 with
+    alpha = 1 and beta = 0.  With ``axpby_f64`` it gives gemm_f64's result bit
+    for bit, so that one product (the expensive part at large sizes) serves
+    several (alpha, beta) pairs."""
+    return gemm_f64(M, N, K, 1.0, A, B, 0.0, None)
+
+
+def axpby_f64(alpha: float, P: np.ndarray, beta: float, C0: np.ndarray | None) -> np.ndarray:
+    """alpha * P + beta * C0 in double, the definition's last step (C0 a
+    float32 storage array, not read when beta == 0)."""
+    lib = _load()
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    M, N = P.shape
+    ldc = 1
+    if beta != 0.0:
+        C0 = _f32(C0)
+        ldc = C0.shape[1]
+    else:
+        C0 = None
+    out = np.empty((M, N), dtype=np.float64)
+    if M == 0 or N == 0:
+        return out
+    lib.oracle_axpby_f64(M, N, ctypes.c_float(alpha), _ptr(P), N, ctypes.c_float(beta), _ptr(C0), ldc,
+                         _ptr(out), N)
+    return out
+
+
 def gemm_f32_seq(M: int, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndarray,
                  beta: float, C0: np.ndarray | None) -> np.ndarray:
     """The definition evaluated in FP32 (k in increasing order, every product
@@ -141,6 +173,11 @@ def gemm_f32_seq(M: int, N: int, K: int, alpha: float, A: np.ndarray, B: np.ndar
     lib.oracle_gemm_f32_seq(M, N, K, ctypes.c_float(alpha), _ptr(A), lda, _ptr(B), ldb,
                             ctypes.c_float(beta), _ptr(C0), ldc, _ptr(out), N)
     return out
+
+
+def set_num_threads(n: int) -> None:
+    """Threads the oracle's OpenMP loops use from now on."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def num_threads() -> int:

@@ -66,6 +66,26 @@ void oracle_gemm_f64_rows(int64_t N, int64_t K, float alpha,
         oracle_row(rows[r], N, K, da, A, lda, B, ldb, db, C0, ldc, out + r * N);
 }
 
+/* The last step of the definition on its own: out = alpha * P + beta * C0,
+ * where P holds the sums sum_k A[i][k] * B[k][j] in double (oracle_gemm_f64
+ * with alpha = 1, beta = 0 computes them: 1 * sum is exact).  The same
+ * arithmetic as oracle_row's last loop, so that the two steps give the
+ * one-step result bit for bit; one product then serves several (alpha,
+ * beta) pairs.  C0 is not read when beta == 0; alpha == 0 ignores P. */
+void oracle_axpby_f64(int64_t M, int64_t N, float alpha, const double* P, int64_t ldp,
+                      float beta, const float* C0, int64_t ldc, double* out, int64_t ldo)
+{
+    const double da = (double)alpha, db = (double)beta;
+    #pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < M; ++i) {
+        for (int64_t j = 0; j < N; ++j) {
+            double v = (da != 0.0) ? da * P[i * ldp + j] : 0.0;
+            if (db != 0.0) v += db * (double)C0[i * ldc + j];
+            out[i * ldo + j] = v;
+        }
+    }
+}
+
 /* The same definition evaluated in FP32 arithmetic, the accuracy of a plain
  * single-precision gemm: for each element, acc = 0 and, k in increasing
  * order, acc = fl(acc + fl(a_ik * b_kj)) (every operation rounded to nearest
@@ -117,6 +137,18 @@ double oracle_rel_frob(int64_t M, int64_t N, const float* got, int64_t ldg,
     }
     if (den == 0.0) return __builtin_sqrt(num);
     return __builtin_sqrt(num / den);
+}
+
+/* Sets the number of OpenMP threads of the loops above (for timing the
+ * oracle on one core and on all of them). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* Threads the OpenMP loops above use (for reporting the CPU baseline). */

@@ -570,6 +570,7 @@ void plan_destroy_impl(gemm_plan_t p) {
   if (!p) return;
   profile_release(p);
   if (p->ws) cudaFree(p->ws);
+  if (p->last_use) cudaEventDestroy(p->last_use);
   delete p;
 }
 
@@ -589,7 +590,36 @@ struct CacheKey {
 static std::mutex g_cache_mutex;
 static std::map<CacheKey, gemm_plan_t> g_cache;
 static std::list<CacheKey> g_lru;
+// Plans the cache has dropped whose last execution may still be queued:
+// each is destroyed once its last-use event has completed, found by polling
+// (cudaEventQuery) on later cache calls.  Nothing waits on the device, so
+// an eviction stalls no stream and is legal next to other streams' captures.
+static std::list<gemm_plan_t> g_retired;
 constexpr size_t kCacheMax = 16;
+
+// (g_cache_mutex held)
+static void reap_retired() {
+  for (auto it = g_retired.begin(); it != g_retired.end();) {
+    gemm_plan_t p = *it;
+    const cudaError_t q = p->last_use ? cudaEventQuery(p->last_use) : cudaSuccess;
+    if (q == cudaErrorNotReady) {
+      ++it;
+      continue;
+    }
+    if (q != cudaSuccess) cudaGetLastError();   // a sticky fault is reported by the next call
+    plan_destroy_impl(p);
+    it = g_retired.erase(it);
+  }
+}
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
 
 gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
                         gemm_mode mode, gemm_select sel, cudaStream_t s, gemm_plan_t* out,
@@ -598,7 +628,11 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
   cudaGetDevice(&dev);
   CacheKey key{dev, M, N, K, lda, ldb, ldc, (int)mode, (int)sel, (transA ? 1 : 0) | (transB ? 2 : 0),
                reinterpret_cast<uintptr_t>(s)};
+  // (the capture status is read first: while this thread's stream is being
+  // captured, no event of an eager execution is queried)
+  const bool capturing = stream_capturing(s);
   std::lock_guard<std::mutex> lk(g_cache_mutex);
+  if (!capturing) reap_retired();
   auto it = g_cache.find(key);
   if (it != g_cache.end()) {
     g_lru.remove(key);
@@ -607,21 +641,31 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
     *out = it->second;
     return GEMM_OK;
   }
+  // a new plan allocates its workspace, and an eviction may free one: neither
+  // belongs inside a stream capture
+  if (capturing)
+    return fail(GEMM_ERR_INVALID_ARG,
+                "no cached plan for this shape and stream while the stream is being captured: "
+                "call once before the capture, or capture an explicit plan (gemm_plan_create)");
   gemm_plan_t p = nullptr;
   gemm_status st = plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, &p, transA, transB);
   if (st != GEMM_OK) return st;
+  cudaError_t e = cudaEventCreateWithFlags(&p->last_use, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    p->last_use = nullptr;
+    plan_destroy_impl(p);
+    return cuda_fail(e, "cudaEventCreate");
+  }
   if (g_cache.size() >= kCacheMax) {
     const CacheKey victim = g_lru.back();
     g_lru.pop_back();
     gemm_plan_t v = g_cache[victim];
     g_cache.erase(victim);
-    if (v->cache_users == 0) {
-      // the victim may still be in use on its stream: wait for the device first
-      cudaDeviceSynchronize();
-      plan_destroy_impl(v);
-    } else {
-      v->cache_evicted = true;   // another call holds it: its last holder destroys it
-    }
+    if (v->cache_users == 0)
+      g_retired.push_back(v);    // destroyed once its last execution has completed
+    else
+      v->cache_evicted = true;   // another call holds it: its last holder retires it
+    reap_retired();
   }
   g_cache[key] = p;
   g_lru.push_front(key);
@@ -630,13 +674,17 @@ gemm_status cached_plan(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ld
   return GEMM_OK;
 }
 
+// Marks the end of one eager execution of a cached plan on stream s (an
+// execution captured into a graph is not tracked: the graph's owner must
+// keep the plan alive, which only an explicit plan guarantees).
+static void note_use(gemm_plan_t p, cudaStream_t s) {
+  if (p && p->last_use && !stream_capturing(s)) cudaEventRecord(p->last_use, s);
+}
+
 void release_cached_plan(gemm_plan_t p) {
   if (!p) return;
   std::lock_guard<std::mutex> lk(g_cache_mutex);
-  if (--p->cache_users == 0 && p->cache_evicted) {
-    cudaDeviceSynchronize();   // its launches may still be queued
-    plan_destroy_impl(p);
-  }
+  if (--p->cache_users == 0 && p->cache_evicted) g_retired.push_back(p);
 }
 
 // Holds a plan of the internal cache for the duration of one call, so that
@@ -833,6 +881,13 @@ gemm_status host_gemm_impl(int64_t M, int64_t N, int64_t K, float alpha, const f
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, GEMM_SELECT_DEFAULT, s, &p, false, false)) != GEMM_OK)
     return st;
   const CachedPlanUse hold(p);
+  // (every path below synchronises its streams before returning, so the plan
+  // is idle once the call ends; the event still marks its last use on s)
+  struct NoteUse {
+    gemm_plan_t p;
+    cudaStream_t s;
+    ~NoteUse() { note_use(p, s); }
+  } note{p, s};
   if (need_ab && p->mode != GEMM_MODE_F32_SIMT && p->args.split_k == 1 && !p->launch.fused &&
       host_panels() > 1 &&
       M >= 4 * 128 && page_locked(A) && page_locked(C))
@@ -874,7 +929,9 @@ gemm_status gemm_f32_ex(int64_t M, int64_t N, int64_t K, float alpha, const floa
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, false, false)) != GEMM_OK) return st;
   const CachedPlanUse hold(p);
-  return plan_execute_impl(p, alpha, A, B, beta, C, s);
+  st = plan_execute_impl(p, alpha, A, B, beta, C, s);
+  note_use(p, s);
+  return st;
 }
 
 gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, float alpha,
@@ -890,7 +947,9 @@ gemm_status gemm_f32_t(int transA, int transB, int64_t M, int64_t N, int64_t K, 
   if ((st = cached_plan(M, N, K, lda, ldb, ldc, mode, sel, s, &p, transA != 0, transB != 0)) != GEMM_OK)
     return st;
   const CachedPlanUse hold(p);
-  return plan_execute_impl(p, alpha, A, B, beta, C, s);
+  st = plan_execute_impl(p, alpha, A, B, beta, C, s);
+  note_use(p, s);
+  return st;
 }
 
 gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int64_t K, int64_t lda,

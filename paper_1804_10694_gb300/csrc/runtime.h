@@ -46,10 +46,13 @@ struct gemm_plan_s {
   // at the start of packing, before and after the main kernel, at the end
   int prof_max = 0, prof_n = 0;
   std::vector<cudaEvent_t> prof_events;
-  // internal plan cache (guarded by its mutex): calls holding the plan, and
-  // whether the cache has dropped it (the last holder then destroys it)
+  // internal plan cache (guarded by its mutex): calls holding the plan,
+  // whether the cache has dropped it (the last holder then retires it), and
+  // an event recorded on the plan's stream after each of its executions (a
+  // retired plan is destroyed once that event has completed)
   int cache_users = 0;
   bool cache_evicted = false;
+  cudaEvent_t last_use = nullptr;
 };
 
 namespace gb {

@@ -48,16 +48,3 @@ def square_inputs(n: int, config_index: int, gen: str = "uniform"):
     sa, sb, sc = W.seeds(config_index)
     f = {"uniform": W.uniform, "wide": W.wide_range, "int": W.integers}[gen]
     return f(n, n, sa + n), f(n, n, sb + n), f(n, n, sc + n)
-
-
-def sample_rows(M: int, count: int, seed: int = 0):
-    """Rows spread over the matrix, always including the first and the last
-    full-tile row and every row of the last (possibly partial) tile edge."""
-    rng = np.random.default_rng(seed)
-    rows = set(rng.choice(M, size=min(count, M), replace=False).tolist())
-    rows |= {0, min(127, M - 1), M - 1, max(0, M - 2), (M // 128) * 128 % M}
-    return sorted(rows)
-
-
-def rel_err_rows(got_full: np.ndarray, rows, ref_rows: np.ndarray, N: int) -> float:
-    return oracle.rel_frob(np.ascontiguousarray(got_full[rows, :N]), ref_rows)

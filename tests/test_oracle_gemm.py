@@ -139,6 +139,24 @@ def test_sampled_rows_equal_full_rows():
     assert np.array_equal(part, full[rows])
 
 
+@pytest.mark.parametrize("alpha,beta", [(1.5, 0.5), (1.0, 0.0), (0.0, 2.0), (-0.75, -1.25), (0.0, 0.0)])
+def test_product_then_epilogue_equals_one_step_definition(alpha, beta):
+    """Two steps (the double sums once, then alpha * P + beta * C0) give the
+    one-step result bit for bit, for any (alpha, beta), with padded leading
+    dimensions; beta == 0 reads no C (NaN there stays out)."""
+    M, N, K = 67, 45, 93
+    A = W.uniform(M, K, 21, ld=K + 3)
+    B = W.uniform(K, N, 22, ld=N + 1)
+    C0 = W.uniform(M, N, 23, ld=N + 2)
+    P = oracle.product_f64(M, N, K, A, B)
+    one = oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)
+    two = oracle.axpby_f64(alpha, P, beta, C0 if beta != 0 else np.full_like(C0, np.nan))
+    assert np.array_equal(one.view(np.uint64), two.view(np.uint64))
+    # and P is the plain sum: numpy's float64 matmul of the widened inputs
+    ref = A[:, :K].astype(np.float64) @ B[:, :N].astype(np.float64)
+    assert np.allclose(P, ref, rtol=1e-13, atol=1e-13)
+
+
 def test_rel_frob_metric():
     ref = np.array([[3.0, 4.0]])
     got = np.array([[3.0, 4.0 + 5e-3]], np.float32)
