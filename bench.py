@@ -324,8 +324,12 @@ def other_workloads(model_path: str | None):
             plan.destroy()
         out["sweep"][str(n)] = row
         del A, B, C
+    model_note = None
     if model_path and os.path.exists(model_path):
-        pkg.costmodel_load(model_path)
+        try:
+            pkg.costmodel_load(model_path)
+        except pkg.GemmError as e:        # (a model file of another feature set)
+            model_note = str(e)
     for (M, N, K) in W.CONV_SHAPES:
         A = torch.empty(M, K, device="cuda").uniform_(-1, 1)
         B = torch.empty(K, N, device="cuda").uniform_(-1, 1)
@@ -446,6 +450,8 @@ def other_workloads(model_path: str | None):
         p_.destroy()
     out["grouped"] = {"problems": len(shapes), "gflop": round(flops / 1e9, 2),
                       "graph_replay": grouped, "one_plan_per_problem_loop": loop}
+    if model_note:
+        out["costmodel_not_loaded"] = model_note
     return out
 
 
@@ -686,7 +692,10 @@ def run_table(args, local):
     del As, Bs, Cs
     # d5: conv-as-gemm shapes, the cost model's pick
     if args.costmodel and os.path.exists(args.costmodel):
-        pkg.costmodel_load(args.costmodel)
+        try:
+            pkg.costmodel_load(args.costmodel)
+        except pkg.GemmError:
+            pass   # the model's pick falls back to the heuristic
     for (M, N, K) in W.CONV_SHAPES:
         sa, sb, _ = W.seeds(W.CONFIG_CONV)
         A, B = W.uniform(M, K, sa), W.uniform(K, N, sb)

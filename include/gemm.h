@@ -80,18 +80,24 @@ typedef struct gemm_grouped_plan_s* gemm_grouped_plan_t;
 
 /* Tile configuration of the tensor-core kernels (one entry of the candidate
  * table that the autotuner and the cost model choose from; the paper tunes
- * tile size and unroll factor, Section VI-A). */
+ * tile size and unroll factor, Section VI-A; the table itself is this
+ * library's). */
 typedef struct {
-  int block_n;     /* output tile width (tile height is 128) */
+  int block_n;     /* output tile width */
   int stages;      /* depth of the shared-memory operand ring */
   int split_k;     /* number of K partitions (partials reduced in fixed order) */
   int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (1..8) */
   int group_m;     /* raster: output tiles walked in groups of this many along M */
   int fused;       /* 1: A is split inside the gemm kernel (no packed copy of A);
                     *    0: A is packed into hi/lo planes by a separate pass */
+  int cluster;     /* CTAs per output tile: 1 (tile 128 x block_n on one SM), or
+                    * 2 (tile 256 x block_n on a pair of SMs, one tensor-core
+                    * operation over both: tcgen05 cta_group::2) */
 } gemm_config;
-/* BF16X3 and TF32X3 share one table of 144 entries (ids 72..143 are the
- * fused twins of ids 0..71); BF16X6 has ids 0..71, each with stages = 2. */
+/* BF16X3 and TF32X3 share one table of 216 entries: ids 0..71 single-CTA
+ * packed (block_n 128 or 64), ids 72..143 CTA pairs (block_n 256 or 128,
+ * packed), ids 144..215 the fused twins of ids 0..71.  BF16X6 has ids
+ * 0..143 (packed and pairs; no fused kernel), each with stages = 2. */
 
 /* ---------------------------------------------------------------- gemm -- */
 

@@ -26,7 +26,7 @@ STATUS_NAMES = {
 
 class GemmConfig(ctypes.Structure):
     _fields_ = [("block_n", i32), ("stages", i32), ("split_k", i32), ("kb", i32), ("group_m", i32),
-                ("fused", i32)]
+                ("fused", i32), ("cluster", i32)]
 
 
 # name -> (restype, argtypes); mirrors include/gemm.h one to one

@@ -38,8 +38,10 @@ EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, i
   int sk = (int)std::max<int64_t>(1, std::min<int64_t>(c.split_k, chunks));
   const int64_t per = (chunks + sk - 1) / sk;
   sk = (int)((chunks + per - 1) / per);
-  const int64_t tiles_m = (M + 127) / 128;
+  const int cl = c.cluster == 2 ? 2 : 1;
+  const int64_t tiles_m = (M + 128 * cl - 1) / (128 * cl);   // a CTA pair's tile is 256 rows
   e.bn = c.block_n;
+  e.cluster = cl;
   e.split_k = sk;
   e.chunks_per_split = (int)per;
   e.kb = (int)std::min<int64_t>(c.kb, per);
@@ -51,13 +53,14 @@ EffConfig effective_config(const gemm_config& c, Prec p, int64_t M, int64_t N, i
 
 std::vector<int> distinct_configs(gemm_mode mode, int64_t M, int64_t N, int64_t K) {
   std::vector<int> out;
-  std::set<std::tuple<int, int, int, int, int>> seen;
+  std::set<std::tuple<int, int, int, int, int, int>> seen;
   const Prec p = prec_of_mode(mode);
   gemm_config c;
   for (int id = 0; id < config_count(mode); ++id) {
     config_get(id, &c);
     const EffConfig e = effective_config(c, p, M, N, K);
-    if (seen.insert(std::make_tuple(e.bn, e.split_k, e.kb, e.group_m, e.fused)).second) out.push_back(id);
+    if (seen.insert(std::make_tuple(e.bn, e.split_k, e.kb, e.group_m, e.fused, e.cluster)).second)
+      out.push_back(id);
   }
   return out;
 }
@@ -89,7 +92,7 @@ int parse_timing_row(const char* line, TimingRow* r) {
   int commas = 0;
   for (const char* c = line; *c; ++c) commas += *c == ',';
   long long M, N, K, lda, ldb, ldc;
-  if (commas == 13) {
+  if (commas >= 13) {
     if (std::sscanf(line, "%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,%f", &M, &N, &K, &lda, &ldb, &ldc,
                     &r->mode, &r->cid, &r->ms) != 9)
       return 0;
@@ -319,7 +322,7 @@ gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps
     if (!f) return fail(GEMM_ERR_IO, "cannot open %s for appending", out_path);
     std::fseek(f, 0, SEEK_END);
     if (std::ftell(f) == 0)
-      std::fprintf(f, "M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused\n");
+      std::fprintf(f, "M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,group_m,fused,cluster\n");
   }
   gemm_status st = GEMM_OK;
   for (int s = 0; s < G && st == GEMM_OK; ++s) {
@@ -334,10 +337,10 @@ gemm_status gemm_autotune(const int64_t* shapes, int G, gemm_mode mode, int reps
           if (!f) return;
           gemm_config c;
           config_get(cid, &c);
-          std::fprintf(f, "%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d,%d\n", (long long)sh.M,
+          std::fprintf(f, "%lld,%lld,%lld,%lld,%lld,%lld,%d,%d,%.6f,%d,%d,%d,%d,%d,%d\n", (long long)sh.M,
                        (long long)sh.N, (long long)sh.K, (long long)sh.lda, (long long)sh.ldb,
                        (long long)sh.ldc, (int)mode, cid, ms, c.block_n, c.split_k, c.kb, c.group_m,
-                       c.fused);
+                       c.fused, c.cluster);
         },
         &best, &best_ms);
     if (f) std::fflush(f);

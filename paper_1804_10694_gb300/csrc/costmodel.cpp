@@ -35,12 +35,15 @@ void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const g
   const EffConfig e = effective_config(c, p, M, N, K);
   const int ck = prec_chunk_elems(p);
   const double chunks = (double)((K + ck - 1) / ck);
+  // units run on sms / cluster processors (SMs, or pairs of SMs)
+  const double procs = (double)(sms / e.cluster);
   const double units = (double)e.tiles * e.split_k;
-  const double waves = units / sms;
-  const double rem = units - std::floor(waves) * sms;
-  const double fill = rem == 0.0 ? 1.0 : rem / sms;
-  const double tiles_m = (double)((M + 127) / 128), tiles_n = (double)((N + e.bn - 1) / e.bn);
-  const double padded = (tiles_m * 128.0) * (tiles_n * e.bn) * (chunks * ck) /
+  const double waves = units / procs;
+  const double rem = units - std::floor(waves) * procs;
+  const double fill = rem == 0.0 ? 1.0 : rem / procs;
+  const double tile_h = 128.0 * e.cluster;
+  const double tiles_m = std::ceil((double)M / tile_h), tiles_n = (double)((N + e.bn - 1) / e.bn);
+  const double padded = (tiles_m * tile_h) * (tiles_n * e.bn) * (chunks * ck) /
                             ((double)M * (double)N * (double)K) - 1.0;
   const double ai = 2.0 * M * N * K / (4.0 * ((double)M * K + (double)K * N + 2.0 * M * N));
   out[0] = (float)std::log2((double)M);
@@ -59,6 +62,7 @@ void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const g
   out[13] = mode == GEMM_MODE_TF32X3 ? 1.0f : 0.0f;
   out[14] = c.fused ? 1.0f : 0.0f;
   out[15] = mode == GEMM_MODE_BF16X6 ? 1.0f : 0.0f;   // six products per k-step, three planes
+  out[16] = e.cluster == 2 ? 1.0f : 0.0f;              // a 256-row tile on a pair of SMs
 }
 
 namespace {

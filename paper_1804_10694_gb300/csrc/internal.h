@@ -61,10 +61,11 @@ struct TcArgs {
 };
 
 struct TcLaunch {
-  int bn;          // tile N (64 or 128)
+  int bn;          // tile N (64 or 128; 128 or 256 for a CTA pair)
   Prec prec;       // BF16, BF16X6 or TF32
   int grid;
   bool fused;      // A split inside the gemm kernel (only B is packed)
+  int cluster;     // 1, or 2: a 256-row tile on a pair of SMs (tc_pair_launch)
 };
 
 // Returns the dynamic shared memory a tensor-core kernel variant needs.
@@ -76,6 +77,14 @@ int tc_chunk_bytes(int bn);
 // current device (call outside stream capture; idempotent).
 cudaError_t tc_prepare(int bn, Prec prec, bool fused = false);
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                           const TcArgs& a, cudaStream_t s);
+// CTA-pair variants (tile 256 x bn, bn 128 or 256; clusters of two CTAs,
+// tcgen05 cta_group::2): raise the shared-memory limit and report how many
+// clusters can be resident at once (call outside stream capture), and
+// launch (grid = 2 x clusters; a.tiles_m in 256-row tiles, a.tm0 even; tmB's
+// box holds bn/2 rows).
+cudaError_t tc_pair_prepare(int bn, Prec prec, int* max_pairs);
+cudaError_t tc_pair_launch(int bn, Prec prec, int grid, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s);
 // C = sum_s partial[s] + beta * C over the split-K partial sums (alpha is
 // already inside the partials).

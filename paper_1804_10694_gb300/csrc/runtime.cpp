@@ -115,38 +115,45 @@ bool device_has_tcgen05(const DeviceState& d) { return d.cc_major == 10 && d.cc_
 constexpr int kMaxFoldChunks = 8;
 
 // Candidates of the tensor-core kernels.  The same table serves BF16X3 and
-// TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way).
-// Ids 0..71 pack both operands; ids 72..143 repeat them with A split inside
-// the gemm kernel.  BF16X6 has ids 0..71 only (its kernel reads packed
-// planes of both operands), each with a two-deep ring: a stage holds six
-// planes.
+// TF32X3 (the k-chunk is 64 bf16 or 32 tf32 elements, 128 bytes either way):
+// ids 0..71 pack both operands and run one CTA per 128 x {128, 64} tile;
+// ids 72..143 pack both operands and run a CTA pair per 256 x {256, 128}
+// tile; ids 144..215 repeat ids 0..71 with A split inside the gemm kernel.
+// BF16X6 has ids 0..143 (its kernels read packed planes of both operands),
+// each with a two-deep ring: a stage holds six planes.
 static const std::vector<gemm_config>& config_table() {
   static const std::vector<gemm_config> table = [] {
     std::vector<gemm_config> t;
     const int splits[] = {1, 2, 3, 4, 6, 8};
     const int kbs[] = {4, 2, 8};
     const int groups[] = {16, 1};
-    for (int fused : {0, 1})
-      for (int bn : {128, 64})
+    // (fused, cluster): packed single CTAs, packed pairs, fused single CTAs
+    const int kinds[3][2] = {{0, 1}, {0, 2}, {1, 1}};
+    for (const auto& kind : kinds) {
+      const int fused = kind[0], cluster = kind[1];
+      const int widths[2][2] = {{128, 64}, {256, 128}};
+      for (int bn : widths[cluster == 2 ? 1 : 0])
         for (int sk : splits)
           for (int kb : kbs)
             for (int g : groups) {
               gemm_config c;
               c.block_n = bn;
-              c.stages = fused ? (bn == 64 ? 3 : 2) : (bn == 64 ? 4 : 3);
+              c.stages = cluster == 2 ? (bn == 256 ? 3 : 4) : fused ? (bn == 64 ? 3 : 2) : (bn == 64 ? 4 : 3);
               c.split_k = sk;
               c.kb = kb;
               c.group_m = g;
               c.fused = fused;
+              c.cluster = cluster;
               t.push_back(c);
             }
+    }
     return t;
   }();
   return table;
 }
 
 int config_count(gemm_mode mode) {
-  if (mode == GEMM_MODE_BF16X6) return (int)config_table().size() / 2;
+  if (mode == GEMM_MODE_BF16X6) return (int)config_table().size() * 2 / 3;
   return (mode == GEMM_MODE_BF16X3 || mode == GEMM_MODE_TF32X3) ? (int)config_table().size() : 0;
 }
 
@@ -163,10 +170,12 @@ bool config_get(gemm_mode mode, int id, gemm_config* out) {
   return true;
 }
 
-static int find_config(int bn, int sk, int kb, int g) {
+// The packed configuration with these fields (single CTA or pair).
+static int find_config(int bn, int sk, int kb, int g, int cluster = 1) {
   const auto& t = config_table();
   for (int i = 0; i < (int)t.size(); ++i)
-    if (t[i].block_n == bn && t[i].split_k == sk && t[i].kb == kb && t[i].group_m == g && !t[i].fused)
+    if (t[i].block_n == bn && t[i].split_k == sk && t[i].kb == kb && t[i].group_m == g && !t[i].fused &&
+        t[i].cluster == cluster)
       return i;
   return 0;
 }
@@ -382,6 +391,9 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
     config_id = find_config(p->cfg.block_n, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
     config_get(m, config_id, &p->cfg);
   }
+  const int cluster = p->cfg.cluster == 2 ? 2 : 1;
+  if (cluster == 2 && conv_image_elems >= 0)
+    return fail(GEMM_ERR_INVALID_ARG, "configuration %d runs on CTA pairs: not for convolutions", config_id);
   p->config_id = config_id;
 
   const Prec pr = p->prec;
@@ -398,7 +410,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   const int kc = 128 / sw;
   const int64_t kchunk = sw / es;                       // elements per kernel chunk
   const int64_t chunks_kernel = (K + kchunk - 1) / kchunk;
-  const int64_t tiles_m = (M + 127) / 128, tiles_n = (N + bn - 1) / bn;
+  // (a CTA pair's tile is 256 rows high)
+  const int64_t tiles_m = (M + 128 * cluster - 1) / (128 * cluster), tiles_n = (N + bn - 1) / bn;
 
   // workspace: A planes (packed variant) | B planes | amax A | amax B | split-K partials
   const bool fused = p->cfg.fused != 0;
@@ -440,7 +453,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   if (!fused && !conv_packed &&
       (st = encode_planes(&p->tmA, pr, p->planesA, M, K, p->pitch, 128, sw)) != GEMM_OK)
     return st;
-  if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn, sw)) != GEMM_OK) return st;
+  // (each CTA of a pair loads half of the tile's rows of B)
+  if ((st = encode_planes(&p->tmB, pr, p->planesB, N, K, p->pitch, bn / cluster, sw)) != GEMM_OK) return st;
 
   TcArgs& a = p->args;
   a.M = (int)M, a.N = (int)N, a.K = (int)K;
@@ -460,9 +474,16 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.lda = lda;
   p->launch.bn = bn;
   p->launch.prec = pr;
-  p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
   p->launch.fused = fused;
-  if ((e = tc_prepare(bn, pr, fused)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
+  p->launch.cluster = cluster;
+  if (cluster == 2) {
+    // one cluster per SM pair that can hold one at a time
+    if ((e = tc_pair_prepare(bn, pr, &p->max_pairs)) != cudaSuccess) return cuda_fail(e, "pair kernel attribute");
+    p->launch.grid = 2 * (int)std::min<int64_t>(a.num_units, p->max_pairs);
+  } else {
+    p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
+    if ((e = tc_prepare(bn, pr, fused)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
+  }
   *out = p.release();
   return GEMM_OK;
 }
@@ -796,7 +817,9 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
   const int64_t M = p->M, N = p->N, K = p->K, lda = p->lda, ldb = p->ldb, ldc = p->ldc;
   const int64_t tiles_m = (M + 127) / 128;
   const int npan = (int)std::min<int64_t>(host_panels(), tiles_m);
-  const int64_t tiles_per = (tiles_m + npan - 1) / npan;
+  // 128-row tiles per panel; even for a CTA-pair plan (its tiles are 256 rows)
+  const int64_t cl = p->launch.cluster == 2 ? 2 : 1;
+  const int64_t tiles_per = ((tiles_m + npan - 1) / npan + cl - 1) / cl * cl;
   gemm_status st = host_streams(2 + 2 * npan);
   if (st != GEMM_OK) return st;
   cudaEvent_t* ev = t_host.ev.data();
@@ -840,12 +863,12 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     a.beta = beta;
     a.C = t_host.C;
     a.tm0 = (int)t0;
-    a.tiles_m = (int)(t1 - t0);
+    a.tiles_m = (int)((t1 - t0 + cl - 1) / cl);   // in the plan's tile height
     a.num_tiles = a.tiles_m * a.tiles_n;
     a.num_units = a.num_tiles;   // split_k == 1
     a.group_m = std::max(1, std::min(a.group_m, a.tiles_m));
     TcLaunch l = p->launch;
-    l.grid = std::min(a.num_units, p->sms);
+    l.grid = cl == 2 ? 2 * std::min(a.num_units, p->max_pairs) : std::min(a.num_units, p->sms);
     if ((e = tc_gemm_launch(l, p->tmA, p->tmB, a, s)) || (e = cudaEventRecord(ev[2 + npan + i], s)) ||
         (e = cudaStreamWaitEvent(t_host.d2h, ev[2 + npan + i], 0)) ||
         (e = copy_rows(C + r0 * ldc, t_host.C + r0 * ldc, r1 - r0, N, ldc, cudaMemcpyDeviceToHost,
@@ -1020,6 +1043,8 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   if (config_id >= 0) {
     if (!config_get(mode, config_id, &c))
       return fail(GEMM_ERR_INVALID_ARG, "configuration %d out of range", config_id);
+    if (c.cluster == 2)
+      return fail(GEMM_ERR_INVALID_ARG, "configuration %d runs on CTA pairs: not for convolutions", config_id);
     if (!c.fused && !pack_shape)
       return fail(GEMM_ERR_INVALID_ARG,
                   "configuration %d is packed: the convolution runs packed only with C a multiple of 16",
@@ -1041,7 +1066,7 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
     const bool want_fused = !can_pack;
     for (int id = 0; id < config_count(mode); ++id) {
       config_get(mode, id, &c);
-      if ((c.fused != 0) == want_fused && c.block_n == d.block_n && c.split_k == d.split_k &&
+      if ((c.fused != 0) == want_fused && c.cluster == 1 && c.block_n == d.block_n && c.split_k == d.split_k &&
           c.kb == d.kb && c.group_m == d.group_m) {
         config_id = id;
         break;

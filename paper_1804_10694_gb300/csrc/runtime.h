@@ -42,6 +42,7 @@ struct gemm_plan_s {
   CUtensorMap tmA{}, tmB{};
   gb::TcArgs args{};
   gb::TcLaunch launch{};
+  int max_pairs = 0;                // CTA-pair plans: clusters resident at once
   // stage timing (gemm_plan_profile): four events per recorded execution,
   // at the start of packing, before and after the main kernel, at the end
   int prof_max = 0, prof_n = 0;

@@ -45,6 +45,8 @@
 #include "ptx.cuh"
 #include "scale.cuh"
 #include "split_arith.cuh"
+#include "epilogue.cuh"
+#include "tile_order.cuh"
 
 namespace gb {
 
@@ -111,25 +113,6 @@ struct TcCfg {
   static_assert(TMEM_COLS <= 512, "tensor memory budget");
 };
 
-// One unit of work of a CTA: an output tile (tm, tn) of problem `prob` and
-// the range [c0, c1) of 128-byte k-chunks it covers (all of K unless split).
-struct Work {
-  int prob, tm, tn, ks, c0, c1;
-};
-
-// Per-problem values the epilogue needs.
-struct EpiView {
-  int M, N;
-  float* C;
-  int64_t ldc;
-  float alpha, beta;
-  const unsigned* amaxA;
-  const unsigned* amaxB;
-  float* partial;
-  int split_k;
-  int amaxA_stride;         // 1: one exponent per 128-row block; 0: one for all of A
-};
-
 // Source of A for the fused-split variant.
 struct FusedA {
   const float* A;
@@ -144,16 +127,6 @@ struct FusedA {
   int box_c;                // channels per im2col box: 32 (128-byte rows) or 16 (64-byte rows)
   int N;                    // images (the packed variant's plane z starts at image z N)
 };
-
-__device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int group_m, int& tm, int& tn) {
-  const int group_tiles = group_m * tiles_n;
-  const int g = t / group_tiles;
-  const int first_m = g * group_m;
-  const int rows_in_group = min(tiles_m - first_m, group_m);
-  const int r = t % group_tiles;
-  tm = first_m + r % rows_in_group;
-  tn = r / rows_in_group;
-}
 
 // Scheduling policy of one gemm: units are (split, tile) pairs.
 struct SingleSched {
@@ -955,106 +928,8 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         for (int i = 0; i < EC; ++i) S[i] = 0.0f;
       }
 
-      // undo the block scaling, acc * 2^(eA + eB).  With e != 0 alpha is
-      // applied before the power of two, so that a result in range is not
-      // lost to an overflow of the unscaled sum (the power of two is exact).
-      float alpha = v.alpha;
-      float beta = v.beta;
-      if (v.split_k > 1 || e != 0) {
-#pragma unroll
-        for (int i = 0; i < EC; ++i) S[i] = e != 0 ? scale_pow2(alpha * S[i], e) : alpha * S[i];
-        alpha = 1.0f;
-      }
-      // destination: C, or this split's partial-sum plane (the reduction
-      // kernel adds beta * C)
-      float* dst = v.C;
-      int64_t ldd = v.ldc;
-      if (v.split_k > 1) {
-        dst = v.partial + static_cast<int64_t>(w.ks) * v.M * v.N;
-        ldd = v.N;
-        beta = 0.0f;
-      }
-      // Two store paths, chosen per 32-column chunk and uniform per warp.
-      // Aligned rows and a full chunk: each thread stores its own row with
-      // float4 accesses (C loads of the chunk issued first).  Otherwise
-      // (unaligned ldc, partial chunk or rows): the warp brings the 32x32
-      // chunk of C into a padded shared buffer by cp.async (lane = column,
-      // every row in flight at once; beta != 0), combines it with its sums
-      // there (lane = row), then walks the buffer one row at a time (lane =
-      // column), so that every global access of the warp covers 128
-      // contiguous bytes of one row whatever the alignment.
-      float* buf = epi_buf + (warp - 2) * 32 * Cfg::EPI_PITCH;
-      const int row0 = w.tm * 128 + q * 32;
-      const int nrows = min(32, v.M - row0);
-      const bool rows_vec = nrows == 32 && (ldd & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
-#pragma unroll
-      for (int j = 0; j < EC / 32; ++j) {
-        const int cb = col0 + j * 32;
-        if (nrows <= 0 || cb >= v.N) break;   // uniform across the warp
-        if (rows_vec && cb + 32 <= v.N) {
-          float4* c4 = reinterpret_cast<float4*>(dst + static_cast<int64_t>(row0 + lane) * ldd + cb);
-          float4 old[8];
-          if (beta != 0.0f) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) old[i] = c4[i];
-          }
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float* sv = &S[j * 32 + 4 * i];
-            float4 o;
-            if (beta != 0.0f) {
-              o.x = fmaf(alpha, sv[0], beta * old[i].x);
-              o.y = fmaf(alpha, sv[1], beta * old[i].y);
-              o.z = fmaf(alpha, sv[2], beta * old[i].z);
-              o.w = fmaf(alpha, sv[3], beta * old[i].w);
-            } else {
-              o.x = alpha * sv[0];
-              o.y = alpha * sv[1];
-              o.z = alpha * sv[2];
-              o.w = alpha * sv[3];
-            }
-            c4[i] = o;
-          }
-          continue;
-        }
-        const bool col_ok = cb + lane < v.N;
-        float* base = dst + static_cast<int64_t>(row0) * ldd + cb + lane;
-        if (beta != 0.0f) {
-          // the chunk of C comes into the buffer by 4-byte cp.async copies
-          // (lane = column, each row 128 contiguous bytes), all 32 rows in
-          // flight at once, then combines with the row-held sums in place
-          const float* src = base;
-          uint32_t sdst = smem_u32(&buf[lane]);
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const bool in = col_ok && r < nrows;
-            cp_async_4(sdst, in ? src : dst, in ? 4u : 0u);
-            src += ldd;
-            sdst += Cfg::EPI_PITCH * 4;
-          }
-          cp_async_commit();
-          cp_async_wait_all();
-          __syncwarp();
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float* bp = &buf[lane * Cfg::EPI_PITCH + i];
-            *bp = fmaf(alpha, S[j * 32 + i], beta * *bp);
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) buf[lane * Cfg::EPI_PITCH + i] = alpha * S[j * 32 + i];
-        }
-        __syncwarp();
-        {
-          float* out = base;
-#pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            if (col_ok && r < nrows) *out = buf[r * Cfg::EPI_PITCH + lane];
-            out += ldd;
-          }
-        }
-        __syncwarp();
-      }
+      epilogue_store<EC, Cfg::EPI_PITCH>(S, v, e, w.ks, w.tm * 128 + q * 32, col0, lane,
+                                         epi_buf + (warp - 2) * 32 * Cfg::EPI_PITCH);
     }
   } else if constexpr (FUSED) {
     // ------------------------------------------------------------ A (fused)
@@ -1436,6 +1311,10 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
 
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s) {
+  if (l.cluster == 2) {
+    if (l.fused || a.conv) return cudaErrorInvalidValue;   // pairs: packed gemm operands only
+    return tc_pair_launch(l.bn, l.prec, l.grid, tmA, tmB, a, s);
+  }
   if (l.prec == Prec::TF32) {
     if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, tmA, tmB, a, s);
     if (l.bn == 128) return launch_variant<128, true>(l.grid, l.fused, tmA, tmB, a, s);

@@ -10,7 +10,7 @@ namespace gb {
 
 // A candidate configuration as it behaves on one shape.
 struct EffConfig {
-  int bn, split_k, chunks_per_split, kb, group_m, fused;
+  int bn, split_k, chunks_per_split, kb, group_m, fused, cluster;
   int64_t tiles;
 };
 
@@ -35,7 +35,7 @@ int parse_timing_row(const char* line, TimingRow* r);
 // when no model is loaded).
 gemm_status costmodel_pick(gemm_mode mode, int64_t M, int64_t N, int64_t K, int* cid, float* ms);
 
-constexpr int kFeatures = 16;
+constexpr int kFeatures = 17;
 constexpr int kHidden = 64;
 // Input features of the cost model for a (shape, configuration) pair.
 void costmodel_features(gemm_mode mode, int64_t M, int64_t N, int64_t K, const gemm_config& c,

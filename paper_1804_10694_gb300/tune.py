@@ -62,8 +62,9 @@ def effective_key(mode, cid, M, N, K):
     sk = max(1, min(c["split_k"], chunks))
     per = -(-chunks // sk)
     sk = -(-chunks // per)
-    tiles_m = -(-M // 128)
-    return (c["block_n"], sk, min(c["kb"], per), max(1, min(c["group_m"], tiles_m)), c["fused"])
+    tiles_m = -(-M // (128 * c["cluster"]))   # a CTA pair's tile is 256 rows
+    return (c["block_n"], sk, min(c["kb"], per), max(1, min(c["group_m"], tiles_m)), c["fused"],
+            c["cluster"])
 
 
 def timed_choice(times, mode, cid, shape):

@@ -43,22 +43,24 @@ def test_config_table():
     seen = set()
     for i in range(n):
         c = pkg.config_get("bf16x3", i)
-        assert c["block_n"] in (64, 128)
+        assert c["block_n"] in ((64, 128) if c["cluster"] == 1 else (128, 256))
+        assert c["cluster"] in (1, 2) and not (c["cluster"] == 2 and c["fused"])
         assert c["split_k"] >= 1 and 1 <= c["kb"] <= 8 and c["group_m"] >= 1
         key = tuple(sorted(c.items()))
         assert key not in seen
         seen.add(key)
     with pytest.raises(pkg.GemmError):
         pkg.config_get("bf16x3", n)
-    # the six-product mode has the packed half of the table, two stages deep
-    assert pkg.config_count("bf16x6") == n // 2
-    for i in range(n // 2):
+    # the six-product mode has the packed two thirds of the table (single
+    # CTAs and pairs), two stages deep
+    assert pkg.config_count("bf16x6") == n * 2 // 3
+    for i in range(n * 2 // 3):
         c6, c3 = pkg.config_get("bf16x6", i), pkg.config_get("bf16x3", i)
         assert c6["fused"] == 0 and c6["stages"] == 2
         assert {k: v for k, v in c6.items() if k != "stages"} == \
             {k: v for k, v in c3.items() if k != "stages"}
     with pytest.raises(pkg.GemmError):
-        pkg.config_get("bf16x6", n // 2)
+        pkg.config_get("bf16x6", n * 2 // 3)
 
 
 def test_invalid_arguments_rejected_before_launch():

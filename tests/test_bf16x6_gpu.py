@@ -125,8 +125,9 @@ def test_integer_inputs_bit_exact(alpha, beta):
 
 # --------------------------------------------------- schedule invariance
 def test_every_configuration():
-    """All 72 BF16X6 configurations (packed ones only) at a shape with
-    several tiles and ragged edges; integer inputs give identical bits."""
+    """All 144 BF16X6 configurations (packed ones only: single CTAs and CTA
+    pairs) at a shape with several tiles and ragged edges; integer inputs
+    give identical bits."""
     M, N, K = 520, 390, 700
     A, B, C0 = W.uniform(M, K, 31), W.uniform(K, N, 32), W.uniform(M, N, 33)
     Ai, Bi, Ci = W.integers(M, K, 34), W.integers(K, N, 35), W.integers(M, N, 36)
@@ -134,7 +135,7 @@ def test_every_configuration():
     bound = fp32_bound(M, N, K, 1.5, A, B, 0.5, C0, ref)
     refi = oracle.gemm_f64(M, N, K, 1.5, Ai, Bi, 0.5, Ci).astype(np.float32)
     n = pkg.config_count(MODE)
-    assert n == 72
+    assert n == 144
     for cid in range(n):
         cfg = pkg.config_get(MODE, cid)
         assert cfg["fused"] == 0 and cfg["stages"] == 2
@@ -145,9 +146,9 @@ def test_every_configuration():
 
 def test_fused_configurations_are_rejected():
     with pytest.raises(pkg.GemmError):
-        pkg.Plan(256, 256, 256, mode=MODE, config_id=72)
+        pkg.Plan(256, 256, 256, mode=MODE, config_id=144)
     with pytest.raises(pkg.GemmError):
-        pkg.config_get(MODE, 72)
+        pkg.config_get(MODE, 144)
 
 
 # ------------------------------------------------------------- full size

@@ -56,7 +56,7 @@ def packed_ids(mode, **want):
     out = []
     for i in range(pkg.config_count(mode)):
         c = pkg.config_get(mode, i)
-        if not c["fused"] and all(c[k] == v for k, v in want.items()):
+        if not c["fused"] and c["cluster"] == 1 and all(c[k] == v for k, v in want.items()):
             out.append(i)
     return out
 

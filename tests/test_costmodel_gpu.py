@@ -16,7 +16,7 @@ from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
 
-F = 16   # the library's feature count (checked in the host-logic tests)
+F = 17   # the library's feature count (checked in the host-logic tests)
 H = 64
 
 
@@ -133,11 +133,12 @@ def _canonical(times, shape):
     if d in times:
         return d
     from oracle import features as ofeat
-    want = ofeat.effective(**{k: pkg.config_get("bf16x3", d)[k] for k in ("block_n", "split_k", "kb", "group_m")},
+    dc = pkg.config_get("bf16x3", d)
+    want = ofeat.effective(**{k: dc[k] for k in ("block_n", "split_k", "kb", "group_m", "cluster")},
                            M=M, N=N, K=K, tf32=False)
     for cid in times:
         c = pkg.config_get("bf16x3", cid)
-        e = ofeat.effective(c["block_n"], c["split_k"], c["kb"], c["group_m"], M, N, K, False)
-        if all(e[k] == want[k] for k in ("bn", "split_k", "kb", "group_m")) and not c["fused"]:
+        e = ofeat.effective(c["block_n"], c["split_k"], c["kb"], c["group_m"], M, N, K, False, c["cluster"])
+        if all(e[k] == want[k] for k in ("bn", "split_k", "kb", "group_m", "cluster")) and not c["fused"]:
             return cid
     raise AssertionError("heuristic configuration was not timed")

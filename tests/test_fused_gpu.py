@@ -29,7 +29,7 @@ def packed_twin(mode, cid):
     c = pkg.config_get(mode, cid)
     for i in range(pkg.config_count(mode)):
         d = pkg.config_get(mode, i)
-        if not d["fused"] and all(d[k] == c[k] for k in KEYS):
+        if not d["fused"] and d["cluster"] == 1 and all(d[k] == c[k] for k in KEYS):
             return i
     raise AssertionError(c)
 
@@ -60,7 +60,7 @@ def run_cfg(mode, cid, M, N, K, alpha, A, B, beta, C0, a_offset=0):
 @pytest.mark.parametrize("mode", ["bf16x3", "tf32x3"])
 def test_fused_table_mirrors_packed(mode):
     ids = fused_ids(mode)
-    assert len(ids) * 2 == pkg.config_count(mode)
+    assert len(ids) * 3 == pkg.config_count(mode)   # single-CTA packed, pairs, fused
     assert len({packed_twin(mode, i) for i in ids}) == len(ids)
 
 

@@ -78,7 +78,7 @@ def test_grouped_equals_single_problem_plans(block_n, kb):
     ncfg = pkg.config_count("bf16x3")
     cid = next(i for i in range(ncfg) if pkg.config_get("bf16x3", i) ==
                {"block_n": block_n, "stages": 4 if block_n == 64 else 3, "split_k": 1, "kb": kb,
-                "group_m": 16, "fused": 0})
+                "group_m": 16, "fused": 0, "cluster": 1})
     for (M, N, K), (A, B, C), out in zip(shapes, probs, outs):
         dA, dB, dC = (torch.from_numpy(x).cuda() for x in (A, B, C))
         single = pkg.Plan(M, N, K, mode="bf16x3", config_id=cid)

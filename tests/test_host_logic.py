@@ -12,6 +12,8 @@ from oracle import features as ofeat
 import workloads as W
 
 
+F = 17   # cost-model features (the oracle's restatement lists them)
+
 SHAPES = [(8192, 8192, 8192), (1060, 1060, 1060), (50176, 64, 576), (12544, 128, 1152),
           (3136, 256, 2304), (33, 17, 5), (1, 1, 1), (129, 4099, 63), (300, 70, 20000)]
 
@@ -19,7 +21,7 @@ SHAPES = [(8192, 8192, 8192), (1060, 1060, 1060), (50176, 64, 576), (12544, 128,
 @pytest.mark.parametrize("mode,tf32", [("bf16x3", False), ("tf32x3", True), ("bf16x6", False)])
 def test_features_match_oracle_restatement(mode, tf32):
     n = pkg.config_count(mode)
-    assert pkg.costmodel_feature_count() == 16
+    assert pkg.costmodel_feature_count() == F
     for (M, N, K) in SHAPES:
         for cid in range(0, n, 5):
             cfg = pkg.config_get(mode, cid)
@@ -31,7 +33,7 @@ def test_features_match_oracle_restatement(mode, tf32):
 
 def test_features_reject_bad_arguments():
     lib = pkg.load()
-    out = np.zeros(16, np.float32)
+    out = np.zeros(F, np.float32)
     assert lib.gemm_costmodel_features(0, 4, 4, 2, 0, 152, out.ctypes.data) == 1
     assert lib.gemm_costmodel_features(4, 4, 4, 1, 0, 152, out.ctypes.data) == 1   # SIMT
     assert lib.gemm_costmodel_features(4, 4, 4, 2, 10 ** 6, 152, out.ctypes.data) == 1
@@ -41,25 +43,25 @@ def test_costmodel_load_rejects_missing_and_corrupt_files(tmp_path):
     lib = pkg.load()
     assert lib.gemm_costmodel_load(str(tmp_path / "missing.txt").encode()) == 7
     bad = tmp_path / "bad.txt"
-    bad.write_text("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params 5\n")
+    bad.write_text("gb300-gemm-costmodel 1\nfeatures %d hidden 64 params 5\n" % F)
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
     assert b"malformed" in lib.gemm_last_error()
     bad.write_text("not a model\n")
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
     # truncated theta
-    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
-    txt = ("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params %d\nmean %s\nstd %s\n"
-           "target 0 1\ntheta %s\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16),
+    P = 64 * F + 64 + 64 * 64 + 64 + 64 + 1
+    txt = ("gb300-gemm-costmodel 1\nfeatures %d hidden 64 params %d\nmean %s\nstd %s\n"
+           "target 0 1\ntheta %s\n" % (F, P, " ".join(["0"] * F), " ".join(["1"] * F),
                                        " ".join(["0.5"] * (P - 3))))
     bad.write_text(txt)
     assert lib.gemm_costmodel_load(str(bad).encode()) == 7
 
 
 def test_costmodel_load_accepts_well_formed_file(tmp_path):
-    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
+    P = 64 * F + 64 + 64 * 64 + 64 + 64 + 1
     good = tmp_path / "good.txt"
-    good.write_text("gb300-gemm-costmodel 1\nfeatures 16 hidden 64 params %d\nmean %s\nstd %s\n"
-                    "target -1.5 2\ntheta %s\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16),
+    good.write_text("gb300-gemm-costmodel 1\nfeatures %d hidden 64 params %d\nmean %s\nstd %s\n"
+                    "target -1.5 2\ntheta %s\n" % (F, P, " ".join(["0"] * F), " ".join(["1"] * F),
                                                    " ".join(["0.01"] * P)))
     assert pkg.load().gemm_costmodel_load(str(good).encode()) == 0
 
@@ -153,9 +155,9 @@ def test_training_shapes_bounded():
 def test_costmodel_ensemble_file_format(tmp_path):
     """Version 2 files hold `members` networks (one theta line each); a
     missing member or a bad member count is rejected."""
-    P = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1
-    head = ("gb300-gemm-costmodel 2\nfeatures 16 hidden 64 params %d members %%d\nmean %s\nstd %s\n"
-            "target -1.5 2\n" % (P, " ".join(["0"] * 16), " ".join(["1"] * 16)))
+    P = 64 * F + 64 + 64 * 64 + 64 + 64 + 1
+    head = ("gb300-gemm-costmodel 2\nfeatures %d hidden 64 params %d members %%d\nmean %s\nstd %s\n"
+            "target -1.5 2\n" % (F, P, " ".join(["0"] * F), " ".join(["1"] * F)))
     theta = "theta %s\n" % " ".join(["0.01"] * P)
     lib = pkg.load()
     f = tmp_path / "m.txt"

@@ -18,11 +18,11 @@ import pytest
 from oracle import features as F
 
 NAMES = ["log2M", "log2N", "log2K", "bn/128", "log2sk", "kb/8", "log2group", "log2tiles",
-         "log2(1+waves)", "fill", "padded", "log2ai", "log2per", "tf32", "fused", "x6"]
+         "log2(1+waves)", "fill", "padded", "log2ai", "log2per", "tf32", "fused", "x6", "pair"]
 
 
-def cfg(bn, sk, kb, g, fused=0):
-    return {"block_n": bn, "split_k": sk, "kb": kb, "group_m": g, "fused": fused}
+def cfg(bn, sk, kb, g, fused=0, cluster=1):
+    return {"block_n": bn, "split_k": sk, "kb": kb, "group_m": g, "fused": fused, "cluster": cluster}
 
 
 CASES = [
@@ -35,7 +35,7 @@ CASES = [
     #   intensity: 2 n^3 / (4 (n^2 + n^2 + 2 n^2)) = n / 8 = 1024, log2 = 10
     #   group: min(16, 64) = 16 (log2 = 4); fold: min(4, 128) = 4, /8 = 0.5
     ((8192, 8192, 8192), cfg(128, 1, 4, 16), False, 152, False,
-     [13, 13, 13, 1.0, 0, 0.5, 4, 12, 4.804640537, 0.947368421, 0, 10, 7, 0, 0, 0]),
+     [13, 13, 13, 1.0, 0, 0.5, 4, 12, 4.804640537, 0.947368421, 0, 10, 7, 0, 0, 0, 0]),
     # 1060^3 (the paper's sgemm size), BN 64, bf16, 152 SMs.
     #   k-chunks: ceil(1060/64) = 17 (16 x 64 = 1024 < 1060), per = 17, log2 = 4.0874628
     #   tiles: ceil(1060/128) = 9 rows x ceil(1060/64) = 17 columns = 153, log2 = 7.2573878
@@ -44,7 +44,7 @@ CASES = [
     #   intensity: 1060/8 = 132.5, log2 = 7.0498485; group: min(16, 9) = 9, log2 = 3.1699250
     ((1060, 1060, 1060), cfg(64, 1, 4, 16), False, 152, False,
      [10.04984855, 10.04984855, 10.04984855, 0.5, 0, 0.5, 3.169925001, 7.257387843,
-      1.004737919, 0.006578947, 0.144966220, 7.049848549, 4.087462841, 0, 0, 0]),
+      1.004737919, 0.006578947, 0.144966220, 7.049848549, 4.087462841, 0, 0, 0, 0]),
     # tf32, 256 x 256 x 96, BN 128, split 8 requested, fold 8, group 1.
     #   k-chunks of 32 tf32 elements: 96/32 = 3 (bf16 would be 2 chunks of 64,
     #   padding K to 128); split: min(8, 3) = 3, per = 1, split = ceil(3/1) = 3,
@@ -54,7 +54,7 @@ CASES = [
     #   intensity: 2*256*256*96 / (4 (256*96 + 96*256 + 2*256*256)) = 17.4545, log2 = 4.1255309
     ((256, 256, 96), cfg(128, 8, 8, 1), True, 152, False,
      [8, 8, 6.584962501, 1.0, 1.584962501, 0.125, 0, 2, 0.109624491, 0.078947368, 0,
-      4.125530882, 0, 1, 0, 0]),
+      4.125530882, 0, 1, 0, 0, 0]),
     # split-K re-derived after rounding: 512 x 512 x 640 bf16, split 6 requested, fold 8, group 16.
     #   k-chunks: 640/64 = 10; per = ceil(10/6) = 2; split = ceil(10/2) = 5 (not 6), log2 5 = 2.3219281
     #   fold: min(8, 2) = 2, /8 = 0.25; group: min(16, 4) = 4, log2 = 2
@@ -63,19 +63,35 @@ CASES = [
     #   fused configuration: feature 1
     ((512, 512, 640), cfg(128, 6, 8, 16, fused=1), False, 152, False,
      [9, 9, 9.321928095, 1.0, 2.321928095, 0.25, 2, 4, 0.610053482, 0.526315789, 0,
-      6.152003093, 1, 0, 1, 0]),
+      6.152003093, 1, 0, 1, 0, 0]),
     # a last wave that is exactly full: 2432 x 1024 x 512 bf16, BN 128 on 152 SMs.
     #   tiles: (2432/128 = 19) x (1024/128 = 8) = 152 = one full wave: log2(1 + 1) = 1, fill 1
     #   k-chunks 512/64 = 8, per 8 (log2 3); group min(16, 19) = 16
     #   intensity: 2*2432*1024*512 / (4 (2432*512 + 512*1024 + 2*2432*1024)), log2 = 6.5614270
     #   six-product mode: feature 1
     ((2432, 1024, 512), cfg(128, 1, 4, 16), False, 152, True,
-     [11.24792751, 10, 9, 1.0, 0, 0.5, 4, 7.247927513, 1, 1.0, 0, 6.561426986, 3, 0, 0, 1]),
+     [11.24792751, 10, 9, 1.0, 0, 0.5, 4, 7.247927513, 1, 1.0, 0, 6.561426986, 3, 0, 0, 1, 0]),
     # the same shape on 148 SMs: 152 units = one wave and 4 units, fill 4/148 = 0.0270270,
     #   log2(1 + 152/148) = 1.0193653
     ((2432, 1024, 512), cfg(128, 1, 4, 16), False, 148, False,
      [11.24792751, 10, 9, 1.0, 0, 0.5, 4, 7.247927513, 1.019365325, 0.027027027, 0,
-      6.561426986, 3, 0, 0, 0]),
+      6.561426986, 3, 0, 0, 0, 0]),
+    # a CTA pair (cluster 2) runs 256 x BN tiles, one unit per pair of SMs:
+    # 8192^3 at BN 256 on 152 SMs = 76 pairs.
+    #   tiles: (8192/256) x (8192/256) = 32 x 32 = 1024 (log2 10); bn/128 = 2
+    #   waves: 1024 / 76 = 13.47..; log2(1 + 13.47..) = 3.8553603
+    #   last wave: 1024 - 13*76 = 36 units, fill 36/76 = 0.4736842
+    #   group min(16, 32) = 16; k-chunks 128 (log2 7); no padding; intensity 1024 (log2 10)
+    ((8192, 8192, 8192), cfg(256, 1, 4, 16, cluster=2), False, 152, False,
+     [13, 13, 13, 2.0, 0, 0.5, 4, 10, 3.855360295, 0.473684211, 0, 10, 7, 0, 0, 0, 1]),
+    # 1060^3 on pairs at BN 128: row tiles of 256: ceil(1060/256) = 5 (4 x 256 = 1024 < 1060),
+    #   column tiles ceil(1060/128) = 9: 45 tiles (log2 5.4918531) on 76 pairs:
+    #   log2(1 + 45/76) = 0.6709357, fill 45/76 = 0.5921053
+    #   padding: (5*256)(9*128)(17*64) / 1060^3 - 1 = 1280*1152*1088/1191016000 - 1 = 0.3470191
+    #   group: min(16, 5) = 5 (log2 2.3219281); k-chunks 17 (log2 4.0874628)
+    ((1060, 1060, 1060), cfg(128, 1, 4, 16, cluster=2), False, 152, False,
+     [10.04984855, 10.04984855, 10.04984855, 1.0, 0, 0.5, 2.321928095, 5.491853096,
+      0.670935724, 0.592105263, 0.347019083, 7.049848549, 4.087462841, 0, 0, 0, 1]),
 ]
 
 
@@ -83,7 +99,7 @@ CASES = [
 def test_features_match_hand_derived_values(shape, c, tf32, sms, x6, want):
     M, N, K = shape
     got = F.features(M, N, K, c, tf32, sms, x6=x6)
-    assert len(got) == len(want) == 16
+    assert len(got) == len(want) == 17
     for name, g, w in zip(NAMES, got, want):
         assert math.isclose(g, w, rel_tol=1e-8, abs_tol=1e-8), (name, g, w)
 
