@@ -37,12 +37,26 @@ ALPHA, BETA = 1.5, 0.5
 METRIC = "sgemm TFLOP/s at <=1e-5 rel err vs FP64 (split-BF16 TC vs plain FP32), % of peak"
 WORKLOAD = ("sgemm M=N=K=8192 row-major, alpha=1.5 beta=0.5, A,B,C iid uniform[-1,1] "
             "(top size of the square sweep), split-precision BF16x3 tcgen05 path")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "tc_gemm_bf16x3_8192_traffic.json")
+# DRAM traffic per launch of the 8192^3 gemm kernel, one file per kernel
+# variant, each from one ncu capture of the source it names
+TRAFFIC_FILES = [os.path.join(ROOT, "profiles", f) for f in
+                 ("tc_gemm_pair_bf16x3_8192_traffic.json", "tc_gemm_bf16x3_8192_traffic.json")]
 # TF32 dense peak and FP32 CUDA-core ceiling measured on a GB300 by
 # `bench.py --measure-peaks --peaks-out FILE` (the driver's peak file holds
 # the HBM and bf16 figures only)
 EXTRA_PEAKS_FILE = os.path.join(ROOT, "profiles", "peaks_tf32_fp32simt_gb300.json")
-TC_SOURCE = os.path.join(ROOT, "paper_1804_10694_gb300", "csrc", "tc_gemm.cu")
+CSRC = os.path.join(ROOT, "paper_1804_10694_gb300", "csrc")
+
+
+def kernel_of(mode: str, cfg: dict) -> tuple[str, str]:
+    """Name of the gemm kernel a configuration launches, and its source file."""
+    prec = "tf32" if mode == "tf32x3" else "bf16"
+    planes = 3 if mode == "bf16x6" else 2
+    if cfg.get("cluster", 1) == 2:
+        return (f"tc_gemm_pair_kernel<{cfg['block_n']},{prec},{planes} planes>",
+                os.path.join(CSRC, "tc_pair.cu"))
+    return (f"tc_gemm_kernel<{cfg['block_n']},{prec},{planes} planes>",
+            os.path.join(CSRC, "tc_gemm.cu"))
 
 
 def parse_args():
@@ -271,16 +285,17 @@ def source_digest(path: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def traffic_per_launch():
-    """DRAM bytes per launch of the gemm kernel from the committed ncu summary,
-    or None if missing or taken on a different kernel source."""
-    if not os.path.exists(TRAFFIC_FILE):
-        return None
-    with open(TRAFFIC_FILE) as f:
-        d = json.load(f)
-    if d.get("source_sha256_16") != source_digest(TC_SOURCE):
-        return None
-    return d.get("dram_bytes_per_launch_full_size")
+def traffic_per_launch(kernel: str, source: str):
+    """DRAM bytes per launch of the gemm kernel from the committed ncu summary
+    of that kernel, or None if missing or taken on a different source."""
+    for path in TRAFFIC_FILES:
+        if not os.path.exists(path):
+            continue
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_key") == kernel and d.get("source_sha256_16") == source_digest(source):
+            return d.get("dram_bytes_per_launch_full_size")
+    return None
 
 
 def _median_ms(fn, reps, stream):
@@ -794,12 +809,11 @@ def run_ours(args, world, rank, local):
             bf16_peak = pk.get("bf16_tflops_sustained", pk["bf16_tflops"]) if capped else pk["bf16_tflops"]
             peak = bf16_peak * (1.1 / 2.25 if args.mode == "tf32x3" else 1.0)
             tf32_kind = "bf16 x 1.1/2.25 (nominal tf32/bf16 ratio)"
-        traffic = traffic_per_launch() if args.mode == "bf16x3" else None
+        kname, ksrc = kernel_of(args.mode, pkg.config_get(args.mode, info["config_id"]))
+        traffic = traffic_per_launch(kname, ksrc)
         roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": peak,
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                    "kernel": {"bf16x3": "tc_gemm_kernel<128,bf16,2 planes>",
-                               "tf32x3": "tc_gemm_kernel<128,tf32,2 planes>",
-                               "bf16x6": "tc_gemm_kernel<128,bf16,3 planes>"}[args.mode],
+                    "kernel": kname,
                     "peak_kind": (tf32_kind if args.mode == "tf32x3" else f"{pk_kind} bf16 dense") + (
                         " sustained (sw_power_cap during the loop)" if capped else " burst"),
                     "frac_of_burst": round(achieved / burst, 4),

@@ -194,6 +194,18 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
     if (tiles * c >= (int64_t)sms * 9 / 10) break;
   }
   if (tiles >= (int64_t)sms) sk = 1;
+  if (sk == 1 && bn == 128 && sms >= 2) {
+    // A CTA pair's 256 x 256 tile moves half the operand bytes per product
+    // of four 128 x 128 tiles: at 8192^3 on GB300 a pair unit took 2 x 0.875
+    // of a single-CTA unit's time for twice its products per SM.  The
+    // coarser tiles pay when they do not leave pairs idle: compare the waves
+    // of units each choice needs (units on sms SMs, or on sms / 2 pairs),
+    // weighted by the time of one unit.
+    const int64_t tiles2 = ((M + 255) / 256) * ((N + 255) / 256);
+    const double waves1 = (double)((tiles + sms - 1) / sms);
+    const double waves2 = (double)((tiles2 + sms / 2 - 1) / (sms / 2));
+    if (waves2 * 2.0 * 0.875 < waves1) return find_config(256, 1, 4, 16, 2);
+  }
   return find_config(bn, sk, 4, 16);
 }
 

@@ -113,3 +113,27 @@ def test_pair_large_square_whole_matrix():
         got = run_gemm("bf16x3", n, n, n, 1.5, A, B, 0.5, C0, config_id=cid)
         assert oracle.rel_frob(got, ref) <= TOL, bn
     pkg.device_error()
+
+
+def test_default_picks_pairs_and_host_panel_pipeline_runs_them():
+    """4096 x 2048 x 512: the default heuristic takes the 256 x 256 pair tile
+    (4 waves of single-CTA units against 2 of pair units).  Through
+    gemm_f32_host with page-locked buffers the row-panel pipeline runs it:
+    panels of an even number of 128-row tiles, each launch starting at an
+    even 128-row block; unaligned ldc, padding untouched."""
+    import torch
+    M, N, K = 4096, 2048, 512
+    cid = pkg.config_default("bf16x3", M, N, K)
+    c = pkg.config_get("bf16x3", cid)
+    assert c["cluster"] == 2 and c["block_n"] == 256, c
+    A, B, C0 = W.uniform(M, K, 651, ld=K + 4), W.uniform(K, N, 652), W.uniform(M, N, 653, ld=N + 2)
+    ref = oracle.gemm_f64(M, N, K, 1.5, A, B, 0.5, C0)
+    lib = pkg.load()
+    hA, hB = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    hC = torch.from_numpy(C0.copy()).pin_memory()
+    st = lib.gemm_f32_host(M, N, K, 1.5, hA.data_ptr(), K + 4, hB.data_ptr(), N, 0.5, hC.data_ptr(),
+                           N + 2, pkg.MODES["bf16x3"], None)
+    assert st == 0, lib.gemm_last_error()
+    got = hC.numpy()
+    assert oracle.rel_frob(got, ref) <= TOL
+    check_padding_untouched(C0, got, N)
