@@ -37,13 +37,14 @@ def _rank(rank: int, world: int, port: int, out_dir: str):
     w, r, local = bench.dist_setup(args, backend="gloo")
     bench.barrier(w)
     slowest = bench.max_over_ranks(1.0 + rank, w)          # the ranks' own step times
+    total = bench.sum_over_ranks(10.0 * (1 + rank), w)      # the ranks' copied bytes
     value = bench.job_throughput(w, 2.0e12, slowest)        # 2 TFLOP of work on every rank
     reference = bench.run_reference(args, w, r) if r != 0 else "rank 0 not run here"
     bench.barrier(w)
     import torch.distributed as dist
     dist.destroy_process_group()
     with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
-        json.dump({"world": w, "rank": r, "slowest": slowest, "value": value,
+        json.dump({"world": w, "rank": r, "slowest": slowest, "value": value, "total": total,
                    "reference": reference}, f)
 
 
@@ -55,5 +56,6 @@ def test_two_gloo_ranks_take_the_max_and_aggregate(tmp_path):
     for r, res in enumerate(results):
         assert res["world"] == world and res["rank"] == r
         assert res["slowest"] == 2.0                  # max over ranks of 1.0 and 2.0
+        assert res["total"] == 30.0                   # sum over ranks of 10 and 20
         assert res["value"] == pytest.approx(2.0)     # 2 ranks x 2 TFLOP / 2 s
     assert results[1]["reference"] is None            # non-zero ranks exit without work
