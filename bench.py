@@ -93,6 +93,9 @@ def parse_args():
     p.add_argument("--table", action="store_true",
                    help="per-configuration results table (every config: median of 30 timed runs, "
                         "error of the whole result against the FP64 oracle, rooflines)")
+    p.add_argument("--table-sections", default="d1,d2,d3,d4,d5",
+                   help="sections of --table to run (comma-separated; d3 also times the "
+                        "compensated epilogue of every tensor-core mode)")
     return p.parse_args()
 
 
@@ -630,10 +633,11 @@ def run_table(args, local):
         return ms, flops / (ms * 1e-3) / 1e12
 
     def entry(cfg, mode, ms, tfl, err, nbytes, extra=None):
+        base = mode.split("+")[0]   # "bf16x3+comp": the compensated epilogue of bf16x3
         e = {"config": cfg, "mode": mode, "ms": round(ms, 4), "tflops": round(tfl, 2),
-             "pct_fp32eq_roofline": round(100 * tfl / fp32eq[mode], 1) if mode in fp32eq else None,
-             "pct_tensor_roofline": (round(100 * raw[mode][0] * tfl / raw[mode][1], 1)
-                                     if mode in raw else None),
+             "pct_fp32eq_roofline": round(100 * tfl / fp32eq[base], 1) if base in fp32eq else None,
+             "pct_tensor_roofline": (round(100 * raw[base][0] * tfl / raw[base][1], 1)
+                                     if base in raw else None),
              "hbm_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
              "rel_frob": err}
         if extra:
@@ -643,7 +647,7 @@ def run_table(args, local):
     def run_plan(M, N, K, mode, A, B, C0, alpha, beta, ref):
         dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
         dC = torch.from_numpy(C0).cuda()
-        plan = pkg.Plan(M, N, K, mode=mode)
+        plan = pkg.Plan(M, N, K, mode=mode.split("+")[0], compensated=mode.endswith("+comp"))
         plan.execute(dA, dB, dC, alpha, beta)
         torch.cuda.synchronize()
         got = dC.cpu().numpy()
@@ -653,13 +657,14 @@ def run_table(args, local):
         return got, err, ms, tfl
 
     rows = []
+    sections = set(args.table_sections.split(","))
     # d1: 512^3, alpha 1.5, beta 0.5, SIMT against the oracle on 1 and all cores
     sa, sb, sc = W.seeds(W.CONFIG_SMALL)
     n = 512
     A, B, C0 = W.uniform(n, n, sa), W.uniform(n, n, sb), W.uniform(n, n, sc)
     cores = oracle.num_threads()
     cpu = {}
-    for th in (1, cores):
+    for th in ((1, cores) if "d1" in sections else ()):
         oracle.set_num_threads(th)
         ts = []
         for _ in range(3):
@@ -668,13 +673,13 @@ def run_table(args, local):
             ts.append(time.perf_counter() - t0)
         cpu[th] = statistics.median(ts)
     oracle.set_num_threads(cores)
-    for mode in modes:
+    for mode in (modes if "d1" in sections else ()):
         _, err, ms, tfl = run_plan(n, n, n, mode, A, B, C0, 1.5, 0.5, ref)
         rows.append(entry("d1 512^3 a=1.5 b=0.5", mode, ms, tfl, err, 4.0 * 4 * n * n,
                           {"oracle_cpu_s_1_thread": round(cpu[1], 4),
                            f"oracle_cpu_s_{cores}_threads": round(cpu[cores], 4)}))
     # d2: square sweep, both (alpha, beta) pairs
-    for n in W.SQUARE_SWEEP:
+    for n in (W.SQUARE_SWEEP if "d2" in sections else ()):
         sa, sb, sc = W.seeds(W.CONFIG_SWEEP)
         A, B, C0 = W.uniform(n, n, sa + n), W.uniform(n, n, sb + n), W.uniform(n, n, sc + n)
         t0 = time.perf_counter()
@@ -691,27 +696,28 @@ def run_table(args, local):
     # d3: 8192^3 wide range (both pairs) and integers (bit-exact count)
     n = 8192
     sa, sb, sc = W.seeds(W.CONFIG_WIDE)
-    for gen in ("wide", "int"):
+    comp_modes = tuple(m + "+comp" for m in modes if m != "simt")
+    for gen in (("wide", "int") if "d3" in sections else ()):
         f = W.wide_range if gen == "wide" else W.integers
         A, B, C0 = f(n, n, sa + n), f(n, n, sb + n), f(n, n, sc + n)
         P = oracle.product_f64(n, n, n, A, B)
         for alpha, beta in W.ALPHA_BETA:
             ref = oracle.axpby_f64(alpha, P, beta, C0)
-            for mode in modes:
+            for mode in modes + comp_modes:
                 got, err, ms, tfl = run_plan(n, n, n, mode, A, B, C0, alpha, beta, ref)
                 extra = {"mismatches": int(np.count_nonzero(got != ref.astype(np.float32)))} if gen == "int" else None
                 rows.append(entry(f"d3 8192^3 {gen} a={alpha} b={beta}", mode, ms, tfl, err,
                                   4.0 * n * n * (3 + (1 if beta != 0 else 0)), extra))
         del P
     # d4: grouped, 512 problems, alpha = beta = 1, graph replay
-    shapes = W.grouped_shapes()
+    shapes = W.grouped_shapes() if "d4" in sections else []
     As = [torch.empty(m, k, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
     Bs = [torch.empty(k, n_, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
     Cs = [torch.empty(m, n_, device="cuda").uniform_(-1, 1) for m, n_, k in shapes]
     ones = [1.0] * len(shapes)
     gflops = sum(2.0 * m * n_ * k for m, n_, k in shapes)
     gbytes = sum(4.0 * (m * k + k * n_ + 2 * m * n_) for m, n_, k in shapes)
-    for mode in ("bf16x3", "tf32x3", "bf16x6"):
+    for mode in (("bf16x3", "tf32x3", "bf16x6") if shapes else ()):
         gp = pkg.GroupedPlan(shapes, mode=mode)
         gp.prepare(As, Bs, Cs, ones, ones)
         ms, tfl = timed(gp.execute, gflops)
@@ -725,7 +731,7 @@ def run_table(args, local):
             pkg.costmodel_load(args.costmodel)
         except pkg.GemmError:
             pass   # the model's pick falls back to the heuristic
-    for (M, N, K) in W.CONV_SHAPES:
+    for (M, N, K) in (W.CONV_SHAPES if "d5" in sections else ()):
         sa, sb, _ = W.seeds(W.CONFIG_CONV)
         A, B = W.uniform(M, K, sa), W.uniform(K, N, sb)
         C0 = np.zeros((M, N), np.float32)

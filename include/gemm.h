@@ -75,6 +75,13 @@ typedef enum {
   GEMM_SELECT_EXHAUSTIVE = 3  /* time every candidate now, keep the fastest */
 } gemm_select;
 
+/* Plan options (bit flags of gemm_plan_create_opts). */
+typedef enum {
+  GEMM_OPT_NONE = 0,
+  GEMM_OPT_COMPENSATED = 1   /* compensated epilogue: the per-fold partial sums are
+                              * added with their rounding errors kept (TwoSum) */
+} gemm_option;
+
 typedef struct gemm_plan_s* gemm_plan_t;
 typedef struct gemm_grouped_plan_s* gemm_grouped_plan_t;
 
@@ -157,6 +164,32 @@ gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64
  * gemm_config_count / gemm_config_get). */
 gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                                     int64_t ldc, gemm_mode mode, int config_id, gemm_plan_t* out);
+
+/* As gemm_plan_create (config_id < 0: chosen by `sel`) or
+ * gemm_plan_create_config (config_id >= 0), with options.
+ * GEMM_OPT_COMPENSATED, the higher-accuracy epilogue of the tensor-core
+ * modes: the tensor core accumulates the products of a fold (kb k-chunks) in
+ * TMEM, an FP32 sum whose rounding is not to nearest and whose error grows
+ * with the fold's length, and the epilogue adds the per-fold partial sums
+ * into FP32 registers.  With this option the fold is one k-chunk (the
+ * configuration's kb is not used), and every addition of a fold into the
+ * registers is an error-free transformation (Knuth's TwoSum: the rounded sum
+ * and its exact rounding error); the errors are summed in a second register
+ * per output and added back once, so that the sum over the folds carries
+ * about one rounding instead of one per fold.  What remains is the error
+ * of the split (the operands' low parts, the dropped products) and of the
+ * tensor core's sum within one k-chunk.  The option runs the single-CTA
+ * packed kernel with 128 x 64 tiles, whose epilogue threads hold each
+ * output's sum and error in registers: any other configuration (wider,
+ * fused-split or CTA-pair) runs as the 128 x 64 packed tile with the same
+ * split-K and raster group, and gemm_plan_info reports that configuration.
+ * It has no effect in F32_SIMT mode and is not available for convolutions.  Errors:
+ * as gemm_plan_create; INVALID_ARG for unknown option bits.  The paper has
+ * no counterpart (it computes in FP32 throughout); this is the
+ * higher-accuracy variant of the split-precision method. */
+gemm_status gemm_plan_create_opts(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                                  int64_t ldc, gemm_mode mode, gemm_select sel, int config_id,
+                                  unsigned opts, gemm_plan_t* out);
 
 /* As gemm_plan_create, with the transposes of gemm_f32_t. */
 gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int64_t K, int64_t lda,
@@ -310,7 +343,7 @@ gemm_status gemm_select_config(int64_t M, int64_t N, int64_t K, int64_t lda, int
 
 /* ------------------------------------------------------------ cost model -- */
 
-/* Number of input features of the cost model (16).  The cost model, its
+/* Number of input features of the cost model (17).  The cost model, its
  * features and its training are this library's (the learned replacement of
  * the paper's tile-size search, Section VI-A); they have no paper passage of
  * their own. */
@@ -321,7 +354,8 @@ int gemm_costmodel_feature_count(void);
  * log2 split-K; fold length / 8; log2 raster group; log2 tiles; log2(1 +
  * waves); fill of the last wave; padded-work fraction; log2 arithmetic
  * intensity; log2 k-chunks per split; 1 for TF32X3; 1 for a fused
- * configuration; 1 for BF16X6. */
+ * configuration; 1 for BF16X6; 1 for a CTA-pair configuration (a 256-row
+ * tile on two SMs, whose waves count SM pairs). */
 gemm_status gemm_costmodel_features(int64_t M, int64_t N, int64_t K, gemm_mode mode, int config_id,
                                     int sms, float* out);
 

@@ -113,7 +113,8 @@ class Plan:
     """A gemm plan for one shape (owns its workspace); see gemm_plan_create."""
 
     def __init__(self, M, N, K, lda=None, ldb=None, ldc=None, mode="auto", select="default",
-                 config_id: int | None = None, trans_a: bool = False, trans_b: bool = False):
+                 config_id: int | None = None, trans_a: bool = False, trans_b: bool = False,
+                 compensated: bool = False):
         lib = load()
         self._lib = lib
         self.M, self.N, self.K = M, N, K
@@ -122,7 +123,13 @@ class Plan:
         self.ldb = ldb if ldb is not None else max(K if trans_b else N, 1)
         self.ldc = ldc if ldc is not None else max(N, 1)
         h = ctypes.c_void_p()
-        if trans_a or trans_b:
+        if compensated:
+            if trans_a or trans_b:
+                raise ValueError("the compensated epilogue is offered for untransposed plans")
+            check(lib.gemm_plan_create_opts(M, N, K, self.lda, self.ldb, self.ldc, _mode(mode),
+                                            _select(select), -1 if config_id is None else int(config_id),
+                                            1, ctypes.byref(h)))
+        elif trans_a or trans_b:
             if config_id is not None:
                 raise ValueError("transposed plans choose their configuration by `select`")
             check(lib.gemm_plan_create_t(int(trans_a), int(trans_b), M, N, K, self.lda, self.ldb,

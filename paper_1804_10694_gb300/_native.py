@@ -36,6 +36,8 @@ SIGNATURES = {
     "gemm_f32_host": (i32, [i64, i64, i64, f32, vp, i64, vp, i64, f32, vp, i64, i32, vp]),
     "gemm_plan_create": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
     "gemm_plan_create_config": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
+    "gemm_plan_create_opts": (i32, [i64, i64, i64, i64, i64, i64, i32, i32, i32, ctypes.c_uint,
+                                    ctypes.POINTER(vp)]),
     "gemm_conv_plan_create": (i32, [i64, i64, i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(vp)]),
     "gemm_conv3x3_plan_create": (i32, [i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),
     "gemm_plan_create_t": (i32, [i32, i32, i64, i64, i64, i64, i64, i64, i32, i32, ctypes.POINTER(vp)]),

@@ -58,6 +58,11 @@ struct TcArgs {
   int conv, conv_N, conv_H, conv_W, conv_C, conv_R, conv_S;
   int conv_box_c;          // fused variant: channels per TMA im2col box (32, or 16), when vecA
   int* unit_ctr;           // packed convolution: units taken so far (zero before the launch)
+  // per-execution state (block maxima, pack counters, unit counter) that the
+  // last CTA of the launch clears, followed by its done counter; 0 words:
+  // nothing to clear (the caller clears the state itself)
+  unsigned* state;
+  int state_words;
 };
 
 struct TcLaunch {
@@ -66,6 +71,7 @@ struct TcLaunch {
   int grid;
   bool fused;      // A split inside the gemm kernel (only B is packed)
   int cluster;     // 1, or 2: a 256-row tile on a pair of SMs (tc_pair_launch)
+  bool comp = false;   // compensated epilogue (single-CTA packed kernels only)
 };
 
 // Returns the dynamic shared memory a tensor-core kernel variant needs.

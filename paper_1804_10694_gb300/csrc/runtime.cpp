@@ -371,9 +371,14 @@ static gemm_status resolve_mode(gemm_mode mode, const DeviceState& d, gemm_mode*
 
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
                              gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
-                             bool transA, bool transB, int64_t conv_image_elems) {
+                             bool transA, bool transB, int64_t conv_image_elems, unsigned opts) {
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
   *out = nullptr;
+  if (opts & ~static_cast<unsigned>(GEMM_OPT_COMPENSATED))
+    return fail(GEMM_ERR_INVALID_ARG, "unknown plan option bits 0x%x", opts);
+  const bool comp = (opts & GEMM_OPT_COMPENSATED) != 0;
+  if (comp && conv_image_elems >= 0)
+    return fail(GEMM_ERR_INVALID_ARG, "the compensated epilogue is for gemm plans, not convolutions");
   gemm_status st = validate_shape_t(transA, transB, M, N, K, lda, ldb, ldc);
   if (st != GEMM_OK) return st;
   DeviceState* dev;
@@ -404,6 +409,13 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   if (transA && p->cfg.fused) {
     // the fused kernel stages rows of A: a transposed A runs as the packed twin
     config_id = find_config(p->cfg.block_n, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
+    config_get(m, config_id, &p->cfg);
+  }
+  if (comp && (p->cfg.fused || p->cfg.cluster == 2 || p->cfg.block_n != 64)) {
+    // the compensated epilogue runs in the single-CTA packed kernel with
+    // 128 x 64 tiles: any other configuration runs as that tile with the
+    // same split-K and raster group
+    config_id = find_config(64, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
     config_get(m, config_id, &p->cfg);
   }
   const int cluster = p->cfg.cluster == 2 ? 2 : 1;
@@ -441,9 +453,12 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   size_t off = 0;
   const size_t offA = off; off = align_up(off + bytesA, 256);
   const size_t offB = off; off = align_up(off + bytesB, 256);
-  // maxima and pack counters of both operands, then one unit counter (the
-  // packed convolution's dynamic tile order), all cleared by one memset
-  const size_t offAmax = off; off = align_up(off + (2 * (nblkA + nblkB) + 1) * sizeof(unsigned), 256);
+  // per-execution state: maxima and pack counters of both operands, then one
+  // unit counter (the packed convolution's dynamic tile order), then the
+  // gemm launch's done counter; zeroed once here, and after each execution
+  // by the last CTA of its gemm launch
+  const int state_words = (int)(2 * (nblkA + nblkB) + 1);
+  const size_t offAmax = off; off = align_up(off + (state_words + 1) * sizeof(unsigned), 256);
   const size_t offPart = off;
   if (sk > 1) off = align_up(off + (size_t)sk * M * N * sizeof(float), 256);
   p->ws_bytes = off;
@@ -458,7 +473,11 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   p->planesB = w + offB;
   p->amaxA = reinterpret_cast<unsigned*>(w + offAmax);
   p->amaxB = p->amaxA + nblkA;
-  p->amax_bytes = (2 * (nblkA + nblkB) + 1) * sizeof(unsigned);   // maxima, per-block counters, unit counter
+  p->amax_bytes = (state_words + 1) * sizeof(unsigned);   // maxima, block counters, unit and done counters
+  if ((e = cudaMemset(p->amaxA, 0, p->amax_bytes)) != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "cudaMemset(plan state)");
+  }
   p->cntA = p->amaxB + nblkB;
   p->cntB = p->cntA + nblkA;
   p->unit_ctr = reinterpret_cast<int*>(p->cntB + nblkB);
@@ -479,7 +498,10 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.num_units = a.num_tiles * sk;
   a.chunks_total = (int)chunks_kernel;
   a.chunks_per_split = (int)(per * kc);
-  a.kb = std::max(1, std::min(p->cfg.kb, kMaxFoldChunks)) * kc;
+  // (the compensated epilogue folds every k-chunk: the tensor core's own
+  // accumulation chain is then one chunk long, and the register sum of the
+  // folds is compensated)
+  a.kb = (comp ? 1 : std::max(1, std::min(p->cfg.kb, kMaxFoldChunks))) * kc;
   a.group_m = std::max(1, std::min<int>(p->cfg.group_m, (int)tiles_m));
   a.ldc = ldc;
   a.amaxA = p->amaxA;
@@ -487,10 +509,13 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   a.partial = p->partial;
   a.err = dev->err_word;
   a.lda = lda;
+  a.state = p->amaxA;
+  a.state_words = state_words;
   p->launch.bn = bn;
   p->launch.prec = pr;
   p->launch.fused = fused;
   p->launch.cluster = cluster;
+  p->launch.comp = comp;
   if (cluster == 2) {
     // one cluster per SM pair that can hold one at a time
     if ((e = tc_pair_prepare(bn, pr, &p->max_pairs)) != cudaSuccess) return cuda_fail(e, "pair kernel attribute");
@@ -530,8 +555,8 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   const bool prof = p->prof_n < p->prof_max;
   cudaEvent_t* ev = prof ? &p->prof_events[4 * p->prof_n] : nullptr;
   if (prof) cudaEventRecord(ev[0], s);
-  if ((e = cudaMemsetAsync(p->amaxA, 0, p->amax_bytes, s)) != cudaSuccess)
-    return cuda_fail(e, "cudaMemsetAsync(amax)");
+  // (the block maxima and counters are zero: the previous execution's gemm
+  // launch cleared them)
   if (p->args.conv) {
     // one exponent for the whole image: its max, scanned as a single row
     if (reinterpret_cast<uintptr_t>(A) % 16 != 0)
@@ -878,6 +903,8 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     a.beta = beta;
     a.C = t_host.C;
     a.tm0 = (int)t0;
+    // the maxima are read by every panel's gemm: only the last one clears them
+    if (t1 < tiles_m) a.state_words = 0;
     a.tiles_m = (int)((t1 - t0 + cl - 1) / cl);   // in the plan's tile height
     a.num_tiles = a.tiles_m * a.tiles_n;
     a.num_units = a.num_tiles;   // split_k == 1
@@ -1015,6 +1042,14 @@ gemm_status gemm_plan_create(int64_t M, int64_t N, int64_t K, int64_t lda, int64
                              gemm_mode mode, gemm_select sel, gemm_plan_t* out) {
   clear_error();
   return plan_create_impl(M, N, K, lda, ldb, ldc, mode, -1, sel, out);
+}
+
+gemm_status gemm_plan_create_opts(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
+                                  int64_t ldc, gemm_mode mode, gemm_select sel, int config_id,
+                                  unsigned opts, gemm_plan_t* out) {
+  clear_error();
+  return plan_create_impl(M, N, K, lda, ldb, ldc, mode, config_id < 0 ? -1 : config_id, sel, out, false,
+                          false, -1, opts);
 }
 
 gemm_status gemm_plan_create_config(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,

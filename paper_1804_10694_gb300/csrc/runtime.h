@@ -79,7 +79,7 @@ int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, 
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,
                              gemm_mode mode, int config_id, gemm_select sel, gemm_plan_t* out,
                              bool transA = false, bool transB = false,
-                             int64_t conv_image_elems = -1);
+                             int64_t conv_image_elems = -1, unsigned opts = 0);
 gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const float* B, float beta,
                               float* C, cudaStream_t s);
 void plan_destroy_impl(gemm_plan_t p);

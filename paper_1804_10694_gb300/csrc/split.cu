@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "internal.h"
 #include "ptx.cuh"
@@ -495,6 +496,10 @@ __device__ __forceinline__ void pack_range(const PackShape& p, int i0, int i1, f
 template <Prec PR>
 __global__ void __launch_bounds__(256, 4) pack_first_kernel(const PackShape p) {
   __shared__ __align__(16) float tile[kColTileFloats];
+  // launched as a programmatic dependent of the stream's previous kernel
+  // (often the previous execution's gemm, which reads these planes and
+  // clears the block maxima and counters at its end)
+  griddep_wait();
   const int total = p.items();
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
@@ -508,6 +513,7 @@ __global__ void __launch_bounds__(256, 4) pack_first_kernel(const PackShape p) {
 template <Prec PR, int MODE>
 __global__ void __launch_bounds__(256, 4) fused_prep_kernel(const AmaxShape a, const PackShape p) {
   __shared__ __align__(16) float tile[kColTileFloats];
+  griddep_wait();   // as pack_first_kernel
   const int64_t na = amax_items<MODE>(a);
   for (int64_t i = blockIdx.x; i < na; i += gridDim.x) amax_item<MODE>(a, i);
   const int total = p.items();
@@ -668,6 +674,24 @@ __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restri
   if (PASS == kFirst) fold_block_max(m, amax);
 }
 
+// Launch with programmatic stream serialization: the kernel's CTAs may be
+// scheduled while the stream's previous kernel finishes (its launch latency
+// hidden); the kernel waits for that kernel (griddep_wait) before it reads
+// or writes anything.
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(Params...), int grid, int threads, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 int grid_for(int64_t items, int sms) {
   const int64_t cap = static_cast<int64_t>(sms) * 8;
   return static_cast<int>(items < cap ? (items > 0 ? items : 1) : cap);
@@ -697,13 +721,14 @@ cudaError_t launch_first(Prec prec, const PackShape& p, int sms, cudaStream_t s)
   const int64_t first = host_items(p.op[0], p.pitch) + host_items(p.op[1], p.pitch);
   if (first == 0) return cudaSuccess;
   const int grid = grid_for(first, sms);
+  cudaError_t e;
   if (prec == Prec::TF32)
-    pack_first_kernel<Prec::TF32><<<grid, 256, 0, s>>>(p);
+    e = launch_pdl(pack_first_kernel<Prec::TF32>, grid, 256, s, p);
   else if (prec == Prec::BF16X6)
-    pack_first_kernel<Prec::BF16X6><<<grid, 256, 0, s>>>(p);
+    e = launch_pdl(pack_first_kernel<Prec::BF16X6>, grid, 256, s, p);
   else
-    pack_first_kernel<Prec::BF16><<<grid, 256, 0, s>>>(p);
-  return cudaGetLastError();
+    e = launch_pdl(pack_first_kernel<Prec::BF16>, grid, 256, s, p);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -750,18 +775,19 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
   const int64_t total = na + host_items(p.op[1], pitch);
   if (total == 0) return cudaSuccess;
   const int grid = grid_for(total, sms);
+  cudaError_t e;
   if (prec == Prec::TF32) {
-    if (mode == kAmaxFlat) fused_prep_kernel<Prec::TF32, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
-    else if (mode == kAmaxRowsVec) fused_prep_kernel<Prec::TF32, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
-    else fused_prep_kernel<Prec::TF32, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxFlat>, grid, 256, s, a, p);
+    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsVec>, grid, 256, s, a, p);
+    else e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsScalar>, grid, 256, s, a, p);
   } else if (prec == Prec::BF16) {
-    if (mode == kAmaxFlat) fused_prep_kernel<Prec::BF16, kAmaxFlat><<<grid, 256, 0, s>>>(a, p);
-    else if (mode == kAmaxRowsVec) fused_prep_kernel<Prec::BF16, kAmaxRowsVec><<<grid, 256, 0, s>>>(a, p);
-    else fused_prep_kernel<Prec::BF16, kAmaxRowsScalar><<<grid, 256, 0, s>>>(a, p);
+    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxFlat>, grid, 256, s, a, p);
+    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsVec>, grid, 256, s, a, p);
+    else e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsScalar>, grid, 256, s, a, p);
   } else {
     return cudaErrorInvalidValue;   // the fused kernel splits A in two (three-product modes only)
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t pack_rows_panel_launch(Prec prec, const float* A, int64_t rows, int64_t K, int64_t lda,

@@ -39,6 +39,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "internal.h"
@@ -64,7 +65,7 @@ namespace gb {
 // running sum at every MMA; kept apart, the small products lose bits only
 // relative to their own (2^-8 smaller) sum, and the hi*hi chain is one MMA
 // per k-step instead of six.
-template <int BN, bool TF32, bool FUSED = false, int NP = 2, bool WIDE_EPI = false>
+template <int BN, bool TF32, bool FUSED = false, int NP = 2, int EPI = 0>
 struct TcCfg {
   static_assert(NP == 2 || (NP == 3 && !TF32 && !FUSED), "three planes: packed bf16 only");
   static constexpr int BM = 128;
@@ -73,16 +74,21 @@ struct TcCfg {
   static constexpr int B_PLANE = BN * SW;
   static constexpr int STAGE = NP * A_PLANE + NP * B_PLANE;
   // operand ring depth (the fused variant gives room to the staging of A)
-  static constexpr int STAGES = (FUSED || NP == 3) ? 2 : (BN == 64 ? 4 : BN == 128 ? 3 : 2);
+  // (EPI = 2, the compensated epilogue: its second epilogue warpgroup's
+  // staging buffers take the fourth stage's room at BN 64)
+  static constexpr int STAGES = (FUSED || NP == 3) ? 2 : (BN == 64 ? (EPI == 2 ? 3 : 4) : BN == 128 ? 3 : 2);
   static constexpr int BK = SW / (TF32 ? 4 : 2);       // elements per k-chunk
   static constexpr int KSTEPS = SW / 32;               // MMAs (32-byte K slices) per chunk and product
   // epilogue warpgroups: two for the 128-wide tiles of the fused variant
   // (with its extra warps, one warpgroup holding 128 columns would run out of
-  // registers) and of the grouped launch (WIDE_EPI: its tiles are short in K,
+  // registers) and of the grouped launch (EPI = 1: its tiles are short in K,
   // so the epilogue, at half the time per tile with each thread draining 64
-  // columns, is what the MMAs wait for); one elsewhere (at long K the
-  // epilogue hides behind the MMAs, and the extra warps cost about 2% there)
-  static constexpr int EPI_WG = (BN == 256 || (BN == 128 && (FUSED || WIDE_EPI))) ? 2 : 1;
+  // columns, is what the MMAs wait for), and for every tile width of the
+  // compensated epilogue (EPI = 2: it folds every k-chunk, six operations an
+  // output per fold, so the fold is what the MMAs wait for); one elsewhere
+  // (at long K the epilogue hides behind the MMAs, and the extra warps cost
+  // about 2% there)
+  static constexpr int EPI_WG = (BN == 256 || EPI == 2 || (BN == 128 && (FUSED || EPI == 1))) ? 2 : 1;
   static constexpr int EPI_COLS = BN / EPI_WG;         // columns per epilogue thread
   static constexpr int ACC_COLS = NP == 3 ? 2 * BN : BN;   // TMEM columns of one accumulator buffer
   // accumulator buffers: as many as TMEM holds, up to four, so that the MMA
@@ -130,7 +136,8 @@ struct FusedA {
 
 // Scheduling policy of one gemm: units are (split, tile) pairs.
 struct SingleSched {
-  static constexpr bool kWideEpilogue = false;
+  static constexpr int kEpi = 0;   // epilogue geometry (TcCfg's EPI)
+  static constexpr bool kCompensated = false;
   static constexpr bool kDynamic = false;     // (the packed convolution takes units dynamically)
   const CUtensorMap* tmA;
   const CUtensorMap* tmB;
@@ -146,6 +153,8 @@ struct SingleSched {
   // wave's other CTAs had read them)
   __device__ int l2_hints() const { return a->group_m > 1 ? 1 : 0; }
   __device__ int* unit_ctr() const { return a->unit_ctr; }
+  __device__ unsigned* state() const { return a->state; }
+  __device__ int state_words() const { return a->state_words; }
   __device__ Work work(int u) const {
     Work w;
     const int t = u % a->num_tiles;
@@ -173,16 +182,30 @@ struct SingleSched {
   }
 };
 
+// A single gemm with the compensated epilogue: the per-fold TMEM partial
+// sums are added into the FP32 registers with an error-free transformation
+// (TwoSum), the rounding error of every addition kept in a second register
+// per output and added back once at the end, so that the register sum of
+// the folds is as accurate as if it were computed in twice the precision.
+// Each thread holds two values per column (32 columns a thread).
+struct SingleSchedComp : SingleSched {
+  static constexpr int kEpi = 2;
+  static constexpr bool kCompensated = true;
+};
+
 // Scheduling policy of a grouped launch: units are the tiles of all problems,
 // listed problem after problem (problems ordered longest-K first on the host,
 // each problem's tiles in grouped raster order); the table gives a unit's
 // problem, tile coordinates and k-chunk count in one 16-byte load.
 struct GroupedSched {
-  static constexpr bool kWideEpilogue = true;
+  static constexpr int kEpi = 1;
+  static constexpr bool kCompensated = false;
   static constexpr bool kDynamic = true;      // problems of every size: units taken dynamically
   const GroupedArgs* a;
   __device__ int l2_hints() const { return 0; }   // problems of every shape: no priority
   __device__ int* unit_ctr() const { return a->unit_ctr; }
+  __device__ unsigned* state() const { return nullptr; }   // (the grouped plan clears its own)
+  __device__ int state_words() const { return 0; }
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
@@ -216,6 +239,20 @@ __device__ __forceinline__ unsigned cvt_bf16x2(float a, float b) {
   unsigned d;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
   return d;
+}
+
+// s + x with its rounding error kept: s becomes fl(s + x) and e gains the
+// exact error (s + x) - fl(s + x) of that addition (Knuth's TwoSum, six
+// round-to-nearest operations, no branch; exact unless an operation
+// overflows).  Summing the errors in e and adding e to s once at the end is
+// the compensated summation of the values x.
+__device__ __forceinline__ void two_sum_acc(float& s, float& e, float x) {
+  const float t = __fadd_rn(s, x);
+  const float xv = __fsub_rn(t, s);             // the part of x that went into t
+  const float sv = __fsub_rn(t, xv);            // the part of s that went into t
+  const float err = __fadd_rn(__fsub_rn(s, sv), __fsub_rn(x, xv));
+  s = t;
+  e = __fadd_rn(e, err);
 }
 
 // Fused variant: split one 16-byte output group (x scaled by sf) into the hi
@@ -326,7 +363,7 @@ __device__ __forceinline__ void fused_split_rows(const uint8_t* sbuf, uint8_t* h
 template <int BN, bool TF32, class Sched, bool FUSED = false, int NP = 2, int FBW = 128,
           int CONVA = 0>
 __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
-  using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kWideEpilogue>;
+  using Cfg = TcCfg<BN, TF32, FUSED, NP, Sched::kEpi>;
   static_assert(CONVA == 0 || (!FUSED && ((CONVA == 32 && NP == 2) || ((CONVA == 16 || CONVA == 64) && !TF32))),
                 "packed convolution: 32 (interleaved planes), or bf16 16- or 64-channel boxes");
   constexpr bool CB16 = CONVA == 16;
@@ -882,6 +919,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         }
       }
       float S[EC];
+      // compensated epilogue: rounding errors of the fold additions
+      constexpr bool COMP = Sched::kCompensated;
+      float E[COMP ? EC : 1];
       int blk = 0;
       for (int cb = w.c0; cb < w.c1; cb += kb, ++blk) {
         // the whole warp must agree before the warp-collective TMEM loads
@@ -893,6 +933,26 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         tc_fence_after();
         const uint32_t taddr =
             tmem_base + (static_cast<uint32_t>(q * 32) << 16) + ab * Cfg::ACC_COLS + half * EC;
+        if constexpr (COMP) {
+          // 32 columns a thread (two epilogue warpgroups)
+          static_assert(EC == 32, "compensated epilogue: 32 columns a thread");
+          uint32_t r[32];
+          tmem_ld_32x32b_x32(taddr, r);
+          tmem_wait_ld();
+          if (blk == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[i] = __uint_as_float(r[i]), E[i] = 0.0f;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) two_sum_acc(S[i], E[i], __uint_as_float(r[i]));
+          }
+          if constexpr (NP == 3) {
+            tmem_ld_32x32b_x32(taddr + BN, r);   // the five smaller products
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) two_sum_acc(S[i], E[i], __uint_as_float(r[i]));
+          }
+        } else {
 #pragma unroll
         for (int j = 0; j < EC / 32; ++j) {
           uint32_t r[32];
@@ -913,6 +973,7 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
             for (int i = 0; i < 32; ++i) S[j * 32 + i] += __uint_as_float(r[i]);
           }
         }
+        }
         tc_fence_before();
         mbar_arrive(acce_bar(ab));
         if (++ab == NACC) {
@@ -921,6 +982,11 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         }
       }
       if (!ok) break;
+      if constexpr (COMP) {
+        // the sum's rounding errors added back once
+#pragma unroll
+        for (int i = 0; i < EC; ++i) S[i] = __fadd_rn(S[i], E[i]);
+      }
       if (blk == 0 || v.alpha == 0.0f) {
         // K == 0 or alpha == 0 (grouped problems only): C = beta * C; the
         // planes of such a problem are not packed, so their TMEM sum is unused
@@ -1112,6 +1178,9 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     tc_fence_after();
     tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
   }
+  // every role of this CTA is past its last read of the block maxima and
+  // the unit counter (the barrier above)
+  clear_execution_state(sc.state(), sc.state_words());
 }
 
 template <int BN, bool TF32, int NP>
@@ -1120,6 +1189,19 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
                    const TcArgs a) {
   SingleSched sc{&tmA, &tmB, &a};
   tc_gemm_body<BN, TF32, SingleSched, false, NP>(sc);
+}
+
+// Compensated epilogue (SingleSchedComp): packed operands, every fold added
+// with its rounding error kept; instantiated for 128 x 64 tiles drained by
+// two epilogue warpgroups, 32 columns a thread (a 128-wide tile would need
+// 64 sums and 64 errors a thread at the 168 registers a thread that 320
+// threads leave, and spilled).
+template <int BN, bool TF32, int NP>
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, 2>::THREADS, 1)
+    tc_gemm_comp_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const TcArgs a) {
+  SingleSchedComp sc{{&tmA, &tmB, &a}};
+  tc_gemm_body<BN, TF32, SingleSchedComp, false, NP>(sc);
 }
 
 // Packed convolution: A's planes loaded as im2col boxes (CB channels) of
@@ -1133,7 +1215,7 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
 }
 
 template <int BN, bool TF32, int NP>
-__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, true>::THREADS, 1)
+__global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, 1>::THREADS, 1)
     tc_grouped_kernel(const GroupedArgs a) {
   GroupedSched sc{&a};
   tc_gemm_body<BN, TF32, GroupedSched, false, NP>(sc);
@@ -1152,19 +1234,48 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, true>::THREADS, 1)
 
 // Split-K fix-up: C = sum_s partial[s] + beta * C, where each partial already
 // holds alpha * (its share of A*B); partials are summed in increasing s (a
-// fixed order, so results do not depend on timing).
+// fixed order, so results do not depend on timing).  A thread covers four
+// consecutive columns of one row (rows by blockIdx.y, strided; columns by
+// blockIdx.x), with float4 loads of the partials when N % 4 == 0 and float4
+// accesses of C when its rows are 16-byte aligned as well: no index
+// division, every warp access contiguous.
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
                                      float beta, float* __restrict__ C, int64_t ldc) {
   griddep_wait();   // launched as a dependent of the gemm kernel
-  const int64_t total = static_cast<int64_t>(M) * N;
-  const int64_t plane = total;
-  for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
-       idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    float s = partial[idx];
-    for (int k = 1; k < splits; ++k) s += partial[k * plane + idx];
-    const int64_t r = idx / N, c = idx % N;
-    float* cp = C + r * ldc + c;
-    *cp = beta != 0.0f ? s + beta * *cp : s;
+  const int64_t plane = static_cast<int64_t>(M) * N;
+  const bool vp = (N & 3) == 0;
+  const bool vc = vp && (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+  const int c = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (c >= N) return;
+  for (int r = blockIdx.y; r < M; r += gridDim.y) {
+    const float* pp = partial + static_cast<int64_t>(r) * N + c;
+    float* cp = C + static_cast<int64_t>(r) * ldc + c;
+    if (vp) {
+      float4 s = __ldg(reinterpret_cast<const float4*>(pp));
+      for (int k = 1; k < splits; ++k) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(pp + k * plane));
+        s.x += t.x, s.y += t.y, s.z += t.z, s.w += t.w;
+      }
+      if (vc) {
+        float4* c4 = reinterpret_cast<float4*>(cp);
+        if (beta != 0.0f) {
+          const float4 o = *c4;
+          s.x = s.x + beta * o.x, s.y = s.y + beta * o.y, s.z = s.z + beta * o.z, s.w = s.w + beta * o.w;
+        }
+        *c4 = s;
+      } else {
+        const float v[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cp[j] = beta != 0.0f ? v[j] + beta * cp[j] : v[j];
+      }
+    } else {
+      const int n = min(4, N - c);
+      for (int j = 0; j < n; ++j) {
+        float s = pp[j];
+        for (int k = 1; k < splits; ++k) s += pp[k * plane + j];
+        cp[j] = beta != 0.0f ? s + beta * cp[j] : s;
+      }
+    }
   }
 }
 
@@ -1223,10 +1334,16 @@ static cudaError_t prepare_variant() {
     } else {
       e = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                Cfg::SMEM);
+      if constexpr (BN == 64) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(tc_gemm_comp_kernel<BN, TF32, NP>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   TcCfg<BN, TF32, false, NP, 2>::SMEM);
+      }
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(tc_grouped_kernel<BN, TF32, NP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TcCfg<BN, TF32, false, NP, true>::SMEM);
+                                 TcCfg<BN, TF32, false, NP, 1>::SMEM);
       if constexpr (!TF32) {
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(tc_conv_kernel<BN, false, NP, 16>,
@@ -1268,8 +1385,22 @@ cudaError_t tc_prepare(int bn, Prec prec, bool fused) {
 }
 
 template <int BN, bool TF32, int NP = 2>
-static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
+static cudaError_t launch_variant(int grid, bool fused, bool comp, const CUtensorMap& tmA,
                                   const CUtensorMap& tmB, const TcArgs& a, cudaStream_t s) {
+  if (comp) {
+    // compensated epilogue: packed gemm operands, 128 x 64 tiles only
+    if constexpr (BN != 64) {
+      return cudaErrorInvalidValue;
+    } else {
+      if (fused || a.conv) return cudaErrorInvalidValue;
+      using Cfg = TcCfg<BN, TF32, false, NP, 2>;
+      cudaError_t e = prepare_variant<BN, TF32, false, NP>();
+      if (e != cudaSuccess) return e;
+      e = launch_dependent(tc_gemm_comp_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+      if (e != cudaSuccess) return e;
+      return cudaGetLastError();
+    }
+  }
   if (fused) {
     if constexpr (NP != 2) {
       return cudaErrorInvalidValue;
@@ -1312,25 +1443,25 @@ static cudaError_t launch_variant(int grid, bool fused, const CUtensorMap& tmA,
 cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUtensorMap& tmB,
                            const TcArgs& a, cudaStream_t s) {
   if (l.cluster == 2) {
-    if (l.fused || a.conv) return cudaErrorInvalidValue;   // pairs: packed gemm operands only
+    if (l.fused || l.comp || a.conv) return cudaErrorInvalidValue;   // pairs: packed gemm operands only
     return tc_pair_launch(l.bn, l.prec, l.grid, tmA, tmB, a, s);
   }
   if (l.prec == Prec::TF32) {
-    if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, tmA, tmB, a, s);
-    if (l.bn == 128) return launch_variant<128, true>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, true>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
   } else if (l.prec == Prec::BF16X6) {
-    if (l.bn == 64) return launch_variant<64, false, 3>(l.grid, l.fused, tmA, tmB, a, s);
-    if (l.bn == 128) return launch_variant<128, false, 3>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 64) return launch_variant<64, false, 3>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, false, 3>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
   } else {
-    if (l.bn == 64) return launch_variant<64, false>(l.grid, l.fused, tmA, tmB, a, s);
-    if (l.bn == 128) return launch_variant<128, false>(l.grid, l.fused, tmA, tmB, a, s);
+    if (l.bn == 64) return launch_variant<64, false>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
+    if (l.bn == 128) return launch_variant<128, false>(l.grid, l.fused, l.comp, tmA, tmB, a, s);
   }
   return cudaErrorInvalidValue;
 }
 
 template <int BN, bool TF32, int NP = 2>
 static cudaError_t launch_grouped_variant(int grid, const GroupedArgs& a, cudaStream_t s) {
-  using Cfg = TcCfg<BN, TF32, false, NP, true>;
+  using Cfg = TcCfg<BN, TF32, false, NP, 1>;
   cudaError_t e = prepare_variant<BN, TF32, false, NP>();
   if (e != cudaSuccess) return e;
   e = launch_dependent(tc_grouped_kernel<BN, TF32, NP>, grid, Cfg::THREADS, Cfg::SMEM, s, a);
@@ -1353,12 +1484,20 @@ cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a,
 }
 cudaError_t splitk_reduce_launch(int M, int N, int splits, const float* partial, float beta,
                                  float* C, int64_t ldc, cudaStream_t s) {
-  const int64_t total = static_cast<int64_t>(M) * N;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
-  cudaError_t e = launch_dependent(splitk_reduce_kernel, static_cast<int>(blocks), 256, 0, s, M, N, splits,
-                                   partial, beta, C, ldc);
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  // 128 threads cover 512 columns of a row; rows spread over blockIdx.y
+  const int gx = (N + 511) / 512;
+  const int gy = std::max(1, std::min(M, std::max(1, 8192 / gx)));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(gx, gy);
+  cfg.blockDim = dim3(128);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, splitk_reduce_kernel, M, N, splits, partial, beta, C, ldc);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

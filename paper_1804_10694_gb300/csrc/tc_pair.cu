@@ -407,6 +407,9 @@ __global__ void __launch_bounds__(PairCfg<BN, TF32, NP>::THREADS, 1)
     tc_fence_after();
     tmem_dealloc_pair(tmem_base, Cfg::TMEM_COLS);
   }
+  // every role of this CTA is past its last read of the block maxima (the
+  // cluster barrier above)
+  clear_execution_state(a.state, a.state_words);
 }
 
 // ------------------------------------------------------------------- launch

@@ -1,5 +1,5 @@
-// Units of work of the persistent tensor-core kernels and the order in which
-// output tiles are walked.
+// Units of work of the persistent tensor-core kernels, the order in which
+// output tiles are walked, and the clearing of a plan's per-execution state.
 #pragma once
 
 namespace gb {
@@ -22,6 +22,31 @@ __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int grou
   const int r = t % group_tiles;
   tm = first_m + r % rows_in_group;
   tn = r / rows_in_group;
+}
+
+// A plan's per-execution state (block maxima, pack counters, the unit
+// counter of a dynamic tile order) must be zero when the next execution's
+// first kernel starts.  Instead of a memset before every execution, the last
+// CTA of the gemm launch to finish clears it: every CTA counts itself done
+// on `done` (the word after the state) once all its threads have finished
+// with the state, and the CTA that completes the count -- all others have
+// then stopped reading -- zeroes the state and then the count.  Every thread
+// of the CTA calls this, after a CTA barrier that follows its last read of
+// the state.  nwords == 0: nothing to clear.
+__device__ __forceinline__ void clear_execution_state(unsigned* state, int nwords) {
+  if (nwords <= 0) return;   // uniform over the grid
+  __shared__ int s_last;
+  unsigned* done = state + nwords;
+  if (threadIdx.x == 0) {
+    __threadfence();   // this CTA's reads of the state come before its count
+    s_last = atomicAdd(done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();   // every other CTA's count, and so its reads, came first
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) state[i] = 0u;
+    if (threadIdx.x == 0) *done = 0u;
+  }
 }
 
 }  // namespace gb

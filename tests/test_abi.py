@@ -125,3 +125,15 @@ def test_transposed_arguments_validated_before_launch():
     assert lib.gemm_plan_create_t(0, 1, 100, 50, 40, 40, 39, 50, 2, 0, ctypes.byref(h)) == 1
     assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 99, 40, 50, 1, 0, ctypes.byref(h)) == 1
     assert lib.gemm_plan_create_t(1, 1, 100, 50, 40, 100, 39, 50, 1, 0, ctypes.byref(h)) == 1
+
+
+def test_plan_options_validated_before_launch():
+    """gemm_plan_create_opts: unknown option bits and bad shapes are rejected
+    before any device work."""
+    import ctypes
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    assert lib.gemm_plan_create_opts(64, 64, 64, 64, 64, 64, 2, 0, -1, 2, ctypes.byref(h)) == 1
+    assert b"option" in lib.gemm_last_error()
+    assert lib.gemm_plan_create_opts(64, 64, 64, 63, 64, 64, 2, 0, -1, 1, ctypes.byref(h)) == 1
+    assert lib.gemm_plan_create_opts(64, 64, 64, 64, 64, 64, 2, 0, -1, 1, None) == 1

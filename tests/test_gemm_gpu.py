@@ -419,3 +419,43 @@ def test_concurrent_host_threads_and_streams():
     assert not errors, errors
     assert len(results) == 4 * 3 * 2 + 24
     assert all(err <= TOL for err in results.values()), results
+
+
+# ------------------------------------------- per-execution state of plans
+def _cfg_ids(mode):
+    """One configuration of each kind: packed single CTA, split-K, fused-split,
+    CTA pair (those the mode has)."""
+    want = [dict(block_n=128, split_k=1, fused=0, cluster=1), dict(block_n=64, split_k=3, fused=0, cluster=1),
+            dict(block_n=128, split_k=1, fused=1, cluster=1), dict(block_n=256, split_k=1, fused=0, cluster=2)]
+    out = []
+    for w in want:
+        for cid in range(pkg.config_count(mode)):
+            c = pkg.config_get(mode, cid)
+            if all(c[k] == v for k, v in w.items()):
+                out.append(cid)
+                break
+    return out
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+def test_plan_state_is_clean_between_executions(mode):
+    """The block maxima and counters of a plan are cleared by the last CTA of
+    each execution's gemm launch (no memset before an execution): one plan
+    run on operands whose blocks need scaling (2^70 and 2^-90), then on
+    ordinary ones, then on the scaled ones again gives, each time, the bits
+    of a fresh plan on the same operands, for every kind of configuration."""
+    M, N, K = 600, 300, 700
+    base_a, base_b, C0 = W.uniform(M, K, 91), W.uniform(K, N, 92), W.uniform(M, N, 93)
+    inputs = [(W.scaled(base_a, 70), W.scaled(base_b, -90)), (base_a, base_b)]
+    for cid in _cfg_ids(mode):
+        fresh = [run_gemm(mode, M, N, K, 1.5, a, b, 0.5, C0, config_id=cid) for a, b in inputs]
+        plan = pkg.Plan(M, N, K, mode=mode, config_id=cid)
+        dC = dev(C0)
+        for i in (0, 1, 0, 1):
+            a, b = inputs[i]
+            dC.copy_(dev(C0))
+            plan.execute(dev(a), dev(b), dC, 1.5, 0.5)
+            torch.cuda.synchronize()
+            assert np.array_equal(dC.cpu().numpy(), fresh[i]), (cid, i)
+        plan.destroy()
+    pkg.device_error()
