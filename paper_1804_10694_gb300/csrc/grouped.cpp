@@ -75,8 +75,8 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
     return GEMM_OK;
   }
   if (p->num_units == 0) return GEMM_OK;
-  if ((e = cudaMemsetAsync(p->d_amax, 0, p->amax_bytes, s)) != cudaSuccess)
-    return cuda_fail(e, "clear block maxima");
+  // (the block maxima, counters and unit counter are zero: the previous
+  // execution's gemm launch cleared them)
   if ((e = grouped_pack_launch(p->prec, p->d_probs, p->d_ptrs, p->d_split_prefix, p->split_total, p->G,
                                p->sms, s)) != cudaSuccess)
     return cuda_fail(e, "grouped pack launch");
@@ -90,6 +90,8 @@ gemm_status launch_all(gemm_grouped_plan_t p, cudaStream_t s) {
   a.group_m = p->group_m;
   a.err = p->err;
   a.unit_ctr = reinterpret_cast<int*>(p->d_amax + p->amax_count);
+  a.state = p->d_amax;
+  a.state_words = (int)(p->amax_count + 1);
   const int grid = std::min(p->num_units, p->sms);
   if ((e = tc_grouped_launch(p->bn, p->prec, grid, a, s)) != cudaSuccess)
     return cuda_fail(e, "grouped tensor-core launch");
@@ -240,10 +242,12 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
     const bool pack = !empty && p->K[i] > 0;
     spl_prefix[slot + 1] = spl_prefix[slot] + (pack ? pack_first_items(p->M[i], p->N[i], pitch) : 0);
   }
-  // block maxima and pack counters of every problem, then the launch's unit
-  // counter (its dynamic tile order), all cleared by one memset
+  // per-execution state: block maxima and pack counters of every problem,
+  // then the launch's unit counter (its dynamic tile order), then the gemm
+  // launch's done counter; zeroed once here and, after every execution, by
+  // the last CTA of the gemm launch
   const size_t off_amax = off;
-  p->amax_bytes = (amax_count + 1) * sizeof(unsigned);
+  p->amax_bytes = (amax_count + 2) * sizeof(unsigned);
   p->amax_count = amax_count;
   off = round256(off + p->amax_bytes);
   const size_t off_probs = off;
@@ -265,6 +269,7 @@ gemm_status grouped_create_impl(int G, const int64_t* M, const int64_t* N, const
   p->d_ptrs = reinterpret_cast<GroupedPtrs*>(w + off_ptrs);
   p->d_units = reinterpret_cast<GroupedUnit*>(w + off_units);
   p->d_split_prefix = reinterpret_cast<int*>(w + off_pref);
+  if ((e = cudaMemset(p->d_amax, 0, p->amax_bytes)) != cudaSuccess) return cuda_fail(e, "cudaMemset(plan state)");
   for (int slot = 0; slot < G; ++slot) {
     const int i = p->order[slot];
     GroupedProblem& g = hp[slot];

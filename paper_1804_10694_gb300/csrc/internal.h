@@ -179,6 +179,8 @@ struct GroupedArgs {
   int G, num_units, kb, group_m;
   int* err;
   int* unit_ctr;              // units taken so far (zero before the launch)
+  unsigned* state;            // per-execution state cleared by the launch's last CTA
+  int state_words;            // (followed by its done counter)
 };
 
 cudaError_t tc_grouped_launch(int bn, Prec prec, int grid, const GroupedArgs& a, cudaStream_t s);

@@ -175,6 +175,18 @@ __device__ __forceinline__ void griddep_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// ------------------------------------------- device-scope counting atomics
+// old = *p; *p += v, with acquire-release semantics at GPU scope: every
+// memory access of the calling thread before it (and, after a CTA barrier,
+// of the whole CTA) is visible to the thread that later observes the sum,
+// and everything that thread wrote before its own release is visible here.
+// Lighter than a sequentially consistent fence followed by a relaxed atomic.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // ------------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem),

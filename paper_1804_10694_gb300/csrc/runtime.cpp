@@ -186,14 +186,17 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
   const int bn = N <= 64 ? 64 : 128;
   const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
   const int64_t chunks = (K + prec_chunk_elems(p) - 1) / prec_chunk_elems(p);
+  // split-K: the largest split count that keeps every unit in one wave
+  // (tiles x splits <= SMs) and at least 4 k-chunks per split; a split
+  // count that spills into a second, partial wave doubles the time of the
+  // CTAs that run two units (1024^3 on GB300: three splits, 192 units on 152
+  // SMs, 25.8 us a call against 21.8 with two)
   int sk = 1;
   const int cand[] = {1, 2, 3, 4, 6, 8};
   for (int c : cand) {
-    if (c > chunks / 4) break;            // keep at least 4 k-chunks per split
+    if (c > 1 && (c > chunks / 4 || tiles * c > (int64_t)sms)) break;
     sk = c;
-    if (tiles * c >= (int64_t)sms * 9 / 10) break;
   }
-  if (tiles >= (int64_t)sms) sk = 1;
   if (sk == 1 && bn == 128 && sms >= 2) {
     // A CTA pair's 256 x 256 tile moves half the operand bytes per product
     // of four 128 x 128 tiles: at 8192^3 on GB300 a pair unit took 2 x 0.875

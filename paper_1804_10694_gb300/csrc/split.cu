@@ -44,10 +44,11 @@ enum Pass { kFirst = 0, kRescale = 1 };
 // into the block's slot and counts the run's items on the block's counter.
 // Returns, uniformly over the CTA, the block's final max bits when this run
 // completed the block, else 0xFFFFFFFF.  The CTA barrier orders every
-// thread's plane writes before thread 0's device-scope fence, which is
-// cumulative: they and the atomicMax are visible before the completing CTA
-// can observe the count (the pattern of a split-K semaphore).  No CTA waits
-// for another.
+// thread's plane writes before thread 0's count, an acquire-release atomic
+// at GPU scope, whose release is cumulative: they and the atomicMax are
+// visible before the completing CTA, whose acquire observes the count, reads
+// the max or re-splits the block (the pattern of a split-K semaphore).  No
+// CTA waits for another.
 __device__ __forceinline__ unsigned finish_run(unsigned m, unsigned* slot, unsigned* cnt,
                                                unsigned run, unsigned items) {
   __shared__ unsigned wm[32];
@@ -60,13 +61,9 @@ __device__ __forceinline__ unsigned finish_run(unsigned m, unsigned* slot, unsig
     unsigned b = wm[0];
     for (int i = 1; i < static_cast<int>(blockDim.x >> 5); ++i) b = max(b, wm[i]);
     if (b) atomicMax(slot, b);
-    __threadfence();
-    const unsigned done = atomicAdd(cnt, run) + run;
+    const unsigned done = atom_add_acq_rel_gpu(cnt, run) + run;
     unsigned v = 0xFFFFFFFFu;
-    if (done == items) {
-      __threadfence();
-      v = *reinterpret_cast<const volatile unsigned*>(slot);
-    }
+    if (done == items) v = *reinterpret_cast<const volatile unsigned*>(slot);
     s_done = v;
   }
   __syncthreads();
@@ -571,6 +568,7 @@ __global__ void __launch_bounds__(256, 4) grouped_pack_kernel(const GroupedProbl
   // the current problem's shape lives in shared memory: built in registers,
   // it held 128 registers a thread (two CTAs a SM)
   __shared__ PackShape shape;
+  griddep_wait();   // launched as a programmatic dependent (as pack_first_kernel)
   const int* prefix = stage_prefix(prefix_g, G);
   const int total = prefix[G];
   const int per = (total + gridDim.x - 1) / gridDim.x;
@@ -679,10 +677,12 @@ __global__ void __launch_bounds__(256) image_split_kernel(const float4* __restri
 // hidden); the kernel waits for that kernel (griddep_wait) before it reads
 // or writes anything.
 template <typename... Params, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(Params...), int grid, int threads, cudaStream_t s, Args&&... args) {
+cudaError_t launch_pdl(void (*kernel)(Params...), int grid, int threads, size_t smem, cudaStream_t s,
+                       Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -723,11 +723,11 @@ cudaError_t launch_first(Prec prec, const PackShape& p, int sms, cudaStream_t s)
   const int grid = grid_for(first, sms);
   cudaError_t e;
   if (prec == Prec::TF32)
-    e = launch_pdl(pack_first_kernel<Prec::TF32>, grid, 256, s, p);
+    e = launch_pdl(pack_first_kernel<Prec::TF32>, grid, 256, 0, s, p);
   else if (prec == Prec::BF16X6)
-    e = launch_pdl(pack_first_kernel<Prec::BF16X6>, grid, 256, s, p);
+    e = launch_pdl(pack_first_kernel<Prec::BF16X6>, grid, 256, 0, s, p);
   else
-    e = launch_pdl(pack_first_kernel<Prec::BF16>, grid, 256, s, p);
+    e = launch_pdl(pack_first_kernel<Prec::BF16>, grid, 256, 0, s, p);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -777,13 +777,13 @@ cudaError_t pack_fused_launch(Prec prec, const float* A, int64_t M, int64_t K, i
   const int grid = grid_for(total, sms);
   cudaError_t e;
   if (prec == Prec::TF32) {
-    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxFlat>, grid, 256, s, a, p);
-    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsVec>, grid, 256, s, a, p);
-    else e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsScalar>, grid, 256, s, a, p);
+    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxFlat>, grid, 256, 0, s, a, p);
+    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsVec>, grid, 256, 0, s, a, p);
+    else e = launch_pdl(fused_prep_kernel<Prec::TF32, kAmaxRowsScalar>, grid, 256, 0, s, a, p);
   } else if (prec == Prec::BF16) {
-    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxFlat>, grid, 256, s, a, p);
-    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsVec>, grid, 256, s, a, p);
-    else e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsScalar>, grid, 256, s, a, p);
+    if (mode == kAmaxFlat) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxFlat>, grid, 256, 0, s, a, p);
+    else if (mode == kAmaxRowsVec) e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsVec>, grid, 256, 0, s, a, p);
+    else e = launch_pdl(fused_prep_kernel<Prec::BF16, kAmaxRowsScalar>, grid, 256, 0, s, a, p);
   } else {
     return cudaErrorInvalidValue;   // the fused kernel splits A in two (three-product modes only)
   }
@@ -834,13 +834,14 @@ cudaError_t grouped_pack_launch(Prec prec, const GroupedProblem* probs, const Gr
   // problems: two waves 363 us, six 354 us; one wave of shares weighted by
   // their elements, without that rebalancing, 431 us)
   const int gf = static_cast<int>(std::min<int64_t>(first_total, static_cast<int64_t>(sms) * 24));
+  cudaError_t e;
   if (prec == Prec::TF32)
-    grouped_pack_kernel<Prec::TF32><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    e = launch_pdl(grouped_pack_kernel<Prec::TF32>, gf, 256, dyn, s, probs, ptrs, first_prefix, G);
   else if (prec == Prec::BF16X6)
-    grouped_pack_kernel<Prec::BF16X6><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
+    e = launch_pdl(grouped_pack_kernel<Prec::BF16X6>, gf, 256, dyn, s, probs, ptrs, first_prefix, G);
   else
-    grouped_pack_kernel<Prec::BF16><<<gf, 256, dyn, s>>>(probs, ptrs, first_prefix, G);
-  return cudaGetLastError();
+    e = launch_pdl(grouped_pack_kernel<Prec::BF16>, gf, 256, dyn, s, probs, ptrs, first_prefix, G);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace gb

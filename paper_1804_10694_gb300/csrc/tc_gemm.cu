@@ -204,8 +204,8 @@ struct GroupedSched {
   const GroupedArgs* a;
   __device__ int l2_hints() const { return 0; }   // problems of every shape: no priority
   __device__ int* unit_ctr() const { return a->unit_ctr; }
-  __device__ unsigned* state() const { return nullptr; }   // (the grouped plan clears its own)
-  __device__ int state_words() const { return 0; }
+  __device__ unsigned* state() const { return a->state; }
+  __device__ int state_words() const { return a->state_words; }
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
@@ -458,9 +458,19 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the first problem's tensor maps (kernel parameters or host-written
+  // tables, not outputs of the previous kernel) are fetched meanwhile
+  if (warp == 0 && lane == 0 && nunits > 0) {
+    if (!FUSED && CONVA == 0) tma_prefetch_desc(sc.mapA(0));
+    tma_prefetch_desc(sc.mapB(0));
+  }
   // the prologue above overlaps the end of the packing kernel; nothing below
   // runs before that kernel has completed and its writes are visible
   griddep_wait();
+  // the stream's next kernel (the split-K fix-up, or the next execution's
+  // packing) may be scheduled now: it waits for this launch to complete
+  // before it touches anything, and only its launch latency overlaps
+  griddep_launch_dependents();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer

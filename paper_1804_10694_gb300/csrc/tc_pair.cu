@@ -156,9 +156,16 @@ __global__ void __launch_bounds__(PairCfg<BN, TF32, NP>::THREADS, 1)
   cluster_sync();   // both CTAs' barriers initialised and tensor memory allocated
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  if (warp == 0 && lane == 0) {   // kernel parameters: fetched meanwhile
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
   // the prologue above overlaps the end of the packing kernel; nothing below
   // runs before that kernel has completed and its writes are visible
   griddep_wait();
+  // the stream's next kernel may be scheduled now (it waits for this launch
+  // to complete before it touches anything)
+  griddep_launch_dependents();
 
   auto work = [&](int u) {
     Work w;

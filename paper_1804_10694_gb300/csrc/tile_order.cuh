@@ -1,6 +1,7 @@
 // Units of work of the persistent tensor-core kernels, the order in which
 // output tiles are walked, and the clearing of a plan's per-execution state.
 #pragma once
+#include "ptx.cuh"
 
 namespace gb {
 
@@ -30,20 +31,20 @@ __device__ __forceinline__ void raster(int t, int tiles_m, int tiles_n, int grou
 // CTA of the gemm launch to finish clears it: every CTA counts itself done
 // on `done` (the word after the state) once all its threads have finished
 // with the state, and the CTA that completes the count -- all others have
-// then stopped reading -- zeroes the state and then the count.  Every thread
-// of the CTA calls this, after a CTA barrier that follows its last read of
-// the state.  nwords == 0: nothing to clear.
+// then stopped reading -- zeroes the state and then the count.  The count
+// is an acquire-release atomic at GPU scope: its release (cumulative over
+// the CTA after the barrier) orders the CTA's reads of the state before it,
+// and the last CTA's acquire orders every count before its zeroing.  Every
+// thread of the CTA calls this, after a CTA barrier that follows its last
+// read of the state.  nwords == 0: nothing to clear.
 __device__ __forceinline__ void clear_execution_state(unsigned* state, int nwords) {
   if (nwords <= 0) return;   // uniform over the grid
   __shared__ int s_last;
   unsigned* done = state + nwords;
-  if (threadIdx.x == 0) {
-    __threadfence();   // this CTA's reads of the state come before its count
-    s_last = atomicAdd(done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1 ? 1 : 0;
-  }
+  if (threadIdx.x == 0)
+    s_last = atom_add_acq_rel_gpu(done, 1u) == gridDim.x * gridDim.y * gridDim.z - 1 ? 1 : 0;
   __syncthreads();
   if (s_last) {
-    __threadfence();   // every other CTA's count, and so its reads, came first
     for (int i = threadIdx.x; i < nwords; i += blockDim.x) state[i] = 0u;
     if (threadIdx.x == 0) *done = 0u;
   }

@@ -136,3 +136,28 @@ def test_grouped_exhaustive_selection_runs_and_is_correct():
         ref = oracle.gemm_f64(M, N, K, 1.0, A, B, 1.0, C)
         assert oracle.rel_frob(out, ref) <= TOL
     plan.destroy()
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_grouped_plan_state_is_clean_between_executions(mode, graph):
+    """The block maxima, pack counters and unit counter of a grouped plan are
+    cleared by the last CTA of each execution's gemm launch: one plan run on
+    problems whose blocks need scaling (2^70 and 2^-90), then ordinary ones,
+    then the scaled ones again gives, each time, the bits of a fresh plan."""
+    shapes = [(300, 200, 100), (129, 65, 1000), (513, 33, 257), (64, 300, 64)]
+    base = _problems(shapes, 500)
+    scaled = [(W.scaled(A, 70), W.scaled(B, -90), C) for A, B, C in base]
+    alphas, betas = [1.5] * len(shapes), [0.5] * len(shapes)
+    fresh = []
+    for probs in (scaled, base):
+        p = pkg.GroupedPlan(shapes, mode=mode)
+        fresh.append(_run(p, probs, alphas, betas, graph=graph))
+        p.destroy()
+    plan = pkg.GroupedPlan(shapes, mode=mode)
+    for i in (0, 1, 0, 1):
+        outs = _run(plan, (scaled, base)[i], alphas, betas, graph=graph)
+        for o, f in zip(outs, fresh[i]):
+            assert np.array_equal(o, f), i
+    plan.destroy()
+    pkg.device_error()

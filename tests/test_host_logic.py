@@ -167,3 +167,23 @@ def test_costmodel_ensemble_file_format(tmp_path):
     assert lib.gemm_costmodel_load(str(f).encode()) == 7
     f.write_text(head % 0 + theta)
     assert lib.gemm_costmodel_load(str(f).encode()) == 7
+
+
+def test_default_split_k_stays_in_one_wave():
+    """The built-in heuristic takes the largest split-K that keeps every unit
+    in one wave of the 152 SMs (and at least 4 k-chunks per split); a split
+    count that would start a second, partial wave is not taken."""
+    def pick(n):
+        return pkg.config_get("bf16x3", pkg.config_default("bf16x3", n, n, n))
+    c = pick(1024)            # 8 x 8 tiles of 128 x 128, 16 chunks: 2 splits (128 units)
+    assert (c["block_n"], c["split_k"], c["cluster"]) == (128, 2, 1)
+    c = pick(1060)            # 9 x 9 tiles: 2 splits would be 162 units
+    assert (c["block_n"], c["split_k"], c["cluster"]) == (128, 1, 1)
+    c = pick(512)             # 4 x 4 tiles, 8 chunks: at most 2 splits of 4 chunks
+    assert (c["block_n"], c["split_k"]) == (128, 2)
+    c = pick(4099)            # 33 x 33 tiles: more than one wave already
+    assert c["split_k"] == 1
+    for n in (1024, 1060, 512, 2048, 4099, 8192):
+        c = pick(n)
+        tiles = -(-n // (128 * c["cluster"])) * -(-n // c["block_n"])
+        assert c["split_k"] == 1 or tiles * c["split_k"] <= 152
