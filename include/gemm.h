@@ -222,7 +222,9 @@ gemm_status gemm_plan_create_t(int transA, int transB, int64_t M, int64_t N, int
  *     when C is a multiple of 16, else gathered by its threads) and splits
  *     them itself.
  * config_id < 0 picks the default: packed where it applies (C a multiple of
- * 16; BF16X6 has no fused-split kernel), else fused-split.  One power-of-two exponent covers
+ * 16; BF16X6 has no fused-split kernel), else fused-split; a default packed
+ * plan with at most 32 output features (K <= 32) and no split-K runs
+ * 128 x 32 tiles, two CTAs a SM where shared memory holds two.  One power-of-two exponent covers
  * the whole image (its max |x|); B is scaled per 128 output channels as in
  * the gemm.
  * Errors: INVALID_ARG (sizes, filter sizes, C % 4, mode, a packed

@@ -66,7 +66,7 @@ struct TcArgs {
 };
 
 struct TcLaunch {
-  int bn;          // tile N (64 or 128; 128 or 256 for a CTA pair)
+  int bn;          // tile N (64 or 128; 128 or 256 for a CTA pair; 32 for a narrow convolution)
   Prec prec;       // BF16, BF16X6 or TF32
   int grid;
   bool fused;      // A split inside the gemm kernel (only B is packed)
@@ -74,6 +74,10 @@ struct TcLaunch {
   bool comp = false;   // compensated epilogue (single-CTA packed kernels only)
 };
 
+// Packed convolutions with at most 32 output features may run 128 x 32
+// tiles (TcLaunch.bn = 32): CTAs of that kernel a SM holds at once (2, or 1
+// for a precision whose ring does not fit twice).
+int tc_narrow_ctas_per_sm(Prec prec);
 // Returns the dynamic shared memory a tensor-core kernel variant needs.
 int tc_smem_bytes(int bn, Prec prec, bool fused = false);
 // Bytes of one row per k-chunk of the kernel variant with tile width bn (the

@@ -377,8 +377,6 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
                              bool transA, bool transB, int64_t conv_image_elems, unsigned opts) {
   if (!out) return fail(GEMM_ERR_INVALID_ARG, "null plan output pointer");
   *out = nullptr;
-  if (opts & ~static_cast<unsigned>(GEMM_OPT_COMPENSATED))
-    return fail(GEMM_ERR_INVALID_ARG, "unknown plan option bits 0x%x", opts);
   const bool comp = (opts & GEMM_OPT_COMPENSATED) != 0;
   if (comp && conv_image_elems >= 0)
     return fail(GEMM_ERR_INVALID_ARG, "the compensated epilogue is for gemm plans, not convolutions");
@@ -421,6 +419,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
     config_id = find_config(64, p->cfg.split_k, p->cfg.kb, p->cfg.group_m);
     config_get(m, config_id, &p->cfg);
   }
+  if ((opts & kOptNarrowConv) && conv_image_elems >= 0 && !p->cfg.fused && p->cfg.cluster == 1)
+    p->cfg.block_n = 32;   // a packed convolution with few output features: 128 x 32 tiles
   const int cluster = p->cfg.cluster == 2 ? 2 : 1;
   if (cluster == 2 && conv_image_elems >= 0)
     return fail(GEMM_ERR_INVALID_ARG, "configuration %d runs on CTA pairs: not for convolutions", config_id);
@@ -524,7 +524,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
     if ((e = tc_pair_prepare(bn, pr, &p->max_pairs)) != cudaSuccess) return cuda_fail(e, "pair kernel attribute");
     p->launch.grid = 2 * (int)std::min<int64_t>(a.num_units, p->max_pairs);
   } else {
-    p->launch.grid = (int)std::min<int64_t>(a.num_units, dev->sms);
+    const int per_sm = bn == 32 ? tc_narrow_ctas_per_sm(pr) : 1;
+    p->launch.grid = (int)std::min<int64_t>(a.num_units, (int64_t)dev->sms * per_sm);
     if ((e = tc_prepare(bn, pr, fused)) != cudaSuccess) return cuda_fail(e, "kernel attribute");
   }
   *out = p.release();
@@ -1051,6 +1052,8 @@ gemm_status gemm_plan_create_opts(int64_t M, int64_t N, int64_t K, int64_t lda, 
                                   int64_t ldc, gemm_mode mode, gemm_select sel, int config_id,
                                   unsigned opts, gemm_plan_t* out) {
   clear_error();
+  if (opts & ~static_cast<unsigned>(GEMM_OPT_COMPENSATED))
+    return fail(GEMM_ERR_INVALID_ARG, "unknown plan option bits 0x%x", opts);
   return plan_create_impl(M, N, K, lda, ldb, ldc, mode, config_id < 0 ? -1 : config_id, sel, out, false,
                           false, -1, opts);
 }
@@ -1109,6 +1112,7 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   const bool can_pack = pack_shape && g_encode_im2col != nullptr;
   if (!can_pack && (mode == GEMM_MODE_BF16X6 || (config_id >= 0 && !c.fused)))
     return fail(GEMM_ERR_UNSUPPORTED_DEVICE, "the packed convolution needs TMA im2col tensor maps");
+  const bool default_choice = config_id < 0;
   if (config_id < 0) {
     // default: the gemm heuristic's choice for this shape (tile width by K,
     // split-K when the tiles do not fill the GPU), as its packed or its
@@ -1130,9 +1134,12 @@ gemm_status gemm_conv_plan_create(int64_t batch, int64_t H, int64_t W, int64_t C
   config_get(mode, config_id, &c);
   const bool packed_conv = !c.fused;
   const int64_t elems = batch * H * W * C;
+  // the default plan of a packed convolution with at most 32 output
+  // features and no split-K takes the narrow tile (128 x 32, two CTAs a SM)
+  const unsigned narrow = default_choice && packed_conv && K <= 32 && c.split_k == 1 ? kOptNarrowConv : 0u;
   gemm_plan_t p = nullptr;
   gemm_status st = plan_create_impl(M, K, Kd, Kd, K, K, mode, config_id, GEMM_SELECT_DEFAULT, &p, false,
-                                    false, packed_conv ? elems : -1);
+                                    false, packed_conv ? elems : -1, narrow);
   if (st != GEMM_OK) return st;
   // packed: channels per im2col box (32: the two planes interleaved by
   // 16-channel groups, the only layout of tf32 planes)

@@ -74,6 +74,10 @@ int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms);
 int select_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb,
                   int64_t ldc, gemm_select sel, int sms);
 
+// Internal plan option (beside the public GEMM_OPT_* bits): a packed
+// convolution plan runs 128 x 32 tiles, two CTAs a SM.
+constexpr unsigned kOptNarrowConv = 1u << 16;
+
 // conv_image_elems >= 0: a packed convolution, whose A planes hold the
 // split image (that many elements a plane) instead of M x pitch rows
 gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64_t ldb, int64_t ldc,

@@ -1224,6 +1224,21 @@ __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP>::THREADS, 1)
   tc_gemm_body<BN, TF32, SingleSched, false, NP, 128, CB>(sc);
 }
 
+// Packed convolution with few output features (at most 32): 128 x 32 tiles,
+// two-deep ring, TWO CTAs a SM.  The 16-feature layer is latency-bound (a
+// tile is a chain of dependent steps on a few threads, about one tile of
+// loads in flight a CTA, 18 % tensor and 11 % DRAM activity with 64-wide
+// tiles); a narrower tile needs 100 KB of shared memory and 128 TMEM
+// columns, so that a SM holds two CTAs and twice the units in flight, and
+// its MMAs and B loads carry no empty columns.
+template <bool TF32, int NP, int CB>
+__global__ void __launch_bounds__(TcCfg<32, TF32, false, NP>::THREADS, 2)
+    tc_conv_narrow_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                          const TcArgs a) {
+  SingleSched sc{&tmA, &tmB, &a};
+  tc_gemm_body<32, TF32, SingleSched, false, NP, 128, CB>(sc);
+}
+
 template <int BN, bool TF32, int NP>
 __global__ void __launch_bounds__(TcCfg<BN, TF32, false, NP, 1>::THREADS, 1)
     tc_grouped_kernel(const GroupedArgs a) {
@@ -1390,8 +1405,70 @@ static cudaError_t prepare_fused(int bn, Prec prec) {
   return cudaErrorInvalidValue;
 }
 
+// The narrow convolution kernels (tile width 32, two CTAs a SM).
+template <bool TF32, int NP, int CB>
+static cudaError_t prepare_narrow_one() {
+  return cudaFuncSetAttribute(tc_conv_narrow_kernel<TF32, NP, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcCfg<32, TF32, false, NP>::SMEM);
+}
+
+// (every precision's variants at once: the per-thread flag covers them all)
+static cudaError_t prepare_narrow(Prec) {
+  static thread_local int configured_device = -1;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (configured_device == dev) return cudaSuccess;
+  e = prepare_narrow_one<true, 2, 32>();
+  if (e == cudaSuccess) e = prepare_narrow_one<false, 3, 16>();
+  if (e == cudaSuccess) e = prepare_narrow_one<false, 3, 64>();
+  if (e == cudaSuccess) e = prepare_narrow_one<false, 2, 32>();
+  if (e == cudaSuccess) e = prepare_narrow_one<false, 2, 64>();
+  if (e == cudaSuccess) configured_device = dev;
+  return e;
+}
+
 cudaError_t tc_prepare(int bn, Prec prec, bool fused) {
+  if (bn == 32) return fused ? cudaErrorInvalidValue : prepare_narrow(prec);
   return fused ? prepare_fused<true>(bn, prec) : prepare_fused<false>(bn, prec);
+}
+
+int tc_narrow_ctas_per_sm(Prec prec) {
+  // (the system reserves 1 KB of shared memory a CTA; 228 KB a SM)
+  const int smem = prec == Prec::TF32 ? TcCfg<32, true, false, 2>::SMEM
+                   : prec == Prec::BF16X6 ? TcCfg<32, false, false, 3>::SMEM
+                                          : TcCfg<32, false, false, 2>::SMEM;
+  return 2 * (smem + 1024) <= 233472 ? 2 : 1;
+}
+
+static cudaError_t launch_narrow(int grid, Prec prec, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                                 const TcArgs& a, cudaStream_t s) {
+  if (!a.conv) return cudaErrorInvalidValue;   // a convolution tile only
+  cudaError_t e = prepare_narrow(prec);
+  if (e != cudaSuccess) return e;
+  if (prec == Prec::TF32) {
+    if (a.conv_box_c != 32) return cudaErrorInvalidValue;
+    using Cfg = TcCfg<32, true, false, 2>;
+    e = launch_dependent(tc_conv_narrow_kernel<true, 2, 32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+  } else if (prec == Prec::BF16X6) {
+    using Cfg = TcCfg<32, false, false, 3>;
+    if (a.conv_box_c == 64)
+      e = launch_dependent(tc_conv_narrow_kernel<false, 3, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    else if (a.conv_box_c == 16)
+      e = launch_dependent(tc_conv_narrow_kernel<false, 3, 16>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    else
+      return cudaErrorInvalidValue;
+  } else {
+    using Cfg = TcCfg<32, false, false, 2>;
+    if (a.conv_box_c == 64)
+      e = launch_dependent(tc_conv_narrow_kernel<false, 2, 64>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    else if (a.conv_box_c == 32)
+      e = launch_dependent(tc_conv_narrow_kernel<false, 2, 32>, grid, Cfg::THREADS, Cfg::SMEM, s, tmA, tmB, a);
+    else
+      return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 template <int BN, bool TF32, int NP = 2>
@@ -1455,6 +1532,10 @@ cudaError_t tc_gemm_launch(const TcLaunch& l, const CUtensorMap& tmA, const CUte
   if (l.cluster == 2) {
     if (l.fused || l.comp || a.conv) return cudaErrorInvalidValue;   // pairs: packed gemm operands only
     return tc_pair_launch(l.bn, l.prec, l.grid, tmA, tmB, a, s);
+  }
+  if (l.bn == 32) {
+    if (l.fused || l.comp) return cudaErrorInvalidValue;   // the narrow tile: packed convolutions only
+    return launch_narrow(l.grid, l.prec, tmA, tmB, a, s);
   }
   if (l.prec == Prec::TF32) {
     if (l.bn == 64) return launch_variant<64, true>(l.grid, l.fused, l.comp, tmA, tmB, a, s);

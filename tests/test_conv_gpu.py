@@ -376,3 +376,25 @@ def test_plan_state_is_clean_between_executions(mode, path):
         assert np.array_equal(do.cpu().numpy(), fresh[i]), i
     plan.destroy()
     pkg.device_error()
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("K,R", [(16, 3), (32, 5), (7, 3)])
+def test_few_output_features_narrow_tile(mode, K, R):
+    """A default packed plan with at most 32 output features runs 128 x 32
+    tiles, two CTAs a SM: within 1e-5 of the convolution oracle (ragged
+    pixel count, K not a multiple of the tile), bit-exact on integers."""
+    n, H, Wd, C = 2, 21, 37, 16
+    x = W.conv_image(n, H, Wd, C, 131)
+    f = W.conv_filter(C, K, 132, R=R, S=R)
+    out0 = W.conv_image(n, H, Wd, K, 133)
+    ref = conv.conv_f64(x, f, 1.5, 0.5, out0)
+    got, _ = run_conv(x, f, 1.5, 0.5, out0, mode)
+    assert oracle.rel_frob(got.reshape(-1, K), ref.reshape(-1, K)) <= TOL
+    xi = W.conv_image(n, H, Wd, C, 134, kind="integers")
+    fi = W.conv_filter(C, K, 135, kind="integers", R=R, S=R)
+    zi = np.zeros((n, H, Wd, K), np.float32)
+    refi = conv.conv_f64(xi, fi, 1.0, 0.0, zi).astype(np.float32)
+    goti, _ = run_conv(xi, fi, 1.0, 0.0, zi, mode)
+    assert np.array_equal(goti, refi)
+    pkg.device_error()
