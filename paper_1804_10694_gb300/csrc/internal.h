@@ -26,6 +26,10 @@ inline int64_t packed_k_pitch(Prec p, int64_t K) {
 }
 
 constexpr int kScaleBlock = 128;   // rows of A / columns of B sharing one exponent
+// Set in a block's pack counter once the block's planes (and maximum) are
+// final: by the CTA that completed the block, after re-splitting it if its
+// exponent is not zero.
+constexpr unsigned kBlockReady = 0x80000000u;
 
 // --------------------------------------------------- tensor-core kernel args
 struct TcArgs {
@@ -63,6 +67,13 @@ struct TcArgs {
   // nothing to clear (the caller clears the state itself)
   unsigned* state;
   int state_words;
+  // per-block pack counters of A's 128-row and B's 128-column blocks, when
+  // the packing kernel right before this launch packs both (it sets
+  // kBlockReady in each): the TMA producer then waits for the blocks each
+  // unit loads instead of for the whole packing kernel (null: it waits for
+  // that kernel, griddepcontrol.wait)
+  const unsigned* readyA;
+  const unsigned* readyB;
 };
 
 struct TcLaunch {

@@ -187,6 +187,45 @@ __device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v
   return old;
 }
 
+// *p |= v with release semantics at GPU scope (no value returned): what the
+// calling thread observed or wrote before it is visible to a thread whose
+// acquire load sees the bit.
+__device__ __forceinline__ void red_or_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.or.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Orders the calling thread's later asynchronous-proxy accesses of global
+// memory (TMA loads) after what it has observed through the generic proxy
+// (another kernel's plane stores, seen through an acquire).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Waits, polling with an acquire load, until bit `bit` of *flag is set;
+// bounded like mbar_wait (false, with the abort flag raised and kErrTimeout
+// recorded, when the limit passes or another thread has aborted).
+__device__ __forceinline__ bool wait_flag_bit(const unsigned* flag, unsigned bit, volatile int* abort_flag,
+                                              int* err) {
+  if (ld_acquire_gpu(flag) & bit) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t i = 1;; ++i) {
+    __nanosleep(64);
+    if (ld_acquire_gpu(flag) & bit) return true;
+    if (*abort_flag) return false;
+    if ((i & 63u) == 0 && global_timer_ns() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+
 // ------------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem),

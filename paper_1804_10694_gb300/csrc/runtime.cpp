@@ -589,6 +589,12 @@ gemm_status plan_execute_impl(gemm_plan_t p, float alpha, const float* A, const 
   a.C = C;
   a.A = A;
   a.vecA = (p->lda % 4 == 0 && reinterpret_cast<uintptr_t>(A) % 16 == 0) ? 1 : 0;
+  if (!p->args.conv && !p->launch.fused) {
+    // the packing kernel just launched packs both operands and marks each
+    // block ready: the gemm's loads of a block may start once it is
+    a.readyA = p->cntA;
+    a.readyB = p->cntB;
+  }
   if (a.conv && p->launch.fused) {
     // TMA im2col staging when C is a multiple of 16: boxes of 32 channels
     // (128-byte rows) when every k-chunk holds whole taps (C a multiple of
@@ -907,6 +913,10 @@ static gemm_status host_gemm_panels(gemm_plan_t p, float alpha, const float* A, 
     a.beta = beta;
     a.C = t_host.C;
     a.tm0 = (int)t0;
+    // this panel's blocks of A are packed by the launch just before, B's
+    // before the first panel: each is marked ready in its counter
+    a.readyA = p->cntA;
+    a.readyB = p->cntB;
     // the maxima are read by every panel's gemm: only the last one clears them
     if (t1 < tiles_m) a.state_words = 0;
     a.tiles_m = (int)((t1 - t0 + cl - 1) / cl);   // in the plan's tile height

@@ -436,6 +436,17 @@ __device__ __forceinline__ unsigned first_item(const PackShape& p, int i, float*
   return i < na ? op_item<PR>(p, p.op[0], i, tile) : op_item<PR>(p, p.op[1], i - na, tile);
 }
 
+// The CTA that completed block b (fin: its final max bits) marks it ready
+// (kBlockReady in its counter) once its planes are final: after the CTA's
+// re-split, when there was one (the barrier orders every thread's stores
+// before thread 0's release, which is cumulative over the counts it
+// acquired as well).  A gemm launched while this kernel runs may load the
+// block's planes as soon as it sees the bit.
+__device__ __forceinline__ void mark_block_ready(unsigned* cnt, bool resplit) {
+  if (resplit) __syncthreads();
+  if (threadIdx.x == 0) red_or_release_gpu(cnt, kBlockReady);
+}
+
 // Close a run of `run` items of block `blk` (encoded as in block_of); the
 // CTA that completes an out-of-range block re-splits it with its exponent.
 template <Prec PR>
@@ -446,19 +457,25 @@ __device__ __forceinline__ void finish_op_block(const PackShape& p, const OpShap
     const int64_t rows_b = min(static_cast<int64_t>(kScaleBlock), o.rows - b * kScaleBlock);
     const unsigned items = (unsigned)(((rows_b + 31) / 32) * kt);
     const unsigned fin = finish_run(m, o.amax + b, o.cnt + b, run, items);
-    if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
+    if (fin == 0xFFFFFFFFu) return;
+    const bool resplit = block_exponent(fin) != 0;
+    if (resplit) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 256)
         for (int64_t q = b * kScaleBlock; q < b * kScaleBlock + rows_b; q += 32)
           split_rows_tile<PR, kRescale>(o.X, o.rows, p.K, o.ld, o.vec, o.amax, o.planes, o.plane,
                                           p.pitch, q, k0);
     }
+    mark_block_ready(o.cnt + b, resplit);
   } else {
     const unsigned fin = finish_run(m, o.amax + b, o.cnt + b, run, (unsigned)kt);
-    if (fin != 0xFFFFFFFFu && block_exponent(fin) != 0) {
+    if (fin == 0xFFFFFFFFu) return;
+    const bool resplit = block_exponent(fin) != 0;
+    if (resplit) {
       for (int64_t k0 = 0; k0 < p.pitch; k0 += 64)
         split_cols_tile<PR, kRescale>(o.X, p.K, o.rows, o.ld, o.vec, o.amax, o.planes, o.plane, p.pitch,
                                         b * 128, k0, tile);
     }
+    mark_block_ready(o.cnt + b, resplit);
   }
 }
 
@@ -497,11 +514,15 @@ __global__ void __launch_bounds__(256, 4) pack_first_kernel(const PackShape p) {
   // (often the previous execution's gemm, which reads these planes and
   // clears the block maxima and counters at its end)
   griddep_wait();
+  // the gemm may be scheduled as soon as every CTA of this launch has
+  // started (and so passed the wait above): its CTAs take the SMs this
+  // launch leaves, run their prologue, and load each block of the planes
+  // once the block is marked ready (or wait for this whole launch)
+  griddep_launch_dependents();
   const int total = p.items();
   const int per = (total + gridDim.x - 1) / gridDim.x;
   const int i0 = blockIdx.x * per;
   pack_range<PR>(p, i0, min(total, i0 + per), tile);
-  griddep_launch_dependents();   // the gemm may start its prologue
 }
 
 // Fused-split preparation in one launch: A's block maxima (grid-stride),

@@ -155,6 +155,10 @@ struct SingleSched {
   __device__ int* unit_ctr() const { return a->unit_ctr; }
   __device__ unsigned* state() const { return a->state; }
   __device__ int state_words() const { return a->state_words; }
+  // pack counters of A's and B's blocks with their ready bit (null: wait
+  // for the whole packing kernel)
+  __device__ const unsigned* readyA() const { return a->readyA; }
+  __device__ const unsigned* readyB() const { return a->readyB; }
   __device__ Work work(int u) const {
     Work w;
     const int t = u % a->num_tiles;
@@ -206,6 +210,8 @@ struct GroupedSched {
   __device__ int* unit_ctr() const { return a->unit_ctr; }
   __device__ unsigned* state() const { return a->state; }
   __device__ int state_words() const { return a->state_words; }
+  __device__ const unsigned* readyA() const { return nullptr; }
+  __device__ const unsigned* readyB() const { return nullptr; }
   __device__ int units() const { return a->num_units; }
   __device__ int kb() const { return a->kb; }
   __device__ int* err() const { return a->err; }
@@ -464,9 +470,17 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
     if (!FUSED && CONVA == 0) tma_prefetch_desc(sc.mapA(0));
     tma_prefetch_desc(sc.mapB(0));
   }
-  // the prologue above overlaps the end of the packing kernel; nothing below
-  // runs before that kernel has completed and its writes are visible
-  griddep_wait();
+  // The prologue above overlaps the packing kernel.  Every role but the TMA
+  // producer waits here until that kernel has completed and its writes are
+  // visible.  The producer of a packed gemm whose operands that kernel packs
+  // (readyA/readyB set; all of its CTAs have started when this launch
+  // starts, so none waits for an SM this launch holds) instead waits for
+  // each block of the planes it loads to be marked ready, so that its first
+  // loads overlap the end of the packing; it reads nothing else that kernel
+  // wrote.
+  const unsigned* const readyA = (!FUSED && CONVA == 0 && !DYN) ? sc.readyA() : nullptr;
+  const unsigned* const readyB = (!FUSED && CONVA == 0 && !DYN) ? sc.readyB() : nullptr;
+  if (warp != 0 || readyA == nullptr) griddep_wait();
   // the stream's next kernel (the split-K fix-up, or the next execution's
   // packing) may be scheduled now: it waits for this launch to complete
   // before it touches anything, and only its launch latency overlaps
@@ -633,10 +647,25 @@ __device__ __forceinline__ void tc_gemm_body(const Sched& sc) {
         u0 = atomicAdd(sc.unit_ctr(), 1);
         if (u0 < nunits) wd = sc.work(u0);
       }
+      int ready_a = -1, ready_b = -1;   // the last blocks seen ready
       for (int u = u0; ok && (ok = publish(u)) && u < nunits; u = DYN ? u_pre : u + static_cast<int>(gridDim.x)) {
         if constexpr (DYN) u_pre = atomicAdd(sc.unit_ctr(), 1);
         const Work w = DYN ? wd : wn;              // next unit's entry loads early
         if (!DYN && u + static_cast<int>(gridDim.x) < nunits) wn = sc.work(u + gridDim.x);
+        if (readyA != nullptr) {
+          // this unit's row block of A and column block of B (tiles start
+          // inside M and N, so both blocks exist)
+          const int ba = w.tm, bb = (w.tn * BN) / kScaleBlock;
+          if (ba != ready_a || bb != ready_b) {
+            if (!wait_flag_bit(readyA + ba, kBlockReady, abort_flag, err) ||
+                !wait_flag_bit(readyB + bb, kBlockReady, abort_flag, err)) {
+              ok = false;
+              break;
+            }
+            fence_proxy_async_global();
+            ready_a = ba, ready_b = bb;
+          }
+        }
         const CUtensorMap* mA = sc.mapA(w.prob);
         const CUtensorMap* mB = sc.mapB(w.prob);
         if (w.prob != last_prob) {

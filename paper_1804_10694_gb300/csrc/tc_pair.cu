@@ -160,9 +160,12 @@ __global__ void __launch_bounds__(PairCfg<BN, TF32, NP>::THREADS, 1)
     tma_prefetch_desc(&tmA);
     tma_prefetch_desc(&tmB);
   }
-  // the prologue above overlaps the end of the packing kernel; nothing below
-  // runs before that kernel has completed and its writes are visible
-  griddep_wait();
+  // The prologue above overlaps the packing kernel.  Every role but the TMA
+  // producer waits here until that kernel has completed and its writes are
+  // visible; with a.readyA set (that kernel packs both operands and marks
+  // each block ready; all of its CTAs have started when this launch starts)
+  // the producer instead waits for each block of the planes it loads.
+  if (warp != 0 || a.readyA == nullptr) griddep_wait();
   // the stream's next kernel may be scheduled now (it waits for this launch
   // to complete before it touches anything)
   griddep_launch_dependents();
@@ -196,10 +199,26 @@ __global__ void __launch_bounds__(PairCfg<BN, TF32, NP>::THREADS, 1)
         bool issued[STAGES];
         for (int s = 0; s < STAGES; ++s) issued[s] = false, last_phase[s] = 0;
         bool ok = true;
+        int ready_a = -1, ready_b = -1;   // the last blocks seen ready
         for (int u = pair0; ok && u < nunits; u += npairs) {
           const Work w = work(u);
           const int rowA = row_block(w.tm) * Cfg::BM;
           const int rowB = w.tn * BN + static_cast<int>(rank) * Cfg::BNH;
+          if (a.readyA != nullptr) {
+            // the blocks of A's rows and B's columns this CTA loads; a block
+            // wholly past M or N (this CTA's half of the last pair tile) has
+            // no planes and no counter: its loads only zero-fill
+            const int ba = row_block(w.tm), bb = rowB / kScaleBlock;
+            if (ba != ready_a || bb != ready_b) {
+              if ((ba * kScaleBlock < a.M && !wait_flag_bit(a.readyA + ba, kBlockReady, abort_flag, err)) ||
+                  (bb * kScaleBlock < a.N && !wait_flag_bit(a.readyB + bb, kBlockReady, abort_flag, err))) {
+                ok = false;
+                break;
+              }
+              fence_proxy_async_global();
+              ready_a = ba, ready_b = bb;
+            }
+          }
           for (int c = w.c0; c < w.c1; ++c) {
             if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, err)) {
               ok = false;

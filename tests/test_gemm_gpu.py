@@ -459,3 +459,79 @@ def test_plan_state_is_clean_between_executions(mode):
             assert np.array_equal(dC.cpu().numpy(), fresh[i]), (cid, i)
         plan.destroy()
     pkg.device_error()
+
+
+# ---------------------------------------------------------- split-K sums
+def _config(mode, **want):
+    for cid in range(pkg.config_count(mode)):
+        c = pkg.config_get(mode, cid)
+        if all(c[k] == v for k, v in want.items()):
+            return cid
+    raise AssertionError(f"no configuration {want}")
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("block_n,split_k,cluster", [(64, 3, 1), (128, 2, 1), (128, 4, 1), (256, 2, 2)])
+def test_split_k_is_the_ordered_sum_of_its_splits(mode, block_n, split_k, cluster):
+    """Split K: each split writes alpha times its share of the product (its
+    k-chunks) as a partial sum, and the fix-up adds the partials in
+    increasing split index, then beta * C.  The result must be, bit for bit,
+    that FP32 sum of the shares -- each share computed by an unsplit plan of
+    the same tile width on the split's range of K -- plus beta * C (beta =
+    0.5: beta * C is exact, so a fused or a separate multiply-add give the
+    same bits), and the same bits on each of ten executions.  Ragged M, N
+    and K (partial tiles, a partial last chunk); operands in the unscaled
+    range, so that every share has the same block exponents."""
+    M, N, K = 333, 290, 1000
+    alpha, beta = 1.25, 0.5
+    A, B, C0 = W.uniform(M, K, 61), W.uniform(K, N, 62), W.uniform(M, N, 63)
+    cid = _config(mode, block_n=block_n, split_k=split_k, kb=4, group_m=16, fused=0, cluster=cluster)
+    one = _config(mode, block_n=block_n, split_k=1, kb=4, group_m=16, fused=0, cluster=cluster)
+    dA, dB = dev(A), dev(B)
+    plan = pkg.Plan(M, N, K, mode=mode, config_id=cid)
+    results = []
+    for _ in range(10):
+        dC = dev(C0)
+        plan.execute(dA, dB, dC, alpha, beta)
+        torch.cuda.synchronize()
+        results.append(dC.cpu().numpy())
+    plan.destroy()
+    for r in results[1:]:
+        assert np.array_equal(r.view(np.uint32), results[0].view(np.uint32))
+    # the splits' k ranges: whole chunks, ceil(chunks / split_k) a split
+    bk = 32 if mode == "tf32x3" else 64
+    chunks = -(-K // bk)
+    per = -(-chunks // split_k)
+    assert -(-chunks // per) == split_k
+    total = np.zeros((M, N), np.float32)
+    for s in range(split_k):
+        k0, k1 = s * per * bk, min(K, (s + 1) * per * bk)
+        sub = pkg.Plan(M, N, k1 - k0, K, N, N, mode=mode, config_id=one)
+        dS = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+        sub.execute_ptrs(alpha, dA.data_ptr() + 4 * k0, dB.data_ptr() + 4 * k0 * N, 0.0, dS.data_ptr())
+        torch.cuda.synchronize()
+        sub.destroy()
+        share = dS.cpu().numpy()
+        total = share if s == 0 else (total + share).astype(np.float32)
+    want = (total + (np.float32(beta) * C0).astype(np.float32)).astype(np.float32)
+    assert np.array_equal(results[0].view(np.uint32), want.view(np.uint32))
+    assert oracle.rel_frob(results[0], oracle.gemm_f64(M, N, K, alpha, A, B, beta, C0)) <= TOL
+    pkg.device_error()
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("M,N,K", [(100, 100, 300), (130, 120, 200), (300, 129, 257), (257, 385, 64)])
+def test_pair_tiles_past_the_matrix(mode, M, N, K):
+    """CTA-pair tiles are 256 rows high and 128 or 256 columns wide: in the
+    last pair tile, the second CTA's half of the rows (or of the columns)
+    can lie wholly past M (or N).  Its loads only zero-fill, and the TMA
+    producer must not wait for a packed block there (there is none): every
+    pair configuration gives the oracle's result, with no timeout recorded."""
+    A, B, C0 = W.uniform(M, K, 71), W.uniform(K, N, 72), W.uniform(M, N, 73)
+    ref = oracle.gemm_f64(M, N, K, 1.5, A, B, 0.5, C0)
+    for bn in (128, 256):
+        for sk in (1, 2):
+            cid = _config(mode, block_n=bn, split_k=sk, kb=4, group_m=16, fused=0, cluster=2)
+            got = run_gemm(mode, M, N, K, 1.5, A, B, 0.5, C0, config_id=cid)
+            pkg.device_error()
+            assert oracle.rel_frob(got, ref) <= TOL, (bn, sk)
