@@ -311,8 +311,9 @@ gemm_status gemm_grouped_plan_destroy(gemm_grouped_plan_t plan);
  * shapes, given as G rows of six numbers (M, N, K, lda, ldb, ldc) in
  * `shapes` (G x 6 int64, row-major; leading dimensions as for gemm_f32_ex),
  * time every distinct candidate configuration of `mode` on synthetic uniform
- * data stored with those leading dimensions, `reps` CUDA-event-timed
- * executions after two warm-ups, median.  Leading dimensions are part of a
+ * data stored with those leading dimensions: after two warm-ups, `reps`
+ * CUDA-event-timed batches of three back-to-back executions (C = A B +
+ * 0.5 C), the median time per execution.  Leading dimensions are part of a
  * shape because they select code paths (TMA or cp.async staging of A, float4
  * or staged stores of C).  Appends one CSV row per (shape, configuration) to
  * out_path ("M,N,K,lda,ldb,ldc,mode,config_id,median_ms,block_n,split_k,kb,

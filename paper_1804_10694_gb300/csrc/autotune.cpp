@@ -4,8 +4,13 @@
 // split-K, TMEM fold length and raster grouping.  For each shape every
 // DISTINCT effective configuration (candidates that behave identically on the
 // shape, e.g. split-K above the number of k-chunks, are timed once) is run
-// `reps` times after two warm-up executions, each execution timed with CUDA
-// events; the median is recorded.  A shape is (M, N, K) with its leading
+// after two warm-up executions in `reps` timed batches of three back-to-back
+// executions (C = A B + 0.5 C), each batch between two CUDA events; the
+// median time per execution is recorded.  Back to back, as a caller's loop
+// runs them, each execution's launches overlap the end of the previous one
+// (programmatic launches), which an event between executions would prevent:
+// the fixed cost of a split-K fix-up launch, for one, is then what a loop of
+// calls pays.  A shape is (M, N, K) with its leading
 // dimensions (lda, ldb, ldc): they choose code paths (TMA or cp.async
 // staging of A in the fused kernel, float4 or staged stores of C), so they
 // are part of what is tuned.  Results are appended to a CSV file
@@ -121,16 +126,20 @@ gemm_status time_config(const Shape6& sh, gemm_mode mode, int cid, const float* 
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) break;
   if (e == cudaSuccess) {
-    for (int w = 0; w < 2 && st == GEMM_OK; ++w) st = plan_execute_impl(p, 1.0f, A, B, 0.0f, C, nullptr);
+    constexpr int kBatch = 3;
+    for (int w = 0; w < 2 && st == GEMM_OK; ++w) st = plan_execute_impl(p, 1.0f, A, B, 0.5f, C, nullptr);
     for (int r = 0; r < reps && st == GEMM_OK; ++r) {
       cudaEventRecord(ev[2 * r], nullptr);
-      st = plan_execute_impl(p, 1.0f, A, B, 0.0f, C, nullptr);
+      for (int b = 0; b < kBatch && st == GEMM_OK; ++b) st = plan_execute_impl(p, 1.0f, A, B, 0.5f, C, nullptr);
       cudaEventRecord(ev[2 * r + 1], nullptr);
     }
     if (st == GEMM_OK && (e = cudaDeviceSynchronize()) != cudaSuccess) st = cuda_fail(e, "tuning run");
     if (st == GEMM_OK) {
       std::vector<float> t(reps);
-      for (int r = 0; r < reps; ++r) cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]);
+      for (int r = 0; r < reps; ++r) {
+        cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]);
+        t[r] /= kBatch;
+      }
       std::sort(t.begin(), t.end());
       *median_ms = reps % 2 ? t[reps / 2] : 0.5f * (t[reps / 2 - 1] + t[reps / 2]);
     }

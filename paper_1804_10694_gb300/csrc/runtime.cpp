@@ -180,39 +180,66 @@ static int find_config(int bn, int sk, int kb, int g, int cluster = 1) {
   return 0;
 }
 
+// Built-in tile choice (no tuned table, no trained model): an estimate of
+// each packed candidate's time, minimised over tile width (128 x 64 and
+// 128 x 128 on one SM, 256 x 256 on a CTA pair) and split-K.  For one
+// candidate, with `chunks` 128-byte k-chunks, `per` of them a split and
+// `units` = tiles x splits on `slots` (SMs, or SM pairs):
+//     waves x (kA0 + per x chunk cost + kEpi) + [splits > 1] (kFix0 + kFix1 x M N splits / 1e6),
+// waves = ceil(units / slots).  Chunk costs relative to a 128 x 64 tile's
+// (the six-product mode's kSix times as much), per-tile costs in the same
+// unit (about a microsecond).  The constants were fitted on GB300 to the autotuner's
+// timings (back-to-back executions, C = A B + 0.5 C) of 700 random shapes
+// and 21 square ones in each of the three modes, minimising the mean regret
+// against the fastest timed configuration (fit_estimate.py); on 103
+// held-out shapes the regret is 4.8 % (BF16x3), 6.2 % (TF32x3) and 2.7 %
+// (BF16x6), against 11.1 %, 11.4 % and 10.0 % for the previous rule
+// (largest one-wave split-K of 128 x 128 tiles, a pair tile when it needs
+// fewer waves).  The fold length stays 4 chunks (8 on a
+// six-product pair tile, whose single accumulator buffer stalls the MMAs at
+// every fold), the raster group 16.
+namespace {
+constexpr double kChunk64 = 1.0, kChunk128 = 1.5, kChunkPair = 2.0;   // per k-chunk of a unit
+constexpr double kEpi64 = 3.3, kEpi128 = 7.2, kEpiPair = 28.8;        // per unit: epilogue
+constexpr double kA0 = 3.6;                                           // per unit: prologue
+constexpr double kFix0 = 4.0, kFix1 = 0.99;                           // split-K fix-up launch
+constexpr double kSix = 1.6;                                          // six products a chunk
+}  // namespace
+
 int default_config(gemm_mode mode, int64_t M, int64_t N, int64_t K, int sms) {
   if (config_count(mode) == 0) return -1;
   const Prec p = prec_of_mode(mode);
-  const int bn = N <= 64 ? 64 : 128;
-  const int64_t tiles = ((M + 127) / 128) * ((N + bn - 1) / bn);
-  const int64_t chunks = (K + prec_chunk_elems(p) - 1) / prec_chunk_elems(p);
-  // split-K: the largest split count that keeps every unit in one wave
-  // (tiles x splits <= SMs) and at least 4 k-chunks per split; a split
-  // count that spills into a second, partial wave doubles the time of the
-  // CTAs that run two units (1024^3 on GB300: three splits, 192 units on 152
-  // SMs, 25.8 us a call against 21.8 with two)
-  int sk = 1;
-  const int cand[] = {1, 2, 3, 4, 6, 8};
-  for (int c : cand) {
-    if (c > 1 && (c > chunks / 4 || tiles * c > (int64_t)sms)) break;
-    sk = c;
+  const bool six = mode == GEMM_MODE_BF16X6;
+  const int64_t chunks = std::max<int64_t>(1, (K + prec_chunk_elems(p) - 1) / prec_chunk_elems(p));
+  struct Tile {
+    int bn, cluster;
+    double chunk, epi;
+  };
+  const Tile cands[3] = {{64, 1, kChunk64, kEpi64}, {128, 1, kChunk128, kEpi128}, {256, 2, kChunkPair, kEpiPair}};
+  const int splits[] = {1, 2, 3, 4, 6, 8};
+  double best = 0.0;
+  int pick = find_config(64, 1, 4, 16);
+  bool have = false;
+  for (const Tile& t : cands) {
+    if (t.cluster == 2 && sms < 2) continue;
+    const int64_t tiles = ((M + 128 * t.cluster - 1) / (128 * t.cluster)) * ((N + t.bn - 1) / t.bn);
+    const int64_t slots = std::max(1, sms / t.cluster);
+    const double chunk = t.chunk * (six ? kSix : 1.0);
+    for (int sk : splits) {
+      if (sk > 1 && sk > chunks) break;
+      const int64_t per = (chunks + sk - 1) / sk;
+      const int64_t splits_eff = (chunks + per - 1) / per;   // (no empty split)
+      const int64_t waves = (tiles * splits_eff + slots - 1) / slots;
+      double est = (double)waves * (kA0 + (double)per * chunk + t.epi);
+      if (splits_eff > 1) est += kFix0 + kFix1 * (double)M * (double)N * (double)splits_eff * 1e-6;
+      if (!have || est < best) {
+        have = true;
+        best = est;
+        pick = find_config(t.bn, sk, six && t.cluster == 2 ? 8 : 4, 16, t.cluster);
+      }
+    }
   }
-  if (sk == 1 && bn == 128 && sms >= 2) {
-    // A CTA pair's 256 x 256 tile moves half the operand bytes per product
-    // of four 128 x 128 tiles: at 8192^3 on GB300 a pair unit took 2 x 0.875
-    // of a single-CTA unit's time for twice its products per SM.  The
-    // coarser tiles pay when they do not leave pairs idle: compare the waves
-    // of units each choice needs (units on sms SMs, or on sms / 2 pairs),
-    // weighted by the time of one unit.
-    const int64_t tiles2 = ((M + 255) / 256) * ((N + 255) / 256);
-    const double waves1 = (double)((tiles + sms - 1) / sms);
-    const double waves2 = (double)((tiles2 + sms / 2 - 1) / (sms / 2));
-    // (BF16X6 on a 256-wide pair tile has one accumulator buffer, so each
-    // fold stalls the MMAs: folding every 8 chunks ran 3.44 ms against 3.78
-    // at 8192^3)
-    if (waves2 * 2.0 * 0.875 < waves1) return find_config(256, 1, mode == GEMM_MODE_BF16X6 ? 8 : 4, 16, 2);
-  }
-  return find_config(bn, sk, 4, 16);
+  return pick;
 }
 
 // -------------------------------------------------------------------- plans

@@ -169,21 +169,57 @@ def test_costmodel_ensemble_file_format(tmp_path):
     assert lib.gemm_costmodel_load(str(f).encode()) == 7
 
 
-def test_default_split_k_stays_in_one_wave():
-    """The built-in heuristic takes the largest split-K that keeps every unit
-    in one wave of the 152 SMs (and at least 4 k-chunks per split); a split
-    count that would start a second, partial wave is not taken."""
-    def pick(n):
-        return pkg.config_get("bf16x3", pkg.config_default("bf16x3", n, n, n))
-    c = pick(1024)            # 8 x 8 tiles of 128 x 128, 16 chunks: 2 splits (128 units)
-    assert (c["block_n"], c["split_k"], c["cluster"]) == (128, 2, 1)
-    c = pick(1060)            # 9 x 9 tiles: 2 splits would be 162 units
-    assert (c["block_n"], c["split_k"], c["cluster"]) == (128, 1, 1)
-    c = pick(512)             # 4 x 4 tiles, 8 chunks: at most 2 splits of 4 chunks
-    assert (c["block_n"], c["split_k"]) == (128, 2)
-    c = pick(4099)            # 33 x 33 tiles: more than one wave already
-    assert c["split_k"] == 1
-    for n in (1024, 1060, 512, 2048, 4099, 8192):
-        c = pick(n)
-        tiles = -(-n // (128 * c["cluster"])) * -(-n // c["block_n"])
-        assert c["split_k"] == 1 or tiles * c["split_k"] <= 152
+def _estimate_pick(M, N, K, mode, sms=152):
+    """The built-in tile choice, restated from its definition: for each
+    packed candidate (128 x 64 or 128 x 128 tiles on one SM, 256 x 256 on a
+    CTA pair) and split count, waves x (prologue + k-chunks a split x chunk
+    cost + epilogue) plus, when K is split, the fix-up's cost; the first
+    minimum in the order 64, 128, pair and 1, 2, 3, 4, 6, 8 splits."""
+    chunk_elems = 32 if mode == "tf32x3" else 64
+    chunks = max(1, -(-K // chunk_elems))
+    six = mode == "bf16x6"
+    best, pick = None, None
+    for bn, cl, tc, te in ((64, 1, 1.0, 3.3), (128, 1, 1.5, 7.2), (256, 2, 2.0, 28.8)):
+        tiles = -(-M // (128 * cl)) * -(-N // bn)
+        slots = sms // cl
+        for sk in (1, 2, 3, 4, 6, 8):
+            if sk > 1 and sk > chunks:
+                break
+            per = -(-chunks // sk)
+            eff = -(-chunks // per)
+            waves = -(-(tiles * eff) // slots)
+            est = waves * (3.6 + per * tc * (1.6 if six else 1.0) + te)
+            if eff > 1:
+                est += 4.0 + 0.99 * M * N * eff * 1e-6
+            if best is None or est < best:
+                best, pick = est, (bn, sk, 8 if (six and cl == 2) else 4, 16, cl)
+    return pick
+
+
+def test_default_tile_choice_is_its_estimate():
+    """The default configuration of a shape is the candidate with the
+    smallest estimated time (the restatement above) for every mode, over
+    squares, the convolution-as-gemm shapes and random shapes; and a few
+    anchors: the paper's 1060^3 runs unsplit 128 x 128 tiles, one 128-row
+    tile (128^3) the narrower 128 x 64 tile, 8192^3 the CTA pair, and an
+    N <= 64 problem 64-wide tiles."""
+    rng = np.random.default_rng(5)
+    shapes = [(n, n, n) for n in (128, 256, 512, 768, 1024, 1060, 2048, 4099, 8192)]
+    shapes += [(50176, 64, 576), (12544, 128, 1152), (3136, 256, 2304), (1, 1, 1), (7, 3000, 5)]
+    shapes += [tuple(int(x) for x in 2 ** rng.uniform(4, 14, 3)) for _ in range(300)]
+    for mode in ("bf16x3", "tf32x3", "bf16x6"):
+        for M, N, K in shapes:
+            c = pkg.config_get(mode, pkg.config_default(mode, M, N, K))
+            got = (c["block_n"], c["split_k"], c["kb"], c["group_m"], c["cluster"])
+            assert c["fused"] == 0
+            assert got == _estimate_pick(M, N, K, mode), (mode, M, N, K)
+
+    def pick(n, mode="bf16x3"):
+        c = pkg.config_get(mode, pkg.config_default(mode, n, n, n))
+        return c["block_n"], c["split_k"], c["cluster"]
+    assert pick(1060) == (128, 1, 1)
+    assert pick(128)[0] == 64 and pick(128)[2] == 1
+    assert pick(8192) == (256, 1, 2)
+    c = pkg.config_get("bf16x3", pkg.config_default("bf16x3", 50176, 64, 576))
+    assert c["block_n"] == 64 and c["cluster"] == 1
+

@@ -116,13 +116,14 @@ def test_pair_large_square_whole_matrix():
 
 
 def test_default_picks_pairs_and_host_panel_pipeline_runs_them():
-    """4096 x 2048 x 512: the default heuristic takes the 256 x 256 pair tile
-    (4 waves of single-CTA units against 2 of pair units).  Through
+    """4096 x 2048 x 1024: the default tile choice takes the 256 x 256 pair
+    tile (its estimate: 2 waves of pair units against 4 of 128 x 128 units
+    and 7 of 128 x 64 units).  Through
     gemm_f32_host with page-locked buffers the row-panel pipeline runs it:
     panels of an even number of 128-row tiles, each launch starting at an
     even 128-row block; unaligned ldc, padding untouched."""
     import torch
-    M, N, K = 4096, 2048, 512
+    M, N, K = 4096, 2048, 1024
     cid = pkg.config_default("bf16x3", M, N, K)
     c = pkg.config_get("bf16x3", cid)
     assert c["cluster"] == 2 and c["block_n"] == 256, c
