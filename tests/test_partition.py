@@ -80,3 +80,71 @@ def test_two_gloo_ranks_assemble_the_whole_product(tmp_path):
     res = [json.load(open(tmp_path / f"rank{r}.json")) for r in range(world)]
     assert [r["block"] for r in res] == [[0, 768], [768, 1300]]   # 6 tiles: 3 + 3 (the last partial)
     assert all(r["equal"] for r in res)
+
+
+# ------------------------------------------------ grouped gemm by problems
+def test_problem_shares_cover_every_problem_once_balanced():
+    """Largest-first greedy shares of the 512 grouped problems: every
+    problem on exactly one rank, indices ascending within a share, and no
+    rank more than the largest problem's flops above the average (the
+    greedy bound); with one rank, all problems in order."""
+    import workloads as W
+    from paper_1804_10694_gb300.partition import problem_shares
+    shapes = W.grouped_shapes()
+    flops = [2 * m * n * k for (m, n, k) in shapes]
+    assert problem_shares(shapes, 1) == [list(range(len(shapes)))]
+    for world in (2, 3, 4, 8):
+        shares = problem_shares(shapes, world)
+        assert sorted(i for s in shares for i in s) == list(range(len(shapes)))
+        assert all(s == sorted(s) for s in shares)
+        loads = [sum(flops[i] for i in s) for s in shares]
+        assert max(loads) - sum(loads) / world <= max(flops)
+    # more ranks than problems: the extra ranks are idle
+    assert problem_shares([(8, 8, 8), (4, 4, 4)], 3) == [[0], [1], []]
+    with pytest.raises(ValueError):
+        problem_shares(shapes, 0)
+
+
+def _rank_problems(rank: int, world: int, port: int, out_dir: str):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    import torch
+    import torch.distributed as dist
+    import oracle
+    from paper_1804_10694_gb300.partition import problem_shares
+    dist.init_process_group("gloo")
+    rng = np.random.default_rng(9)
+    shapes = [tuple(int(x) for x in rng.integers(1, 40, 3)) for _ in range(9)]
+    data = [tuple(rng.uniform(-1, 1, sh).astype(np.float32) for sh in ((m, k), (k, n), (m, n)))
+            for (m, n, k) in shapes]
+    mine = problem_shares(shapes, world)[rank]
+    # each rank computes its problems (the FP64 oracle standing in for its
+    # GPU's grouped launch) and the results are gathered on every rank
+    flat = np.concatenate([oracle.gemm_f64(*shapes[i], 1.5, data[i][0], data[i][1], 0.5, data[i][2]).ravel()
+                           for i in mine] or [np.zeros(0)])
+    total = sum(m * n for (m, n, k) in shapes)
+    buf = np.zeros(total)
+    buf[:flat.size] = flat
+    parts = [torch.zeros(total, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(parts, torch.from_numpy(buf))
+    got = {}
+    for r, share in enumerate(problem_shares(shapes, world)):
+        off = 0
+        for i in share:
+            m, n, _ = shapes[i]
+            got[i] = parts[r].numpy()[off:off + m * n].reshape(m, n)
+            off += m * n
+    equal = all(np.array_equal(got[i], oracle.gemm_f64(*shapes[i], 1.5, data[i][0], data[i][1], 0.5,
+                                                         data[i][2])) for i in range(len(shapes)))
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, f"prob{rank}.json"), "w") as f:
+        json.dump({"share": mine, "equal": bool(equal)}, f)
+
+
+def test_two_gloo_ranks_split_a_grouped_gemm_by_problems(tmp_path):
+    world = 2
+    mp.start_processes(_rank_problems, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn")
+    res = [json.load(open(tmp_path / f"prob{r}.json")) for r in range(world)]
+    assert sorted(res[0]["share"] + res[1]["share"]) == list(range(9))
+    assert all(r["equal"] for r in res)
