@@ -69,7 +69,7 @@ typedef enum {
 } gemm_mode;
 
 typedef enum {
-  GEMM_SELECT_DEFAULT = 0,    /* built-in heuristic */
+  GEMM_SELECT_DEFAULT = 0,    /* built-in heuristic: the candidate of least estimated time */
   GEMM_SELECT_MODEL = 1,      /* argmin of the loaded MLP cost model (else heuristic) */
   GEMM_SELECT_TABLE = 2,      /* loaded autotune table, exact shape match (else heuristic) */
   GEMM_SELECT_EXHAUSTIVE = 3  /* time every candidate now, keep the fastest */
@@ -336,7 +336,10 @@ gemm_status gemm_autotune_best(int64_t M, int64_t N, int64_t K, int64_t lda, int
 
 /* The configuration id a plan created now would get for this shape under
  * policy `sel` (defined by this library, like the policies themselves):
- * DEFAULT = the built-in heuristic, TABLE = the tuned table's entry for the
+ * DEFAULT = the built-in heuristic (the packed candidate with the least
+ * estimated time: waves of units x (per-unit prologue + k-chunks x chunk cost
+ * + epilogue) + the split-K fix-up, constants fitted to this library's
+ * autotuner timings on GB300), TABLE = the tuned table's entry for the
  * exact six numbers (else the heuristic), MODEL = the loaded cost model's
  * argmin (runs on the GPU; else the heuristic), EXHAUSTIVE = time every
  * candidate now.  -1 for F32_SIMT or an empty problem.  DEFAULT and TABLE
