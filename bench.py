@@ -298,13 +298,19 @@ def run_kernel_only(args, local):
 
 
 def source_digest(path: str) -> str:
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Digest of a kernel's source file and of the plan code that sets its
+    launch arguments (tile order, raster group), which decide its traffic."""
+    h = hashlib.sha256()
+    for p in (path, os.path.join(CSRC, "runtime.cpp")):
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def traffic_per_launch(kernel: str, source: str):
     """DRAM bytes per launch of the gemm kernel from the committed ncu summary
-    of that kernel, or None if missing or taken on a different source."""
+    of that kernel, or None if missing or taken on a different source or
+    plan code."""
     for path in TRAFFIC_FILES:
         if not os.path.exists(path):
             continue

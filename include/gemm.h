@@ -94,7 +94,8 @@ typedef struct {
   int stages;      /* depth of the shared-memory operand ring */
   int split_k;     /* number of K partitions (partials reduced in fixed order) */
   int kb;          /* k-chunks accumulated in tensor memory per epilogue fold (1..8) */
-  int group_m;     /* raster: output tiles walked in groups of this many along M */
+  int group_m;     /* raster: output tiles walked in groups spanning this many
+                    * 128-row blocks along M (group_m / 2 CTA-pair tile rows) */
   int fused;       /* 1: A is split inside the gemm kernel (no packed copy of A);
                     *    0: A is packed into hi/lo planes by a separate pass */
   int cluster;     /* CTAs per output tile: 1 (tile 128 x block_n on one SM), or

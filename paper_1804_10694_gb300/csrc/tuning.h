@@ -8,7 +8,11 @@
 
 namespace gb {
 
-// A candidate configuration as it behaves on one shape.
+// A candidate configuration as it behaves on one shape.  group_m is the
+// configuration's raster group clamped to the shape's tile rows, a cost-model
+// feature (the CTA-pair kernel walks groups of half the configuration's value
+// in pair rows); candidates with equal effective fields launch the same
+// kernel arguments.
 struct EffConfig {
   int bn, split_k, chunks_per_split, kb, group_m, fused, cluster;
   int64_t tiles;
