@@ -92,6 +92,15 @@ def integers(rows: int, cols: int, seed: int, ld: int | None = None,
     return _with_ld(vals, ld, pad_value)
 
 
+def int_pattern(i, k, a: int, b: int, m: int, off: int):
+    """Integer entries (a*i + b*k) mod m - off at row indices i and column
+    indices k (broadcastable integer arrays, numpy or torch alike; the caller
+    converts to float32).  With m <= 17 they are exact in FP32, bf16 and tf32:
+    closed-form inputs for problems too large to draw and copy from the host,
+    whose rows can be rebuilt one at a time for the oracle."""
+    return (a * i + b * k) % m - off
+
+
 def scaled(arr: np.ndarray, log2_scale: int) -> np.ndarray:
     """Multiply by an exact power of two (input shaping for range tests)."""
     return (arr.astype(np.float64) * math.ldexp(1.0, log2_scale)).astype(np.float32)
