@@ -535,8 +535,8 @@ gemm_status plan_create_impl(int64_t M, int64_t N, int64_t K, int64_t lda, int64
   // group_m counts 128-row blocks of C, so a raster group spans the same
   // rows of A in both kernels: 16 blocks are 16 single-CTA tile rows or 8
   // CTA-pair tile rows.  (At 8192^3 on pairs, groups of 4, 6, 8, 12, 16
-  // and 32 pair rows ran within 2.5 % of one another; 8 read the least:
-  // 2.81 GB a launch against 3.17 GB for 16.)
+  // and 32 pair rows ran within 2.5 % of one another; of 4, 8 and 16, 8
+  // read the least from DRAM: 2.81 GB a launch against 3.46 and 3.17 GB.)
   a.group_m = std::max(1, std::min<int>(p->cfg.group_m / cluster, (int)tiles_m));
   a.ldc = ldc;
   a.amaxA = p->amaxA;
